@@ -1,0 +1,398 @@
+"""Benchmark of the SEM Q-isosurface render path on GB300.
+
+One step = one snapshot through the whole path: sem_qcriterion on all elements, sem_isosurface
+for each isovalue (triangles of all isovalues packed into one buffer), and one sem_render of
+the frame.  Workload: the 32x32x32-element channel, N = 7 (16.8M GLL nodes, 201 MB of FP32
+velocity), three Q isovalues {0.05, 0.1, 0.2} * max Q, 1920x1080 perspective frame.
+
+Prints one JSON line (rank 0).  ``value`` is elements/s with the velocity already resident in
+HBM; ``e2e`` is the same metric with the velocity copied from pinned host memory and the frame
+read back inside the timed region.  ``roofline`` reports the dominant kernel against the
+measured HBM bandwidth; ``cpu_baseline`` times the FP64 CPU oracle on a bounded sample.
+
+``--impl reference`` times the CPU oracle alone (the reference arm) on the same workload.
+Under torchrun each rank runs an independent replica on its own GPU (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SEM elements/s through Q-isosurface render; frames/s; fraction of HBM roofline"
+UNIT = "elements/s"
+WORKLOAD = "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, 1920x1080 perspective"
+KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
+                  "k_iso_count": "paper_2312_09888_gb300/csrc/sem_iso.cu",
+                  "k_iso_emit": "paper_2312_09888_gb300/csrc/sem_iso.cu",
+                  "k_raster": "paper_2312_09888_gb300/csrc/sem_render.cu",
+                  "k_setup": "paper_2312_09888_gb300/csrc/sem_render.cu",
+                  "k_bin": "paper_2312_09888_gb300/csrc/sem_render.cu"}
+# kernels the library launches per step: qcrit 1; per isovalue count + 3 scan + emit = 5;
+# render setup + 3 scan + bin + raster = 6
+LAUNCHES_PER_STEP = lambda n_iso: 1 + 5 * n_iso + 6  # noqa: E731
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(per_rank_elems, per_rank_seconds):
+    """Whole-job throughput: all units processed / the slowest rank's time."""
+    return float(sum(per_rank_elems)) / float(max(per_rank_seconds))
+
+
+def _file_sha(path):
+    with open(os.path.join(ROOT, path), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic_for(kernel):
+    """DRAM bytes per launch from a committed ncu summary, or None if absent or stale."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(kernel)
+        if d and d.get("source_sha") == _file_sha(KERNEL_SOURCES[kernel]):
+            return d.get("bytes_per_launch_full")
+    except Exception:
+        return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------ workload
+
+def make_workload(device):
+    import sem_inputs as si
+    return si.channel(device=device)
+
+
+class Pipeline:
+    """Device buffers and the per-step call sequence through the C ABI."""
+
+    def __init__(self, S, w, device_index=0):
+        import numpy as np
+        import torch
+        self.S, self.w, self.torch = S, w, torch
+        self.stream = torch.cuda.current_stream()
+        self.sess = S.Session(device_index, self.stream)
+        self.ctx = self.sess.ctx
+        xyz = w.mesh.xyz(w.fields.device).cpu().numpy()
+        self.mesh = self.sess.mesh(w.mesh.N, xyz)
+        self.E = w.E
+        self.npts = w.E * w.mesh.NP ** 3
+        self.vel = [w.fields[c].float().contiguous() for c in range(3)]
+        self.Q = torch.empty_like(self.vel[0])
+        S.sem_qcriterion(self.ctx, self.mesh, *self.vel, self.Q)
+        qmax = S.sem_field_max(self.ctx, self.Q)
+        self.isos = [float(np.float32(f * qmax)) for f in w.iso_fracs]
+        counts = [S.sem_isosurface(self.ctx, self.mesh, self.Q, iso, None, cap=0) for iso in self.isos]
+        self.cap = int(sum(counts) * 1.05) + 1024
+        self.tris = torch.empty(self.cap * 9, device="cuda")
+        self.W, self.H = w.camera["W"], w.camera["H"]
+        self.rgba = torch.empty(self.W * self.H * 4, dtype=torch.uint8, device="cuda")
+        self.depth = torch.empty(self.W * self.H, device="cuda")
+        self.counts = counts
+        self.ev = None
+
+    def step(self, events=None):
+        S, ctx, m = self.S, self.ctx, self.mesh
+        if events is not None:
+            events[0].record(self.stream)
+        S.sem_qcriterion(ctx, m, *self.vel, self.Q)
+        if events is not None:
+            events[1].record(self.stream)
+        off = 0
+        seg = []
+        for iso in self.isos:
+            n = S.sem_isosurface(ctx, m, self.Q, iso, self.tris[off * 9:], cap=self.cap - off)
+            seg.append(n)
+            off += n
+        if events is not None:
+            events[2].record(self.stream)
+        S.sem_render(ctx, self.tris, off, seg, None, self.w.camera, self.W, self.H, self.rgba, self.depth)
+        if events is not None:
+            events[3].record(self.stream)
+        self.last_ntri = off
+        return off
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2312_09888_gb300 as S
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S.get_lib()
+    w = make_workload("cuda")
+    P = Pipeline(S, w, local)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        P.step()
+    # device-resident timed region
+    K = args.steps
+    stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(P.stream)
+    for k in range(K):
+        P.step(stage_ev[k])
+    t1.record(P.stream)
+    barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    stage_ms = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in stage_ev])
+    secs = ms / 1e3
+    if world > 1:
+        t = torch.tensor([secs], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    value = aggregate([P.E * K] * world, [secs])
+
+    # end to end: velocity from pinned host memory, frame back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host_vel = [v.cpu().pin_memory() for v in P.vel]
+        host_img = torch.empty(P.rgba.numel(), dtype=torch.uint8).pin_memory()
+        host_dep = torch.empty(P.depth.numel(), dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            for d, h in zip(P.vel, host_vel):
+                d.copy_(h, non_blocking=True)
+            P.step()
+            host_img.copy_(P.rgba, non_blocking=True)
+            host_dep.copy_(P.depth, non_blocking=True)
+
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(P.stream)
+        for _ in range(K):
+            e2e_step()
+        b.record(P.stream)
+        barrier()
+        es = a.elapsed_time(b) / 1e3
+        if world > 1:
+            t = torch.tensor([es], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            es = float(t.item())
+        e2e = {"value": aggregate([P.E * K] * world, [es]), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in host_vel)),
+               "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4),
+               "ms_per_step": es * 1e3 / K}
+
+    # roofline of the dominant kernel
+    mean_stage = stage_ms.mean(axis=0)
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    q_ms = float(mean_stage[0])
+    q_bytes = 16 * P.npts   # read u, v, w (12 B/node) + write Q (4 B/node)
+    achieved = q_bytes / (q_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_sem_grad<8,3> (sem_qcriterion)", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+            "traffic": _traffic_for("k_sem_grad"), "algorithmic_bytes_per_launch": q_bytes,
+            "launch_ms": round(q_ms, 5)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, P.isos, budget_s=args.cpu_seconds)
+
+    n_iso = len(P.isos)
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / K, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "frames_per_s": round(K * world / secs, 2),
+           "config": {"workload": WORKLOAD, "elements": P.E, "order": w.mesh.N, "nodes": P.npts,
+                      "isovalues": w.iso_fracs, "image": [P.W, P.H], "triangles": int(P.last_ntri),
+                      "l2": "inputs 201 MB of velocity > 129 MB L2 (no flush)",
+                      "parallelism": f"replicas x{world}"},
+           "stage_ms": {"qcriterion": round(float(mean_stage[0]), 4),
+                        "isosurface_all": round(float(mean_stage[1]), 4),
+                        "render": round(float(mean_stage[2]), 4)},
+           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+           "gpu_launches": LAUNCHES_PER_STEP(n_iso) * K}
+    P.sess.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+
+def _oracle_sample(w, isos, nelem, seed=0):
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    E = w.E
+    e0 = int(rng.integers(0, max(1, E - nelem)))
+    idx = torch.arange(e0, e0 + nelem, device=w.fields.device)
+    xyz = w.mesh.xyz(w.fields.device)[:, idx].cpu().numpy()
+    vel = w.fields[:, idx].float().double().cpu().numpy()
+    return xyz, vel
+
+
+def _oracle_step(oracle, N, xyz, vel, isos, cam):
+    import numpy as np
+    Q = oracle.qcriterion(N, xyz, vel)
+    tris, seg = [], []
+    for iso in isos:
+        r = oracle.isosurface(N, xyz, Q, iso)
+        tris.append(r["tris"])
+        seg.append(r["ntri"])
+    allt = np.concatenate(tris) if tris else np.zeros((0, 3, 3))
+    oracle.render(allt, seg, [[0.9, 0.35, 0.25], [0.25, 0.6, 0.9], [0.35, 0.85, 0.4]][:len(seg)], cam)
+
+
+def cpu_baseline(w, isos, budget_s=15.0, nelem=1024):
+    """Times the FP64 oracle (single thread) on a contiguous slab of ``nelem`` elements of the
+    same workload -- Q, all isovalues, and a full-size frame of the slab's triangles --
+    repeating until ``budget_s`` of CPU time; elements/s = elements processed / seconds."""
+    import oracle
+    oracle.lib()
+    xyz, vel = _oracle_sample(w, isos, nelem)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
+        done += nelem
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": round(done / el, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nelem} contiguous elements of the workload (Q + {len(isos)} isosurfaces + "
+                      f"{w.camera['W']}x{w.camera['H']} frame), repeated {done // nelem}x in {el:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    import numpy as np
+    import torch
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    oracle.lib()
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    w = make_workload(dev)
+    import paper_2312_09888_gb300  # noqa: F401  (isovalues come from the oracle's own Q below)
+    nelem = args.ref_elements
+    xyz, vel = _oracle_sample(w, None, nelem)
+    Q = oracle.qcriterion(w.mesh.N, xyz, vel)
+    isos = [float(np.float32(f * Q.max())) for f in w.iso_fracs]
+    for _ in range(args.warmup):
+        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
+    el = time.perf_counter() - t0
+    value = nelem * args.steps / el
+    sample = f"each step: {nelem} contiguous elements of the workload (Q + {len(isos)} isosurfaces + frame)"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD},
+           "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-elements", type=int, default=512)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

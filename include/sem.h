@@ -1,0 +1,201 @@
+/*
+ * sem.h -- C ABI of libsem, the GB300 (sm_103a) library for the in situ render path of
+ * spectral-element (SEM) velocity fields: spectral derivative -> Q-criterion -> marching-cubes
+ * isosurface -> z-buffer raster.
+ *
+ * Where the operations come from.  The paper instruments NekRS, a spectral-element code
+ * (Sec. 1), so that fields resident in GPU memory are rendered to images every n time steps
+ * (Sec. 3.1, Listing 1: an analysis with frequency="100"; Sec. 4.1: images every 100 steps
+ * instead of checkpoints).  Its bridge is called once to initialise with the solver's data
+ * and then once per step (Sec. 3.2, Listing 3), and its DataAdaptor hands over the mesh and
+ * the field arrays (Sec. 3.2, Listing 2: GetMesh / AddArray).  The paper does this on the CPU
+ * after a device-to-host copy (Sec. 3.2) through third-party renderers; it does not define
+ * the visualisation arithmetic.  This library keeps the data on the device and states that
+ * arithmetic from textbook definitions, cited per call below.  sem_create/sem_load_mesh play
+ * the role of the bridge's initialise + GetMesh; sem_qcriterion/sem_isosurface/sem_render
+ * are the per-step analysis.
+ *
+ * Conventions (all calls):
+ *   - Element e of order N has (N+1)^3 Gauss-Lobatto-Legendre (GLL) nodes ordered
+ *     n = i + (N+1)(j + (N+1)k) (r fastest); a field is float f[E][(N+1)^3] (element-major,
+ *     the Nek layout), one array per component.
+ *   - Device pointers are CUDA device pointers of the context's device and must be 16-byte
+ *     aligned, else SEM_ERR_ARG; triangle buffers (tris, tri_elem) need only 4-byte alignment,
+ *     so several isosurfaces can be written back to back into one buffer.  The caller owns every field, triangle and image buffer; the
+ *     library owns sem_ctx, sem_mesh and its own scratch memory.
+ *   - Every call is stream-ordered on the context's stream and returns without waiting,
+ *     except where a call states that it synchronises.  Kernel-side failures that are only
+ *     visible later (a bounded wait that ran out) are reported by sem_synchronize.
+ *   - No call throws, aborts or falls back to the CPU.  On failure a call returns a nonzero
+ *     sem_status, writes no output past the stated bounds, and sem_last_error(ctx) describes
+ *     the failure.
+ *   - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SEM_API __attribute__((visibility("default")))
+#else
+#define SEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem_ctx sem_ctx;   /* opaque: device, stream, scratch, error text        */
+typedef struct sem_mesh sem_mesh; /* opaque: per-element affine boxes + GLL tables      */
+
+typedef enum {
+    SEM_OK = 0,
+    SEM_ERR_ARG = 1,          /* bad pointer, size, alignment, order N or precision       */
+    SEM_ERR_CAPACITY = 2,     /* output buffer too small; the required size is returned   */
+    SEM_ERR_OOM = 3,          /* device scratch allocation failed                         */
+    SEM_ERR_CUDA = 4,         /* a CUDA runtime call failed                               */
+    SEM_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out (kernel returned)     */
+    SEM_ERR_UNSUPPORTED = 6   /* valid request this build does not implement (e.g. a
+                                 curved mesh, an unimplemented precision)                 */
+} sem_status;
+
+/* Arithmetic of the derivative contraction (sem_derivatives, sem_qcriterion). */
+typedef enum {
+    SEM_FP32 = 0,   /* FP32 FFMA (the plain path)                                            */
+    SEM_TF32 = 1,   /* tensor cores, TF32 operands, FP32 accumulation                        */
+    SEM_FP16 = 2,   /* tensor cores, FP16 operands, FP32 accumulation                        */
+    SEM_BF16 = 3,   /* tensor cores, BF16 operands, FP32 accumulation                        */
+    SEM_BF16X2 = 4  /* tensor cores, operands split into BF16 hi + lo, FP32 accumulation      */
+} sem_prec;
+
+/* Largest polynomial order accepted by sem_load_mesh. */
+#define SEM_MAX_ORDER 15
+/* Triangle slots per marching-cubes case in sem_mc_table. */
+#define SEM_MC_MAXT 12
+
+/* Camera of sem_render.  View basis f = unit(center-eye), s = unit(f x up), u = s x f;
+ * view coordinates xv = s.(p-eye), yv = u.(p-eye), zv = f.(p-eye).
+ *   ortho != 0: x_ndc = xv/(half_h*W/H), y_ndc = yv/half_h, depth = (zv-znear)/(zfar-znear)
+ *   ortho == 0: x_ndc = xv/(zv*tan(fovy/2)*W/H), y_ndc = yv/(zv*tan(fovy/2)),
+ *               depth = zfar/(zfar-znear) * (1 - znear/zv)
+ * screen x = (x_ndc+1)/2*W, y = (1-y_ndc)/2*H (row 0 at the top). */
+typedef struct {
+    int32_t ortho;
+    float eye[3];
+    float center[3];
+    float up[3];
+    float fovy_deg;
+    float half_h;
+    float znear;
+    float zfar;
+} sem_camera;
+
+/* ABI version of this header (bumped on any signature change). */
+SEM_API int sem_version(void);
+
+/* Create a context on CUDA device `device` that issues all work on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  Uploads the constant tables (GLL, marching cubes).
+ * Synchronous.  *out is NULL on failure. */
+SEM_API sem_status sem_create(int device, void *stream, sem_ctx **out);
+
+/* Destroy a context (waits for its stream, frees its scratch).  NULL is a no-op. */
+SEM_API void sem_destroy(sem_ctx *ctx);
+
+/* Text of the last failure on this context ("" if none).  Owned by the context; valid until
+ * the next call on it.  With ctx == NULL, the last failure of sem_create on this thread. */
+SEM_API const char *sem_last_error(const sem_ctx *ctx);
+
+/* Switch the context to another stream of the same device. */
+SEM_API sem_status sem_set_stream(sem_ctx *ctx, void *stream);
+
+/* Wait for the context's stream; report any device-side failure flagged since the last call
+ * (SEM_ERR_TIMEOUT) and clear it. */
+SEM_API sem_status sem_synchronize(sem_ctx *ctx);
+
+/* Load a mesh of E hexahedral elements of order N (1 <= N <= SEM_MAX_ORDER).
+ * xyz_host: HOST array of 3*E*(N+1)^3 doubles, SoA x | y | z, node order as above; copied.
+ * Each element must be an axis-aligned affine box (x depends only on i, y on j, z on k, with
+ * the GLL spacing): this covers every box/channel mesh, stretched or not.  Curved
+ * (non-affine) elements return SEM_ERR_UNSUPPORTED.  The element map x = x0 + (xi+1)/2 (x1-x0)
+ * is Nek's isoparametric map restricted to boxes (Deville, Fischer & Mund, Sec. 4.5).
+ * Synchronous.  Free with sem_mesh_free. */
+SEM_API sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz_host, sem_mesh **out);
+SEM_API void sem_mesh_free(sem_mesh *mesh);
+SEM_API sem_status sem_mesh_info(const sem_mesh *mesh, int *N, int64_t *E);
+
+/* Spectral derivative of one field u (device, E*(N+1)^3 floats):
+ *   du/dr[k][j][i] = sum_m D[i][m] u[k][j][m]  (likewise s over j, t over k),
+ *   du/dx = 2/(x1-x0) du/dr, du/dy = 2/(y1-y0) du/ds, du/dz = 2/(z1-z0) du/dt,
+ * with D the GLL collocation derivative matrix (Canuto et al., Spectral Methods, Sec. 2.3).
+ * Derivatives are element-local (no averaging across element faces).
+ * dudx, dudy, dudz: device, E*(N+1)^3 floats each, must not alias u. */
+SEM_API sem_status sem_derivatives(sem_ctx *ctx, const sem_mesh *mesh, const float *u, float *dudx,
+                           float *dudy, float *dudz, sem_prec prec);
+
+/* Q-criterion (Hunt, Wray & Moin 1988) of the velocity (u, v, w) at every node:
+ *   J_ij = du_i/dx_j (as in sem_derivatives),  Q = 1/2(|Omega|^2 - |S|^2) = -1/2 sum_ij J_ij J_ji.
+ * u, v, w, Q: device, E*(N+1)^3 floats each; Q must not alias the inputs. */
+SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const float *u, const float *v,
+                          const float *w, float *Q, sem_prec prec);
+
+/* Marching-cubes isosurface (Lorensen & Cline 1987) of f = iso over the N^3 sub-hexes of each
+ * element's GLL lattice.  Cell (i,j,k), corner v = a + 2b + 4c at node (i+a, j+b, k+c);
+ * case = sum_v [f_v >= iso] 2^v (NaN counts as below).  The case table is the library's own,
+ * generated from a face-consistent rule (see sem_mc_table); the surface is crack-free across
+ * cells and elements and its normals (p1-p0)x(p2-p0) point toward increasing f.
+ * Cut edge (lo, hi), lo the lower corner: t = (iso - f_lo)/(f_hi - f_lo),
+ * p = p_lo + t (p_hi - p_lo).  Triangles are written in (element, cell i + N(j + Nk), table)
+ * order as float tris[ntri][3][3] (vertex-major xyz) with tri_elem[ntri] = element index.
+ *   f:        device, E*(N+1)^3 floats
+ *   tris:     device, cap*9 floats;   tri_elem: device, cap int32 (may be NULL)
+ *   cap:      capacity in triangles (>= 0)
+ *   ntri_out: HOST; receives the triangle count
+ *   cases:    device, E*N^3 bytes, or NULL; receives every cell's case index
+ * Synchronises once (to read the count back).  If the count exceeds cap, returns
+ * SEM_ERR_CAPACITY with *ntri_out = the required count and writes no triangle. */
+SEM_API sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *mesh, const float *f, float iso, float *tris,
+                          int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
+
+/* Z-buffer raster of a triangle soup into a headless RGBA8 + depth image.
+ * Triangles are coloured per contiguous segment: segment s holds seg_ntri[s] triangles and
+ * colour seg_rgb[3s..3s+2] (HOST arrays; seg_rgb NULL = built-in palette).  Pixel (x, y)
+ * samples (x+0.5, y+0.5); coverage uses edge functions with the top-left fill rule; zero-area
+ * triangles and triangles with a vertex outside znear < zv < zfar are dropped; no back-face
+ * culling.  Depth is interpolated in screen space; the smallest (depth, triangle index) wins,
+ * so the image does not depend on execution order.  Flat headlight shading:
+ * c = rgb * (0.15 + 0.85 |n.l|), n the face normal, l = -f; rgba8 = floor(clamp(c)*255 + .5),
+ * alpha 255.  Background: rgba (0,0,0,0), depth 1.
+ *   tris:  device, ntri*9 floats;  rgba: device, H*W*4 bytes;  depth: device, H*W floats (may
+ *   be NULL).  nseg in [1, 16]; sum(seg_ntri) == ntri.
+ * Synchronises once (to size the tile lists). */
+SEM_API sem_status sem_render(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
+                      float *depth);
+
+/* FP64 reductions of a triangle soup (device, ntri*9 floats): out_host[0] = total area
+ * sum |(p1-p0)x(p2-p0)|/2, out_host[1] = enclosed volume sum p0.(p1 x p2)/6 (divergence
+ * theorem; positive when normals point out of the enclosed region).  Synchronises. */
+SEM_API sem_status sem_surface_measures(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);
+
+/* Largest value of a device float array (NaNs ignored), e.g. for iso = fraction * max Q.
+ * Synchronises.  n >= 1. */
+SEM_API sem_status sem_field_max(sem_ctx *ctx, const float *f, int64_t n, float *max_host);
+
+/* Host-only queries (no device needed). */
+
+/* The library's marching-cubes case table: ntri[256] triangles per case and
+ * edges[256][SEM_MC_MAXT][3] edge indices (-1 padded), edges numbered in lexicographic order
+ * of their (lower, upper) corner pair.  Returns the largest ntri, or a negative value if the
+ * generator failed. */
+SEM_API int sem_mc_table(int32_t *ntri, int8_t *edges);
+
+/* The library's GLL nodes xi[N+1] and derivative matrix D[(N+1)*(N+1)] (row-major, D[i][j] =
+ * l_j'(xi_i)) in FP64, as computed for the device tables (which round them to FP32). */
+SEM_API sem_status sem_gll(int N, double *xi, double *D);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

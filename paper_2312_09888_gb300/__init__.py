@@ -1,0 +1,302 @@
+"""Python binding of libsem, the GB300 (sm_103a) CUDA library for the in situ render path
+of spectral-element velocity fields (spectral derivative -> Q-criterion -> marching-cubes
+isosurface -> z-buffer raster).
+
+This module only marshals arguments into the C ABI declared in ``include/sem.h``; every
+step of the path runs in the library's CUDA kernels.  PyTorch provides device memory and
+streams.  There is no CPU fallback: if ``lib/libsem.so`` has not been built, every call
+raises.  Functions keep the C names (``sem_create``, ``sem_load_mesh``, ``sem_derivatives``,
+``sem_qcriterion``, ``sem_isosurface``, ``sem_render``, ...).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libsem.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sem.h")
+
+SEM_OK, SEM_ERR_ARG, SEM_ERR_CAPACITY, SEM_ERR_OOM, SEM_ERR_CUDA, SEM_ERR_TIMEOUT, SEM_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = ["SEM_OK", "SEM_ERR_ARG", "SEM_ERR_CAPACITY", "SEM_ERR_OOM", "SEM_ERR_CUDA", "SEM_ERR_TIMEOUT",
+                "SEM_ERR_UNSUPPORTED"]
+SEM_FP32, SEM_TF32, SEM_FP16, SEM_BF16, SEM_BF16X2 = range(5)
+SEM_MAX_ORDER = 15
+SEM_MC_MAXT = 12
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SemError(RuntimeError):
+    def __init__(self, status: int, msg: str, required: Optional[int] = None):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+        self.status = status
+        self.required = required
+
+
+class sem_camera(C.Structure):
+    _fields_ = [("ortho", C.c_int32), ("eye", C.c_float * 3), ("center", C.c_float * 3), ("up", C.c_float * 3),
+                ("fovy_deg", C.c_float), ("half_h", C.c_float), ("znear", C.c_float), ("zfar", C.c_float)]
+
+
+def _declare(L):
+    vp, i32, i64, f32, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_float, C.c_double
+    L.sem_version.restype = i32
+    L.sem_create.argtypes = [i32, vp, C.POINTER(vp)]
+    L.sem_destroy.argtypes = [vp]
+    L.sem_destroy.restype = None
+    L.sem_last_error.argtypes = [vp]
+    L.sem_last_error.restype = C.c_char_p
+    L.sem_set_stream.argtypes = [vp, vp]
+    L.sem_synchronize.argtypes = [vp]
+    L.sem_load_mesh.argtypes = [vp, i32, i64, vp, C.POINTER(vp)]
+    L.sem_mesh_free.argtypes = [vp]
+    L.sem_mesh_free.restype = None
+    L.sem_mesh_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64)]
+    L.sem_derivatives.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+    L.sem_qcriterion.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+    L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
+    L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
+    L.sem_surface_measures.argtypes = [vp, vp, i64, vp]
+    L.sem_field_max.argtypes = [vp, vp, i64, C.POINTER(f32)]
+    L.sem_mc_table.argtypes = [vp, vp]
+    L.sem_mc_table.restype = i32
+    L.sem_gll.argtypes = [i32, vp, vp]
+    for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
+                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_render", "sem_surface_measures",
+                 "sem_field_max", "sem_gll"):
+        getattr(L, name).restype = i32
+
+
+def get_lib():
+    """Load lib/libsem.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is missing: build it with paper_2312_09888_gb300.build_library()")
+            L = C.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+        return _lib
+
+
+def build_library(force: bool = False) -> str:
+    """Compile lib/libsem.so for sm_103a (incremental)."""
+    import importlib
+    return importlib.import_module(__name__ + ".build").build(force=force)
+
+
+# ------------------------------------------------------------------------------ marshalling
+
+def _dev(t, name, dtype=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is None")
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(ctx, st: int, required: Optional[int] = None):
+    if st != SEM_OK:
+        msg = get_lib().sem_last_error(ctx).decode(errors="replace")
+        raise SemError(st, msg, required)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------------------ C ABI mirrors
+
+def sem_version() -> int:
+    return get_lib().sem_version()
+
+
+def sem_create(device: int = 0, stream=None):
+    out = C.c_void_p()
+    st = get_lib().sem_create(device, C.c_void_p(_stream_handle(stream)), C.byref(out))
+    _check(None, st)
+    return out
+
+
+def sem_destroy(ctx) -> None:
+    get_lib().sem_destroy(ctx)
+
+
+def sem_last_error(ctx) -> str:
+    return get_lib().sem_last_error(ctx).decode(errors="replace")
+
+
+def sem_set_stream(ctx, stream) -> None:
+    _check(ctx, get_lib().sem_set_stream(ctx, C.c_void_p(_stream_handle(stream))))
+
+
+def sem_synchronize(ctx) -> None:
+    _check(ctx, get_lib().sem_synchronize(ctx))
+
+
+def sem_load_mesh(ctx, N: int, xyz) -> C.c_void_p:
+    """xyz: host float64 array (3, E, (N+1)^3) of node coordinates (torch or numpy)."""
+    a = xyz.detach().cpu().numpy() if hasattr(xyz, "detach") else xyz
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    E = a.shape[1] if a.ndim == 3 else a.size // (3 * (N + 1) ** 3)
+    out = C.c_void_p()
+    _check(ctx, get_lib().sem_load_mesh(ctx, int(N), int(E), a.ctypes.data_as(C.c_void_p), C.byref(out)))
+    return out
+
+
+def sem_mesh_free(mesh) -> None:
+    get_lib().sem_mesh_free(mesh)
+
+
+def sem_mesh_info(mesh):
+    n = C.c_int()
+    e = C.c_int64()
+    st = get_lib().sem_mesh_info(mesh, C.byref(n), C.byref(e))
+    if st:
+        raise SemError(st, "bad mesh")
+    return n.value, e.value
+
+
+def sem_derivatives(ctx, mesh, u, dudx, dudy, dudz, prec: int = SEM_FP32) -> None:
+    import torch
+    f = torch.float32
+    _check(ctx, get_lib().sem_derivatives(ctx, mesh, _dev(u, "u", f), _dev(dudx, "dudx", f), _dev(dudy, "dudy", f),
+                                          _dev(dudz, "dudz", f), int(prec)))
+
+
+def sem_qcriterion(ctx, mesh, u, v, w, Q, prec: int = SEM_FP32) -> None:
+    import torch
+    f = torch.float32
+    _check(ctx, get_lib().sem_qcriterion(ctx, mesh, _dev(u, "u", f), _dev(v, "v", f), _dev(w, "w", f),
+                                         _dev(Q, "Q", f), int(prec)))
+
+
+def sem_isosurface(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None, cap: Optional[int] = None) -> int:
+    """Returns the triangle count.  Raises SemError(SEM_ERR_CAPACITY, required=n) if tris is
+    too small (cap defaults to tris.numel() // 9)."""
+    import torch
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    n = C.c_int64(0)
+    st = get_lib().sem_isosurface(ctx, mesh, _dev(f, "f", torch.float32), C.c_float(iso),
+                                  _dev(tris, "tris", torch.float32, allow_none=True),
+                                  _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap), C.byref(n),
+                                  _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st, n.value)
+    return n.value
+
+
+def make_camera(cam: dict) -> sem_camera:
+    c = sem_camera()
+    c.ortho = int(cam["ortho"])
+    for k in ("eye", "center", "up"):
+        getattr(c, k)[:] = [float(x) for x in cam[k]]
+    c.fovy_deg = float(cam.get("fovy_deg", 40.0))
+    c.half_h = float(cam.get("half_h", 1.0))
+    c.znear = float(cam["znear"])
+    c.zfar = float(cam["zfar"])
+    return c
+
+
+def sem_render(ctx, tris, ntri: int, seg_ntri: Sequence[int], seg_rgb, cam: dict, W: int, H: int, rgba,
+               depth=None) -> None:
+    import torch
+    seg = np.ascontiguousarray(np.asarray(seg_ntri, dtype=np.int64))
+    rgb = None if seg_rgb is None else np.ascontiguousarray(np.asarray(seg_rgb, dtype=np.float32).reshape(-1))
+    camc = make_camera(cam)
+    st = get_lib().sem_render(ctx, _dev(tris, "tris", torch.float32, allow_none=ntri == 0), int(ntri),
+                              seg.ctypes.data_as(C.c_void_p), len(seg),
+                              None if rgb is None else rgb.ctypes.data_as(C.c_void_p), C.byref(camc), int(W), int(H),
+                              _dev(rgba, "rgba", torch.uint8), _dev(depth, "depth", torch.float32, allow_none=True))
+    _check(ctx, st)
+
+
+def sem_surface_measures(ctx, tris, ntri: int):
+    import torch
+    out = np.zeros(2)
+    _check(ctx, get_lib().sem_surface_measures(ctx, _dev(tris, "tris", torch.float32, allow_none=ntri == 0),
+                                               int(ntri), out.ctypes.data_as(C.c_void_p)))
+    return float(out[0]), float(out[1])
+
+
+def sem_field_max(ctx, f) -> float:
+    import torch
+    m = C.c_float(0)
+    _check(ctx, get_lib().sem_field_max(ctx, _dev(f, "f", torch.float32), int(f.numel()), C.byref(m)))
+    return m.value
+
+
+def sem_mc_table():
+    n = np.zeros(256, dtype=np.int32)
+    e = np.zeros((256, SEM_MC_MAXT, 3), dtype=np.int8)
+    mx = get_lib().sem_mc_table(n.ctypes.data_as(C.c_void_p), e.ctypes.data_as(C.c_void_p))
+    if mx < 0:
+        raise SemError(SEM_ERR_CUDA, f"table generator failed ({mx})")
+    return n, e
+
+
+def sem_gll(N: int):
+    xi = np.zeros(N + 1)
+    D = np.zeros((N + 1, N + 1))
+    st = get_lib().sem_gll(int(N), xi.ctypes.data_as(C.c_void_p), D.ctypes.data_as(C.c_void_p))
+    if st:
+        raise SemError(st, f"sem_gll({N})")
+    return xi, D
+
+
+def exported_symbols():
+    """Function names declared in include/sem.h (for the ABI test)."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"SEM_API[^;(]*?\b(sem_\w+)\s*\(", txt)))
+
+
+# ------------------------------------------------------------------------------ convenience
+
+class Session:
+    """A context plus its meshes, freed together (``with Session() as s: ...``)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.ctx = sem_create(device, stream)
+        self._meshes = []
+
+    def mesh(self, N: int, xyz):
+        m = sem_load_mesh(self.ctx, N, xyz)
+        self._meshes.append(m)
+        return m
+
+    def close(self):
+        for m in self._meshes:
+            sem_mesh_free(m)
+        self._meshes = []
+        if self.ctx:
+            sem_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,525 @@
+// sem_api.cu -- C ABI of libsem: contexts, meshes, argument checking, host-side table
+// generators (GLL nodes / derivative matrix, marching-cubes case table).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "sem_internal.cuh"
+
+#define SEM_ABI_VERSION 1
+
+static thread_local std::string g_create_err;
+
+sem_status sem_fail(sem_ctx *ctx, sem_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_err = buf;
+    return st;
+}
+
+sem_status sem_cuda(sem_ctx *ctx, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SEM_OK;
+    cudaGetLastError();  // clear a non-sticky error
+    return sem_fail(ctx, e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA, "%s: %s (%s)", what,
+                    cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+sem_status sem_scratch(sem_ctx *ctx, int slot, size_t bytes, void **out)
+{
+    if (bytes == 0) bytes = 256;
+    if (ctx->scratch_bytes[slot] < bytes) {
+        size_t nb = bytes + bytes / 4 + 4096;
+        if (ctx->scratch[slot]) {
+            SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+            SEM_CU(ctx, cudaFree(ctx->scratch[slot]));
+            ctx->scratch[slot] = nullptr;
+            ctx->scratch_bytes[slot] = 0;
+        }
+        SEM_CU(ctx, cudaMalloc(&ctx->scratch[slot], nb));
+        ctx->scratch_bytes[slot] = nb;
+    }
+    *out = ctx->scratch[slot];
+    return SEM_OK;
+}
+
+// ==========================================================================================
+// GLL nodes and derivative matrix (host, FP64).
+//
+// Interior GLL nodes are the zeros of P_N' = ((N+1)/2) P^{(1,1)}_{N-1}, the Jacobi polynomial
+// with alpha = beta = 1 (Canuto et al., Spectral Methods, Sec. 2.3).  They are found by
+// Newton's method on P^{(1,1)}_{N-1}, evaluated with its three-term recurrence
+//   2n(n+2) P_n = (2n+1)(2n+2) x P_{n-1} - n(2n+2) P_{n-2},  P_0 = 1, P_1 = 2x.
+// D is the derivative of the Lagrange basis in barycentric form (Berrut & Trefethen 2004):
+//   lambda_j = 1 / prod_{k != j} (x_j - x_k),  D_ij = (lambda_j / lambda_i) / (x_i - x_j),
+//   D_ii = -sum_{j != i} D_ij.
+// ==========================================================================================
+static void jacobi11(int n, double x, double *p, double *dp)
+{
+    double p0 = 1.0, p1 = 2.0 * x, d0 = 0.0, d1 = 2.0;
+    if (n == 0) {
+        *p = 1.0;
+        *dp = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        double a = (2.0 * k + 1.0) * (2.0 * k + 2.0), b = k * (2.0 * k + 2.0), c = 2.0 * k * (k + 2.0);
+        double p2 = (a * x * p1 - b * p0) / c;
+        double d2 = (a * (p1 + x * d1) - b * d0) / c;
+        p0 = p1;
+        p1 = p2;
+        d0 = d1;
+        d1 = d2;
+    }
+    *p = p1;
+    *dp = d1;
+}
+
+static void gll_nodes(int N, double *x)
+{
+    x[0] = -1.0;
+    x[N] = 1.0;
+    for (int j = 1; j < N; ++j) {
+        double t = -cos(M_PI * j / N);
+        for (int it = 0; it < 200; ++it) {
+            double p, dp;
+            jacobi11(N - 1, t, &p, &dp);
+            double step = p / dp;
+            t -= step;
+            if (fabs(step) < 1e-17) break;
+        }
+        x[j] = t;
+    }
+}
+
+static void gll_dmat(int N, const double *x, double *D)
+{
+    int NP = N + 1;
+    std::vector<double> lam(NP);
+    for (int j = 0; j < NP; ++j) {
+        double pr = 1.0;
+        for (int k = 0; k < NP; ++k)
+            if (k != j) pr *= (x[j] - x[k]);
+        lam[j] = 1.0 / pr;
+    }
+    for (int i = 0; i < NP; ++i) {
+        double diag = 0.0;
+        for (int j = 0; j < NP; ++j) {
+            if (j == i) continue;
+            double v = (lam[j] / lam[i]) / (x[i] - x[j]);
+            D[i * NP + j] = v;
+            diag -= v;
+        }
+        D[i * NP + i] = diag;
+    }
+}
+
+// ==========================================================================================
+// Marching-cubes case table (host).  Corners v = a + 2b + 4c, edges = corner pairs differing
+// in one bit, numbered lexicographically by (lower, upper) corner.  Rule: on every face, walk
+// the corners counter-clockwise as seen from outside the cell; each maximal run of inside
+// corners (f >= iso) is bounded by an entry edge (outside -> inside) and an exit edge
+// (inside -> outside); the face contributes the segment exit -> entry.  A face with
+// diagonal inside corners has two runs, so each inside corner is cut off on its own, and two
+// cells sharing a face derive the same segments (crack-free).  Segments chain into closed
+// loops (each cut edge lies on two faces); loops are taken by their lowest edge, start at it
+// and are fan-triangulated.  The walk direction makes (p1-p0)x(p2-p0) point toward
+// increasing f (Lorensen & Cline 1987 for the method; the table is generated, not copied).
+// ==========================================================================================
+static int mc_build(int32_t *ntri, int8_t *edges)
+{
+    int eid[8][8];
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) eid[a][b] = -1;
+    int ne = 0;
+    for (int lo = 0; lo < 8; ++lo)
+        for (int hi = lo + 1; hi < 8; ++hi) {
+            int x = lo ^ hi;
+            if (x == 1 || x == 2 || x == 4) {
+                eid[lo][hi] = eid[hi][lo] = ne++;
+            }
+        }
+    static const int ccw_pos[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+    int maxt = 0;
+    for (int cs = 0; cs < 256; ++cs) {
+        int succ[12];
+        for (int e = 0; e < 12; ++e) succ[e] = -1;
+        for (int d = 0; d < 3; ++d) {
+            int a = (d + 1) % 3, b = (d + 2) % 3;  // e_a x e_b = e_d
+            for (int side = 0; side < 2; ++side) {
+                int cyc[4];
+                for (int m = 0; m < 4; ++m) {
+                    // counter-clockwise about the outward normal: +e_d keeps the (a,b) order,
+                    // -e_d reverses it
+                    int mm = side ? m : (4 - m) % 4;
+                    cyc[m] = (side << d) | (ccw_pos[mm][0] << a) | (ccw_pos[mm][1] << b);
+                }
+                for (int m = 0; m < 4; ++m) {
+                    int prev = cyc[(m + 3) % 4], cur = cyc[m];
+                    bool pin = (cs >> prev) & 1, cin = (cs >> cur) & 1;
+                    if (pin || !cin) continue;  // not the first corner of an inside run
+                    int e_in = eid[prev][cur];
+                    int q = m;
+                    while ((cs >> cyc[(q + 1) % 4]) & 1) q = (q + 1) % 4;
+                    int e_out = eid[cyc[q]][cyc[(q + 1) % 4]];
+                    if (succ[e_out] != -1) return -1;
+                    succ[e_out] = e_in;
+                }
+            }
+        }
+        bool seen[12] = {false};
+        int nt = 0;
+        for (int k = 0; k < SEM_MC_MAXT * 3; ++k) edges[cs * SEM_MC_MAXT * 3 + k] = -1;
+        for (int e0 = 0; e0 < 12; ++e0) {
+            if (succ[e0] < 0 || seen[e0]) continue;
+            int loop[12], len = 0;
+            for (int e = e0; !seen[e]; e = succ[e]) {
+                if (succ[e] < 0 || len == 12) return -2;
+                seen[e] = true;
+                loop[len++] = e;
+            }
+            for (int q = 1; q + 1 < len; ++q) {
+                int8_t *t = edges + (cs * SEM_MC_MAXT + nt) * 3;
+                t[0] = (int8_t)loop[0];
+                t[1] = (int8_t)loop[q];
+                t[2] = (int8_t)loop[q + 1];
+                ++nt;
+            }
+        }
+        ntri[cs] = nt;
+        if (nt > maxt) maxt = nt;
+    }
+    return maxt;
+}
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+int sem_version(void) { return SEM_ABI_VERSION; }
+
+int sem_mc_table(int32_t *ntri, int8_t *edges)
+{
+    if (!ntri || !edges) return -100;
+    return mc_build(ntri, edges);
+}
+
+sem_status sem_gll(int N, double *xi, double *D)
+{
+    if (N < 1 || N > SEM_MAX_ORDER || !xi) return SEM_ERR_ARG;
+    gll_nodes(N, xi);
+    if (D) gll_dmat(N, xi, D);
+    return SEM_OK;
+}
+
+const char *sem_last_error(const sem_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+static sem_status upload_tables(sem_ctx *ctx)
+{
+    const int MP = SEM_MAX_ORDER + 1;
+    std::vector<float> D_all((size_t)(SEM_MAX_ORDER + 1) * MP * MP, 0.f), s_all((size_t)(SEM_MAX_ORDER + 1) * MP, 0.f);
+    double x[MP], D[MP * MP];
+    for (int N = 1; N <= SEM_MAX_ORDER; ++N) {
+        int NP = N + 1;
+        gll_nodes(N, x);
+        gll_dmat(N, x, D);
+        for (int i = 0; i < NP; ++i) {
+            s_all[(size_t)N * MP + i] = (float)((x[i] + 1.0) * 0.5);
+            for (int j = 0; j < NP; ++j) D_all[((size_t)N * MP + i) * MP + j] = (float)D[i * NP + j];
+        }
+        s_all[(size_t)N * MP + 0] = 0.f;
+        s_all[(size_t)N * MP + N] = 1.f;
+    }
+    int32_t ntri[256];
+    std::vector<int8_t> edges(256 * SEM_MC_MAXT * 3);
+    int mx = mc_build(ntri, edges.data());
+    if (mx < 0 || mx > 5) return sem_fail(ctx, SEM_ERR_CUDA, "marching-cubes table generator failed (%d)", mx);
+    SEM_TRY(qcrit_upload_tables(ctx, D_all.data(), s_all.data()));
+    SEM_TRY(iso_upload_tables(ctx, s_all.data(), ntri, edges.data()));
+    return SEM_OK;
+}
+
+sem_status sem_create(int device, void *stream, sem_ctx **out)
+{
+    if (!out) return sem_fail(nullptr, SEM_ERR_ARG, "sem_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return sem_fail(nullptr, SEM_ERR_CUDA, "sem_create: no CUDA device (%s)", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return sem_fail(nullptr, SEM_ERR_ARG, "sem_create: bad device %d", device);
+    sem_ctx *ctx = new sem_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    sem_status st = SEM_OK;
+    do {
+        if ((st = sem_cuda(ctx, cudaSetDevice(device), "cudaSetDevice")) != SEM_OK) break;
+        cudaDeviceProp prop;
+        if ((st = sem_cuda(ctx, cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties")) != SEM_OK) break;
+        if (prop.major * 10 + prop.minor < 100) {
+            st = sem_fail(ctx, SEM_ERR_UNSUPPORTED, "device %d is sm_%d%d; this build targets sm_103a", device,
+                          prop.major, prop.minor);
+            break;
+        }
+        ctx->sm_count = prop.multiProcessorCount;
+        if ((st = sem_cuda(ctx, cudaMalloc(&ctx->d_flag, 64), "cudaMalloc(flag)")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaMemset(ctx->d_flag, 0, 64), "cudaMemset(flag)")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaMallocHost(&ctx->h_pinned, 16 * sizeof(int64_t)), "cudaMallocHost")) != SEM_OK)
+            break;
+        if ((st = sem_cuda(ctx, cudaMallocHost(&ctx->h_pinned_d, 4 * sizeof(double)), "cudaMallocHost")) != SEM_OK)
+            break;
+        if ((st = upload_tables(ctx)) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaDeviceSynchronize(), "cudaDeviceSynchronize")) != SEM_OK) break;
+    } while (0);
+    if (st != SEM_OK) {
+        g_create_err = ctx->err;
+        sem_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return SEM_OK;
+}
+
+void sem_destroy(sem_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (int s = 0; s < 4; ++s)
+        if (ctx->scratch[s]) cudaFree(ctx->scratch[s]);
+    if (ctx->d_flag) cudaFree(ctx->d_flag);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
+    delete ctx;
+}
+
+sem_status sem_set_stream(sem_ctx *ctx, void *stream)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    ctx->stream = (cudaStream_t)stream;
+    return SEM_OK;
+}
+
+sem_status sem_synchronize(sem_ctx *ctx)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    int flag = 0;
+    SEM_CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (flag) {
+        SEM_CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+        SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        if (flag & (1 << SEM_ERR_TIMEOUT))
+            return sem_fail(ctx, SEM_ERR_TIMEOUT, "a bounded device-side wait ran out (flag 0x%x)", flag);
+        return sem_fail(ctx, SEM_ERR_CUDA, "device-side failure flag 0x%x", flag);
+    }
+    return SEM_OK;
+}
+
+sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz, sem_mesh **out)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    if (!out) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: out is NULL");
+    *out = nullptr;
+    if (N < 1 || N > SEM_MAX_ORDER) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: N=%d outside [1,%d]", N, SEM_MAX_ORDER);
+    if (E < 0 || E > (int64_t)1 << 31) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: bad E=%lld", (long long)E);
+    if (E > 0 && !xyz) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: xyz is NULL");
+    const int NP = N + 1, NP3 = NP * NP * NP;
+    double xi[SEM_MAX_ORDER + 1];
+    gll_nodes(N, xi);
+    std::vector<float4> lo(E), hi(E), g(E);
+    const int64_t tot = E * NP3;
+    for (int64_t e = 0; e < E; ++e) {
+        const double *X = xyz + e * NP3, *Y = xyz + tot + e * NP3, *Z = xyz + 2 * tot + e * NP3;
+        double a[3] = {X[0], Y[0], Z[0]};
+        double b[3] = {X[N], Y[N * NP], Z[N * NP * NP]};
+        for (int d = 0; d < 3; ++d)
+            if (!(b[d] != a[d]) || !isfinite(a[d]) || !isfinite(b[d]))
+                return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "sem_load_mesh: element %lld is degenerate", (long long)e);
+        for (int k = 0; k < NP; ++k)
+            for (int j = 0; j < NP; ++j)
+                for (int i = 0; i < NP; ++i) {
+                    int n = (k * NP + j) * NP + i;
+                    int idx[3] = {i, j, k};
+                    const double *P[3] = {X, Y, Z};
+                    for (int d = 0; d < 3; ++d) {
+                        double s = (xi[idx[d]] + 1.0) * 0.5;
+                        double expect = a[d] + s * (b[d] - a[d]);
+                        double tol = 1e-9 * (fabs(b[d] - a[d]) + fabs(a[d]));
+                        if (!(fabs(P[d][n] - expect) <= tol))
+                            return sem_fail(ctx, SEM_ERR_UNSUPPORTED,
+                                            "sem_load_mesh: element %lld is not an axis-aligned affine box "
+                                            "(node %d, axis %d: %.17g vs %.17g); curved meshes are not supported",
+                                            (long long)e, n, d, P[d][n], expect);
+                    }
+                }
+        lo[e] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.f);
+        hi[e] = make_float4((float)b[0], (float)b[1], (float)b[2], 0.f);
+        g[e] = make_float4((float)(2.0 / (b[0] - a[0])), (float)(2.0 / (b[1] - a[1])), (float)(2.0 / (b[2] - a[2])), 0.f);
+    }
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    sem_mesh *m = new sem_mesh();
+    m->N = N;
+    m->E = E;
+    m->device = ctx->device;
+    size_t bytes = sizeof(float4) * (size_t)(E > 0 ? E : 1);
+    sem_status st = SEM_OK;
+    do {
+        if ((st = sem_cuda(ctx, cudaMalloc(&m->lo, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaMalloc(&m->hi, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaMalloc(&m->g, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
+        if (E > 0) {
+            if ((st = sem_cuda(ctx, cudaMemcpy(m->lo, lo.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
+            if ((st = sem_cuda(ctx, cudaMemcpy(m->hi, hi.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
+            if ((st = sem_cuda(ctx, cudaMemcpy(m->g, g.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
+        }
+    } while (0);
+    if (st != SEM_OK) {
+        sem_mesh_free(m);
+        return st;
+    }
+    *out = m;
+    return SEM_OK;
+}
+
+void sem_mesh_free(sem_mesh *m)
+{
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->lo) cudaFree(m->lo);
+    if (m->hi) cudaFree(m->hi);
+    if (m->g) cudaFree(m->g);
+    delete m;
+}
+
+sem_status sem_mesh_info(const sem_mesh *m, int *N, int64_t *E)
+{
+    if (!m) return SEM_ERR_ARG;
+    if (N) *N = m->N;
+    if (E) *E = m->E;
+    return SEM_OK;
+}
+
+static sem_status check_common(sem_ctx *ctx, const sem_mesh *m, const char *fn)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    if (!m) return sem_fail(ctx, SEM_ERR_ARG, "%s: mesh is NULL", fn);
+    if (m->device != ctx->device) return sem_fail(ctx, SEM_ERR_ARG, "%s: mesh lives on another device", fn);
+    return sem_cuda(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+}
+
+static sem_status check_ptr(sem_ctx *ctx, const void *p, const char *fn, const char *name, bool may_null = false,
+                            unsigned align = 16)
+{
+    if (!p) return may_null ? SEM_OK : sem_fail(ctx, SEM_ERR_ARG, "%s: %s is NULL", fn, name);
+    if ((reinterpret_cast<uintptr_t>(p) & (align - 1)) != 0)
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: %s is not %u-byte aligned", fn, name, align);
+    return SEM_OK;
+}
+
+sem_status sem_derivatives(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dudx, float *dudy, float *dudz,
+                           sem_prec prec)
+{
+    SEM_TRY(check_common(ctx, m, "sem_derivatives"));
+    if (m->E == 0) return SEM_OK;
+    SEM_TRY(check_ptr(ctx, u, "sem_derivatives", "u"));
+    SEM_TRY(check_ptr(ctx, dudx, "sem_derivatives", "dudx"));
+    SEM_TRY(check_ptr(ctx, dudy, "sem_derivatives", "dudy"));
+    SEM_TRY(check_ptr(ctx, dudz, "sem_derivatives", "dudz"));
+    if (prec != SEM_FP32)
+        return sem_fail(ctx, prec >= SEM_FP32 && prec <= SEM_BF16X2 ? SEM_ERR_UNSUPPORTED : SEM_ERR_ARG,
+                        "sem_derivatives: precision %d not available", (int)prec);
+    return deriv_launch(ctx, m, u, dudx, dudy, dudz);
+}
+
+sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q,
+                          sem_prec prec)
+{
+    SEM_TRY(check_common(ctx, m, "sem_qcriterion"));
+    if (m->E == 0) return SEM_OK;
+    SEM_TRY(check_ptr(ctx, u, "sem_qcriterion", "u"));
+    SEM_TRY(check_ptr(ctx, v, "sem_qcriterion", "v"));
+    SEM_TRY(check_ptr(ctx, w, "sem_qcriterion", "w"));
+    SEM_TRY(check_ptr(ctx, Q, "sem_qcriterion", "Q"));
+    if (Q == u || Q == v || Q == w) return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion: Q aliases an input");
+    if (prec != SEM_FP32)
+        return sem_fail(ctx, prec >= SEM_FP32 && prec <= SEM_BF16X2 ? SEM_ERR_UNSUPPORTED : SEM_ERR_ARG,
+                        "sem_qcriterion: precision %d not available", (int)prec);
+    return qcrit_launch(ctx, m, u, v, w, Q);
+}
+
+sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
+                          int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    SEM_TRY(check_common(ctx, m, "sem_isosurface"));
+    if (!ntri_out) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface: ntri_out is NULL");
+    *ntri_out = 0;
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface: negative cap");
+    if (m->E == 0) return SEM_OK;
+    SEM_TRY(check_ptr(ctx, f, "sem_isosurface", "f"));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface", "tris", cap == 0, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface", "tri_elem", true, 4));
+    SEM_TRY(check_ptr(ctx, cases, "sem_isosurface", "cases", true));
+    if (isnan(iso)) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface: iso is NaN");
+    return iso_run(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
+}
+
+sem_status sem_render(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (!cam) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: cam is NULL");
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: bad size %dx%d", W, H);
+    if (ntri < 0 || nseg < 1 || nseg > 16 || !seg_ntri) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: bad segments");
+    int64_t sum = 0;
+    for (int s = 0; s < nseg; ++s) {
+        if (seg_ntri[s] < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: negative segment size");
+        sum += seg_ntri[s];
+    }
+    if (sum != ntri) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: segments sum to %lld, ntri=%lld", (long long)sum, (long long)ntri);
+    if (ntri >= ((int64_t)1 << 31)) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: ntri >= 2^31");
+    SEM_TRY(check_ptr(ctx, tris, "sem_render", "tris", ntri == 0, 4));
+    SEM_TRY(check_ptr(ctx, rgba, "sem_render", "rgba"));
+    SEM_TRY(check_ptr(ctx, depth, "sem_render", "depth", true));
+    if (!(cam->znear > 0.f) || !(cam->zfar > cam->znear))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_render: need 0 < znear < zfar");
+    if (cam->ortho ? !(cam->half_h > 0.f) : !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_render: bad projection parameters");
+    return render_run(ctx, tris, ntri, seg_ntri, nseg, seg_rgb, cam, W, H, rgba, depth);
+}
+
+sem_status sem_surface_measures(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (!out_host || ntri < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_surface_measures: bad arguments");
+    out_host[0] = out_host[1] = 0.0;
+    if (ntri == 0) return SEM_OK;
+    SEM_TRY(check_ptr(ctx, tris, "sem_surface_measures", "tris", false, 4));
+    return measures_run(ctx, tris, ntri, out_host);
+}
+
+sem_status sem_field_max(sem_ctx *ctx, const float *f, int64_t n, float *max_host)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (!max_host || n < 1) return sem_fail(ctx, SEM_ERR_ARG, "sem_field_max: bad arguments");
+    SEM_TRY(check_ptr(ctx, f, "sem_field_max", "f"));
+    return fieldmax_run(ctx, f, n, max_host);
+}
+
+}  // extern "C"

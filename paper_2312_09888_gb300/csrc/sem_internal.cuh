@@ -1,0 +1,137 @@
+// sem_internal.cuh -- shared internals of libsem (context, mesh, device helpers).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sem.h"
+
+// ------------------------------------------------------------------------------------------
+// Host-side objects
+
+struct sem_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int sm_count = 0;
+    // device error word: kernels with bounded waits OR a code in here (SEM_ERR_TIMEOUT ...)
+    int *d_flag = nullptr;
+    // pinned host words for small read-backs (counts, totals)
+    int64_t *h_pinned = nullptr;   // 16 int64 slots
+    double *h_pinned_d = nullptr;  // 4 double slots
+    // grow-only device scratch arenas
+    void *scratch[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t scratch_bytes[4] = {0, 0, 0, 0};
+};
+
+struct sem_mesh {
+    int N = 0;
+    int64_t E = 0;
+    int device = 0;
+    float4 *lo = nullptr;   // element box lower corner (x0, y0, z0, 0)
+    float4 *hi = nullptr;   // element box upper corner (x1, y1, z1, 0)
+    float4 *g = nullptr;    // 2/(x1-x0), 2/(y1-y0), 2/(z1-z0), 0
+};
+
+// scratch arenas (each call uses its own so calls never overlap in scratch)
+enum { SCR_ISO = 0, SCR_RENDER = 1, SCR_MISC = 2, SCR_TRI = 3 };
+
+// set ctx->err and return st
+sem_status sem_fail(sem_ctx *ctx, sem_status st, const char *fmt, ...);
+// check a CUDA call; on failure records it and returns SEM_ERR_CUDA
+sem_status sem_cuda(sem_ctx *ctx, cudaError_t e, const char *what);
+// ensure scratch arena `slot` has at least `bytes`
+sem_status sem_scratch(sem_ctx *ctx, int slot, size_t bytes, void **out);
+
+#define SEM_TRY(expr)                           \
+    do {                                        \
+        sem_status _st = (expr);                \
+        if (_st != SEM_OK) return _st;          \
+    } while (0)
+
+#define SEM_CU(ctx, expr) SEM_TRY(sem_cuda((ctx), (expr), #expr))
+
+static inline bool sem_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// ------------------------------------------------------------------------------------------
+// Per-translation-unit table uploads (constant memory lives in the unit that uses it)
+
+// GLL derivative matrices (FP32) for N = 1..SEM_MAX_ORDER and node fractions (xi+1)/2
+sem_status qcrit_upload_tables(sem_ctx *ctx, const float *D_all, const float *s_all);
+sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *ntri, const int8_t *edges);
+
+// launchers (argument checking happens in sem_api.cu)
+sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                        float *Q);
+sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
+sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
+                   int64_t cap, int64_t *ntri_out, uint8_t *cases);
+sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth);
+sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);
+sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host);
+
+// exclusive scan of n int32 counts into n+1 int64 offsets (out[n] = total).  `tmp` must hold
+// scan_tmp_bytes(n) bytes.  Stream-ordered on ctx->stream.
+size_t scan_tmp_bytes(int64_t n);
+sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp);
+
+// ------------------------------------------------------------------------------------------
+// Device helpers: mbarrier + bulk async copy (TMA engine, non-tensor form)
+
+#define SEM_WAIT_LIMIT (1ll << 24)   // bounded spin on an mbarrier phase (~ seconds)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait; returns false (and flags `err`) if the phase never completed
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+{
+    for (long long it = 0; it < SEM_WAIT_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicOr(err, 1 << SEM_ERR_TIMEOUT);
+    return false;
+}
+
+// global -> shared bulk copy completing on `bar` (bytes: multiple of 16, both addresses 16B aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}

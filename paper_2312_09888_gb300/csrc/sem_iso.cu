@@ -1,0 +1,252 @@
+// sem_iso.cu -- marching-cubes isosurface over the GLL sub-hexes of each element.
+//
+// Method: Lorensen & Cline 1987, applied to the N^3 sub-hexes of each element's
+// (N+1)^3 GLL lattice.  Cell (i,j,k) has corners v = a + 2b + 4c at node (i+a, j+b, k+c);
+// case = sum_v [f_v >= iso] 2^v; triangles come from the library's generated case table;
+// a cut edge (lo, hi) gets t = (iso - f_lo)/(f_hi - f_lo), p = p_lo + t (p_hi - p_lo).
+//
+// Three passes, one warp per element in each:
+//   k_iso_count  reads the element once (16-byte loads), culls it with warp votes (active
+//                iff some node is >= iso and some is < iso), classifies its cells and writes
+//                the element's triangle count (and optionally every cell's case);
+//   scan         exclusive scan of the counts -> each element's first triangle;
+//   k_iso_emit   re-reads only active elements (the field is usually still in L2),
+//                classifies again, scans the per-cell counts across the warp and writes the
+//                triangles in (element, cell, table) order.
+// Node positions are lerps of the element box with exact end points, so nodes shared by two
+// elements get bit-identical coordinates.
+#include <cuda_runtime.h>
+
+#include "sem_internal.cuh"
+
+#define MP (SEM_MAX_ORDER + 1)
+#define ISO_MAXT 5      // largest triangle count of the generated table (checked on upload)
+// elements (warps) per block: 8, fewer for large orders so static shared memory stays < 40 KB
+template <int NP>
+struct IsoW {
+    static constexpr int B = 4 * NP * NP * NP;
+    static constexpr int V = (40960 / B) < 1 ? 1 : ((40960 / B) > 8 ? 8 : (40960 / B));
+};
+
+__constant__ float c_s[(SEM_MAX_ORDER + 1) * MP];        // (xi+1)/2 per order
+__constant__ uint8_t c_ntri[256];
+__constant__ int8_t c_edge[256 * ISO_MAXT * 3];
+
+sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *ntri, const int8_t *edges)
+{
+    uint8_t n8[256];
+    int8_t e8[256 * ISO_MAXT * 3];
+    for (int c = 0; c < 256; ++c) {
+        if (ntri[c] > ISO_MAXT) return sem_fail(ctx, SEM_ERR_CUDA, "case table has %d triangles", ntri[c]);
+        n8[c] = (uint8_t)ntri[c];
+        for (int q = 0; q < ISO_MAXT * 3; ++q) e8[c * ISO_MAXT * 3 + q] = edges[c * SEM_MC_MAXT * 3 + q];
+    }
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_s, s_all, sizeof(float) * (SEM_MAX_ORDER + 1) * MP));
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_ntri, n8, sizeof n8));
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_edge, e8, sizeof e8));
+    return SEM_OK;
+}
+
+// edge e -> (lower corner, upper corner), lexicographic numbering
+// (0,1)(0,2)(0,4)(1,3)(1,5)(2,3)(2,6)(3,7)(4,5)(4,6)(5,7)(6,7), packed one nibble per edge
+__device__ __forceinline__ void edge_ends(int e, int &lo, int &hi)
+{
+    lo = (int)((0x654432211000ull >> (4 * e)) & 15u);
+    hi = (int)((0x776576353421ull >> (4 * e)) & 15u);
+}
+
+template <int NP>
+__device__ __forceinline__ void load_element(const float *__restrict__ fe, float *__restrict__ sf, int lane, float iso,
+                                             bool &any_in, bool &any_out)
+{
+    constexpr int NP3 = NP * NP * NP;
+    bool ai = false, ao = false;
+    if constexpr (NP3 % 128 == 0) {
+        const float4 *f4 = reinterpret_cast<const float4 *>(fe);
+        float4 *s4 = reinterpret_cast<float4 *>(sf);
+#pragma unroll
+        for (int q = 0; q < NP3 / 128; ++q) {
+            float4 v = __ldg(f4 + q * 32 + lane);
+            s4[q * 32 + lane] = v;
+            ai |= (v.x >= iso) | (v.y >= iso) | (v.z >= iso) | (v.w >= iso);
+            ao |= !(v.x >= iso) | !(v.y >= iso) | !(v.z >= iso) | !(v.w >= iso);
+        }
+    } else {
+        for (int idx = lane; idx < NP3; idx += 32) {
+            float v = __ldg(fe + idx);
+            sf[idx] = v;
+            ai |= v >= iso;
+            ao |= !(v >= iso);
+        }
+    }
+    any_in = __any_sync(0xffffffffu, ai);
+    any_out = __any_sync(0xffffffffu, ao);
+}
+
+template <int NP>
+__device__ __forceinline__ int cell_case(const float *__restrict__ sf, int c, float iso, int &i, int &j, int &k)
+{
+    constexpr int N = NP - 1;
+    i = c % N;
+    j = (c / N) % N;
+    k = c / (N * N);
+    const int b = (k * NP + j) * NP + i;
+    int cs = 0;
+    cs |= (sf[b] >= iso) << 0;
+    cs |= (sf[b + 1] >= iso) << 1;
+    cs |= (sf[b + NP] >= iso) << 2;
+    cs |= (sf[b + NP + 1] >= iso) << 3;
+    cs |= (sf[b + NP * NP] >= iso) << 4;
+    cs |= (sf[b + NP * NP + 1] >= iso) << 5;
+    cs |= (sf[b + NP * NP + NP] >= iso) << 6;
+    cs |= (sf[b + NP * NP + NP + 1] >= iso) << 7;
+    return cs;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * IsoW<NP>::V) k_iso_count(const float *__restrict__ f, float iso, int64_t E,
+                                                             int32_t *__restrict__ elem_cnt, uint8_t *__restrict__ cases)
+{
+    constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N;
+    __shared__ __align__(16) float s_f[IsoW<NP>::V][NP3];
+    __shared__ uint8_t s_nt[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * IsoW<NP>::V + w;
+    if (e >= E) return;
+    float *sf = s_f[w];
+    bool any_in, any_out;
+    load_element<NP>(f + e * NP3, sf, lane, iso, any_in, any_out);
+    if (!(any_in && any_out)) {
+        if (lane == 0) elem_cnt[e] = 0;
+        if (cases) {
+            const uint8_t v = any_in ? 255 : 0;
+            for (int c = lane; c < N3; c += 32) cases[e * N3 + c] = v;
+        }
+        return;
+    }
+    __syncwarp();
+    int cnt = 0;
+    for (int c = lane; c < N3; c += 32) {
+        int i, j, k;
+        const int cs = cell_case<NP>(sf, c, iso, i, j, k);
+        cnt += s_nt[cs];
+        if (cases) cases[e * N3 + c] = (uint8_t)cs;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, d);
+    if (lane == 0) elem_cnt[e] = cnt;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * IsoW<NP>::V) k_iso_emit(const float *__restrict__ f, float iso, int64_t E,
+                                                            const int64_t *__restrict__ offs,
+                                                            const float4 *__restrict__ blo,
+                                                            const float4 *__restrict__ bhi, float *__restrict__ tris,
+                                                            int32_t *__restrict__ tri_elem, int64_t cap)
+{
+    constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N;
+    __shared__ __align__(16) float s_f[IsoW<NP>::V][NP3];
+    __shared__ uint8_t s_nt[256];
+    __shared__ int8_t s_ed[256 * ISO_MAXT * 3];
+    __shared__ float s_s[NP];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
+    for (int t = threadIdx.x; t < 256 * ISO_MAXT * 3; t += blockDim.x) s_ed[t] = c_edge[t];
+    if (threadIdx.x < NP) s_s[threadIdx.x] = c_s[(NP - 1) * MP + threadIdx.x];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * IsoW<NP>::V + w;
+    if (e >= E) return;
+    int64_t base = offs[e];
+    if (offs[e + 1] == base) return;
+    float *sf = s_f[w];
+    bool ai, ao;
+    load_element<NP>(f + e * NP3, sf, lane, iso, ai, ao);
+    __syncwarp();
+    const float4 L = blo[e], H = bhi[e];
+    for (int c0 = 0; c0 < N3; c0 += 32) {
+        const int c = c0 + lane;
+        int cs = 0, nt = 0, i = 0, j = 0, k = 0;
+        if (c < N3) {
+            cs = cell_case<NP>(sf, c, iso, i, j, k);
+            nt = s_nt[cs];
+        }
+        int incl = nt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int64_t o = base + (incl - nt);
+        for (int q = 0; q < nt; ++q, ++o) {
+            float p[9];
+#pragma unroll
+            for (int sv = 0; sv < 3; ++sv) {
+                int lo, hi;
+                edge_ends(s_ed[(cs * ISO_MAXT + q) * 3 + sv], lo, hi);
+                const int ia = i + (lo & 1), ja = j + ((lo >> 1) & 1), ka = k + ((lo >> 2) & 1);
+                const int ib = i + (hi & 1), jb = j + ((hi >> 1) & 1), kb = k + ((hi >> 2) & 1);
+                const float fa = sf[(ka * NP + ja) * NP + ia], fb = sf[(kb * NP + jb) * NP + ib];
+                const float t = (iso - fa) / (fb - fa);
+                const float xa = fmaf(s_s[ia], H.x, (1.f - s_s[ia]) * L.x), xb = fmaf(s_s[ib], H.x, (1.f - s_s[ib]) * L.x);
+                const float ya = fmaf(s_s[ja], H.y, (1.f - s_s[ja]) * L.y), yb = fmaf(s_s[jb], H.y, (1.f - s_s[jb]) * L.y);
+                const float za = fmaf(s_s[ka], H.z, (1.f - s_s[ka]) * L.z), zb = fmaf(s_s[kb], H.z, (1.f - s_s[kb]) * L.z);
+                p[sv * 3 + 0] = fmaf(t, xb - xa, xa);
+                p[sv * 3 + 1] = fmaf(t, yb - ya, ya);
+                p[sv * 3 + 2] = fmaf(t, zb - za, za);
+            }
+            if (o < cap) {
+                float *dst = tris + o * 9;
+#pragma unroll
+                for (int r = 0; r < 9; ++r) dst[r] = p[r];
+                if (tri_elem) tri_elem[o] = (int32_t)e;
+            }
+        }
+        base += total;
+    }
+}
+
+template <int NP>
+static sem_status iso_run_np(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
+                             int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    const int64_t E = m->E;
+    const size_t cnt_bytes = ((sizeof(int32_t) * E + 255) / 256) * 256;
+    const size_t off_bytes = ((sizeof(int64_t) * (E + 1) + 255) / 256) * 256;
+    const size_t tmp_bytes = scan_tmp_bytes(E);
+    void *scr;
+    SEM_TRY(sem_scratch(ctx, SCR_ISO, cnt_bytes + off_bytes + tmp_bytes, &scr));
+    int32_t *cnt = reinterpret_cast<int32_t *>(scr);
+    int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
+    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes;
+    constexpr int WV = IsoW<NP>::V;
+    const unsigned grid = (unsigned)((E + WV - 1) / WV);
+    k_iso_count<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, cnt, cases);
+    SEM_CU(ctx, cudaGetLastError());
+    SEM_TRY(scan_i32_i64(ctx, cnt, offs, E, tmp));
+    SEM_CU(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + E, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t total = ctx->h_pinned[0];
+    *ntri_out = total;
+    if (total > cap)
+        return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface: %lld triangles exceed capacity %lld", (long long)total,
+                        (long long)cap);
+    if (total == 0) return SEM_OK;
+    k_iso_emit<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, offs, m->lo, m->hi, tris, tri_elem, cap);
+    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit launch");
+}
+
+sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
+                   int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    switch (m->N + 1) {
+#define SEM_CASE(NPV) \
+    case NPV: return iso_run_np<NPV>(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
+}

@@ -1,0 +1,325 @@
+// sem_qcrit.cu -- spectral derivative and Q-criterion kernels (FP32, the plain path).
+//
+// Per element of order N the three reference derivatives are tensor-product contractions
+// with the GLL collocation derivative matrix D (Canuto et al., Spectral Methods, Sec. 2.3):
+//   u_r[k][j][i] = sum_m D[i][m] u[k][j][m],  u_s = sum_m D[j][m] u[k][m][i],
+//   u_t = sum_m D[k][m] u[m][j][i]
+// and on an affine box du/dx = (2/hx) u_r, du/dy = (2/hy) u_s, du/dz = (2/hz) u_t.
+// Q = -1/2 sum_ij J_ij J_ji with J_ij = du_i/dx_j (Hunt, Wray & Moin 1988).
+//
+// Design (GB300): the kernel is HBM-bound (16 B of traffic per node for Q, 144 FLOP per node:
+// about 9 FLOP/B, at the FP32 FFMA ridge), so it streams elements through shared memory with
+// the TMA engine (cp.async.bulk, double-buffered, mbarrier completion) in a persistent grid,
+// keeps D in constant memory (FFMA operands straight from the constant bank), and gives each
+// thread one r-line (k, j) of (N+1) nodes of one element: it reads its own row for u_r, its
+// slab k for u_s and its column j for u_t, forms all 9 gradient entries of its (N+1) nodes in
+// registers and writes Q (or the 3 derivatives) with 16-byte stores.  For N = 7 the reads
+// are staggered so that no shared-memory access is bank-conflicted.  Tensor cores are not
+// used here: the contractions have K = N+1 = 8, and the element data would have to be
+// transposed between the three directions, costing more shared-memory traffic than the
+// FFMA work they would replace.
+#include <cuda_runtime.h>
+
+#include "sem_internal.cuh"
+
+#define MP (SEM_MAX_ORDER + 1)
+
+__constant__ float c_D[(SEM_MAX_ORDER + 1) * MP * MP];  // [N][i][m], FP32
+
+sem_status qcrit_upload_tables(sem_ctx *ctx, const float *D_all, const float *s_all)
+{
+    (void)s_all;
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_D, D_all, sizeof(float) * (SEM_MAX_ORDER + 1) * MP * MP));
+    return SEM_OK;
+}
+
+template <int NP>
+__device__ __forceinline__ float Dc(int i, int m)
+{
+    return c_D[((NP - 1) * MP + i) * MP + m];
+}
+
+// Derivatives of one component along the three directions for the r-line (k, j) of one
+// element held in shared memory U[k][j][i].  Dj[m] = D[j][(m + k) % NP] when NP == 8 (the
+// slab reads are rotated by k), else D[j][m]; Dk[m] = D[k][m].
+template <int NP>
+__device__ __forceinline__ void line_derivs(const float *__restrict__ U, int k, int j, const float (&Dj)[NP],
+                                            const float (&Dk)[NP], float (&dr)[NP], float (&ds)[NP],
+                                            float (&dt)[NP])
+{
+    if constexpr (NP == 8) {
+        const int sw = (j >> 2) & 1;  // chunk stagger: j = 0..3 and 4..7 hit different banks
+        // --- r: own row, chunk order staggered
+        float row[8];
+        {
+            const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
+            float4 A = rp[sw], B = rp[sw ^ 1];
+            float4 lo = sw ? B : A, hi = sw ? A : B;
+            row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
+            row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < 8; ++m) a = fmaf(Dc<8>(i, m), row[m], a);
+            dr[i] = a;
+        }
+        // --- s: slab k, row order rotated by k (Dj pre-rotated to match)
+        {
+            float acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+#pragma unroll
+            for (int mm = 0; mm < 8; ++mm) {
+                const int m = (mm + k) & 7;
+                const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
+                float4 A = sp[0], B = sp[1];
+                const float d = Dj[mm];
+                acc[0] = fmaf(d, A.x, acc[0]); acc[1] = fmaf(d, A.y, acc[1]);
+                acc[2] = fmaf(d, A.z, acc[2]); acc[3] = fmaf(d, A.w, acc[3]);
+                acc[4] = fmaf(d, B.x, acc[4]); acc[5] = fmaf(d, B.y, acc[5]);
+                acc[6] = fmaf(d, B.z, acc[6]); acc[7] = fmaf(d, B.w, acc[7]);
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ds[i] = acc[i];
+        }
+        // --- t: column j, chunk order staggered; swap the two accumulator halves at the end
+        {
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
+                float4 A = tp[sw], B = tp[sw ^ 1];
+                const float d = Dk[m];
+                a0[0] = fmaf(d, A.x, a0[0]); a0[1] = fmaf(d, A.y, a0[1]);
+                a0[2] = fmaf(d, A.z, a0[2]); a0[3] = fmaf(d, A.w, a0[3]);
+                a1[0] = fmaf(d, B.x, a1[0]); a1[1] = fmaf(d, B.y, a1[1]);
+                a1[2] = fmaf(d, B.z, a1[2]); a1[3] = fmaf(d, B.w, a1[3]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                dt[i] = sw ? a1[i] : a0[i];
+                dt[i + 4] = sw ? a0[i] : a1[i];
+            }
+        }
+    } else {
+        float row[NP];
+#pragma unroll
+        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            float a = 0.f;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
+            dr[i] = a;
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            ds[i] = 0.f;
+            dt[i] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i], ds[i]);
+                dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i], dt[i]);
+            }
+        }
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void store_line(float *__restrict__ dst, const float (&v)[NP])
+{
+    if constexpr (NP % 4 == 0) {
+        float4 *p = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) dst[i] = v[i];
+    }
+}
+
+template <int NP>
+struct QCfg {
+    static constexpr int L = NP * NP;
+    static constexpr int NP3 = NP * NP * NP;
+    static constexpr bool BULK = (NP % 2) == 0;  // element byte size is a multiple of 16
+    static constexpr int EPB_RAW = (256 / L) > 0 ? (256 / L) : 1;
+    static constexpr int EPB = EPB_RAW;
+    static constexpr int NT = ((EPB * L + 31) / 32) * 32;
+    static constexpr int NSTAGE = BULK ? 2 : 1;
+};
+
+// NC = 3: Q of (f0, f1, f2) -> out0.   NC = 1: gradient of f0 -> (out0, out1, out2).
+template <int NP, int NC>
+__global__ void __launch_bounds__(QCfg<NP>::NT) k_sem_grad(const float *__restrict__ f0, const float *__restrict__ f1,
+                                                           const float *__restrict__ f2, float *__restrict__ out0,
+                                                           float *__restrict__ out1, float *__restrict__ out2,
+                                                           const float4 *__restrict__ gfac, int64_t E, int *err)
+{
+    using C = QCfg<NP>;
+    constexpr int NP3 = C::NP3, L = C::L, EPB = C::EPB;
+    constexpr int STAGE = NC * EPB * NP3;
+    constexpr uint32_t BYTES = EPB * NP3 * 4;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const bool active = tid < EPB * L;
+    const int el = tid / L, line = tid % L, j = line % NP, k = line / NP;
+    const int64_t ngroups = (E + EPB - 1) / EPB;
+    const int64_t nfull = C::BULK ? E / EPB : 0;
+    const float *src[3] = {f0, f1, f2};
+
+    float Dj[NP], Dk[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int mj = (NP == 8) ? ((m + k) & 7) : m;
+        Dj[m] = c_D[((NP - 1) * MP + (active ? j : 0)) * MP + mj];
+        Dk[m] = c_D[((NP - 1) * MP + (active ? k : 0)) * MP + m];
+    }
+
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t grp, int s) {
+        float *dst = smem + s * STAGE;
+        mbar_arrive_expect_tx(&bar[s], NC * BYTES);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) bulk_g2s(dst + c * EPB * NP3, src[c] + grp * EPB * NP3, BYTES, &bar[s]);
+    };
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    if (C::BULK && tid == 0) {
+        if ((int64_t)blockIdx.x < nfull) issue(blockIdx.x, 0);
+        if ((int64_t)blockIdx.x + gridDim.x < nfull) issue(blockIdx.x + gridDim.x, 1);
+    }
+    if (C::BULK) {
+        pending[0] = (int64_t)blockIdx.x < nfull;
+        pending[1] = (int64_t)blockIdx.x + gridDim.x < nfull;
+    }
+
+    int it = 0;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+        const int s = C::BULK ? (it & 1) : 0;
+        float *st = smem + s * STAGE;
+        if (C::BULK && grp < nfull) {
+            if (!mbar_wait_bounded(&bar[s], phase[s], err)) s_abort = 1;
+            phase[s] ^= 1u;
+            pending[s] = false;
+        } else {
+            const int64_t ne = E - grp * EPB < EPB ? E - grp * EPB : EPB;
+            for (int c = 0; c < NC; ++c)
+                for (int64_t idx = tid; idx < ne * NP3; idx += blockDim.x) st[c * EPB * NP3 + idx] = src[c][grp * EPB * NP3 + idx];
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const int64_t e = grp * EPB + el;
+        if (active && e < E) {
+            const float4 g = gfac[e];
+            float dr[NP], ds[NP], dt[NP];
+            const int64_t off = e * NP3 + (k * NP + j) * NP;
+            if constexpr (NC == 1) {
+                line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    dr[i] *= g.x;
+                    ds[i] *= g.y;
+                    dt[i] *= g.z;
+                }
+                store_line<NP>(out0 + off, dr);
+                store_line<NP>(out1 + off, ds);
+                store_line<NP>(out2 + off, dt);
+            } else {
+                float q[NP], J13[NP], J23[NP];
+                // u: J11 = gx u_r, J12 = gy u_s, J13 = gz u_t
+                line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+                float J11[NP], J12[NP];
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    J11[i] = g.x * dr[i];
+                    J12[i] = g.y * ds[i];
+                    J13[i] = g.z * dt[i];
+                }
+                // v: J21, J22, J23
+                line_derivs<NP>(st + EPB * NP3 + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const float J21 = g.x * dr[i], J22 = g.y * ds[i];
+                    J23[i] = g.z * dt[i];
+                    q[i] = fmaf(J11[i], J11[i], fmaf(J22, J22, 2.f * J12[i] * J21));
+                }
+                // w: J31, J32, J33
+                line_derivs<NP>(st + 2 * EPB * NP3 + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const float J31 = g.x * dr[i], J32 = g.y * ds[i], J33 = g.z * dt[i];
+                    q[i] = -0.5f * fmaf(J33, J33, fmaf(2.f * J13[i], J31, fmaf(2.f * J23[i], J32, q[i])));
+                }
+                store_line<NP>(out0 + off, q);
+            }
+        }
+        __syncthreads();
+        if (C::BULK && tid == 0 && grp + 2 * (int64_t)gridDim.x < nfull) {
+            issue(grp + 2 * gridDim.x, s);
+            pending[s] = true;
+        }
+    }
+    // on an abort, wait (bounded) for copies still in flight into this CTA's shared memory
+    if (C::BULK && s_abort && tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait_bounded(&bar[s], phase[s], nullptr);
+    }
+}
+
+template <int NP, int NC>
+static sem_status launch_grad(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
+                              float *o0, float *o1, float *o2)
+{
+    using C = QCfg<NP>;
+    const size_t smem = sizeof(float) * (size_t)C::NSTAGE * NC * C::EPB * C::NP3;
+    auto kern = k_sem_grad<NP, NC>;
+    SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ngroups = (m->E + C::EPB - 1) / C::EPB;
+    int64_t grid = (int64_t)ctx->sm_count * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(f0, f1, f2, o0, o1, o2, m->g, m->E, ctx->d_flag);
+    return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
+}
+
+template <int NC>
+static sem_status dispatch(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
+                           float *o0, float *o1, float *o2)
+{
+    switch (m->N + 1) {
+#define SEM_CASE(NPV) \
+    case NPV: return launch_grad<NPV, NC>(ctx, m, f0, f1, f2, o0, o1, o2);
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
+}
+
+sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
+{
+    return dispatch<3>(ctx, m, u, v, w, Q, nullptr, nullptr);
+}
+
+sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz)
+{
+    return dispatch<1>(ctx, m, u, nullptr, nullptr, dx, dy, dz);
+}

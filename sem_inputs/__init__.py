@@ -361,3 +361,21 @@ def element_slice(w: Workload, e0: int, e1: int) -> dict:
     """Contiguous element range [e0, e1) of a workload: node coordinates and fields."""
     xyz = w.mesh.xyz(w.fields.device)[:, e0:e1]
     return dict(xyz=xyz, fields=w.fields[:, e0:e1], N=w.mesh.N)
+
+
+def random_nodal(mesh: BoxMesh, ncomp: int = 1, seed: int = 0, scale: float = 1.0) -> torch.Tensor:
+    """(ncomp, E, NP^3) float64 i.i.d. N(0, scale^2) per element node (not continuous across
+    elements; the derivative path is element-local)."""
+    rng = np.random.default_rng(seed)
+    return torch.as_tensor(rng.normal(0.0, scale, size=(ncomp, mesh.E, mesh.NP ** 3)))
+
+
+def stretched_box(nel, N: int, seed: int = 0) -> BoxMesh:
+    """Box mesh with seeded uneven element widths along each axis."""
+    rng = np.random.default_rng(seed)
+    faces = []
+    for d, n in enumerate(nel):
+        w = rng.uniform(0.5, 1.5, size=n)
+        f = np.concatenate([[0.0], np.cumsum(w)]) - 0.3 * d
+        faces.append(f)
+    return BoxMesh(N, faces[0], faces[1], faces[2])

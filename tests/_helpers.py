@@ -1,0 +1,57 @@
+"""Shared test helpers: FP32 error bounds for the derivative / Q kernels and comparisons.
+
+The bounds follow from the arithmetic: an FP32 dot product of n terms (fused multiply-adds)
+has error at most about n * 2^-24 * sum |D_im u_m|; rounding D to FP32 adds 2^-24 * sum |D_im
+u_m|; scaling by the FP32 factor 2/h adds 2 * 2^-24 |result|.  A safety factor of 2 covers
+the remaining second-order terms.  Q = -1/2 sum J_ij J_ji then inherits
+|dQ| <= sum_ij |J_ij| dJ_ji + 8 * 2^-24 sum |J_ij J_ji|.
+"""
+import numpy as np
+import torch
+
+EPS32 = 2.0 ** -24
+
+
+def dev32(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).cuda().contiguous()
+
+
+def host64(t):
+    return t.detach().cpu().double().numpy()
+
+
+def ref_abs_contractions(D, u, NP):
+    """sum_m |D[i][m]| |u| along r, s, t for u (E, NP^3) -> three (E, NP^3) arrays."""
+    A = np.abs(D)
+    U = np.abs(u).reshape(-1, NP, NP, NP)  # [e][k][j][i]
+    br = np.einsum("im,ekjm->ekji", A, U)
+    bs = np.einsum("jm,ekmi->ekji", A, U)
+    bt = np.einsum("km,emji->ekji", A, U)
+    return [b.reshape(u.shape) for b in (br, bs, bt)]
+
+
+def grad_bounds(D, u, g, NP, ref):
+    """Per-node bounds on |grad_gpu - grad_oracle| for one FP32 field u (E, NP^3); g (E, 3) the
+    factors 2/h; ref (3, E, NP^3) the oracle gradient."""
+    bs = ref_abs_contractions(D, u, NP)
+    return np.stack([2.0 * ((NP + 1) * np.abs(g[:, a:a + 1]) * bs[a] + 2.0 * np.abs(ref[a])) * EPS32
+                     for a in range(3)])
+
+
+def q_bound(J, dJ):
+    """J, dJ: (3, 3, ...) gradient and its per-entry bound -> per-node bound on Q."""
+    b = np.zeros(J.shape[2:])
+    s = np.zeros(J.shape[2:])
+    for i in range(3):
+        for j in range(3):
+            b += np.abs(J[i, j]) * dJ[j, i]
+            s += np.abs(J[i, j] * J[j, i])
+    return b + 8.0 * EPS32 * s + 1e-30
+
+
+def box_factors(xyz):
+    """2/h per element and axis from node coordinates (3, E, NP^3)."""
+    NP = round(xyz.shape[2] ** (1 / 3))
+    x0 = xyz[:, :, 0]
+    x1 = np.stack([xyz[0, :, NP - 1], xyz[1, :, NP * (NP - 1)], xyz[2, :, NP * NP * (NP - 1)]])
+    return (2.0 / (x1 - x0)).T

@@ -1,0 +1,126 @@
+"""GPU parity of sem_render against the oracle's rasteriser (through the C ABI).
+
+Same FP32 triangles on both sides.  Bar: every channel within 1/255 on at least 99.9% of
+pixels; depth within 1e-5 where both sides cover the pixel; exact coverage on cases whose
+projected coordinates are exact in FP32.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import sem_inputs as si
+from _helpers import dev32, host64
+
+pytestmark = pytest.mark.gpu
+
+
+def _render(S, sess, tris32, seg, rgb, cam):
+    W, H = cam["W"], cam["H"]
+    rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+    depth = torch.zeros(H * W, device="cuda")
+    n = tris32.numel() // 9
+    S.sem_render(sess.ctx, tris32 if n else None, n, seg, rgb, cam, W, H, rgba, depth)
+    torch.cuda.synchronize()
+    return rgba.cpu().numpy().reshape(H, W, 4), depth.cpu().numpy().reshape(H, W)
+
+
+def _compare_images(img, dep, ref_img, ref_dep, min_frac=0.999):
+    close = (np.abs(img.astype(int) - ref_img.astype(int)) <= 1).all(axis=2)
+    frac = close.mean()
+    assert frac >= min_frac, frac
+    both = (img[..., 3] > 0) & (ref_img[..., 3] > 0)
+    if both.any():
+        assert np.abs(dep[both] - ref_dep[both]).max() <= 1e-5
+    return frac
+
+
+def test_random_triangles_perspective(gpu, sess, orc):
+    rng = np.random.default_rng(1)
+    cam = si.camera(False, (3, 2, 9.0), (0, 0, 0), (0, 1, 0), 320, 200, fovy_deg=50.0, znear=1.0, zfar=20.0)
+    c = rng.uniform(-3, 3, size=(3000, 1, 3))
+    tris = c + rng.normal(0, 0.3, size=(3000, 3, 3))
+    t32 = dev32(tris.reshape(-1))
+    seg, rgb = [1000, 1500, 500], [[0.9, 0.3, 0.2], [0.2, 0.6, 0.9], [0.95, 0.95, 0.95]]
+    img, dep = _render(gpu, sess, t32, seg, rgb, cam)
+    ref_img, ref_dep, _ = orc.render(host64(t32).reshape(-1, 3, 3), seg, rgb, cam)
+    _compare_images(img, dep, ref_img, ref_dep)
+
+
+def test_random_triangles_ortho_large_and_clipped(gpu, sess, orc):
+    rng = np.random.default_rng(2)
+    cam = si.camera(True, (0, 0, 10.0), (0, 0, 0), (0, 1, 0), 257, 131, half_h=4.0, znear=2.0, zfar=18.0)
+    tris = rng.uniform(-9, 9, size=(400, 3, 3))  # large, partly off-screen, some crossing the clip range
+    t32 = dev32(tris.reshape(-1))
+    img, dep = _render(gpu, sess, t32, [400], None, cam)
+    pal = [[0.90, 0.35, 0.25]]
+    ref_img, ref_dep, _ = orc.render(host64(t32).reshape(-1, 3, 3), [400], pal, cam)
+    _compare_images(img, dep, ref_img, ref_dep)
+
+
+def test_exact_fan_coverage(gpu, sess, orc):
+    # pixel-centre-aligned square split into 4 triangles: every covered pixel exactly once
+    W = H = 16
+    cam = si.camera(True, (8, 8, 10.0), (8, 8, 0), (0, 1, 0), W, H, half_h=8.0, znear=1.0, zfar=19.0)
+    corners = [(1.5, 1.5, 0), (13.5, 1.5, 0), (13.5, 13.5, 0), (1.5, 13.5, 0)]
+    c = (7.5, 7.5, 0)
+    tris = np.array([[corners[i], corners[(i + 1) % 4], c] for i in range(4)], float)
+    cnt = np.zeros((H, W), int)
+    for i in range(4):
+        img, _ = _render(gpu, sess, dev32(tris[i].reshape(-1)), [1], [[1, 1, 1]], cam)
+        _, _, win = orc.render(tris[i:i + 1], [1], [[1, 1, 1]], cam)
+        np.testing.assert_array_equal(img[..., 3] > 0, win >= 0)
+        cnt += img[..., 3] > 0
+    assert cnt.max() == 1
+    assert cnt.sum() == 12 * 12
+
+
+def test_tie_break_lower_index_and_determinism(gpu, sess, orc):
+    cam = si.camera(True, (0, 0, 10.0), (0, 0, 0), (0, 1, 0), 64, 64, half_h=2.0, znear=1.0, zfar=19.0)
+    t = np.array([[(-1.5, -1.5, 0.5), (1.7, -1.1, 0.5), (0.2, 1.8, 0.5)]])
+    tris = np.concatenate([t, t])
+    img, _ = _render(gpu, sess, dev32(tris.reshape(-1)), [1, 1], [[1, 0, 0], [0, 1, 0]], cam)
+    cov = img[..., 3] > 0
+    assert cov.any() and (img[cov][:, 1] == 0).all()  # the first triangle (red) wins every tie
+    rng = np.random.default_rng(4)
+    many = dev32(rng.uniform(-2, 2, size=(5000 * 9,)))
+    a = _render(gpu, sess, many, [5000], None, cam)
+    b = _render(gpu, sess, many, [5000], None, cam)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_empty_scene(gpu, sess):
+    cam = si.camera(True, (0, 0, 10.0), (0, 0, 0), (0, 1, 0), 40, 30, half_h=2.0, znear=1.0, zfar=19.0)
+    img, dep = _render(gpu, sess, torch.zeros(0, device="cuda"), [0], None, cam)
+    assert (img == 0).all() and (dep == 1.0).all()
+
+
+def test_taylor_green_frame(gpu, sess, orc):
+    """The 8^3, N=7 workload's Q-isosurface (GPU triangles) rendered 256x256 by both sides."""
+    w = si.tgv_box()
+    xyz = w.mesh.xyz().numpy()
+    m = sess.mesh(7, xyz)
+    u, v, ww = (dev32(w.fields[c].numpy()) for c in range(3))
+    Q = torch.empty_like(u)
+    gpu.sem_qcriterion(sess.ctx, m, u, v, ww, Q)
+    iso = float(np.float32(0.1 * gpu.sem_field_max(sess.ctx, Q)))
+    n = gpu.sem_isosurface(sess.ctx, m, Q, iso, None, cap=0)
+    tris = torch.empty(n * 9, device="cuda")
+    gpu.sem_isosurface(sess.ctx, m, Q, iso, tris)
+    img, dep = _render(gpu, sess, tris, [n], None, w.camera)
+    ref_img, ref_dep, _ = orc.render(host64(tris).reshape(-1, 3, 3), [n], [[0.90, 0.35, 0.25]], w.camera)
+    _compare_images(img, dep, ref_img, ref_dep)
+    assert (img[..., 3] > 0).mean() > 0.2
+
+
+def test_bad_camera_and_segments(gpu, sess):
+    cam = si.camera(True, (0, 0, 10.0), (0, 0, 0), (0, 0, 1), 8, 8, half_h=2.0, znear=1.0, zfar=19.0)
+    rgba = torch.zeros(8 * 8 * 4, dtype=torch.uint8, device="cuda")
+    t = torch.zeros(9, device="cuda")
+    with pytest.raises(gpu.SemError):  # up parallel to the view direction
+        gpu.sem_render(sess.ctx, t, 1, [1], None, cam, 8, 8, rgba)
+    cam["up"] = [0, 1, 0]
+    with pytest.raises(gpu.SemError):  # segments do not sum to ntri
+        gpu.sem_render(sess.ctx, t, 1, [2], None, cam, 8, 8, rgba)
