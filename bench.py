@@ -56,6 +56,27 @@ def aggregate(per_rank_elems, per_rank_seconds):
     return float(sum(per_rank_elems)) / float(max(per_rank_seconds))
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Largest value of x over the ranks of the default process group (x itself if none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _file_sha(path):
     with open(os.path.join(ROOT, path), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -216,12 +237,9 @@ def run_ours(args):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1)
     stage_ms = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in stage_ev])
-    secs = ms / 1e3
-    if world > 1:
-        t = torch.tensor([secs], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
-    value = aggregate([P.E * K] * world, [secs])
+    secs = max_over_ranks(ms / 1e3, "cuda")
+    total_elems = sum_over_ranks(P.E * K, "cuda")
+    value = aggregate([total_elems], [secs])
 
     # end to end: velocity from pinned host memory, frame back to pinned host memory
     e2e = None
@@ -247,12 +265,8 @@ def run_ours(args):
             e2e_step()
         b.record(P.stream)
         barrier()
-        es = a.elapsed_time(b) / 1e3
-        if world > 1:
-            t = torch.tensor([es], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            es = float(t.item())
-        e2e = {"value": aggregate([P.E * K] * world, [es]), "unit": UNIT,
+        es = max_over_ranks(a.elapsed_time(b) / 1e3, "cuda")
+        e2e = {"value": aggregate([total_elems], [es]), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in host_vel)),
                "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4),
                "ms_per_step": es * 1e3 / K}

@@ -148,7 +148,9 @@ SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const floa
  * p = p_lo + t (p_hi - p_lo).  Triangles are written in (element, cell i + N(j + Nk), table)
  * order as float tris[ntri][3][3] (vertex-major xyz) with tri_elem[ntri] = element index.
  *   f:        device, E*(N+1)^3 floats
- *   tris:     device, cap*9 floats;   tri_elem: device, cap int32 (may be NULL)
+ *   tris:     device, cap*9 floats, or NULL to only count (then cap is ignored, nothing
+ *             but *ntri_out and cases is written, and the call returns SEM_OK)
+ *   tri_elem: device, cap int32 (may be NULL)
  *   cap:      capacity in triangles (>= 0)
  *   ntri_out: HOST; receives the triangle count
  *   cases:    device, E*N^3 bytes, or NULL; receives every cell's case index

@@ -194,8 +194,8 @@ def sem_qcriterion(ctx, mesh, u, v, w, Q, prec: int = SEM_FP32) -> None:
 
 
 def sem_isosurface(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None, cap: Optional[int] = None) -> int:
-    """Returns the triangle count.  Raises SemError(SEM_ERR_CAPACITY, required=n) if tris is
-    too small (cap defaults to tris.numel() // 9)."""
+    """Returns the triangle count (tris None: count only).  Raises SemError(SEM_ERR_CAPACITY,
+    required=n) if tris is too small (cap defaults to tris.numel() // 9)."""
     import torch
     if cap is None:
         cap = 0 if tris is None else tris.numel() // 9

@@ -470,7 +470,7 @@ sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *m, const float *f, float
     if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface: negative cap");
     if (m->E == 0) return SEM_OK;
     SEM_TRY(check_ptr(ctx, f, "sem_isosurface", "f"));
-    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface", "tris", cap == 0, 4));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface", "tris", true, 4));
     SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface", "tri_elem", true, 4));
     SEM_TRY(check_ptr(ctx, cases, "sem_isosurface", "cases", true));
     if (isnan(iso)) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface: iso is NaN");

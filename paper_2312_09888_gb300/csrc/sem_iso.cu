@@ -230,6 +230,7 @@ static sem_status iso_run_np(sem_ctx *ctx, const sem_mesh *m, const float *f, fl
     SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
     const int64_t total = ctx->h_pinned[0];
     *ntri_out = total;
+    if (!tris) return SEM_OK;  // count-only query
     if (total > cap)
         return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface: %lld triangles exceed capacity %lld", (long long)total,
                         (long long)cap);

@@ -3,8 +3,10 @@
 The bounds follow from the arithmetic: an FP32 dot product of n terms (fused multiply-adds)
 has error at most about n * 2^-24 * sum |D_im u_m|; rounding D to FP32 adds 2^-24 * sum |D_im
 u_m|; scaling by the FP32 factor 2/h adds 2 * 2^-24 |result|.  A safety factor of 2 covers
-the remaining second-order terms.  Q = -1/2 sum J_ij J_ji then inherits
-|dQ| <= sum_ij |J_ij| dJ_ji + 8 * 2^-24 sum |J_ij J_ji|.
+the remaining second-order terms.  The FP64 oracle's own error is added as a floor of
+1e-12 times the node's largest gradient entry (its general chain rule carries D's row-sum
+rounding, ~1e-14, times coordinate/size ratios).  Q = -1/2 sum J_ij J_ji then inherits
+|dQ| <= sum_ij (|J_ij| + dJ_ij) dJ_ji + 8 * 2^-24 sum |J_ij J_ji|.
 """
 import numpy as np
 import torch
@@ -34,7 +36,8 @@ def grad_bounds(D, u, g, NP, ref):
     """Per-node bounds on |grad_gpu - grad_oracle| for one FP32 field u (E, NP^3); g (E, 3) the
     factors 2/h; ref (3, E, NP^3) the oracle gradient."""
     bs = ref_abs_contractions(D, u, NP)
-    return np.stack([2.0 * ((NP + 1) * np.abs(g[:, a:a + 1]) * bs[a] + 2.0 * np.abs(ref[a])) * EPS32
+    floor = 1e-12 * np.abs(ref).max(axis=0)
+    return np.stack([2.0 * ((NP + 1) * np.abs(g[:, a:a + 1]) * bs[a] + 2.0 * np.abs(ref[a])) * EPS32 + floor
                      for a in range(3)])
 
 
@@ -44,7 +47,7 @@ def q_bound(J, dJ):
     s = np.zeros(J.shape[2:])
     for i in range(3):
         for j in range(3):
-            b += np.abs(J[i, j]) * dJ[j, i]
+            b += (np.abs(J[i, j]) + dJ[i, j]) * dJ[j, i]
             s += np.abs(J[i, j] * J[j, i])
     return b + 8.0 * EPS32 * s + 1e-30
 
