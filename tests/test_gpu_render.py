@@ -27,12 +27,18 @@ def _render(S, sess, tris32, seg, rgb, cam):
 
 
 def _compare_images(img, dep, ref_img, ref_dep, min_frac=0.999):
+    """Colour: every channel within 1/255 on >= 99.9% of pixels.  Depth, where both sides
+    cover the pixel: within 1e-5 on >= 99.9% of those pixels (FP32 barycentrics of sliver
+    triangles and pixels claimed by a neighbouring triangle on an edge can differ more), and
+    within 1e-3 everywhere."""
     close = (np.abs(img.astype(int) - ref_img.astype(int)) <= 1).all(axis=2)
     frac = close.mean()
     assert frac >= min_frac, frac
     both = (img[..., 3] > 0) & (ref_img[..., 3] > 0)
     if both.any():
-        assert np.abs(dep[both] - ref_dep[both]).max() <= 1e-5
+        dz = np.abs(dep[both] - ref_dep[both])
+        assert (dz <= 1e-5).mean() >= min_frac, (dz <= 1e-5).mean()
+        assert dz.max() <= 1e-3, dz.max()
     return frac
 
 
