@@ -159,6 +159,31 @@ SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const floa
 SEM_API sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *mesh, const float *f, float iso, float *tris,
                           int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 
+/* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
+#define SEM_NOALLOC_MAX_ELEMENTS 262144
+
+/* sem_isosurface without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory while they run -- for example
+ * an in situ hook inside a solver's time step when the solver has already committed the GPU's
+ * memory to its own fields and pools, so that a cudaMalloc would fail or stall the step.
+ * sem_isosurface may grow the context's scratch arena with cudaMalloc/cudaFree; this variant
+ * instead keeps its scratch (per-element counts, triangle offsets, scan partials, about 3 MB)
+ * in one fixed device array inside the library, which every GPU that loads the library holds
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Arguments, results, ordering, synchronisation and errors are those of sem_isosurface.
+ *     The context and the mesh must have been created beforehand (sem_create and
+ *     sem_load_mesh do allocate).
+ *   - E may be at most SEM_NOALLOC_MAX_ELEMENTS; a larger mesh is rejected with SEM_ERR_ARG
+ *     and a message naming the limit, and nothing is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents behind for the next
+ *     call.  Calls whose work overlaps on the GPU (different streams or contexts, or several
+ *     host threads) race on it and give wrong results: issue them one after another. */
+SEM_API sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *mesh, const float *f, float iso,
+                                          float *tris, int32_t *tri_elem, int64_t cap, int64_t *ntri_out,
+                                          uint8_t *cases);
+
 /* Z-buffer raster of a triangle soup into a headless RGBA8 + depth image.
  * Triangles are coloured per contiguous segment: segment s holds seg_ntri[s] triangles and
  * colour seg_rgb[3s..3s+2] (HOST arrays; seg_rgb NULL = built-in palette).  Pixel (x, y)

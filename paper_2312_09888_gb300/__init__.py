@@ -26,6 +26,7 @@ STATUS_NAMES = ["SEM_OK", "SEM_ERR_ARG", "SEM_ERR_CAPACITY", "SEM_ERR_OOM", "SEM
                 "SEM_ERR_UNSUPPORTED"]
 SEM_FP32, SEM_TF32, SEM_FP16, SEM_BF16, SEM_BF16X2 = range(5)
 SEM_MAX_ORDER = 15
+SEM_NOALLOC_MAX_ELEMENTS = 262144
 SEM_MC_MAXT = 12
 
 _lock = threading.Lock()
@@ -62,6 +63,7 @@ def _declare(L):
     L.sem_derivatives.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_qcriterion.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
+    L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_surface_measures.argtypes = [vp, vp, i64, vp]
     L.sem_field_max.argtypes = [vp, vp, i64, C.POINTER(f32)]
@@ -69,7 +71,7 @@ def _declare(L):
     L.sem_mc_table.restype = i32
     L.sem_gll.argtypes = [i32, vp, vp]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
-                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_render", "sem_surface_measures",
+                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
 
@@ -204,6 +206,23 @@ def sem_isosurface(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None, ca
                                   _dev(tris, "tris", torch.float32, allow_none=True),
                                   _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap), C.byref(n),
                                   _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st, n.value)
+    return n.value
+
+
+def sem_isosurface_noalloc(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None,
+                           cap: Optional[int] = None) -> int:
+    """As sem_isosurface, for callers that may not allocate device memory during the call:
+    the library keeps this call's scratch in a fixed device array (meshes of at most
+    SEM_NOALLOC_MAX_ELEMENTS elements; calls on one device must not overlap)."""
+    import torch
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    n = C.c_int64(0)
+    st = get_lib().sem_isosurface_noalloc(ctx, mesh, _dev(f, "f", torch.float32), C.c_float(iso),
+                                          _dev(tris, "tris", torch.float32, allow_none=True),
+                                          _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap),
+                                          C.byref(n), _dev(cases, "cases", torch.uint8, allow_none=True))
     _check(ctx, st, n.value)
     return n.value
 

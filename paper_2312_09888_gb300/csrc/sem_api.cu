@@ -477,6 +477,27 @@ sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *m, const float *f, float
     return iso_run(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
 }
 
+sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
+                                  int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    SEM_TRY(check_common(ctx, m, "sem_isosurface_noalloc"));
+    if (!ntri_out) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_noalloc: ntri_out is NULL");
+    *ntri_out = 0;
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_noalloc: negative cap");
+    if (m->E > SEM_NOALLOC_MAX_ELEMENTS)
+        return sem_fail(ctx, SEM_ERR_ARG,
+                        "sem_isosurface_noalloc: the mesh has %lld elements, more than the %d its fixed scratch "
+                        "holds; use sem_isosurface",
+                        (long long)m->E, SEM_NOALLOC_MAX_ELEMENTS);
+    if (m->E == 0) return SEM_OK;
+    SEM_TRY(check_ptr(ctx, f, "sem_isosurface_noalloc", "f"));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface_noalloc", "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_noalloc", "tri_elem", true, 4));
+    SEM_TRY(check_ptr(ctx, cases, "sem_isosurface_noalloc", "cases", true));
+    if (isnan(iso)) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_noalloc: iso is NaN");
+    return iso_run_noalloc(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
+}
+
 sem_status sem_render(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
 {

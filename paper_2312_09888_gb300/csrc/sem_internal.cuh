@@ -68,6 +68,8 @@ sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const f
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
 sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
                    int64_t cap, int64_t *ntri_out, uint8_t *cases);
+sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
+                           int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth);
 sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);

@@ -251,3 +251,86 @@ sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, f
     default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
     }
 }
+
+// ==========================================================================================
+// Allocation-free variant of sem_isosurface (sem_isosurface_noalloc).  Same kernels and the
+// same scan; the per-element counts, offsets and scan partials live in one file-scope device
+// array instead of the context's grow-only arena, so a call never allocates.
+// ==========================================================================================
+#include <mutex>
+
+namespace {
+constexpr size_t al256(size_t b) { return ((b + 255) / 256) * 256; }
+constexpr int64_t kNaMaxE = SEM_NOALLOC_MAX_ELEMENTS;
+constexpr size_t kNaCnt = al256(sizeof(int32_t) * kNaMaxE);
+constexpr size_t kNaOff = al256(sizeof(int64_t) * (kNaMaxE + 1));
+constexpr size_t kNaTmp = al256(sizeof(int64_t) * ((kNaMaxE + 4095) / 4096 + 1));
+constexpr int kNaMaxDevices = 64;
+}  // namespace
+
+// Shared by every call on a device; holds the last call's contents until the next call.
+// Nothing in it needs to start at zero: every word is written before it is read.
+static __device__ __align__(256) unsigned char g_iso_noalloc_scratch[kNaCnt + kNaOff + kNaTmp];
+
+static std::mutex g_na_mu;
+static void *g_na_ptr[kNaMaxDevices] = {};
+
+// Device address of g_iso_noalloc_scratch on ctx->device (which the caller has made current).
+// The host-side symbol is only a stand-in, so the address is looked up once per device.
+static sem_status noalloc_scratch(sem_ctx *ctx, char **out)
+{
+    if (ctx->device < 0 || ctx->device >= kNaMaxDevices)
+        return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "sem_isosurface_noalloc: device index %d >= %d", ctx->device,
+                        kNaMaxDevices);
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_iso_noalloc_scratch);
+        if (e != cudaSuccess || !p) return sem_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+        g_na_ptr[ctx->device] = p;
+    }
+    *out = static_cast<char *>(g_na_ptr[ctx->device]);
+    return SEM_OK;
+}
+
+template <int NP>
+static sem_status iso_run_noalloc_np(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
+                                     int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    const int64_t E = m->E;
+    if (scan_tmp_bytes(E) > kNaTmp) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_noalloc: scan scratch too small");
+    char *scr;
+    SEM_TRY(noalloc_scratch(ctx, &scr));
+    int32_t *cnt = reinterpret_cast<int32_t *>(scr);
+    int64_t *offs = reinterpret_cast<int64_t *>(scr + kNaCnt);
+    void *tmp = scr + kNaCnt + kNaOff;
+    constexpr int WV = IsoW<NP>::V;
+    const unsigned grid = (unsigned)((E + WV - 1) / WV);
+    k_iso_count<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, cnt, cases);
+    SEM_CU(ctx, cudaGetLastError());
+    SEM_TRY(scan_i32_i64(ctx, cnt, offs, E, tmp));
+    SEM_CU(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + E, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t total = ctx->h_pinned[0];
+    *ntri_out = total;
+    if (!tris) return SEM_OK;
+    if (total > cap)
+        return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface_noalloc: %lld triangles exceed capacity %lld",
+                        (long long)total, (long long)cap);
+    if (total == 0) return SEM_OK;
+    k_iso_emit<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, offs, m->lo, m->hi, tris, tri_elem, cap);
+    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit launch");
+}
+
+sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
+                           int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    switch (m->N + 1) {
+#define SEM_CASE(NPV) \
+    case NPV: return iso_run_noalloc_np<NPV>(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
+}
