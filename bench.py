@@ -34,14 +34,13 @@ METRIC = "SEM elements/s through Q-isosurface render; frames/s; fraction of HBM 
 UNIT = "elements/s"
 WORKLOAD = "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, 1920x1080 perspective"
 KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
-                  "k_iso_count": "paper_2312_09888_gb300/csrc/sem_iso.cu",
-                  "k_iso_emit": "paper_2312_09888_gb300/csrc/sem_iso.cu",
-                  "k_raster": "paper_2312_09888_gb300/csrc/sem_render.cu",
-                  "k_setup": "paper_2312_09888_gb300/csrc/sem_render.cu",
-                  "k_bin": "paper_2312_09888_gb300/csrc/sem_render.cu"}
-# kernels the library launches per step: qcrit 1; per isovalue count + 3 scan + emit = 5;
-# render setup + 3 scan + bin + raster = 6
-LAUNCHES_PER_STEP = lambda n_iso: 1 + 5 * n_iso + 6  # noqa: E731
+                  "k_iso_count_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
+                  "k_iso_emit_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
+                  "k_raster_small": "paper_2312_09888_gb300/csrc/sem_render.cu",
+                  "k_resolve": "paper_2312_09888_gb300/csrc/sem_render.cu"}
+# kernels the library launches per step: qcriterion 1; multi-isovalue count + 3 scan + emit = 5;
+# render small + large + resolve = 3
+LAUNCHES_PER_STEP = 1 + 5 + 3
 
 
 def _dist():
@@ -168,7 +167,7 @@ class Pipeline:
         S.sem_qcriterion(self.ctx, self.mesh, *self.vel, self.Q)
         qmax = S.sem_field_max(self.ctx, self.Q)
         self.isos = [float(np.float32(f * qmax)) for f in w.iso_fracs]
-        counts = [S.sem_isosurface(self.ctx, self.mesh, self.Q, iso, None, cap=0) for iso in self.isos]
+        counts = S.sem_isosurface_multi(self.ctx, self.mesh, self.Q, self.isos, None)
         self.cap = int(sum(counts) * 1.05) + 1024
         self.tris = torch.empty(self.cap * 9, device="cuda")
         self.W, self.H = w.camera["W"], w.camera["H"]
@@ -184,12 +183,8 @@ class Pipeline:
         S.sem_qcriterion(ctx, m, *self.vel, self.Q)
         if events is not None:
             events[1].record(self.stream)
-        off = 0
-        seg = []
-        for iso in self.isos:
-            n = S.sem_isosurface(ctx, m, self.Q, iso, self.tris[off * 9:], cap=self.cap - off)
-            seg.append(n)
-            off += n
+        seg = S.sem_isosurface_multi(ctx, m, self.Q, self.isos, self.tris, cap=self.cap)
+        off = sum(seg)
         if events is not None:
             events[2].record(self.stream)
         S.sem_render(ctx, self.tris, off, seg, None, self.w.camera, self.W, self.H, self.rgba, self.depth)
@@ -305,7 +300,7 @@ def run_ours(args):
                         "isosurface_all": round(float(mean_stage[1]), 4),
                         "render": round(float(mean_stage[2]), 4)},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-           "gpu_launches": LAUNCHES_PER_STEP(n_iso) * K}
+           "gpu_launches": LAUNCHES_PER_STEP * K}
     P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -73,6 +73,8 @@ typedef enum {
 #define SEM_MAX_ORDER 15
 /* Triangle slots per marching-cubes case in sem_mc_table. */
 #define SEM_MC_MAXT 12
+/* Most isovalues one sem_isosurface_multi call extracts. */
+#define SEM_MAX_ISO 8
 
 /* Camera of sem_render.  View basis f = unit(center-eye), s = unit(f x up), u = s x f;
  * view coordinates xv = s.(p-eye), yv = u.(p-eye), zv = f.(p-eye).
@@ -158,6 +160,17 @@ SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const floa
  * SEM_ERR_CAPACITY with *ntri_out = the required count and writes no triangle. */
 SEM_API sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *mesh, const float *f, float iso, float *tris,
                           int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
+
+/* sem_isosurface for several isovalues of one field at once (1 <= niso <= SEM_MAX_ISO).  The
+ * result equals niso sem_isosurface calls written back to back: the triangles of isovalue q
+ * follow those of isovalue q-1, each in (element, cell, table) order, and ntri_out[q] (HOST,
+ * niso entries) receives isovalue q's count.  The field is read once per pass for all
+ * isovalues, and the call synchronises once.  cases (device, niso*E*N^3 bytes, or NULL) is laid
+ * out [q][e][cell].  tris NULL: count only.  If the total exceeds cap, returns
+ * SEM_ERR_CAPACITY with ntri_out filled and writes no triangle. */
+SEM_API sem_status sem_isosurface_multi(sem_ctx *ctx, const sem_mesh *mesh, const float *f, const float *isos_host,
+                                        int niso, float *tris, int32_t *tri_elem, int64_t cap, int64_t *ntri_out,
+                                        uint8_t *cases);
 
 /* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
 #define SEM_NOALLOC_MAX_ELEMENTS 262144

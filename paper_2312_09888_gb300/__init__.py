@@ -28,6 +28,7 @@ SEM_FP32, SEM_TF32, SEM_FP16, SEM_BF16, SEM_BF16X2 = range(5)
 SEM_MAX_ORDER = 15
 SEM_NOALLOC_MAX_ELEMENTS = 262144
 SEM_MC_MAXT = 12
+SEM_MAX_ISO = 8
 
 _lock = threading.Lock()
 _lib = None
@@ -63,6 +64,7 @@ def _declare(L):
     L.sem_derivatives.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_qcriterion.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
+    L.sem_isosurface_multi.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_surface_measures.argtypes = [vp, vp, i64, vp]
@@ -71,7 +73,7 @@ def _declare(L):
     L.sem_mc_table.restype = i32
     L.sem_gll.argtypes = [i32, vp, vp]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
-                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
+                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
 
@@ -208,6 +210,23 @@ def sem_isosurface(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None, ca
                                   _dev(cases, "cases", torch.uint8, allow_none=True))
     _check(ctx, st, n.value)
     return n.value
+
+
+def sem_isosurface_multi(ctx, mesh, f, isos, tris, tri_elem=None, cases=None, cap: Optional[int] = None):
+    """Several isovalues in one call; returns the per-isovalue triangle counts (a list).  The
+    triangles of isovalue q follow those of q-1 in ``tris`` (tris None: count only)."""
+    import torch
+    iv = np.ascontiguousarray(np.asarray(isos, dtype=np.float32).reshape(-1))
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    n = np.zeros(len(iv), dtype=np.int64)
+    st = get_lib().sem_isosurface_multi(ctx, mesh, _dev(f, "f", torch.float32), iv.ctypes.data_as(C.c_void_p),
+                                        len(iv), _dev(tris, "tris", torch.float32, allow_none=True),
+                                        _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap),
+                                        n.ctypes.data_as(C.c_void_p),
+                                        _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st, int(n.sum()))
+    return [int(x) for x in n]
 
 
 def sem_isosurface_noalloc(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None,

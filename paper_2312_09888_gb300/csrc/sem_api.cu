@@ -477,6 +477,28 @@ sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *m, const float *f, float
     return iso_run(ctx, m, f, iso, tris, tri_elem, cap, ntri_out, cases);
 }
 
+sem_status sem_isosurface_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
+                                float *tris, int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
+{
+    SEM_TRY(check_common(ctx, m, "sem_isosurface_multi"));
+    if (!ntri_out || !isos) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi: isos or ntri_out is NULL");
+    if (niso < 1 || niso > SEM_MAX_ISO)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi: niso=%d outside [1,%d]", niso, SEM_MAX_ISO);
+    for (int q = 0; q < niso; ++q) {
+        ntri_out[q] = 0;
+        if (isnan(isos[q])) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi: isovalue %d is NaN", q);
+    }
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi: negative cap");
+    if (m->E == 0) return SEM_OK;
+    if (m->E * (int64_t)niso > ((int64_t)1 << 31))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi: E*niso too large");
+    SEM_TRY(check_ptr(ctx, f, "sem_isosurface_multi", "f"));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface_multi", "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_multi", "tri_elem", true, 4));
+    SEM_TRY(check_ptr(ctx, cases, "sem_isosurface_multi", "cases", true));
+    return iso_run_multi(ctx, m, f, isos, niso, tris, tri_elem, cap, ntri_out, cases);
+}
+
 sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                                   int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
 {

@@ -24,6 +24,8 @@ struct sem_ctx {
     // grow-only device scratch arenas
     void *scratch[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t scratch_bytes[4] = {0, 0, 0, 0};
+    // the render key buffer must read "empty" (all ones) at the start of a frame
+    bool render_keys_dirty = true;
 };
 
 struct sem_mesh {
@@ -68,6 +70,8 @@ sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const f
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
 sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
                    int64_t cap, int64_t *ntri_out, uint8_t *cases);
+sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso, float *tris,
+                         int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                            int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,

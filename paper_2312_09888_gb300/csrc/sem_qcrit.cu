@@ -23,6 +23,9 @@
 #include "sem_internal.cuh"
 
 #define MP (SEM_MAX_ORDER + 1)
+#ifndef SEM_Q_FOLD
+#define SEM_Q_FOLD 1
+#endif
 
 __constant__ float c_D[(SEM_MAX_ORDER + 1) * MP * MP];  // [N][i][m], FP32
 
@@ -130,6 +133,90 @@ __device__ __forceinline__ void line_derivs(const float *__restrict__ U, int k, 
     }
 }
 
+// The three directions one at a time (same arithmetic and shared-memory order as
+// line_derivs), so the Q kernel can fold each into Q before computing the next.
+template <int NP>
+__device__ __forceinline__ void deriv_r(const float *__restrict__ U, int k, int j, float (&dr)[NP])
+{
+    float row[NP];
+    if constexpr (NP == 8) {
+        const int sw = (j >> 2) & 1;
+        const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
+        float4 A = rp[sw], B = rp[sw ^ 1];
+        float4 lo = sw ? B : A, hi = sw ? A : B;
+        row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
+        row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
+    } else {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float a = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
+        dr[i] = a;
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void deriv_s(const float *__restrict__ U, int k, int j, const float (&Dj)[NP], float (&ds)[NP])
+{
+    if constexpr (NP == 8) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ds[i] = 0.f;
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const int m = (mm + k) & 7;
+            const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
+            const float4 A = sp[0], B = sp[1];
+            const float d = Dj[mm];
+            ds[0] = fmaf(d, A.x, ds[0]); ds[1] = fmaf(d, A.y, ds[1]);
+            ds[2] = fmaf(d, A.z, ds[2]); ds[3] = fmaf(d, A.w, ds[3]);
+            ds[4] = fmaf(d, B.x, ds[4]); ds[5] = fmaf(d, B.y, ds[5]);
+            ds[6] = fmaf(d, B.z, ds[6]); ds[7] = fmaf(d, B.w, ds[7]);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) ds[i] = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i], ds[i]);
+    }
+}
+
+template <int NP>
+__device__ __forceinline__ void deriv_t(const float *__restrict__ U, int j, const float (&Dk)[NP], float (&dt)[NP])
+{
+    if constexpr (NP == 8) {
+        const int sw = (j >> 2) & 1;
+        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
+            const float4 A = tp[sw], B = tp[sw ^ 1];
+            const float d = Dk[m];
+            a0[0] = fmaf(d, A.x, a0[0]); a0[1] = fmaf(d, A.y, a0[1]);
+            a0[2] = fmaf(d, A.z, a0[2]); a0[3] = fmaf(d, A.w, a0[3]);
+            a1[0] = fmaf(d, B.x, a1[0]); a1[1] = fmaf(d, B.y, a1[1]);
+            a1[2] = fmaf(d, B.z, a1[2]); a1[3] = fmaf(d, B.w, a1[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            dt[i] = sw ? a1[i] : a0[i];
+            dt[i + 4] = sw ? a0[i] : a1[i];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) dt[i] = 0.f;
+#pragma unroll
+        for (int m = 0; m < NP; ++m)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i], dt[i]);
+    }
+}
+
 template <int NP>
 __device__ __forceinline__ void store_line(float *__restrict__ dst, const float (&v)[NP])
 {
@@ -152,11 +239,15 @@ struct QCfg {
     static constexpr int EPB = EPB_RAW;
     static constexpr int NT = ((EPB * L + 31) / 32) * 32;
     static constexpr int NSTAGE = BULK ? 2 : 1;
+#ifndef SEM_Q_MINB
+#define SEM_Q_MINB 2
+#endif
+    static constexpr int MINB = (NP == 8) ? SEM_Q_MINB : 1;
 };
 
 // NC = 3: Q of (f0, f1, f2) -> out0.   NC = 1: gradient of f0 -> (out0, out1, out2).
 template <int NP, int NC>
-__global__ void __launch_bounds__(QCfg<NP>::NT) k_sem_grad(const float *__restrict__ f0, const float *__restrict__ f1,
+__global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const float *__restrict__ f0, const float *__restrict__ f1,
                                                            const float *__restrict__ f2, float *__restrict__ out0,
                                                            float *__restrict__ out1, float *__restrict__ out2,
                                                            const float4 *__restrict__ gfac, int64_t E, int *err)
@@ -241,6 +332,35 @@ __global__ void __launch_bounds__(QCfg<NP>::NT) k_sem_grad(const float *__restri
                 store_line<NP>(out1 + off, ds);
                 store_line<NP>(out2 + off, dt);
             } else {
+#if SEM_Q_FOLD
+                // Q = -1/2 sum_ij J_ij J_ji with J_ij = g_j d_j(u_i): six product terms, each
+                // folded in as soon as its second factor is known; c = -1/2 g_i g_j (x2 off-diagonal)
+                const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
+                const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
+                const float *U0 = st + el * NP3, *U1 = U0 + EPB * NP3, *U2 = U1 + EPB * NP3;
+                float q[NP], su[NP], tu[NP], tv[NP], d[NP];
+                deriv_r<NP>(U0, k, j, d);  // u_r
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = c11 * d[i] * d[i];
+                deriv_s<NP>(U0, k, j, Dj, su);  // u_s
+                deriv_t<NP>(U0, j, Dk, tu);     // u_t
+                deriv_r<NP>(U1, k, j, d);       // v_r
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = fmaf(c12 * su[i], d[i], q[i]);
+                deriv_s<NP>(U1, k, j, Dj, d);   // v_s
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = fmaf(c22 * d[i], d[i], q[i]);
+                deriv_t<NP>(U1, j, Dk, tv);     // v_t
+                deriv_r<NP>(U2, k, j, d);       // w_r
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = fmaf(c13 * tu[i], d[i], q[i]);
+                deriv_s<NP>(U2, k, j, Dj, d);   // w_s
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = fmaf(c23 * tv[i], d[i], q[i]);
+                deriv_t<NP>(U2, j, Dk, d);      // w_t
+#pragma unroll
+                for (int i = 0; i < NP; ++i) q[i] = fmaf(c33 * d[i], d[i], q[i]);
+#else
                 float q[NP], J13[NP], J23[NP];
                 // u: J11 = gx u_r, J12 = gy u_s, J13 = gz u_t
                 line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
@@ -266,6 +386,7 @@ __global__ void __launch_bounds__(QCfg<NP>::NT) k_sem_grad(const float *__restri
                     const float J31 = g.x * dr[i], J32 = g.y * ds[i], J33 = g.z * dt[i];
                     q[i] = -0.5f * fmaf(J33, J33, fmaf(2.f * J13[i], J31, fmaf(2.f * J23[i], J32, q[i])));
                 }
+#endif
                 store_line<NP>(out0 + off, q);
             }
         }

@@ -6,7 +6,9 @@ u_m|; scaling by the FP32 factor 2/h adds 2 * 2^-24 |result|.  A safety factor o
 the remaining second-order terms.  The FP64 oracle's own error is added as a floor of
 1e-12 times the node's largest gradient entry (its general chain rule carries D's row-sum
 rounding, ~1e-14, times coordinate/size ratios).  Q = -1/2 sum J_ij J_ji then inherits
-|dQ| <= sum_ij (|J_ij| + dJ_ij) dJ_ji + 8 * 2^-24 sum |J_ij J_ji|.
+|dQ| <= sum_ij (|J_ij| + dJ_ij) dJ_ji + 16 * 2^-24 sum |J_ij J_ji| (each of the six product
+terms carries at most 5 roundings from its coefficient -g_i g_j/2 and products, and the
+accumulation of six terms at most 6 more).
 """
 import numpy as np
 import torch
@@ -49,7 +51,7 @@ def q_bound(J, dJ):
         for j in range(3):
             b += (np.abs(J[i, j]) + dJ[i, j]) * dJ[j, i]
             s += np.abs(J[i, j] * J[j, i])
-    return b + 8.0 * EPS32 * s + 1e-30
+    return b + 16.0 * EPS32 * s + 1e-30
 
 
 def box_factors(xyz):

@@ -118,6 +118,43 @@ def test_nan_counts_below_and_flat_elements(gpu, sess, orc):
     assert (got[4][1] == 255).all() and (got[4][2] == 0).all()
 
 
+def test_multi_isovalues_match_oracle_and_single_calls(gpu, sess, orc):
+    """Three isovalues in one call: each segment equals the oracle's extraction (cases,
+    counts, element map, positions) and the single-isovalue call."""
+    w = si.tgv_box(nel=5, N=7)
+    xyz = w.mesh.xyz().numpy()
+    m = sess.mesh(7, xyz)
+    u, v, ww = (dev32(w.fields[c].numpy()) for c in range(3))
+    Q = torch.empty_like(u)
+    gpu.sem_qcriterion(sess.ctx, m, u, v, ww, Q)
+    qmax = gpu.sem_field_max(sess.ctx, Q)
+    isos = [float(np.float32(f * qmax)) for f in (0.05, 0.1, 0.2, -0.05)]
+    E, N3 = w.E, 343
+    counts = gpu.sem_isosurface_multi(sess.ctx, m, Q, isos, None)
+    tris = torch.empty(sum(counts) * 9, device="cuda")
+    te = torch.empty(sum(counts), dtype=torch.int32, device="cuda")
+    cs = torch.zeros(len(isos) * E * N3, dtype=torch.uint8, device="cuda")
+    assert gpu.sem_isosurface_multi(sess.ctx, m, Q, isos, tris, te, cs) == counts
+    torch.cuda.synchronize()
+    q64 = host64(Q)
+    t_h, e_h, c_h = host64(tris).reshape(-1, 3, 3), te.cpu().numpy(), cs.cpu().numpy().reshape(len(isos), E, N3)
+    off = 0
+    for q, iso in enumerate(isos):
+        ref = orc.isosurface(7, xyz, q64, iso)
+        n = counts[q]
+        assert n == ref["ntri"]
+        np.testing.assert_array_equal(c_h[q], ref["cases"])
+        np.testing.assert_array_equal(e_h[off:off + n], ref["tri_elem"])
+        assert np.abs(t_h[off:off + n] - ref["tris"]).max() <= 1e-5 * 2 * math.pi
+        one = torch.empty(n * 9, device="cuda")
+        assert gpu.sem_isosurface(sess.ctx, m, Q, iso, one) == n
+        assert torch.equal(one, tris[off * 9:(off + n) * 9])
+        off += n
+    with pytest.raises(gpu.SemError) as ex:
+        gpu.sem_isosurface_multi(sess.ctx, m, Q, isos, tris[:9 * (sum(counts) - 1)])
+    assert ex.value.status == gpu.SEM_ERR_CAPACITY and ex.value.required == sum(counts)
+
+
 def test_channel_full_size_sampled(gpu, sess, orc):
     """32^3 elements, N = 7, the benchmark's three isovalues; GPU Q on the full mesh, the
     oracle extracts 256 sampled elements from the same FP32 Q."""
