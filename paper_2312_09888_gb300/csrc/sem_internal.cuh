@@ -26,6 +26,8 @@ struct sem_ctx {
     size_t scratch_bytes[4] = {0, 0, 0, 0};
     // the render key buffer must read "empty" (all ones) at the start of a frame
     bool render_keys_dirty = true;
+    // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
+    void *tc_A[2] = {nullptr, nullptr};
 };
 
 struct sem_mesh {
@@ -67,6 +69,8 @@ sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *nt
 // launchers (argument checking happens in sem_api.cu)
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                         float *Q);
+sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q,
+                           sem_prec prec, const double *D64);
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
 sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
                    int64_t cap, int64_t *ntri_out, uint8_t *cases);
@@ -116,6 +120,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// non-blocking test of a phase (for threads that poll several barriers)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)

@@ -43,6 +43,23 @@ def grad_bounds(D, u, g, NP, ref):
                      for a in range(3)])
 
 
+def grad_bounds_prec(D, u, g, NP, ref, eps_st, abs_st=0.0):
+    """As grad_bounds, with the s- and t-contractions done in a 16-bit type: rounding the
+    element data and D to it (unit roundoff eps_st each) adds 2 eps_st sum |D||u| per node;
+    values below the type's normal range round with an absolute error abs_st instead (FP16:
+    2^-25), adding abs_st sum |D|."""
+    bs = ref_abs_contractions(D, u, NP)
+    dsum = np.abs(D).sum(axis=1).max()
+    floor = 1e-12 * np.abs(ref).max(axis=0)
+    out = []
+    for a in range(3):
+        e_in = 0.0 if a == 0 else 2.0 * eps_st
+        a_in = 0.0 if a == 0 else 2.0 * abs_st * dsum
+        out.append(((2.0 * (NP + 1) * EPS32 + 2.0 * e_in) * bs[a] + a_in) * np.abs(g[:, a:a + 1])
+                   + 4.0 * EPS32 * np.abs(ref[a]) + floor)
+    return np.stack(out)
+
+
 def q_bound(J, dJ):
     """J, dJ: (3, 3, ...) gradient and its per-entry bound -> per-node bound on Q."""
     b = np.zeros(J.shape[2:])
