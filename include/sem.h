@@ -172,6 +172,17 @@ SEM_API sem_status sem_isosurface_multi(sem_ctx *ctx, const sem_mesh *mesh, cons
                                         int niso, float *tris, int32_t *tri_elem, int64_t cap, int64_t *ntri_out,
                                         uint8_t *cases);
 
+/* sem_isosurface_multi without host synchronisation, for work captured in a CUDA graph.
+ * counts_dev: device int64[niso + 1] receives the segment starts (counts_dev[q] = first triangle
+ * of isovalue q, counts_dev[niso] = total).  If the total exceeds cap, no triangle is written and
+ * the context's device flag records SEM_ERR_CAPACITY (reported by sem_synchronize); counts_dev
+ * still holds the required sizes.  The library's scratch must already be large enough when the
+ * stream is being captured: make one uncaptured call with the same mesh and niso first
+ * (otherwise SEM_ERR_CAPACITY, nothing launched).  Other arguments as sem_isosurface_multi. */
+SEM_API sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *mesh, const float *f,
+                                              const float *isos_host, int niso, float *tris, int32_t *tri_elem,
+                                              int64_t cap, int64_t *counts_dev, uint8_t *cases);
+
 /* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
 #define SEM_NOALLOC_MAX_ELEMENTS 262144
 
@@ -212,6 +223,15 @@ SEM_API sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *mesh, co
 SEM_API sem_status sem_render(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
                       float *depth);
+
+/* sem_render without host synchronisation, segments read from the device: seg_start_dev is a
+ * device int64[nseg + 1] of segment starts (e.g. counts_dev of sem_isosurface_multi_async);
+ * triangles [seg_start_dev[0], seg_start_dev[nseg]) are drawn, at most ntri_max (a HOST upper
+ * bound that sizes the launch; tris must hold ntri_max triangles).  Scratch as in
+ * sem_isosurface_multi_async: make one uncaptured call with the same W, H and ntri_max first. */
+SEM_API sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
+                                    int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H,
+                                    uint8_t *rgba, float *depth);
 
 /* FP64 reductions of a triangle soup (device, ntri*9 floats): out_host[0] = total area
  * sum |(p1-p0)x(p2-p0)|/2, out_host[1] = enclosed volume sum p0.(p1 x p2)/6 (divergence

@@ -65,6 +65,8 @@ def _declare(L):
     L.sem_qcriterion.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_isosurface_multi.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
+    L.sem_isosurface_multi_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
+    L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_surface_measures.argtypes = [vp, vp, i64, vp]
@@ -73,7 +75,8 @@ def _declare(L):
     L.sem_mc_table.restype = i32
     L.sem_gll.argtypes = [i32, vp, vp]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
-                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
+                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async", "sem_render_async",
+                 "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
 
@@ -227,6 +230,35 @@ def sem_isosurface_multi(ctx, mesh, f, isos, tris, tri_elem=None, cases=None, ca
                                         _dev(cases, "cases", torch.uint8, allow_none=True))
     _check(ctx, st, int(n.sum()))
     return [int(x) for x in n]
+
+
+def sem_isosurface_multi_async(ctx, mesh, f, isos, tris, counts_dev, tri_elem=None, cases=None,
+                               cap: Optional[int] = None) -> None:
+    """No host synchronisation (CUDA-graph capturable); segment starts land in counts_dev
+    (int64 CUDA tensor of len(isos) + 1); an overflow raises the device flag."""
+    import torch
+    iv = np.ascontiguousarray(np.asarray(isos, dtype=np.float32).reshape(-1))
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    st = get_lib().sem_isosurface_multi_async(ctx, mesh, _dev(f, "f", torch.float32), iv.ctypes.data_as(C.c_void_p),
+                                              len(iv), _dev(tris, "tris", torch.float32, allow_none=True),
+                                              _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap),
+                                              _dev(counts_dev, "counts_dev", torch.int64),
+                                              _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st)
+
+
+def sem_render_async(ctx, tris, ntri_max: int, seg_start_dev, nseg: int, seg_rgb, cam: dict, W: int, H: int, rgba,
+                     depth=None) -> None:
+    import torch
+    rgb = None if seg_rgb is None else np.ascontiguousarray(np.asarray(seg_rgb, dtype=np.float32).reshape(-1))
+    camc = make_camera(cam)
+    st = get_lib().sem_render_async(ctx, _dev(tris, "tris", torch.float32, allow_none=ntri_max == 0), int(ntri_max),
+                                    _dev(seg_start_dev, "seg_start_dev", torch.int64), int(nseg),
+                                    None if rgb is None else rgb.ctypes.data_as(C.c_void_p), C.byref(camc), int(W),
+                                    int(H), _dev(rgba, "rgba", torch.uint8),
+                                    _dev(depth, "depth", torch.float32, allow_none=True))
+    _check(ctx, st)
 
 
 def sem_isosurface_noalloc(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None,

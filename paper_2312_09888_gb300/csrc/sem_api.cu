@@ -54,6 +54,20 @@ sem_status sem_scratch(sem_ctx *ctx, int slot, size_t bytes, void **out)
     return SEM_OK;
 }
 
+sem_status sem_scratch_nogrow_in_capture(sem_ctx *ctx, int slot, size_t bytes, void **out)
+{
+    if (ctx->scratch_bytes[slot] < (bytes ? bytes : 256)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return sem_fail(ctx, SEM_ERR_CAPACITY,
+                            "scratch arena %d too small while the stream is captured (%zu < %zu bytes): make the "
+                            "same call once before capturing",
+                            slot, ctx->scratch_bytes[slot], bytes);
+    }
+    return sem_scratch(ctx, slot, bytes, out);
+}
+
 // ==========================================================================================
 // GLL nodes and derivative matrix (host, FP64).
 //
@@ -326,6 +340,9 @@ sem_status sem_synchronize(sem_ctx *ctx)
         SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
         if (flag & (1 << SEM_ERR_TIMEOUT))
             return sem_fail(ctx, SEM_ERR_TIMEOUT, "a bounded device-side wait ran out (flag 0x%x)", flag);
+        if (flag & (1 << SEM_ERR_CAPACITY))
+            return sem_fail(ctx, SEM_ERR_CAPACITY,
+                            "an asynchronous call found more triangles than its buffer holds (flag 0x%x)", flag);
         return sem_fail(ctx, SEM_ERR_CUDA, "device-side failure flag 0x%x", flag);
     }
     return SEM_OK;
@@ -504,6 +521,48 @@ sem_status sem_isosurface_multi(sem_ctx *ctx, const sem_mesh *m, const float *f,
     SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_multi", "tri_elem", true, 4));
     SEM_TRY(check_ptr(ctx, cases, "sem_isosurface_multi", "cases", true));
     return iso_run_multi(ctx, m, f, isos, niso, tris, tri_elem, cap, ntri_out, cases);
+}
+
+sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
+                                      float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases)
+{
+    SEM_TRY(check_common(ctx, m, "sem_isosurface_multi_async"));
+    if (!isos || niso < 1 || niso > SEM_MAX_ISO)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_async: need 1 <= niso <= %d isovalues", SEM_MAX_ISO);
+    for (int q = 0; q < niso; ++q)
+        if (isnan(isos[q])) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_async: isovalue %d is NaN", q);
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_async: negative cap");
+    SEM_TRY(check_ptr(ctx, counts_dev, "sem_isosurface_multi_async", "counts_dev", false, 8));
+    if (m->E == 0) return sem_cuda(ctx, cudaMemsetAsync(counts_dev, 0, sizeof(int64_t) * (niso + 1), ctx->stream),
+                                   "cudaMemsetAsync");
+    if (m->E * (int64_t)niso > ((int64_t)1 << 31))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_async: E*niso too large");
+    SEM_TRY(check_ptr(ctx, f, "sem_isosurface_multi_async", "f"));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface_multi_async", "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_multi_async", "tri_elem", true, 4));
+    SEM_TRY(check_ptr(ctx, cases, "sem_isosurface_multi_async", "cases", true));
+    return iso_run_multi_async(ctx, m, f, isos, niso, tris, tri_elem, cap, counts_dev, cases);
+}
+
+sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
+                            const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (!cam) return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: cam is NULL");
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad size");
+    if (ntri_max < 0 || ntri_max >= ((int64_t)1 << 31) || nseg < 1 || nseg > 16)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad ntri_max or nseg");
+    SEM_TRY(check_ptr(ctx, seg_start_dev, "sem_render_async", "seg_start_dev", false, 8));
+    SEM_TRY(check_ptr(ctx, tris, "sem_render_async", "tris", ntri_max == 0, 4));
+    SEM_TRY(check_ptr(ctx, rgba, "sem_render_async", "rgba"));
+    SEM_TRY(check_ptr(ctx, depth, "sem_render_async", "depth", true));
+    if (!(cam->znear > 0.f) || !(cam->zfar > cam->znear))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: need 0 < znear < zfar");
+    if (cam->ortho ? !(cam->half_h > 0.f) : !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad projection parameters");
+    std::vector<int64_t> dummy(nseg, 0);
+    return render_run(ctx, tris, ntri_max, dummy.data(), nseg, seg_rgb, cam, W, H, rgba, depth, seg_start_dev);
 }
 
 sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,

@@ -48,6 +48,8 @@ sem_status sem_fail(sem_ctx *ctx, sem_status st, const char *fmt, ...);
 sem_status sem_cuda(sem_ctx *ctx, cudaError_t e, const char *what);
 // ensure scratch arena `slot` has at least `bytes`
 sem_status sem_scratch(sem_ctx *ctx, int slot, size_t bytes, void **out);
+// as sem_scratch, but refuses to grow the arena while ctx->stream is being captured into a graph
+sem_status sem_scratch_nogrow_in_capture(sem_ctx *ctx, int slot, size_t bytes, void **out);
 
 #define SEM_TRY(expr)                           \
     do {                                        \
@@ -76,10 +78,13 @@ sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, f
                    int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso, float *tris,
                          int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
+sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
+                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases);
 sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                            int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
-                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth);
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
+                      const int64_t *seg_start_dev = nullptr);
 sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);
 sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host);
 

@@ -366,10 +366,16 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                                                                  const float4 *__restrict__ blo,
                                                                  const float4 *__restrict__ bhi,
                                                                  float *__restrict__ tris,
-                                                                 int32_t *__restrict__ tri_elem, int64_t cap)
+                                                                 int32_t *__restrict__ tri_elem, int64_t cap,
+                                                                 int *flag)
 {
     constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N;
     using EW = EmitW<NP>;
+    // all-or-nothing capacity check (the host-synchronised path has checked already)
+    if (offs[S.niso * E] > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicOr(flag, 1 << SEM_ERR_CAPACITY);
+        return;
+    }
     constexpr int WV = EW::V;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint8_t s_nt[256];
@@ -488,8 +494,54 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
     SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     k_iso_emit_m<NP><<<(unsigned)((E + EV - 1) / EV), 32 * EV, dyn, ctx->stream>>>(
-        f, S, E, offs, m->lo, m->hi, tris, tri_elem, cap);
+        f, S, E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag);
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+}
+
+// No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
+// raises the context's device flag and writes no triangle.
+template <int NP>
+static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, float *tris,
+                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases)
+{
+    const int64_t E = m->E, n = E * S.niso;
+    const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
+    const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
+    void *scr;
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, cnt_bytes + off_bytes + scan_tmp_bytes(n), &scr));
+    int32_t *cnt = reinterpret_cast<int32_t *>(scr);
+    int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
+    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes;
+    constexpr int WV = IsoW<NP>::V;
+    k_iso_count_m<NP><<<(unsigned)((E + WV - 1) / WV), 32 * WV, 0, ctx->stream>>>(f, S, E, cnt, cases);
+    SEM_CU(ctx, cudaGetLastError());
+    SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
+    SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t), S.niso + 1,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    if (!tris) return SEM_OK;
+    constexpr int EV = EmitW<NP>::V;
+    constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
+    SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k_iso_emit_m<NP><<<(unsigned)((E + EV - 1) / EV), 32 * EV, dyn, ctx->stream>>>(
+        f, S, E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag);
+    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+}
+
+sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
+                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases)
+{
+    IsoSet S;
+    memset(&S, 0, sizeof S);
+    S.niso = niso;
+    for (int q = 0; q < niso; ++q) S.iso[q] = isos[q];
+    switch (m->N + 1) {
+#define SEM_CASE(NPV) \
+    case NPV: return iso_multi_async_np<NPV>(ctx, m, f, S, tris, tri_elem, cap, counts_dev, cases);
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
 }
 
 sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso, float *tris,

@@ -42,6 +42,7 @@ struct RenderParams {
     int nseg;
     int seg_end[16];
     float rgb[16][3];
+    const int64_t *seg_dev;  // device segment starts [nseg + 1] (asynchronous render), or null
 };
 
 __device__ __forceinline__ bool top_left(float ax, float ay, float bx, float by)
@@ -160,7 +161,11 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
 {
     __shared__ float s_tri[256 * 9];
     __shared__ SmallRec s_rec[256];
+    if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
     const int t0 = blockIdx.x * 256;
+    // blocks past the (device-clamped) triangle count have no work; the whole block leaves
+    // before its first barrier
+    if (t0 >= ntri) return;
     const int nt_blk = min(256, ntri - t0);
     for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = tris[(int64_t)t0 * 9 + q];
     __syncthreads();
@@ -168,7 +173,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     const int t = t0 + threadIdx.x;
     bool is_large = false;
     int npx = 0;
-    if (threadIdx.x < nt_blk) {
+    if ((int)threadIdx.x < nt_blk) {
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
@@ -273,7 +278,11 @@ __global__ void __launch_bounds__(256) k_resolve(const float *__restrict__ tris,
     const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
     const float shade = nn > 0.f ? 0.15f + 0.85f * fabsf(nx * P.f[0] + ny * P.f[1] + nz * P.f[2]) / nn : 0.15f;
     int sg = 0;
-    while (sg < P.nseg - 1 && t >= P.seg_end[sg]) ++sg;
+    if (P.seg_dev) {
+        while (sg < P.nseg - 1 && (int64_t)t >= P.seg_dev[sg + 1]) ++sg;
+    } else {
+        while (sg < P.nseg - 1 && t >= P.seg_end[sg]) ++sg;
+    }
     unsigned char c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -299,7 +308,8 @@ static void unit3(double *a)
 }
 
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int64_t *seg_ntri, int nseg,
-                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
+                      const int64_t *seg_start_dev)
 {
     RenderParams P;
     memset(&P, 0, sizeof P);
@@ -343,6 +353,7 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     P.W = W;
     P.H = H;
     P.nseg = nseg;
+    P.seg_dev = seg_start_dev;
     int64_t acc = 0;
     for (int k = 0; k < nseg; ++k) {
         acc += seg_ntri[k];
@@ -358,13 +369,13 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     void *kscr = nullptr, *lscr = nullptr;
     void *const prev = ctx->scratch[SCR_RENDER];
     const size_t prev_bytes = ctx->scratch_bytes[SCR_RENDER];
-    SEM_TRY(sem_scratch(ctx, SCR_RENDER, b_keys, &kscr));
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_RENDER, b_keys, &kscr));
     if (kscr != prev || ctx->scratch_bytes[SCR_RENDER] != prev_bytes || ctx->render_keys_dirty) {
         // a new arena holds no valid keys yet: set every key to "empty" once
         SEM_CU(ctx, cudaMemsetAsync(kscr, 0xff, ctx->scratch_bytes[SCR_RENDER], ctx->stream));
         ctx->render_keys_dirty = false;
     }
-    SEM_TRY(sem_scratch(ctx, SCR_TRI, 256 + sizeof(int32_t) * (size_t)(ntri > 0 ? ntri : 1), &lscr));
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_TRI, 256 + sizeof(int32_t) * (size_t)(ntri > 0 ? ntri : 1), &lscr));
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(kscr);
     int32_t *nlarge = reinterpret_cast<int32_t *>(lscr);
     int32_t *large = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(lscr) + 256);

@@ -1,0 +1,190 @@
+"""Host-synchronisation-free frames (sem_isosurface_multi_async + sem_render_async) and their
+capture in one CUDA graph per time step, against the synchronous path; batches of partitions
+with uneven element counts and mixed orders in one graph."""
+import numpy as np
+import pytest
+import torch
+
+import sem_inputs as si
+from _helpers import host64
+
+pytestmark = pytest.mark.gpu
+
+
+class Frame:
+    """Device buffers of one partition's frame: Q, triangles of all isovalues, image."""
+
+    def __init__(self, S, ctx, w, isos, cap, mesh=None):
+        self.S, self.ctx, self.w = S, ctx, w
+        self.mesh = mesh if mesh is not None else S.sem_load_mesh(ctx, w.mesh.N, w.mesh.xyz().numpy())
+        self.vel = [w.fields[c].float().cuda().contiguous() for c in range(3)]
+        self.Q = torch.empty_like(self.vel[0])
+        self.isos = isos
+        self.cap = cap
+        self.tris = torch.full((cap * 9,), -1.0, device="cuda")
+        self.counts = torch.zeros(len(isos) + 1, dtype=torch.int64, device="cuda")
+        W, H = w.camera["W"], w.camera["H"]
+        self.rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+        self.depth = torch.zeros(H * W, device="cuda")
+
+    def run(self):
+        S = self.S
+        S.sem_qcriterion(self.ctx, self.mesh, *self.vel, self.Q)
+        S.sem_isosurface_multi_async(self.ctx, self.mesh, self.Q, self.isos, self.tris, self.counts, cap=self.cap)
+        S.sem_render_async(self.ctx, self.tris, self.cap, self.counts, len(self.isos), None, self.w.camera,
+                           self.w.camera["W"], self.w.camera["H"], self.rgba, self.depth)
+
+
+def _sync_reference(S, ctx, mesh, vel, isos, cam):
+    Q = torch.empty_like(vel[0])
+    S.sem_qcriterion(ctx, mesh, *vel, Q)
+    counts = S.sem_isosurface_multi(ctx, mesh, Q, isos, None)
+    tris = torch.empty(max(1, sum(counts)) * 9, device="cuda")
+    S.sem_isosurface_multi(ctx, mesh, Q, isos, tris)
+    W, H = cam["W"], cam["H"]
+    rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+    depth = torch.zeros(H * W, device="cuda")
+    S.sem_render(ctx, tris, sum(counts), counts, None, cam, W, H, rgba, depth)
+    torch.cuda.synchronize()
+    return counts, tris[:sum(counts) * 9].clone(), rgba.clone(), depth.clone()
+
+
+def test_async_frame_equals_sync(gpu, sess):
+    S = gpu
+    w = si.tgv_box(nel=6)
+    isos = [0.05, 0.2, 0.4]
+    fr = Frame(S, sess.ctx, w, isos, cap=400000)
+    fr.run()
+    S.sem_synchronize(sess.ctx)
+    counts, tris, rgba, depth = _sync_reference(S, sess.ctx, fr.mesh, fr.vel, isos, w.camera)
+    starts = fr.counts.cpu().numpy()
+    assert list(np.diff(starts)) == counts and starts[0] == 0
+    assert torch.equal(fr.tris[:sum(counts) * 9], tris)
+    assert torch.equal(fr.rgba, rgba) and torch.equal(fr.depth, depth)
+    S.sem_mesh_free(fr.mesh)
+
+
+def test_graph_replay_on_new_snapshots(gpu, sess):
+    S = gpu
+    w = si.tgv_box(nel=6)
+    isos = [0.05, 0.2, 0.4]
+    fr = Frame(S, sess.ctx, w, isos, cap=400000)
+    fr.run()  # sizes the library's scratch before capture
+    S.sem_synchronize(sess.ctx)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        fr.run()
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    for snap in (1, 2):
+        ws = si.tgv_box(nel=6, snapshot=snap, phase=0.3 * snap)
+        for c in range(3):
+            fr.vel[c].copy_(ws.fields[c].float())
+        g.replay()
+        torch.cuda.synchronize()
+        S.sem_synchronize(sess.ctx)
+        g_rgba, g_depth = fr.rgba.clone(), fr.depth.clone()
+        counts, tris, rgba, depth = _sync_reference(S, sess.ctx, fr.mesh, fr.vel, isos, w.camera)
+        assert list(np.diff(fr.counts.cpu().numpy())) == counts
+        assert torch.equal(fr.tris[:sum(counts) * 9], tris)
+        fr.run()  # the same frame, eager
+        torch.cuda.synchronize()
+        assert torch.equal(g_rgba, rgba) and torch.equal(g_depth, depth), snap
+        assert torch.equal(fr.rgba, rgba) and torch.equal(fr.depth, depth), snap
+    S.sem_mesh_free(fr.mesh)
+
+
+def test_async_render_ignores_triangles_past_the_device_count(gpu, sess):
+    """The device count, not ntri_max, bounds the rasterised triangles: a buffer whose tail
+    holds valid triangles past the count renders like the synchronous call on the prefix
+    (the raster grid is sized by ntri_max, so most of its blocks have nothing to do)."""
+    S = gpu
+    w = si.tgv_box(nel=6)
+    fr = Frame(S, sess.ctx, w, [0.05, 0.2], cap=200000)
+    fr.run()
+    S.sem_synchronize(sess.ctx)
+    n = int(fr.counts[-1])
+    keep = n // 5
+    cam, W, H = w.camera, w.camera["W"], w.camera["H"]
+    for k in (0, 1, keep, n):
+        cnt = torch.tensor([0, min(k, int(fr.counts[1])), k], dtype=torch.int64, device="cuda")
+        rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+        depth = torch.zeros(H * W, device="cuda")
+        S.sem_render_async(sess.ctx, fr.tris, n, cnt, 2, None, cam, W, H, rgba, depth)
+        segs = [int(cnt[1]), k - int(cnt[1])]
+        r2 = torch.zeros_like(rgba)
+        d2 = torch.zeros_like(depth)
+        torch.cuda.synchronize()
+        S.sem_render(sess.ctx, fr.tris[:max(k, 1) * 9].clone(), k, segs, None, cam, W, H, r2, d2)
+        torch.cuda.synchronize()
+        assert torch.equal(rgba, r2) and torch.equal(depth, d2), k
+        if k == 0:
+            assert (rgba == 0).all() and (depth == 1.0).all()
+    S.sem_mesh_free(fr.mesh)
+
+
+def test_async_overflow_is_flagged_and_writes_nothing(gpu, sess):
+    S = gpu
+    w = si.tgv_box(nel=4)
+    fr = Frame(S, sess.ctx, w, [0.1], cap=50)
+    S.sem_qcriterion(sess.ctx, fr.mesh, *fr.vel, fr.Q)
+    S.sem_isosurface_multi_async(sess.ctx, fr.mesh, fr.Q, [0.1], fr.tris, fr.counts, cap=50)
+    with pytest.raises(S.SemError) as ex:
+        S.sem_synchronize(sess.ctx)
+    assert ex.value.status == S.SEM_ERR_CAPACITY
+    assert fr.counts[-1].item() > 50
+    assert (fr.tris == -1.0).all()
+    S.sem_synchronize(sess.ctx)  # the flag was cleared
+    S.sem_mesh_free(fr.mesh)
+
+
+def test_batched_partitions_mixed_orders_one_graph(gpu, sess, orc):
+    """Partitions of uneven element counts and orders N in {5, 7, 9}, two fields (Q and the
+    x-velocity) x 4 isovalues each, all captured in one CUDA graph per time step; checked
+    against the oracle's isosurfaces (cases are bit-exact, so triangle counts match)."""
+    S = gpu
+    rng = np.random.default_rng(si.seed_for(4))
+    parts = []
+    for p in range(5):
+        N = int(rng.choice([5, 7, 9]))
+        nel = (int(rng.integers(2, 5)), int(rng.integers(2, 5)), int(rng.integers(1, 4)))
+        lo = np.array([p * 1.3, 0.0, 0.0])
+        mesh = si.uniform_box(nel, lo, lo + np.array([1.2, 1.5, 1.1]), N)
+        vel = si.taylor_green(mesh, 1e-3, si.seed_for(4, p), phase=0.2 * p)
+        cam = si.box_camera_persp(lo, lo + np.array([1.2, 1.5, 1.1]), 96, 64)
+        parts.append((mesh, vel, cam))
+    frames = []
+    for mesh, vel, cam in parts:
+        w = si.Workload("part", 4, mesh, [], cam, vel)
+        f = Frame(S, sess.ctx, w, [-0.2, -0.05, 0.05, 0.2], cap=200000)
+        f.ufield = f.vel[0]
+        f.tris2 = torch.zeros(200000 * 9, device="cuda")
+        f.counts2 = torch.zeros(5, dtype=torch.int64, device="cuda")
+        frames.append(f)
+
+    def step():
+        for f in frames:
+            f.run()
+            S.sem_isosurface_multi_async(sess.ctx, f.mesh, f.ufield, [-0.5, 0.0, 0.25, 0.5], f.tris2, f.counts2)
+
+    step()
+    S.sem_synchronize(sess.ctx)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        step()
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    for f in frames:
+        f.Q.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    S.sem_synchronize(sess.ctx)
+    for f, (mesh, vel, cam) in zip(frames, parts):
+        xyz = mesh.xyz().numpy()
+        for field, isos, counts in ((host64(f.Q), f.isos, f.counts), (host64(f.ufield), [-0.5, 0.0, 0.25, 0.5],
+                                                                      f.counts2)):
+            c = counts.cpu().numpy()
+            for q, iso in enumerate(isos):
+                ref = orc.isosurface(mesh.N, xyz, field, float(np.float32(iso)), want_tris=False)
+                assert c[q + 1] - c[q] == ref["ntri"], (mesh.N, q)
+        S.sem_mesh_free(f.mesh)
