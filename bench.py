@@ -38,9 +38,26 @@ KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_iso_emit_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
                   "k_raster_small": "paper_2312_09888_gb300/csrc/sem_render.cu",
                   "k_resolve": "paper_2312_09888_gb300/csrc/sem_render.cu"}
-# kernels the library launches per step: qcriterion 1; multi-isovalue count + 3 scan + emit = 5;
-# render small + large + resolve = 3
-LAUNCHES_PER_STEP = 1 + 5 + 3
+
+
+def algorithmic_bytes(name, P):
+    """Bytes a kernel must move per launch at the least (each input read once, each output
+    written once), for the roofline of the step's kernels."""
+    NP3 = (P.w.mesh.N + 1) ** 3
+    niso = len(P.isos)
+    table = {
+        # u, v, w read (12 B/node) + Q written (4 B/node)
+        "k_sem_grad": 16 * P.npts,
+        # the field read once for all isovalues + one int32 count per element and isovalue
+        "k_iso_count_m": 4 * P.npts + 4 * P.E * niso,
+        # the active elements' field read + 36 B per triangle written + the offsets read
+        "k_iso_emit_m": 4 * NP3 * P.active_elems + 36 * P.last_ntri + 8 * (niso * P.E + 1),
+        # 36 B per triangle read (the 64-bit depth keys live in L2)
+        "k_raster_small": 36 * P.last_ntri,
+        # key read 8 B + RGBA 4 B + depth 4 B per pixel, and the winner's 36 B triangle per covered pixel
+        "k_resolve": 16 * P.W * P.H + 36 * P.covered,
+    }
+    return table.get(name)
 
 
 def _dist():
@@ -108,14 +125,28 @@ class Clocks:
         self.path = None
 
     def start(self):
+        """Start sampling every 20 ms; returns once the first sample is written, so that the
+        samples that follow fall inside the region timed next."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            t_end = time.time() + 10.0
+            while time.time() < t_end and self.proc.poll() is None and not self._rows():
+                time.sleep(0.01)
+            self.skip = len(self._rows())
         except Exception:
             self.proc = None
+
+    def _rows(self):
+        rows = []
+        for ln in open(self.path):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        return rows
 
     def stop(self):
         if self.proc is None:
@@ -125,12 +156,10 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for ln in open(self.path):
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) >= 9:
-                rows.append(f)
+        rows = self._rows()
         os.unlink(self.path)
+        # samples taken while the timed region ran (at least the last one before it ended)
+        rows = rows[self.skip:] or rows[-1:]
         if not rows:
             return None
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
@@ -177,6 +206,13 @@ class Pipeline:
         self.ev = None
         self.counts_dev = torch.zeros(len(self.isos) + 1, dtype=torch.int64, device="cuda")
         self.graph = None
+        # elements holding a triangle of some isovalue (the emit pass reads only those)
+        te = torch.empty(self.cap, dtype=torch.int32, device="cuda")
+        S.sem_isosurface_multi(self.ctx, self.mesh, self.Q, self.isos, self.tris, tri_elem=te, cap=self.cap)
+        self.active_elems = int(torch.unique(te[:sum(counts)]).numel())
+        del te
+        self.covered = 0
+        self.last_ntri = sum(counts)
 
     def step_async(self):
         """The same step without host synchronisation (device-side triangle counts)."""
@@ -242,9 +278,13 @@ def run_ours(args):
         P.step()
     stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     barrier()
+    S.sem_trace_enable(P.ctx, True)
     for k in range(K):
         P.step(stage_ev[k])
     barrier()
+    trace = S.sem_trace_collect(P.ctx)
+    S.sem_trace_enable(P.ctx, False)
+    P.covered = int((P.rgba.view(-1, 4)[:, 3] > 0).sum())
     stage_ms = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in stage_ev])
     eager_ms = float(stage_ms.sum(axis=1).mean())
     # headline: the whole step as one CUDA graph, replayed K times (device-resident inputs)
@@ -301,7 +341,8 @@ def run_ours(args):
                "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4),
                "ms_per_step": es * 1e3 / K}
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel: its CUDA-event launch time from the library's kernel trace
+    # (events on the library's stream around each launch, eager steps above)
     mean_stage = stage_ms.mean(axis=0)
     peaks = {}
     pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -310,13 +351,25 @@ def run_ours(args):
     hbm_peak = peaks.get("hbm_gbs")
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
-    q_ms = float(mean_stage[0])
-    q_bytes = 16 * P.npts   # read u, v, w (12 B/node) + write Q (4 B/node)
-    achieved = q_bytes / (q_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_sem_grad<8,3> (sem_qcriterion)", "bound": "hbm", "achieved": round(achieved, 1),
-            "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
-            "traffic": _traffic_for("k_sem_grad"), "algorithmic_bytes_per_launch": q_bytes,
-            "launch_ms": round(q_ms, 5)}
+    kernels = {}
+    for name, (tot_ms, n) in trace.items():
+        kb = algorithmic_bytes(name, P)
+        ent = {"ms_per_step": round(tot_ms / K, 5), "launches_per_step": n / K}
+        if kb is not None and n:
+            gbs = kb / (tot_ms / n * 1e-3) / 1e9
+            ent.update({"algorithmic_bytes_per_launch": int(kb), "achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / hbm_peak, 4)})
+        kernels[name] = ent
+    dom = max(trace, key=lambda k: trace[k][0])
+    dom_ms = trace[dom][0] / trace[dom][1]
+    dom_bytes = algorithmic_bytes(dom, P)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+            "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": round(achieved / hbm_peak, 4) if achieved else None,
+            "traffic": _traffic_for(dom), "algorithmic_bytes_per_launch": dom_bytes,
+            "launch_ms": round(dom_ms, 5)}
+    launches_per_step = sum(n for _, n in trace.values()) / K
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -336,7 +389,7 @@ def run_ours(args):
                         "isosurface_all": round(float(mean_stage[1]), 4),
                         "render": round(float(mean_stage[2]), 4), "eager_step": round(eager_ms, 4)},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-           "gpu_launches": LAUNCHES_PER_STEP * K}
+           "kernels": kernels, "gpu_launches": int(round(launches_per_step * K))}
     P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -425,8 +478,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of the captured graph")

@@ -115,6 +115,17 @@ SEM_API sem_status sem_set_stream(sem_ctx *ctx, void *stream);
  * (SEM_ERR_TIMEOUT) and clear it. */
 SEM_API sem_status sem_synchronize(sem_ctx *ctx);
 
+/* Kernel trace (instrumentation; no counterpart in the paper).  While on, every kernel the
+ * library launches on the context's stream outside a stream capture is bracketed by a pair of
+ * CUDA events on that stream.  sem_trace_collect waits for the recorded launches, sums their
+ * device time per kernel name (in first-launch order) and returns the number of kernels in
+ * *n_kernels; sem_trace_entry reads entry k: *name (a static string owned by the library),
+ * the summed milliseconds and the launch count.  Collecting clears the record.  Tracing adds
+ * two event records per launch and is off by default. */
+SEM_API sem_status sem_trace_enable(sem_ctx *ctx, int on);
+SEM_API sem_status sem_trace_collect(sem_ctx *ctx, int *n_kernels);
+SEM_API sem_status sem_trace_entry(sem_ctx *ctx, int k, const char **name, double *total_ms, int64_t *launches);
+
 /* Load a mesh of E hexahedral elements of order N (1 <= N <= SEM_MAX_ORDER).
  * xyz_host: HOST array of 3*E*(N+1)^3 doubles, SoA x | y | z, node order as above; copied.
  * Each element must be an axis-aligned affine box (x depends only on i, y on j, z on k, with

@@ -57,6 +57,9 @@ def _declare(L):
     L.sem_last_error.restype = C.c_char_p
     L.sem_set_stream.argtypes = [vp, vp]
     L.sem_synchronize.argtypes = [vp]
+    L.sem_trace_enable.argtypes = [vp, i32]
+    L.sem_trace_collect.argtypes = [vp, C.POINTER(i32)]
+    L.sem_trace_entry.argtypes = [vp, i32, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64)]
     L.sem_load_mesh.argtypes = [vp, i32, i64, vp, C.POINTER(vp)]
     L.sem_mesh_free.argtypes = [vp]
     L.sem_mesh_free.restype = None
@@ -161,6 +164,23 @@ def sem_set_stream(ctx, stream) -> None:
 
 def sem_synchronize(ctx) -> None:
     _check(ctx, get_lib().sem_synchronize(ctx))
+
+
+def sem_trace_enable(ctx, on: bool = True) -> None:
+    _check(ctx, get_lib().sem_trace_enable(ctx, 1 if on else 0))
+
+
+def sem_trace_collect(ctx) -> dict:
+    """{kernel name: (summed device ms, launches)} of the launches traced since the last call."""
+    L = get_lib()
+    n = C.c_int32(0)
+    _check(ctx, L.sem_trace_collect(ctx, C.byref(n)))
+    out = {}
+    for k in range(n.value):
+        name, ms, cnt = C.c_char_p(), C.c_double(0), C.c_int64(0)
+        _check(ctx, L.sem_trace_entry(ctx, k, C.byref(name), C.byref(ms), C.byref(cnt)))
+        out[name.value.decode()] = (ms.value, cnt.value)
+    return out
 
 
 def sem_load_mesh(ctx, N: int, xyz) -> C.c_void_p:

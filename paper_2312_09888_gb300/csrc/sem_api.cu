@@ -311,6 +311,11 @@ void sem_destroy(sem_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (auto &r : ctx->trace) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t ev : ctx->trace_pool) cudaEventDestroy(ev);
     for (int s = 0; s < 4; ++s)
         if (ctx->scratch[s]) cudaFree(ctx->scratch[s]);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
@@ -319,6 +324,73 @@ void sem_destroy(sem_ctx *ctx)
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
     delete ctx;
+}
+
+// ------------------------------------------------------------------------------------------
+// Kernel trace
+// ------------------------------------------------------------------------------------------
+TraceScope::TraceScope(sem_ctx *c, const char *name) : ctx(c)
+{
+    if (!c->trace_on) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    sem_ctx::TraceRec r{name, nullptr, nullptr};
+    for (cudaEvent_t *ev : {&r.a, &r.b}) {
+        if (!c->trace_pool.empty()) {
+            *ev = c->trace_pool.back();
+            c->trace_pool.pop_back();
+        } else if (cudaEventCreate(ev) != cudaSuccess) {
+            return;  // tracing is best effort: an event that cannot be made skips this launch
+        }
+    }
+    if (cudaEventRecord(r.a, c->stream) != cudaSuccess) return;
+    c->trace.push_back(r);
+    idx = (int)c->trace.size() - 1;
+}
+
+TraceScope::~TraceScope()
+{
+    if (idx >= 0) cudaEventRecord(ctx->trace[idx].b, ctx->stream);
+}
+
+sem_status sem_trace_enable(sem_ctx *ctx, int on)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    ctx->trace_on = on != 0;
+    return SEM_OK;
+}
+
+sem_status sem_trace_collect(sem_ctx *ctx, int *n_kernels)
+{
+    if (!ctx || !n_kernels) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    ctx->trace_sum.clear();
+    for (auto &r : ctx->trace) {
+        SEM_CU(ctx, cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        SEM_CU(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+        size_t k = 0;
+        while (k < ctx->trace_sum.size() && strcmp(ctx->trace_sum[k].name, r.name) != 0) ++k;
+        if (k == ctx->trace_sum.size()) ctx->trace_sum.push_back({r.name, 0.0, 0});
+        ctx->trace_sum[k].ms += ms;
+        ctx->trace_sum[k].launches += 1;
+        ctx->trace_pool.push_back(r.a);
+        ctx->trace_pool.push_back(r.b);
+    }
+    ctx->trace.clear();
+    *n_kernels = (int)ctx->trace_sum.size();
+    return SEM_OK;
+}
+
+sem_status sem_trace_entry(sem_ctx *ctx, int k, const char **name, double *total_ms, int64_t *launches)
+{
+    if (!ctx || !name || !total_ms || !launches) return SEM_ERR_ARG;
+    if (k < 0 || k >= (int)ctx->trace_sum.size())
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_trace_entry: index %d outside [0, %d)", k, (int)ctx->trace_sum.size());
+    *name = ctx->trace_sum[k].name;
+    *total_ms = ctx->trace_sum[k].ms;
+    *launches = ctx->trace_sum[k].launches;
+    return SEM_OK;
 }
 
 sem_status sem_set_stream(sem_ctx *ctx, void *stream)

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/sem.h"
 
@@ -28,7 +29,35 @@ struct sem_ctx {
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
     void *tc_A[2] = {nullptr, nullptr};
+    // kernel trace: an event pair around every launch while tracing is on (not while the
+    // stream is being captured); collected per kernel name by sem_trace_collect
+    bool trace_on = false;
+    struct TraceRec {
+        const char *name;
+        cudaEvent_t a, b;
+    };
+    std::vector<TraceRec> trace;
+    std::vector<cudaEvent_t> trace_pool;
+    struct TraceSum {
+        const char *name;
+        double ms;
+        int64_t launches;
+    };
+    std::vector<TraceSum> trace_sum;
 };
+
+// Records ctx's trace events around the launch in its scope (see SEM_TRACED).
+struct TraceScope {
+    sem_ctx *ctx;
+    int idx = -1;
+    TraceScope(sem_ctx *c, const char *name);
+    ~TraceScope();
+};
+#define SEM_TRACED(ctx, name, ...) \
+    do {                           \
+        TraceScope sem_ts_(ctx, name); \
+        __VA_ARGS__;               \
+    } while (0)
 
 struct sem_mesh {
     int N = 0;

@@ -32,6 +32,8 @@ struct IsoW {
 __constant__ float c_s[(SEM_MAX_ORDER + 1) * MP];        // (xi+1)/2 per order
 __constant__ uint8_t c_ntri[256];
 __constant__ int8_t c_edge[256 * ISO_MAXT * 3];
+// per (case, triangle): the corner pairs (lo | hi << 3) of its three edges, 6 bits each
+__constant__ uint32_t c_tri_corners[256 * ISO_MAXT];
 
 sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *ntri, const int8_t *edges)
 {
@@ -42,6 +44,21 @@ sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *nt
         n8[c] = (uint8_t)ntri[c];
         for (int q = 0; q < ISO_MAXT * 3; ++q) e8[c * ISO_MAXT * 3 + q] = edges[c * SEM_MC_MAXT * 3 + q];
     }
+    // edge e -> (lower corner, upper corner) in lexicographic edge order
+    static const int kLo[12] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 5, 6}, kHi[12] = {1, 2, 4, 3, 5, 3, 6, 7, 5, 6, 7, 7};
+    uint32_t tc[256 * ISO_MAXT];
+    for (int c = 0; c < 256; ++c)
+        for (int t = 0; t < ISO_MAXT; ++t) {
+            uint32_t x = 0;
+            if (t < ntri[c])
+                for (int v = 0; v < 3; ++v) {
+                    const int e = e8[(c * ISO_MAXT + t) * 3 + v];
+                    if (e < 0 || e > 11) return sem_fail(ctx, SEM_ERR_CUDA, "case table edge %d out of range", e);
+                    x |= (uint32_t)(kLo[e] | (kHi[e] << 3)) << (6 * v);
+                }
+            tc[c * ISO_MAXT + t] = x;
+        }
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_tri_corners, tc, sizeof tc));
     SEM_CU(ctx, cudaMemcpyToSymbol(c_s, s_all, sizeof(float) * (SEM_MAX_ORDER + 1) * MP));
     SEM_CU(ctx, cudaMemcpyToSymbol(c_ntri, n8, sizeof n8));
     SEM_CU(ctx, cudaMemcpyToSymbol(c_edge, e8, sizeof e8));
@@ -221,144 +238,159 @@ struct IsoSet {
     float iso[SEM_MAX_ISO];
 };
 
-// per-warp dynamic shared memory of the emit kernel: the element's field, the triangle map and
-// the cell cases; warps (elements) per block: up to 8 within ~96 KB
+// Node masks.  For isovalue q, bit b of word w of the element's mask is [f_n >= iso_q] for node
+// n = 32w + b (NaN is never inside).  One warp ballot makes one word, so the masks come out of
+// the coalesced load of the element at one vote per 32 nodes and isovalue, and the same votes
+// cull the element: it is active for q iff some node is inside and some is not.
 template <int NP>
-struct EmitW {
-    static constexpr int NP3 = NP * NP * NP, N3 = (NP - 1) * (NP - 1) * (NP - 1);
-    static constexpr int F_BYTES = 4 * NP3;
-    static constexpr int MAP_BYTES = ((2 * N3 * ISO_MAXT + 15) / 16) * 16;
-    static constexpr int CASE_BYTES = ((N3 + 15) / 16) * 16;
-    static constexpr int B = F_BYTES + MAP_BYTES + CASE_BYTES;
-    static constexpr int R = 98304 / B;
-    static constexpr int V = R < 1 ? 1 : (R > 8 ? 8 : R);
+struct MaskGeo {
+    static constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N, NRP = N * N;
+    static constexpr int NW = (NP3 + 31) / 32;
+    static constexpr int MW = NW + 1;  // one zero word of padding for the funnel shift below
 };
 
+// Loads element fe (and copies it to sf unless null); writes the masks of all S.niso isovalues
+// to m[q * MW + w]; returns the activity bits of the isovalues.
 template <int NP>
-__device__ __forceinline__ void load_minmax(const float *__restrict__ fe, float *__restrict__ sf, int lane, float &mn,
-                                            float &mx, bool &has_nan)
+__device__ __forceinline__ unsigned load_masks(const float *__restrict__ fe, float *__restrict__ sf, const IsoSet &S,
+                                               uint32_t *__restrict__ m, int lane)
 {
-    constexpr int NP3 = NP * NP * NP;
-    float a = INFINITY, b = -INFINITY;
-    bool nn = false;
-    if constexpr (NP3 % 128 == 0) {
-        const float4 *f4 = reinterpret_cast<const float4 *>(fe);
-        float4 *s4 = reinterpret_cast<float4 *>(sf);
+    using G = MaskGeo<NP>;
+    // loads in chunks of up to 16 words, all issued before the chunk's votes
+    constexpr int CH = G::NW < 16 ? G::NW : 16;
+    unsigned any_in = 0, not_all = 0;
+    for (int w0 = 0; w0 < G::NW; w0 += CH) {
+        float v[CH];
 #pragma unroll
-        for (int q = 0; q < NP3 / 128; ++q) {
-            const float4 v = __ldg(f4 + q * 32 + lane);
-            s4[q * 32 + lane] = v;
-            a = fminf(a, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
-            b = fmaxf(b, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-            nn |= isnan(v.x) | isnan(v.y) | isnan(v.z) | isnan(v.w);
+        for (int c = 0; c < CH; ++c) {
+            const int w = w0 + c, n = w * 32 + lane;
+            const bool valid = (G::NW % CH == 0 || w < G::NW) && ((G::NP3 % 32 == 0) || n < G::NP3);
+            v[c] = valid ? __ldg(fe + n) : 0.f;
         }
-    } else {
-        for (int idx = lane; idx < NP3; idx += 32) {
-            const float v = __ldg(fe + idx);
-            sf[idx] = v;
-            a = fminf(a, v);
-            b = fmaxf(b, v);
-            nn |= isnan(v);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int w = w0 + c, n = w * 32 + lane;
+            if (G::NW % CH != 0 && w >= G::NW) break;
+            const bool valid = (G::NP3 % 32 == 0) || n < G::NP3;
+            if (sf && valid) sf[n] = v[c];
+            const uint32_t vmask = (G::NP3 % 32 == 0 || w < G::NW - 1) ? ~0u : ((1u << (G::NP3 % 32)) - 1u);
+#pragma unroll
+            for (int q = 0; q < SEM_MAX_ISO; ++q) {
+                if (q >= S.niso) break;
+                const uint32_t b = __ballot_sync(0xffffffffu, valid && v[c] >= S.iso[q]);
+                if (lane == 0) m[q * G::MW + w] = b;
+                any_in |= (b != 0u ? 1u : 0u) << q;
+                not_all |= ((b | ~vmask) != ~0u ? 1u : 0u) << q;
+            }
         }
     }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        a = fminf(a, __shfl_xor_sync(0xffffffffu, a, d));
-        b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, d));
-    }
-    mn = a;
-    mx = b;
-    has_nan = __any_sync(0xffffffffu, nn);
+    if (lane < S.niso) m[lane * G::MW + G::NW] = 0u;
+    return any_in & not_all;
 }
+
+// The NP inside-bits of node row (k, j) (nodes i = 0..N along r).
+template <int NP>
+__device__ __forceinline__ uint32_t row_bits(const uint32_t *__restrict__ m, int k, int j)
+{
+    const int o = (k * NP + j) * NP;
+    if constexpr (NP == 8) return reinterpret_cast<const uint8_t *>(m)[o >> 3];
+    else if constexpr (NP == 16) return reinterpret_cast<const uint16_t *>(m)[o >> 4];
+    else return __funnelshift_r(m[o >> 5], m[(o >> 5) + 1], o & 31) & ((1u << NP) - 1u);
+}
+
+// Cells (i, j, k), i = 0..N-1, of the row pair (j, k) whose corners are neither all inside nor
+// all outside, from the four node rows that bound them.
+template <int NP>
+__device__ __forceinline__ uint32_t cut_cells(uint32_t r00, uint32_t r01, uint32_t r10, uint32_t r11)
+{
+    const uint32_t A = r00 & r01 & r10 & r11, O = r00 | r01 | r10 | r11;
+    return (O | (O >> 1)) & ~(A & (A >> 1)) & ((1u << (NP - 1)) - 1u);
+}
+
+// case of cell i of the row pair: corner v = a + 2b + 4c is bit (i + a) of row (k + c, j + b)
+__device__ __forceinline__ int pair_case(uint32_t r00, uint32_t r01, uint32_t r10, uint32_t r11, int i)
+{
+    return (int)(((r00 >> i) & 3u) | (((r01 >> i) & 3u) << 2) | (((r10 >> i) & 3u) << 4) | (((r11 >> i) & 3u) << 6));
+}
+
+#define COUNT_WARPS 8
 
 template <int NP>
-__device__ __forceinline__ void cell_corners(const float *__restrict__ sf, int c, float (&v)[8], int &i, int &j, int &k)
-{
-    constexpr int N = NP - 1;
-    i = c % N;
-    j = (c / N) % N;
-    k = c / (N * N);
-    const int b = (k * NP + j) * NP + i;
-    v[0] = sf[b];
-    v[1] = sf[b + 1];
-    v[2] = sf[b + NP];
-    v[3] = sf[b + NP + 1];
-    v[4] = sf[b + NP * NP];
-    v[5] = sf[b + NP * NP + 1];
-    v[6] = sf[b + NP * NP + NP];
-    v[7] = sf[b + NP * NP + NP + 1];
-}
-
-__device__ __forceinline__ int corner_case(const float (&v)[8], float iso)
-{
-    int cs = 0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cs |= (v[q] >= iso) << q;
-    return cs;
-}
-
-template <int NP>
-__global__ void __launch_bounds__(32 * IsoW<NP>::V) k_iso_count_m(const float *__restrict__ f,
+__global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
                                                                  int32_t *__restrict__ cnt, uint8_t *__restrict__ cases)
 {
-    constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N;
-    __shared__ __align__(16) float s_f[IsoW<NP>::V][NP3];
+    using G = MaskGeo<NP>;
+    constexpr int N = G::N, N3 = G::N3, MW = G::MW;
+    __shared__ uint32_t s_m[COUNT_WARPS][SEM_MAX_ISO * MW];
     __shared__ uint8_t s_nt[256];
     for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = (int64_t)blockIdx.x * IsoW<NP>::V + w;
+    const int64_t e = (int64_t)blockIdx.x * COUNT_WARPS + w;
     if (e >= E) return;
-    float *sf = s_f[w];
-    float mn, mx;
-    bool has_nan;
-    load_minmax<NP>(f + e * NP3, sf, lane, mn, mx, has_nan);
-    unsigned active = 0;
+    uint32_t *m = s_m[w];
+    const unsigned active = load_masks<NP>(f + e * G::NP3, nullptr, S, m, lane);
+    __syncwarp();
     for (int q = 0; q < S.niso; ++q) {
-        const bool any_in = mx >= S.iso[q], any_out = (mn < S.iso[q]) || has_nan;
-        if (any_in && any_out) {
-            active |= 1u << q;
-        } else {
+        const uint32_t *mq = m + q * MW;
+        if (!((active >> q) & 1u)) {
             if (lane == 0) cnt[q * E + e] = 0;
             if (cases) {
-                const uint8_t v = any_in ? 255 : 0;
+                const uint8_t v = (mq[0] & 1u) ? 255 : 0;  // every node on the same side as node 0
                 for (int c = lane; c < N3; c += 32) cases[(q * E + e) * N3 + c] = v;
             }
+            continue;
         }
-    }
-    if (!active) return;
-    __syncwarp();
-    int acc[SEM_MAX_ISO];
-#pragma unroll
-    for (int q = 0; q < SEM_MAX_ISO; ++q) acc[q] = 0;
-    for (int c = lane; c < N3; c += 32) {
-        float v[8];
-        int i, j, k;
-        cell_corners<NP>(sf, c, v, i, j, k);
-#pragma unroll
-        for (int q = 0; q < SEM_MAX_ISO; ++q) {
-            if (!((active >> q) & 1u)) continue;
-            const int cs = corner_case(v, S.iso[q]);
-            acc[q] += s_nt[cs];
-            if (cases) cases[(q * E + e) * N3 + c] = (uint8_t)cs;
+        int acc = 0;
+        for (int rp = lane; rp < G::NRP; rp += 32) {
+            const int j = rp % N, k = rp / N;
+            const uint32_t r00 = row_bits<NP>(mq, k, j), r01 = row_bits<NP>(mq, k, j + 1);
+            const uint32_t r10 = row_bits<NP>(mq, k + 1, j), r11 = row_bits<NP>(mq, k + 1, j + 1);
+            if (cases)
+                for (int i = 0; i < N; ++i) cases[(q * E + e) * N3 + i + N * rp] = (uint8_t)pair_case(r00, r01, r10, r11, i);
+            for (uint32_t act = cut_cells<NP>(r00, r01, r10, r11); act; act &= act - 1u)
+                acc += s_nt[pair_case(r00, r01, r10, r11, __ffs(act) - 1)];
         }
-    }
 #pragma unroll
-    for (int q = 0; q < SEM_MAX_ISO; ++q) {
-        if (!((active >> q) & 1u)) continue;
-        int a = acc[q];
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
-        if (lane == 0) cnt[q * E + e] = a;
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (lane == 0) cnt[q * E + e] = acc;
     }
 }
 
-// One warp per element.  For each isovalue: (1) 32 cells at a time, classify, warp-scan the
-// triangle counts and write, for every triangle of the element, its (cell, index in cell)
-// into a shared-memory map; (2) give each lane one output triangle: lane L takes triangles
-// L, L+32, ... of the element, reads its cell from the map and writes it.  Every lane does
-// one triangle's work and consecutive lanes write consecutive triangles.
+// per-warp dynamic shared memory of the emit kernel: the element's field, a window of the
+// triangle map, the mask of one isovalue, the element's node coordinates and a store staging
+// area; warps per block: up to 8 within ~96 KB
+#define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
+#define EMIT_CHUNK 4     // (element, isovalue) units a warp takes per atomic
+template <int NP>
+struct EmitW {
+    using G = MaskGeo<NP>;
+    static constexpr int r16(int b) { return ((b + 15) / 16) * 16; }
+    static constexpr int F_BYTES = r16(4 * G::NP3);
+    static constexpr int MAP_BYTES = 4 * EMIT_MAPCAP;
+    static constexpr int M_BYTES = r16(4 * G::MW);
+    static constexpr int X_BYTES = r16(4 * 3 * NP);
+    static constexpr int STG_BYTES = 32 * 9 * 4;
+    static constexpr int B = F_BYTES + MAP_BYTES + M_BYTES + X_BYTES + STG_BYTES;
+    static constexpr int R = 98304 / B;
+    static constexpr int V = R < 1 ? 1 : (R > 8 ? 8 : R);
+};
+
+// node offset of corner v = a + 2b + 4c from the cell's corner 0
+template <int NP>
+__device__ __forceinline__ int corner_off(int v)
+{
+    return (v & 1) + ((v >> 1) & 1) * NP + (v >> 2) * NP * NP;
+}
+
+// Persistent warps over (element, isovalue) units u = q E + e, EMIT_CHUNK units per atomic
+// on a counter the host zeroes before the launch.  For a unit with triangles: load the element
+// and its mask, then per window of EMIT_MAPCAP triangles (1) lane per row pair, find the cut
+// cells, warp-scan their triangle counts and write each triangle's packed (case, cell, index
+// in cell) into the map, in cell order; (2) lane per output triangle: interpolate its three
+// vertices, stage them, and store each round of 32 triangles (1152 contiguous bytes) with
+// coalesced 4-byte stores.
 template <int NP>
 __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
@@ -367,100 +399,152 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                                                                  const float4 *__restrict__ bhi,
                                                                  float *__restrict__ tris,
                                                                  int32_t *__restrict__ tri_elem, int64_t cap,
-                                                                 int *flag)
+                                                                 int *flag, unsigned long long *__restrict__ next)
 {
-    constexpr int NP3 = NP * NP * NP, N = NP - 1, N3 = N * N * N;
     using EW = EmitW<NP>;
+    using G = MaskGeo<NP>;
+    constexpr int N = G::N;
+    const int64_t U = (int64_t)S.niso * E;
     // all-or-nothing capacity check (the host-synchronised path has checked already)
-    if (offs[S.niso * E] > cap) {
+    if (offs[U] > cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicOr(flag, 1 << SEM_ERR_CAPACITY);
         return;
     }
-    constexpr int WV = EW::V;
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint8_t s_nt[256];
-    __shared__ int8_t s_ed[256 * ISO_MAXT * 3];
+    __shared__ uint32_t s_tc[256 * ISO_MAXT];
     __shared__ float s_s[NP];
     for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
-    for (int t = threadIdx.x; t < 256 * ISO_MAXT * 3; t += blockDim.x) s_ed[t] = c_edge[t];
+    for (int t = threadIdx.x; t < 256 * ISO_MAXT; t += blockDim.x) s_tc[t] = c_tri_corners[t];
     if (threadIdx.x < NP) s_s[threadIdx.x] = c_s[(NP - 1) * MP + threadIdx.x];
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = (int64_t)blockIdx.x * WV + w;
-    if (e >= E) return;
-    unsigned active = 0;
-    for (int q = 0; q < S.niso; ++q)
-        if (offs[q * E + e + 1] != offs[q * E + e]) active |= 1u << q;
-    if (!active) return;
     unsigned char *mine = s_dyn + (size_t)w * EW::B;
     float *sf = reinterpret_cast<float *>(mine);
-    uint16_t *map = reinterpret_cast<uint16_t *>(mine + EW::F_BYTES);  // (cell << 3) | index in cell
-    uint8_t *sc = mine + EW::F_BYTES + EW::MAP_BYTES;
-    {
-        float mn, mx;
-        bool hn;
-        load_minmax<NP>(f + e * NP3, sf, lane, mn, mx, hn);
-    }
-    __syncwarp();
-    const float4 L = blo[e], H = bhi[e];
-    for (int q = 0; q < S.niso; ++q) {
-        if (!((active >> q) & 1u)) continue;
-        const float iso = S.iso[q];
-        // (1) cases and the triangle -> (cell, index) map, in cell order
-        int running = 0;
-        for (int c0 = 0; c0 < N3; c0 += 32) {
-            const int c = c0 + lane;
-            int cs = 0, nt = 0;
-            if (c < N3) {
-                float v[8];
-                int i, j, k;
-                cell_corners<NP>(sf, c, v, i, j, k);
-                cs = corner_case(v, iso);
-                nt = s_nt[cs];
-                sc[c] = (uint8_t)cs;
+    uint32_t *map = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES);  // cs << 16 | k << 12 | j << 8 | i << 4 | t
+    uint32_t *m = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES + EW::MAP_BYTES);
+    float *X = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES);
+    float *Y = X + NP, *Z = X + 2 * NP;
+    float *stg = reinterpret_cast<float *>(mine + EW::B - EW::STG_BYTES);
+    IsoSet S1;  // the unit's isovalue alone, for load_masks
+    S1.niso = 1;
+    for (;;) {
+        unsigned long long u0 = 0;
+        if (lane == 0) u0 = atomicAdd(next, (unsigned long long)EMIT_CHUNK);
+        u0 = __shfl_sync(0xffffffffu, u0, 0);
+        if (u0 >= (unsigned long long)U) break;
+        const int64_t u1 = min((int64_t)u0 + EMIT_CHUNK, U);
+        for (int64_t u = (int64_t)u0; u < u1; ++u) {
+            const int64_t o = offs[u], n = offs[u + 1] - o;
+            if (n <= 0 || o + n > cap) continue;
+            const int q = (int)(u / E);
+            const int64_t e = u - (int64_t)q * E;
+            const float iso = S.iso[q];
+            S1.iso[0] = iso;
+            __syncwarp();  // the previous unit's readers of sf, m and X are done
+            load_masks<NP>(f + e * G::NP3, sf, S1, m, lane);
+            if (lane < NP) {
+                // node coordinates: lerps of the element box with exact end points
+                const float4 L = blo[e], H = bhi[e];
+                const float s = s_s[lane];
+                X[lane] = fmaf(s, H.x, (1.f - s) * L.x);
+                Y[lane] = fmaf(s, H.y, (1.f - s) * L.y);
+                Z[lane] = fmaf(s, H.z, (1.f - s) * L.z);
             }
-            int incl = nt;
+            __syncwarp();
+            for (int64_t win = 0; win < n; win += EMIT_MAPCAP) {
+                // (1) the map entries of triangles win .. win + EMIT_MAPCAP - 1, in cell order
+                int running = 0;
+                for (int rp0 = 0; rp0 < G::NRP && running < win + EMIT_MAPCAP; rp0 += 32) {
+                    const int rp = rp0 + lane;
+                    uint32_t act = 0, r00 = 0, r01 = 0, r10 = 0, r11 = 0;
+                    int nt = 0, j = 0, k = 0;
+                    if (rp < G::NRP) {
+                        j = rp % N;
+                        k = rp / N;
+                        r00 = row_bits<NP>(m, k, j);
+                        r01 = row_bits<NP>(m, k, j + 1);
+                        r10 = row_bits<NP>(m, k + 1, j);
+                        r11 = row_bits<NP>(m, k + 1, j + 1);
+                        act = cut_cells<NP>(r00, r01, r10, r11);
+                        for (uint32_t a = act; a; a &= a - 1u) nt += s_nt[pair_case(r00, r01, r10, r11, __ffs(a) - 1)];
+                    }
+                    int incl = nt;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                if (lane >= d) incl += y;
-            }
-            const int first = running + incl - nt;
-            for (int t = 0; t < nt; ++t) map[first + t] = (uint16_t)((c << 3) | t);
-            running += __shfl_sync(0xffffffffu, incl, 31);
-        }
-        __syncwarp();
-        // (2) one output triangle per lane
-        const int64_t o = offs[q * E + e];
-        if (o + running <= cap) {
-            for (int idx = lane; idx < running; idx += 32) {
-                const int mc = map[idx];
-                const int c = mc >> 3, t = mc & 7, cs = sc[c];
-                const int i = c % N, j = (c / N) % N, k = c / (N * N);
-                float p[9];
-#pragma unroll
-                for (int sv = 0; sv < 3; ++sv) {
-                    int la, lb;
-                    edge_ends(s_ed[(cs * ISO_MAXT + t) * 3 + sv], la, lb);
-                    const int ia = i + (la & 1), ja = j + ((la >> 1) & 1), ka = k + ((la >> 2) & 1);
-                    const int ib = i + (lb & 1), jb = j + ((lb >> 1) & 1), kb = k + ((lb >> 2) & 1);
-                    const float fa = sf[(ka * NP + ja) * NP + ia], fb = sf[(kb * NP + jb) * NP + ib];
-                    const float tt = (iso - fa) / (fb - fa);
-                    const float xa = fmaf(s_s[ia], H.x, (1.f - s_s[ia]) * L.x), xb = fmaf(s_s[ib], H.x, (1.f - s_s[ib]) * L.x);
-                    const float ya = fmaf(s_s[ja], H.y, (1.f - s_s[ja]) * L.y), yb = fmaf(s_s[jb], H.y, (1.f - s_s[jb]) * L.y);
-                    const float za = fmaf(s_s[ka], H.z, (1.f - s_s[ka]) * L.z), zb = fmaf(s_s[kb], H.z, (1.f - s_s[kb]) * L.z);
-                    p[sv * 3 + 0] = fmaf(tt, xb - xa, xa);
-                    p[sv * 3 + 1] = fmaf(tt, yb - ya, ya);
-                    p[sv * 3 + 2] = fmaf(tt, zb - za, za);
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d) incl += y;
+                    }
+                    int slot = running + incl - nt - (int)win;
+                    for (uint32_t a = act; a; a &= a - 1u) {
+                        const int i = __ffs(a) - 1;
+                        const int cs = pair_case(r00, r01, r10, r11, i);
+                        const uint32_t key = ((uint32_t)cs << 16) | ((uint32_t)k << 12) | ((uint32_t)j << 8) | ((uint32_t)i << 4);
+                        const int nc = s_nt[cs];
+                        for (int t = 0; t < nc; ++t, ++slot)
+                            if (slot >= 0 && slot < EMIT_MAPCAP) map[slot] = key | (uint32_t)t;
+                    }
+                    running += __shfl_sync(0xffffffffu, incl, 31);
                 }
-                float *dst = tris + (o + idx) * 9;
+                __syncwarp();
+                // (2) one output triangle per lane, stored through the staging area
+                const int cnt = (int)min((int64_t)EMIT_MAPCAP, n - win);
+                for (int base = 0; base < cnt; base += 32) {
+                    const int idx = base + lane;
+                    if (idx < cnt) {
+                        const uint32_t key = map[idx];
+                        const int t = key & 15, i = (key >> 4) & 15, j = (key >> 8) & 15, k = (key >> 12) & 15;
+                        const int cs = key >> 16;
+                        const int c0 = (k * NP + j) * NP + i;
+                        const uint32_t pairs = s_tc[cs * ISO_MAXT + t];
 #pragma unroll
-                for (int r = 0; r < 9; ++r) dst[r] = p[r];
-                if (tri_elem) tri_elem[o + idx] = (int32_t)e;
+                        for (int sv = 0; sv < 3; ++sv) {
+                            const int la = (pairs >> (6 * sv)) & 7, lb = (pairs >> (6 * sv + 3)) & 7;
+                            const float fa = sf[c0 + corner_off<NP>(la)], fb = sf[c0 + corner_off<NP>(lb)];
+                            const float tt = __fdividef(iso - fa, fb - fa);
+                            const int ia = i + (la & 1), ja = j + ((la >> 1) & 1), ka = k + (la >> 2);
+                            const int ib = i + (lb & 1), jb = j + ((lb >> 1) & 1), kb = k + (lb >> 2);
+                            stg[lane * 9 + sv * 3 + 0] = fmaf(tt, X[ib] - X[ia], X[ia]);
+                            stg[lane * 9 + sv * 3 + 1] = fmaf(tt, Y[jb] - Y[ja], Y[ja]);
+                            stg[lane * 9 + sv * 3 + 2] = fmaf(tt, Z[kb] - Z[ka], Z[ka]);
+                        }
+                        if (tri_elem) tri_elem[o + win + idx] = (int32_t)e;
+                    }
+                    __syncwarp();
+                    const int nflt = 9 * min(32, cnt - base);
+                    float *dst = tris + (o + win + base) * 9;
+#pragma unroll
+                    for (int r = 0; r < 9; ++r) {
+                        const int g = r * 32 + lane;
+                        if (g < nflt) dst[g] = stg[g];
+                    }
+                    __syncwarp();
+                }
             }
         }
-        __syncwarp();
     }
+}
+
+// Launch the persistent emit kernel: one resident wave (SMs x blocks per SM), work counter
+// `next` zeroed first.
+template <int NP>
+static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
+                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next)
+{
+    constexpr int EV = EmitW<NP>::V;
+    constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
+    static int blocks_per_sm = 0;  // per order; the same on every device of one architecture
+    if (!blocks_per_sm) {
+        SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int nb = 0;
+        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iso_emit_m<NP>, 32 * EV, dyn));
+        blocks_per_sm = nb > 0 ? nb : 1;
+    }
+    SEM_CU(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
+    const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
+    SEM_TRACED(ctx, "k_iso_emit_m", k_iso_emit_m<NP><<<grid, 32 * EV, dyn, ctx->stream>>>(
+                                        f, S, m->E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag, next));
+    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
 }
 
 template <int NP>
@@ -471,12 +555,13 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
     const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
     void *scr;
-    SEM_TRY(sem_scratch(ctx, SCR_ISO, cnt_bytes + off_bytes + scan_tmp_bytes(n), &scr));
+    SEM_TRY(sem_scratch(ctx, SCR_ISO, cnt_bytes + off_bytes + 256 + scan_tmp_bytes(n), &scr));
     int32_t *cnt = reinterpret_cast<int32_t *>(scr);
     int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
-    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes;
-    constexpr int WV = IsoW<NP>::V;
-    k_iso_count_m<NP><<<(unsigned)((E + WV - 1) / WV), 32 * WV, 0, ctx->stream>>>(f, S, E, cnt, cases);
+    auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
+    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
+    SEM_TRACED(ctx, "k_iso_count_m", k_iso_count_m<NP><<<(unsigned)((E + COUNT_WARPS - 1) / COUNT_WARPS), 32 * COUNT_WARPS, 0, ctx->stream>>>(
+        f, S, E, cnt, cases));
     SEM_CU(ctx, cudaGetLastError());
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
     // segment starts offs[q*E], q = 0..niso (the last one is the grand total)
@@ -490,12 +575,7 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
         return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface: %lld triangles exceed capacity %lld", (long long)total,
                         (long long)cap);
     if (total == 0) return SEM_OK;
-    constexpr int EV = EmitW<NP>::V;
-    constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
-    SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    k_iso_emit_m<NP><<<(unsigned)((E + EV - 1) / EV), 32 * EV, dyn, ctx->stream>>>(
-        f, S, E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag);
-    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+    return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
 }
 
 // No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
@@ -508,23 +588,19 @@ static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const floa
     const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
     const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
     void *scr;
-    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, cnt_bytes + off_bytes + scan_tmp_bytes(n), &scr));
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, cnt_bytes + off_bytes + 256 + scan_tmp_bytes(n), &scr));
     int32_t *cnt = reinterpret_cast<int32_t *>(scr);
     int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
-    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes;
-    constexpr int WV = IsoW<NP>::V;
-    k_iso_count_m<NP><<<(unsigned)((E + WV - 1) / WV), 32 * WV, 0, ctx->stream>>>(f, S, E, cnt, cases);
+    auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
+    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
+    SEM_TRACED(ctx, "k_iso_count_m", k_iso_count_m<NP><<<(unsigned)((E + COUNT_WARPS - 1) / COUNT_WARPS), 32 * COUNT_WARPS, 0, ctx->stream>>>(
+        f, S, E, cnt, cases));
     SEM_CU(ctx, cudaGetLastError());
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
     SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t), S.niso + 1,
                                   cudaMemcpyDeviceToDevice, ctx->stream));
     if (!tris) return SEM_OK;
-    constexpr int EV = EmitW<NP>::V;
-    constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
-    SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    k_iso_emit_m<NP><<<(unsigned)((E + EV - 1) / EV), 32 * EV, dyn, ctx->stream>>>(
-        f, S, E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag);
-    return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+    return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
 }
 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
@@ -621,7 +697,7 @@ static sem_status iso_run_noalloc_np(sem_ctx *ctx, const sem_mesh *m, const floa
     void *tmp = scr + kNaCnt + kNaOff;
     constexpr int WV = IsoW<NP>::V;
     const unsigned grid = (unsigned)((E + WV - 1) / WV);
-    k_iso_count<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, cnt, cases);
+    SEM_TRACED(ctx, "k_iso_count", k_iso_count<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, cnt, cases));
     SEM_CU(ctx, cudaGetLastError());
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, E, tmp));
     SEM_CU(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + E, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -633,7 +709,7 @@ static sem_status iso_run_noalloc_np(sem_ctx *ctx, const sem_mesh *m, const floa
         return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface_noalloc: %lld triangles exceed capacity %lld",
                         (long long)total, (long long)cap);
     if (total == 0) return SEM_OK;
-    k_iso_emit<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, offs, m->lo, m->hi, tris, tri_elem, cap);
+    SEM_TRACED(ctx, "k_iso_emit", k_iso_emit<NP><<<grid, 32 * WV, 0, ctx->stream>>>(f, iso, E, offs, m->lo, m->hi, tris, tri_elem, cap));
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit launch");
 }
 

@@ -417,7 +417,7 @@ static sem_status launch_grad(sem_ctx *ctx, const sem_mesh *m, const float *f0, 
     const int64_t ngroups = (m->E + C::EPB - 1) / C::EPB;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
     if (grid > ngroups) grid = ngroups;
-    kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(f0, f1, f2, o0, o1, o2, m->g, m->E, ctx->d_flag);
+    SEM_TRACED(ctx, "k_sem_grad", kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(f0, f1, f2, o0, o1, o2, m->g, m->E, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
 }
 

@@ -376,7 +376,7 @@ static sem_status launch_tc(sem_ctx *ctx, const sem_mesh *m, const float *u, con
     const int64_t ntiles = (m->E + NE - 1) / NE;
     int64_t grid = (int64_t)ctx->sm_count;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, THREADS, L::ALLOC, ctx->stream>>>(u, v, w, Q, m->g, m->E, A, ctx->d_flag);
+    SEM_TRACED(ctx, "k_sem_q_tc", kern<<<(unsigned)grid, THREADS, L::ALLOC, ctx->stream>>>(u, v, w, Q, m->g, m->E, A, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_sem_q_tc launch");
 }
 

@@ -383,13 +383,13 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     ctx->render_keys_dirty = true;
     SEM_CU(ctx, cudaMemsetAsync(nlarge, 0, sizeof(int32_t), ctx->stream));
     if (ntri > 0) {
-        k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge);
+        SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge));
         SEM_CU(ctx, cudaGetLastError());
-        k_raster_large<<<4 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys);
+        SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<4 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys));
         SEM_CU(ctx, cudaGetLastError());
     }
-    k_resolve<<<(unsigned)((npx + 255) / 256), 256, 0, ctx->stream>>>(tris, P, keys, reinterpret_cast<uchar4 *>(rgba),
-                                                                      depth);
+    SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)((npx + 255) / 256), 256, 0, ctx->stream>>>(tris, P, keys, reinterpret_cast<uchar4 *>(rgba),
+                                                                      depth));
     SEM_CU(ctx, cudaGetLastError());
     ctx->render_keys_dirty = false;
     return SEM_OK;

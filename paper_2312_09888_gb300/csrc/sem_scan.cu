@@ -106,9 +106,9 @@ sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *bsum = reinterpret_cast<int64_t *>(tmp);
-    k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum);
-    k_scan_blocks<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb);
-    k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum, nb, out);
+    SEM_TRACED(ctx, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum));
+    SEM_TRACED(ctx, "k_scan_blocks", k_scan_blocks<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb));
+    SEM_TRACED(ctx, "k_scan_apply", k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum, nb, out));
     return sem_cuda(ctx, cudaGetLastError(), "scan launch");
 }
 
@@ -165,7 +165,7 @@ sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *o
     SEM_CU(ctx, cudaMemsetAsync(acc, 0, 2 * sizeof(double), ctx->stream));
     int64_t grid = (ntri + 255) / 256;
     if (grid > 8 * ctx->sm_count) grid = 8 * ctx->sm_count;
-    k_measures<<<(unsigned)grid, 256, 0, ctx->stream>>>(tris, ntri, acc);
+    SEM_TRACED(ctx, "k_measures", k_measures<<<(unsigned)grid, 256, 0, ctx->stream>>>(tris, ntri, acc));
     SEM_CU(ctx, cudaGetLastError());
     SEM_CU(ctx, cudaMemcpyAsync(ctx->h_pinned_d, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -202,7 +202,7 @@ sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host
     SEM_CU(ctx, cudaMemsetAsync(key, 0, sizeof(unsigned), ctx->stream));
     int64_t grid = (n + 255) / 256;
     if (grid > 8 * ctx->sm_count) grid = 8 * ctx->sm_count;
-    k_fieldmax<<<(unsigned)grid, 256, 0, ctx->stream>>>(f, n, key);
+    SEM_TRACED(ctx, "k_fieldmax", k_fieldmax<<<(unsigned)grid, 256, 0, ctx->stream>>>(f, n, key));
     SEM_CU(ctx, cudaGetLastError());
     SEM_CU(ctx, cudaMemcpyAsync(ctx->h_pinned, key, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
