@@ -51,26 +51,33 @@ __device__ __forceinline__ bool top_left(float ax, float ay, float bx, float by)
     return (dy < 0.f) || (dy == 0.f && dx > 0.f);
 }
 
-__device__ __forceinline__ bool project(const RenderParams &P, const float *p, float &sx, float &sy, float &sz)
+// Screen position of one vertex; the NDC depth is finished in setup_tri only for triangles that
+// cover a pixel centre.  Perspective: one reciprocal of the view depth per vertex (__frcp_rn,
+// correctly rounded) instead of three divisions.
+__device__ __forceinline__ bool project(const RenderParams &P, const float *p, float &sx, float &sy, float &zv)
 {
     const float dx = p[0] - P.eye[0], dy = p[1] - P.eye[1], dz = p[2] - P.eye[2];
     const float xv = P.s[0] * dx + P.s[1] * dy + P.s[2] * dz;
     const float yv = P.u[0] * dx + P.u[1] * dy + P.u[2] * dz;
-    const float zv = P.f[0] * dx + P.f[1] * dy + P.f[2] * dz;
+    zv = P.f[0] * dx + P.f[1] * dy + P.f[2] * dz;
     if (!(zv > P.znear && zv < P.zfar)) return false;
     float xn, yn;
     if (P.ortho) {
         xn = xv * P.ax;
         yn = yv * P.ay;
-        sz = (zv - P.znear) * P.za;
     } else {
-        xn = xv / zv * P.ax;
-        yn = yv / zv * P.ay;
-        sz = P.zb * (1.f - P.znear / zv);
+        const float rz = __frcp_rn(zv);
+        xn = xv * rz * P.ax;
+        yn = yv * rz * P.ay;
     }
     sx = (xn + 1.f) * 0.5f * (float)P.W;
     sy = (1.f - yn) * 0.5f * (float)P.H;
     return true;
+}
+
+__device__ __forceinline__ float ndc_depth(const RenderParams &P, float zv)
+{
+    return P.ortho ? (zv - P.znear) * P.za : P.zb * (1.f - P.znear * __frcp_rn(zv));
 }
 
 // Screen-space setup of one triangle; false if it is dropped or contains no pixel centre.
@@ -83,23 +90,28 @@ struct Setup {
 
 __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__restrict__ p, Setup &S)
 {
-    if (!(project(P, p, S.x[0], S.y[0], S.z[0]) && project(P, p + 3, S.x[1], S.y[1], S.z[1]) &&
-          project(P, p + 6, S.x[2], S.y[2], S.z[2])))
+    float zv0, zv1, zv2;
+    if (!(project(P, p, S.x[0], S.y[0], zv0) && project(P, p + 3, S.x[1], S.y[1], zv1) &&
+          project(P, p + 6, S.x[2], S.y[2], zv2)))
         return false;
+    // pixel centres c = p + 0.5 inside the box: ceil(min - .5) <= p <= floor(max - .5); most
+    // small triangles contain none and stop here
+    const float mnx = fminf(S.x[0], fminf(S.x[1], S.x[2])), mxx = fmaxf(S.x[0], fmaxf(S.x[1], S.x[2]));
+    const float mny = fminf(S.y[0], fminf(S.y[1], S.y[2])), mxy = fmaxf(S.y[0], fmaxf(S.y[1], S.y[2]));
+    const float fx0 = fmaxf(0.f, ceilf(mnx - 0.5f)), fx1 = fminf((float)(P.W - 1), floorf(mxx - 0.5f));
+    const float fy0 = fmaxf(0.f, ceilf(mny - 0.5f)), fy1 = fminf((float)(P.H - 1), floorf(mxy - 0.5f));
+    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
     float area = (S.x[1] - S.x[0]) * (S.y[2] - S.y[0]) - (S.x[2] - S.x[0]) * (S.y[1] - S.y[0]);
     if (!(area != 0.f) || isnan(area)) return false;
+    S.z[0] = ndc_depth(P, zv0);
+    S.z[1] = ndc_depth(P, zv1);
+    S.z[2] = ndc_depth(P, zv2);
     if (area < 0.f) {
         float tx = S.x[1], ty = S.y[1], tz = S.z[1];
         S.x[1] = S.x[2]; S.y[1] = S.y[2]; S.z[1] = S.z[2];
         S.x[2] = tx; S.y[2] = ty; S.z[2] = tz;
         area = -area;
     }
-    const float mnx = fminf(S.x[0], fminf(S.x[1], S.x[2])), mxx = fmaxf(S.x[0], fmaxf(S.x[1], S.x[2]));
-    const float mny = fminf(S.y[0], fminf(S.y[1], S.y[2])), mxy = fmaxf(S.y[0], fmaxf(S.y[1], S.y[2]));
-    // pixel centres c = p + 0.5 inside the box: ceil(min - .5) <= p <= floor(max - .5)
-    const float fx0 = fmaxf(0.f, ceilf(mnx - 0.5f)), fx1 = fminf((float)(P.W - 1), floorf(mxx - 0.5f));
-    const float fy0 = fmaxf(0.f, ceilf(mny - 0.5f)), fy1 = fminf((float)(P.H - 1), floorf(mxy - 0.5f));
-    if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
     S.px0 = (int)fx0;
     S.px1 = (int)fx1;
     S.py0 = (int)fy0;
@@ -127,25 +139,32 @@ __device__ __forceinline__ void shade_pixel(const Setup &S, int px, int py, int 
     atomicMin(&keys[(int64_t)py * W + px], key);
 }
 
-// Compact per-triangle setup kept in shared memory for the warp's pixel work.
+// Compact per-triangle setup kept in shared memory for the warp's pixel work: four 16-byte
+// words per triangle, each in its own array (a lane's four stores are contiguous with its
+// neighbours'), read with four vector loads per pixel test.
+//   a: x0 y0 x1 y1   b: x2 y2 z0 z1   c: z2, 1/area, 1/nx, top-left flags   d: px0 py0 nx -
 struct SmallRec {
-    float x[3], y[3], z[3];
-    float inv_area;
-    int px0, py0, nx;
-    int flags;  // bit 0..2: top-left flags of edges 0..2
+    float4 a, b, c;
+    int4 d;
 };
 
-__device__ __forceinline__ void test_pixel(const SmallRec &R, int px, int py, int W, unsigned t,
+__device__ __forceinline__ void test_pixel(const SmallRec &R, int k, int W, unsigned t,
                                            unsigned long long *__restrict__ keys)
 {
+    const float4 a = R.a, b = R.b, c = R.c;
+    const int4 d = R.d;
+    // box row of candidate k: floor((k + .5) / nx), exact for k, nx <= 32
+    const int ky = (int)(((float)k + 0.5f) * c.z), kx = k - ky * d.z;
+    const int px = d.x + kx, py = d.y + ky;
+    const int flags = __float_as_int(c.w);
     const float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
-    const float e0 = (R.x[1] - R.x[0]) * (cy - R.y[0]) - (R.y[1] - R.y[0]) * (cx - R.x[0]);
-    const float e1 = (R.x[2] - R.x[1]) * (cy - R.y[1]) - (R.y[2] - R.y[1]) * (cx - R.x[1]);
-    const float e2 = (R.x[0] - R.x[2]) * (cy - R.y[2]) - (R.y[0] - R.y[2]) * (cx - R.x[2]);
-    const bool in = (e0 > 0.f || (e0 == 0.f && (R.flags & 1))) && (e1 > 0.f || (e1 == 0.f && (R.flags & 2))) &&
-                    (e2 > 0.f || (e2 == 0.f && (R.flags & 4)));
+    const float e0 = (a.z - a.x) * (cy - a.y) - (a.w - a.y) * (cx - a.x);
+    const float e1 = (b.x - a.z) * (cy - a.w) - (b.y - a.w) * (cx - a.z);
+    const float e2 = (a.x - b.x) * (cy - b.y) - (a.y - b.y) * (cx - b.x);
+    const bool in = (e0 > 0.f || (e0 == 0.f && (flags & 1))) && (e1 > 0.f || (e1 == 0.f && (flags & 2))) &&
+                    (e2 > 0.f || (e2 == 0.f && (flags & 4)));
     if (!in) return;
-    float z = (e1 * R.z[0] + e2 * R.z[1] + e0 * R.z[2]) * R.inv_area;
+    float z = (e1 * b.z + e2 * b.w + e0 * c.x) * c.y;
     z = fminf(fmaxf(z, 0.f), 1.f);
     const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | t;
     atomicMin(&keys[(int64_t)py * W + px], key);
@@ -153,21 +172,34 @@ __device__ __forceinline__ void test_pixel(const SmallRec &R, int px, int py, in
 
 // One thread per triangle for the setup (its 36 bytes staged through shared memory with
 // coalesced loads); then each warp spreads the pixel-centre tests of its 32 triangles evenly
-// over its lanes, so a lane never idles while a neighbour walks a bigger box.
+// over its lanes, so a lane never idles while a neighbour walks a bigger box.  Each lane
+// writes its own lane number over its candidates' slots of a per-warp owner map, so a pixel
+// test finds its triangle with one shared-memory byte load.
 __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
                                                       const __grid_constant__ RenderParams P,
                                                       unsigned long long *__restrict__ keys,
                                                       int32_t *__restrict__ large, int32_t *__restrict__ nlarge)
 {
-    __shared__ float s_tri[256 * 9];
-    __shared__ SmallRec s_rec[256];
+    __shared__ __align__(16) float s_tri[256 * 9];
+    __shared__ float4 s_ra[256], s_rb[256], s_rc[256];
+    __shared__ int4 s_rd[256];
+    __shared__ uint8_t s_own[8][32 * SMALL_PX];
     if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
     const int t0 = blockIdx.x * 256;
     // blocks past the (device-clamped) triangle count have no work; the whole block leaves
     // before its first barrier
     if (t0 >= ntri) return;
     const int nt_blk = min(256, ntri - t0);
-    for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = tris[(int64_t)t0 * 9 + q];
+    const float *src = tris + (int64_t)t0 * 9;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        // 16-byte loads when the block's 36-byte triangles start on a 16-byte boundary
+        const int n4 = nt_blk * 9 / 4;
+        for (int q = threadIdx.x; q < n4; q += 256)
+            reinterpret_cast<float4 *>(s_tri)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
+        for (int q = n4 * 4 + threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = src[q];
+    } else {
+        for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = src[q];
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
@@ -179,18 +211,11 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
                 npx = nx * ny;
-                SmallRec &R = s_rec[threadIdx.x];
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    R.x[v] = S.x[v];
-                    R.y[v] = S.y[v];
-                    R.z[v] = S.z[v];
-                }
-                R.inv_area = S.inv_area;
-                R.px0 = S.px0;
-                R.py0 = S.py0;
-                R.nx = nx;
-                R.flags = (S.tl0 ? 1 : 0) | (S.tl1 ? 2 : 0) | (S.tl2 ? 4 : 0);
+                const int flags = (S.tl0 ? 1 : 0) | (S.tl1 ? 2 : 0) | (S.tl2 ? 4 : 0);
+                s_ra[threadIdx.x] = make_float4(S.x[0], S.y[0], S.x[1], S.y[1]);
+                s_rb[threadIdx.x] = make_float4(S.x[2], S.y[2], S.z[0], S.z[1]);
+                s_rc[threadIdx.x] = make_float4(S.z[2], S.inv_area, 1.f / (float)nx, __int_as_float(flags));
+                s_rd[threadIdx.x] = make_int4(S.px0, S.py0, nx, 0);
             } else {
                 is_large = true;
             }
@@ -212,25 +237,19 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         if (lane >= d) incl += y;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    __syncwarp();
     const int wbase = threadIdx.x & ~31;
     const int excl = incl - npx;
+    uint8_t *own = s_own[threadIdx.x >> 5];
+    for (int q = 0; q < npx; ++q) own[excl + q] = (uint8_t)lane;
+    __syncwarp();
     for (int r = 0; r < total; r += 32) {
         const int idx = r + lane;
-        // owner: first lane whose inclusive count exceeds idx (5-step search over the warp)
-        int lo = 0, hi = 31;
-#pragma unroll
-        for (int st = 0; st < 5; ++st) {
-            const int mid = (lo + hi) >> 1;
-            const int v = __shfl_sync(0xffffffffu, incl, mid);
-            if (v <= idx) lo = mid + 1;
-            else hi = mid;
-        }
-        const int first = __shfl_sync(0xffffffffu, excl, lo);
+        const int L = idx < total ? own[idx] : 31;
+        const int first = __shfl_sync(0xffffffffu, excl, L);
         if (idx < total) {
-            const SmallRec &R = s_rec[wbase + lo];
-            const int k = idx - first;
-            test_pixel(R, R.px0 + k % R.nx, R.py0 + k / R.nx, P.W, (unsigned)(t0 + wbase + lo), keys);
+            const int r8 = wbase + L;
+            const SmallRec R{s_ra[r8], s_rb[r8], s_rc[r8], s_rd[r8]};
+            test_pixel(R, idx - first, P.W, (unsigned)(t0 + r8), keys);
         }
     }
 }
