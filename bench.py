@@ -34,6 +34,7 @@ METRIC = "SEM elements/s through Q-isosurface render; frames/s; fraction of HBM 
 UNIT = "elements/s"
 WORKLOAD = "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, 1920x1080 perspective"
 KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
+                  "k_sem_q8": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_iso_count_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
                   "k_iso_emit_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
                   "k_raster_small": "paper_2312_09888_gb300/csrc/sem_render.cu",
@@ -48,6 +49,7 @@ def algorithmic_bytes(name, P):
     table = {
         # u, v, w read (12 B/node) + Q written (4 B/node)
         "k_sem_grad": 16 * P.npts,
+        "k_sem_q8": 16 * P.npts,
         # the field read once for all isovalues + one int32 count per element and isovalue
         "k_iso_count_m": 4 * P.npts + 4 * P.E * niso,
         # the active elements' field read + 36 B per triangle written + the offsets read

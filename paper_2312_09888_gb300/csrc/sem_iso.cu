@@ -16,6 +16,8 @@
 // Node positions are lerps of the element box with exact end points, so nodes shared by two
 // elements get bit-identical coordinates.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <string.h>
 
 #include "sem_internal.cuh"
@@ -315,23 +317,55 @@ __device__ __forceinline__ int pair_case(uint32_t r00, uint32_t r01, uint32_t r1
 
 #define COUNT_WARPS 8
 
+// The masks of all isovalues of element fe, built from register-held values: lane w keeps
+// mask word w of each isovalue and stores it; the activity bits come from warp AND/OR
+// reductions of the words.  For orders with at most 32 mask words (N <= 9).
 template <int NP>
-__global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *__restrict__ f,
-                                                                 const __grid_constant__ IsoSet S, int64_t E,
-                                                                 int32_t *__restrict__ cnt, uint8_t *__restrict__ cases)
+__device__ __forceinline__ unsigned load_masks_reg(const float *__restrict__ fe, const IsoSet &S,
+                                                   uint32_t *__restrict__ m, int lane)
+{
+    using G = MaskGeo<NP>;
+    static_assert(G::NW <= 32, "one mask word per lane");
+    float v[G::NW];
+#pragma unroll
+    for (int w = 0; w < G::NW; ++w) {
+        const int n = w * 32 + lane;
+        v[w] = ((G::NP3 % 32 == 0) || n < G::NP3) ? __ldg(fe + n) : 0.f;
+    }
+    // lanes >= NW hold the neutral words of the reductions (AND: all ones, OR: zero)
+    const uint32_t vmask = lane >= G::NW ? 0u
+                           : (G::NP3 % 32 == 0 || lane < G::NW - 1) ? ~0u
+                                                                     : ((1u << (G::NP3 % 32)) - 1u);
+    unsigned active = 0;
+#pragma unroll
+    for (int q = 0; q < SEM_MAX_ISO; ++q) {
+        if (q >= S.niso) break;
+        uint32_t mine = 0;
+#pragma unroll
+        for (int w = 0; w < G::NW; ++w) {
+            const int n = w * 32 + lane;
+            const bool valid = (G::NP3 % 32 == 0) || n < G::NP3;
+            const uint32_t b = __ballot_sync(0xffffffffu, valid && v[w] >= S.iso[q]);
+            if (lane == w) mine = b;
+        }
+        if (lane < G::NW) m[q * G::MW + lane] = mine;
+        if (lane == G::NW) m[q * G::MW + lane] = 0u;  // padding word
+        const uint32_t any_in = __reduce_or_sync(0xffffffffu, mine & vmask);
+        const uint32_t all_in = __reduce_and_sync(0xffffffffu, mine | ~vmask);
+        if (any_in != 0u && all_in != ~0u) active |= 1u << q;
+    }
+    return active;
+}
+
+// Triangle counts of element e for every isovalue from its masks (and every cell's case when
+// `cases` is not null).
+template <int NP>
+__device__ __forceinline__ void count_element(const uint32_t *__restrict__ m, unsigned active, const IsoSet &S,
+                                              int64_t e, int64_t E, const uint8_t *__restrict__ s_nt,
+                                              int32_t *__restrict__ cnt, uint8_t *__restrict__ cases, int lane)
 {
     using G = MaskGeo<NP>;
     constexpr int N = G::N, N3 = G::N3, MW = G::MW;
-    __shared__ uint32_t s_m[COUNT_WARPS][SEM_MAX_ISO * MW];
-    __shared__ uint8_t s_nt[256];
-    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e = (int64_t)blockIdx.x * COUNT_WARPS + w;
-    if (e >= E) return;
-    uint32_t *m = s_m[w];
-    const unsigned active = load_masks<NP>(f + e * G::NP3, nullptr, S, m, lane);
-    __syncwarp();
     for (int q = 0; q < S.niso; ++q) {
         const uint32_t *mq = m + q * MW;
         if (!((active >> q) & 1u)) {
@@ -356,6 +390,28 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *_
         for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
         if (lane == 0) cnt[q * E + e] = acc;
     }
+}
+
+// One warp per element.
+template <int NP>
+__global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *__restrict__ f,
+                                                                 const __grid_constant__ IsoSet S, int64_t E,
+                                                                 int32_t *__restrict__ cnt, uint8_t *__restrict__ cases)
+{
+    using G = MaskGeo<NP>;
+    __shared__ uint32_t s_m[COUNT_WARPS][SEM_MAX_ISO * G::MW];
+    __shared__ uint8_t s_nt[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * COUNT_WARPS + w;
+    if (e >= E) return;
+    uint32_t *m = s_m[w];
+    unsigned active;
+    if constexpr (G::NW <= 32) active = load_masks_reg<NP>(f + e * G::NP3, S, m, lane);
+    else active = load_masks<NP>(f + e * G::NP3, nullptr, S, m, lane);
+    __syncwarp();
+    count_element<NP>(m, active, S, e, E, s_nt, cnt, cases, lane);
 }
 
 // per-warp dynamic shared memory of the emit kernel: the element's field, a window of the
@@ -516,7 +572,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
 #pragma unroll
                     for (int r = 0; r < 9; ++r) {
                         const int g = r * 32 + lane;
-                        if (g < nflt) dst[g] = stg[g];
+                        if (g < nflt) __stcs(dst + g, stg[g]);  // streamed: read once, by the raster
                     }
                     __syncwarp();
                 }

@@ -403,6 +403,197 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Q for N = 7 with direction-owned lines.  In the kernel above every thread contracts along
+// all three directions for its own r-line, so it reads its whole slab and column (128 values
+// per component, mostly broadcast).  Here each direction is contracted by the threads that
+// own its lines: warp w is the s-line owner of slab k = w (lanes: element el = lane/8, node
+// i = lane%8) and the t-line owner of plane j = w; each reads 8 values with conflict-free
+// 4-byte loads (elements sit 520 floats apart in shared memory, shifting their banks by 8) and
+// passes its 8 derivatives through an exchange buffer to the r-line owner (el, k, j), which
+// contracts its own row and folds the six products of Q exactly as k_sem_grad does.
+// 4 elements per stage, 2 stages fed by per-element bulk copies; 3 CTAs per SM.
+// ------------------------------------------------------------------------------------------
+namespace q8 {
+constexpr int EPB = 4, NP3 = 512, ES = 520;              // elements per stage, padded element stride
+constexpr int CS = EPB * ES;                              // one component of a stage
+constexpr int STAGE = 3 * CS;                             // floats per stage
+constexpr int XS = 2 * CS;                                // exchange: s then t derivatives
+constexpr size_t SMEM = sizeof(float) * (2 * STAGE + XS);
+}  // namespace q8
+
+__global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0, const float *__restrict__ f1,
+                                                   const float *__restrict__ f2, float *__restrict__ Q,
+                                                   const float4 *__restrict__ gfac, int64_t E, int *err)
+{
+    using namespace q8;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_abort;
+    float *X = smem + 2 * STAGE;  // exchange buffer
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // r-line owner (el, k, j)
+    const int el = tid >> 6, k = (tid >> 3) & 7, j = tid & 7;
+    // s-/t-line owner: element lane/8, node i = lane%8, slab k = warp (s), plane j = warp (t)
+    const int oe = lane >> 3, oi = lane & 7;
+    const int64_t ngroups = (E + EPB - 1) / EPB, nfull = E / EPB;
+    const float *src[3] = {f0, f1, f2};
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t grp, int s) {
+        float *dst = smem + s * STAGE;
+        mbar_arrive_expect_tx(&bar[s], 3 * EPB * NP3 * 4);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int e = 0; e < EPB; ++e)
+                bulk_g2s(dst + c * CS + e * ES, src[c] + (grp * EPB + e) * NP3, NP3 * 4, &bar[s]);
+    };
+    // per stage s: bit s of `phase` is its mbarrier parity, bit s of `pending` a copy in flight
+    uint32_t phase = 0u;
+    uint32_t pending = ((int64_t)blockIdx.x < nfull ? 1u : 0u) | ((int64_t)blockIdx.x + gridDim.x < nfull ? 2u : 0u);
+    if (tid == 0) {
+        if (pending & 1u) issue(blockIdx.x, 0);
+        if (pending & 2u) issue(blockIdx.x + gridDim.x, 1);
+    }
+    const int sw = (j >> 2) & 1;  // row chunk stagger: j = 0..3 and 4..7 hit different banks
+    int it = 0;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+        const int s = it & 1;
+        float *st = smem + s * STAGE;
+        if (grp < nfull) {
+            if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err)) s_abort = 1;
+            phase ^= 1u << s;
+            pending &= ~(1u << s);
+        } else {
+            const int ne = (int)(E - grp * EPB);
+            for (int c = 0; c < 3; ++c)
+                for (int idx = tid; idx < ne * NP3; idx += 256)
+                    st[c * CS + (idx / NP3) * ES + idx % NP3] = src[c][grp * EPB * NP3 + idx];
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const int64_t e = grp * EPB + el;
+        const float4 g = gfac[e < E ? e : E - 1];
+        const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
+        const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
+        float q[8], su[8], tu[8], tv[8];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float *U = st + c * CS;
+            // s-lines of slab `warp`: d/ds at nodes (i, j', k) for j' = 0..7
+            {
+                float u[8], d[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) u[m] = U[oe * ES + (warp * 8 + m) * 8 + oi];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    float a = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) a = fmaf(Dc<8>(jj, m), u[m], a);
+                    d[jj] = a;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) X[oe * ES + (warp * 8 + jj) * 8 + oi] = d[jj];
+            }
+            // t-lines of plane `warp`: d/dt at nodes (i, j, k') for k' = 0..7
+            {
+                float u[8], d[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) u[m] = U[oe * ES + (m * 8 + warp) * 8 + oi];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) {
+                    float a = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) a = fmaf(Dc<8>(kk, m), u[m], a);
+                    d[kk] = a;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) X[CS + oe * ES + (kk * 8 + warp) * 8 + oi] = d[kk];
+            }
+            // r-line of the owner (el, k, j)
+            float dr[8];
+            {
+                const float4 *rp = reinterpret_cast<const float4 *>(U + el * ES + (k * 8 + j) * 8);
+                const float4 A = rp[sw], B = rp[sw ^ 1];
+                const float4 lo = sw ? B : A, hi = sw ? A : B;
+                const float row[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float a = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) a = fmaf(Dc<8>(i, m), row[m], a);
+                    dr[i] = a;
+                }
+            }
+            __syncthreads();  // the exchange holds this component's s and t derivatives
+            float ds[8], dt[8];
+            {
+                const float4 *sp = reinterpret_cast<const float4 *>(X + el * ES + (k * 8 + j) * 8);
+                const float4 *tp = reinterpret_cast<const float4 *>(X + CS + el * ES + (k * 8 + j) * 8);
+                const float4 sA = sp[sw], sB = sp[sw ^ 1], tA = tp[sw], tB = tp[sw ^ 1];
+                const float4 slo = sw ? sB : sA, shi = sw ? sA : sB, tlo = sw ? tB : tA, thi = sw ? tA : tB;
+                ds[0] = slo.x; ds[1] = slo.y; ds[2] = slo.z; ds[3] = slo.w;
+                ds[4] = shi.x; ds[5] = shi.y; ds[6] = shi.z; ds[7] = shi.w;
+                dt[0] = tlo.x; dt[1] = tlo.y; dt[2] = tlo.z; dt[3] = tlo.w;
+                dt[4] = thi.x; dt[5] = thi.y; dt[6] = thi.z; dt[7] = thi.w;
+            }
+            // Q = -1/2 sum_ij J_ij J_ji, J_ij = g_j d_j(u_i): the six products in k_sem_grad's order
+            if (c == 0) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    q[i] = c11 * dr[i] * dr[i];
+                    su[i] = ds[i];
+                    tu[i] = dt[i];
+                }
+            } else if (c == 1) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    q[i] = fmaf(c12 * su[i], dr[i], q[i]);
+                    q[i] = fmaf(c22 * ds[i], ds[i], q[i]);
+                    tv[i] = dt[i];
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    q[i] = fmaf(c13 * tu[i], dr[i], q[i]);
+                    q[i] = fmaf(c23 * tv[i], ds[i], q[i]);
+                    q[i] = fmaf(c33 * dt[i], dt[i], q[i]);
+                }
+            }
+            __syncthreads();  // the exchange is free for the next component
+        }
+        if (e < E) store_line<8>(Q + e * NP3 + (k * 8 + j) * 8, q);
+        if (tid == 0 && grp + 2 * (int64_t)gridDim.x < nfull) {
+            issue(grp + 2 * gridDim.x, s);
+            pending |= 1u << s;
+        }
+    }
+    if (s_abort && tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if ((pending >> s) & 1u) mbar_wait_bounded(&bar[s], (phase >> s) & 1u, nullptr);
+    }
+}
+
+static sem_status launch_q8(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
+{
+    SEM_CU(ctx, cudaFuncSetAttribute(k_sem_q8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q8::SMEM));
+    int per_sm = 0;
+    SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_q8, 256, q8::SMEM));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ngroups = (m->E + q8::EPB - 1) / q8::EPB;
+    int64_t grid = (int64_t)ctx->sm_count * per_sm;
+    if (grid > ngroups) grid = ngroups;
+    SEM_TRACED(ctx, "k_sem_q8", k_sem_q8<<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(u, v, w, Q, m->g, m->E,
+                                                                                         ctx->d_flag));
+    return sem_cuda(ctx, cudaGetLastError(), "k_sem_q8 launch");
+}
+
 template <int NP, int NC>
 static sem_status launch_grad(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
                               float *o0, float *o1, float *o2)
@@ -437,6 +628,7 @@ static sem_status dispatch(sem_ctx *ctx, const sem_mesh *m, const float *f0, con
 
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
 {
+    if (m->N == 7) return launch_q8(ctx, m, u, v, w, Q);
     return dispatch<3>(ctx, m, u, v, w, Q, nullptr, nullptr);
 }
 

@@ -27,6 +27,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "sem_internal.cuh"
 
 #define SMALL_PX 32        // boxes with at most this many pixel centres are rasterised per thread
@@ -170,6 +172,30 @@ __device__ __forceinline__ void test_pixel(const SmallRec &R, int k, int W, unsi
     atomicMin(&keys[(int64_t)py * W + px], key);
 }
 
+// Flat headlight shade of triangle t (colour of its segment times 0.15 + 0.85 |n.l|, l the view
+// direction), packed as RGBA8 with alpha 255.
+__device__ __forceinline__ uint32_t shade_rgba(const RenderParams &P, const float *__restrict__ p, int t)
+{
+    const float ax = p[3] - p[0], ay = p[4] - p[1], az = p[5] - p[2];
+    const float bx = p[6] - p[0], by = p[7] - p[1], bz = p[8] - p[2];
+    const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+    const float n2 = nx * nx + ny * ny + nz * nz;
+    const float shade = n2 > 0.f ? 0.15f + 0.85f * fabsf(nx * P.f[0] + ny * P.f[1] + nz * P.f[2]) * rsqrtf(n2) : 0.15f;
+    int sg = 0;
+    if (P.seg_dev) {
+        while (sg < P.nseg - 1 && (int64_t)t >= __ldg(P.seg_dev + sg + 1)) ++sg;
+    } else {
+        while (sg < P.nseg - 1 && t >= P.seg_end[sg]) ++sg;
+    }
+    uint32_t c = 0xff000000u;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float v = fminf(fmaxf(P.rgb[sg][k] * shade, 0.f), 1.f);
+        c |= (uint32_t)(unsigned char)floorf(v * 255.f + 0.5f) << (8 * k);
+    }
+    return c;
+}
+
 // One thread per triangle for the setup (its 36 bytes staged through shared memory with
 // coalesced loads); then each warp spreads the pixel-centre tests of its 32 triangles evenly
 // over its lanes, so a lane never idles while a neighbour walks a bigger box.  Each lane
@@ -178,7 +204,8 @@ __device__ __forceinline__ void test_pixel(const SmallRec &R, int k, int W, unsi
 __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
                                                       const __grid_constant__ RenderParams P,
                                                       unsigned long long *__restrict__ keys,
-                                                      int32_t *__restrict__ large, int32_t *__restrict__ nlarge)
+                                                      int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
+                                                      uint32_t *__restrict__ colors)
 {
     __shared__ __align__(16) float s_tri[256 * 9];
     __shared__ float4 s_ra[256], s_rb[256], s_rc[256];
@@ -195,10 +222,10 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         // 16-byte loads when the block's 36-byte triangles start on a 16-byte boundary
         const int n4 = nt_blk * 9 / 4;
         for (int q = threadIdx.x; q < n4; q += 256)
-            reinterpret_cast<float4 *>(s_tri)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
-        for (int q = n4 * 4 + threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = src[q];
+            reinterpret_cast<float4 *>(s_tri)[q] = __ldcs(reinterpret_cast<const float4 *>(src) + q);
+        for (int q = n4 * 4 + threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = __ldcs(src + q);
     } else {
-        for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = src[q];
+        for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = __ldcs(src + q);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -208,6 +235,8 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     if ((int)threadIdx.x < nt_blk) {
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
+            // only triangles that cover a pixel centre can win a pixel: their colour, once
+            colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, t);
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
                 npx = nx * ny;
@@ -276,40 +305,52 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_raster_large(const float *__r
     }
 }
 
-__global__ void __launch_bounds__(256) k_resolve(const float *__restrict__ tris, const __grid_constant__ RenderParams P,
-                                                 unsigned long long *__restrict__ keys, uchar4 *__restrict__ rgba,
+// Per pixel: the winning key's depth and its triangle's colour (computed by the raster pass);
+// resets the key for the next frame.  Grid-stride over groups of four pixels (16-byte key,
+// colour and depth accesses); the last npx % 4 pixels go to the first threads.
+__device__ __forceinline__ void resolve_one(unsigned long long key, const uint32_t *__restrict__ colors, uint32_t &c,
+                                            float &d)
+{
+    if (key == ~0ull) {
+        c = 0u;
+        d = 1.f;
+    } else {
+        c = colors[key & 0xffffffffu];
+        d = __uint_as_float((unsigned)(key >> 32));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_resolve(const uint32_t *__restrict__ colors, int64_t npx,
+                                                 unsigned long long *__restrict__ keys, uint32_t *__restrict__ rgba,
                                                  float *__restrict__ depth)
 {
-    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= (int64_t)P.W * P.H) return;
-    const unsigned long long key = keys[pix];
-    keys[pix] = ~0ull;  // ready for the next frame
-    if (key == ~0ull) {
-        rgba[pix] = make_uchar4(0, 0, 0, 0);
-        if (depth) depth[pix] = 1.f;
-        return;
+    const int64_t n4 = npx >> 2, stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    ulonglong2 *k2 = reinterpret_cast<ulonglong2 *>(keys);
+    const ulonglong2 empty = make_ulonglong2(~0ull, ~0ull);
+    for (int64_t q = tid; q < n4; q += stride) {
+        const ulonglong2 a = k2[2 * q], b = k2[2 * q + 1];
+        k2[2 * q] = empty;  // ready for the next frame
+        k2[2 * q + 1] = empty;
+        uint4 c;
+        float4 d;
+        resolve_one(a.x, colors, c.x, d.x);
+        resolve_one(a.y, colors, c.y, d.y);
+        resolve_one(b.x, colors, c.z, d.z);
+        resolve_one(b.y, colors, c.w, d.w);
+        __stcs(reinterpret_cast<uint4 *>(rgba) + q, c);
+        if (depth) __stcs(reinterpret_cast<float4 *>(depth) + q, d);
     }
-    const int t = (int)(key & 0xffffffffu);
-    const float *p = tris + (int64_t)t * 9;
-    const float ax = p[3] - p[0], ay = p[4] - p[1], az = p[5] - p[2];
-    const float bx = p[6] - p[0], by = p[7] - p[1], bz = p[8] - p[2];
-    const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
-    const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
-    const float shade = nn > 0.f ? 0.15f + 0.85f * fabsf(nx * P.f[0] + ny * P.f[1] + nz * P.f[2]) / nn : 0.15f;
-    int sg = 0;
-    if (P.seg_dev) {
-        while (sg < P.nseg - 1 && (int64_t)t >= P.seg_dev[sg + 1]) ++sg;
-    } else {
-        while (sg < P.nseg - 1 && t >= P.seg_end[sg]) ++sg;
+    const int64_t pix = 4 * n4 + tid;
+    if (pix < npx) {
+        const unsigned long long key = keys[pix];
+        keys[pix] = ~0ull;
+        uint32_t c;
+        float d;
+        resolve_one(key, colors, c, d);
+        rgba[pix] = c;
+        if (depth) depth[pix] = d;
     }
-    unsigned char c[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float v = fminf(fmaxf(P.rgb[sg][k] * shade, 0.f), 1.f);
-        c[k] = (unsigned char)floorf(v * 255.f + 0.5f);
-    }
-    rgba[pix] = make_uchar4(c[0], c[1], c[2], 255);
-    if (depth) depth[pix] = __uint_as_float((unsigned)(key >> 32));
 }
 
 static const float kPalette[16][3] = {
@@ -394,21 +435,28 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
         SEM_CU(ctx, cudaMemsetAsync(kscr, 0xff, ctx->scratch_bytes[SCR_RENDER], ctx->stream));
         ctx->render_keys_dirty = false;
     }
-    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_TRI, 256 + sizeof(int32_t) * (size_t)(ntri > 0 ? ntri : 1), &lscr));
+    // large-triangle counter, list (int32 per triangle) and per-triangle colours (RGBA8)
+    const size_t nt1 = (size_t)(ntri > 0 ? ntri : 1);
+    const size_t list_bytes = ((sizeof(int32_t) * nt1 + 255) / 256) * 256;
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_TRI, 256 + list_bytes + sizeof(uint32_t) * nt1, &lscr));
     unsigned long long *keys = reinterpret_cast<unsigned long long *>(kscr);
     int32_t *nlarge = reinterpret_cast<int32_t *>(lscr);
     int32_t *large = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(lscr) + 256);
+    uint32_t *colors = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(lscr) + 256 + list_bytes);
     // until k_resolve has run, the keys are not all "empty"
     ctx->render_keys_dirty = true;
     SEM_CU(ctx, cudaMemsetAsync(nlarge, 0, sizeof(int32_t), ctx->stream));
     if (ntri > 0) {
-        SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge));
+        SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge,
+                                                                                            colors));
         SEM_CU(ctx, cudaGetLastError());
         SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<4 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys));
         SEM_CU(ctx, cudaGetLastError());
     }
-    SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)((npx + 255) / 256), 256, 0, ctx->stream>>>(tris, P, keys, reinterpret_cast<uchar4 *>(rgba),
-                                                                      depth));
+    SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((npx / 4 + 255) / 256,
+                                                                                          8 * ctx->sm_count)),
+                                               256, 0, ctx->stream>>>(
+                                     colors, npx, keys, reinterpret_cast<uint32_t *>(rgba), depth));
     SEM_CU(ctx, cudaGetLastError());
     ctx->render_keys_dirty = false;
     return SEM_OK;
