@@ -25,8 +25,13 @@ def host64(t):
 
 
 def ref_abs_contractions(D, u, NP):
-    """sum_m |D[i][m]| |u| along r, s, t for u (E, NP^3) -> three (E, NP^3) arrays."""
-    A = np.abs(D)
+    """sum_m M[i][m] |u| along r, s, t for u (E, NP^3) -> three (E, NP^3) arrays, with
+    M[i][m] = max(|D[i][m]|, |D[i][N-m]|).  D is centro-antisymmetric (GLL nodes are symmetric),
+    so a kernel may contract with the even/odd parts u_m +- u_{N-m} and the coefficients
+    (D[i][m] +- D[i][N-m])/2; their rounding error is bounded by the same sums with
+    |(x+y)/2| + |(x-y)/2| = max(|x|, |y|) in place of |D[i][m]|.  M >= |D|, so the bound also
+    covers the plain contraction."""
+    A = np.maximum(np.abs(D), np.abs(D[:, ::-1]))
     U = np.abs(u).reshape(-1, NP, NP, NP)  # [e][k][j][i]
     br = np.einsum("im,ekjm->ekji", A, U)
     bs = np.einsum("jm,ekmi->ekji", A, U)
