@@ -379,3 +379,45 @@ def stretched_box(nel, N: int, seed: int = 0) -> BoxMesh:
         f = np.concatenate([[0.0], np.cumsum(w)]) - 0.3 * d
         faces.append(f)
     return BoxMesh(N, faces[0], faces[1], faces[2])
+
+
+# --------------------------------------------------------------------------- learned compression
+
+AE_DIMS = (1536, 512, 48, 512, 1536)   # per-element autoencoder widths (N = 7, 3 components)
+AE_SNAPSHOTS_TRAIN = 200
+AE_SNAPSHOTS_TOTAL = 250
+
+
+def ae_init_params(seed: int = None, dims=AE_DIMS) -> dict:
+    """Initial weights of the four layers: W_l ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from a
+    seeded numpy generator, biases zero; float32 arrays W_l (out, in), b_l (out,)."""
+    rng = np.random.default_rng(seed_for(5) if seed is None else seed)
+    p = {}
+    for layer in range(4):
+        fin, fout = dims[layer], dims[layer + 1]
+        a = 1.0 / math.sqrt(fin)
+        p[f"W{layer + 1}"] = rng.uniform(-a, a, size=(fout, fin)).astype(np.float32)
+        p[f"b{layer + 1}"] = np.zeros(fout, dtype=np.float32)
+    return p
+
+
+def ae_snapshot(s: int, nel: int = 32, N: int = 7, noise: float = 1e-3, device="cpu") -> torch.Tensor:
+    """Snapshot s of the learned-compression data: the Taylor-Green field of the small
+    workload on nel^3 elements, phase 2 pi s / 250 in x and y, plus i.i.d. N(0, noise^2) per
+    global node (shared face nodes share the sample, as in the small workload), drawn from
+    torch's generator on `device` seeded with seed_for(5, s).  Returns (3, E, (N+1)^3)
+    float32 on `device` (noise-free when noise == 0)."""
+    mesh = uniform_box((nel,) * 3, (0.0,) * 3, (TWO_PI,) * 3, N)
+    f = taylor_green(mesh, 0.0, 0, device, phase=TWO_PI * s / AE_SNAPSHOTS_TOTAL)
+    if noise > 0.0:
+        g = torch.Generator(device=device)
+        g.manual_seed(seed_for(5, s))
+        nz = noise * torch.randn((3,) + mesh.global_shape(), generator=g, device=device, dtype=torch.float64)
+        idx = mesh.flat_index(device)
+        f = f + torch.stack([mesh.gather(nz[c], idx) for c in range(3)])
+    return f.float()
+
+
+def ae_samples(fields: torch.Tensor) -> torch.Tensor:
+    """(3, E, NP^3) fields -> (E, 3 NP^3) samples [u_e | v_e | w_e] (a pure relayout)."""
+    return fields.permute(1, 0, 2).reshape(fields.shape[1], -1).contiguous()
