@@ -253,6 +253,81 @@ SEM_API sem_status sem_surface_measures(sem_ctx *ctx, const float *tris, int64_t
  * Synchronises.  n >= 1. */
 SEM_API sem_status sem_field_max(sem_ctx *ctx, const float *f, int64_t n, float *max_host);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned per-element compression (no counterpart in the paper's code; its motivation is the
+ * transfer volume of in-transit analysis, Sec. 4.2).  An MLP autoencoder per element of order
+ * N = 7: the 3 x 512 nodal velocity values, normalised per component, go through
+ *   encoder  H1 = X W1^T + b1, A1 = gelu(H1), Z = A1 W2^T + b2      1536 -> 512 -> 48
+ *   decoder  H3 = Z W3^T + b3, A3 = gelu(H3), Y = A3 W4^T + b4      48 -> 512 -> 1536
+ * with gelu(x) = x Phi(x) (exact erf form), loss = mean over all entries of (Y - X)^2 and
+ * AdamW updates (Loshchilov & Hutter 2019, bias-corrected moments, weight decay decoupled:
+ * w -= lr (mhat / (sqrt(vhat) + eps) + wd w)).  All products run on the tensor cores in BF16
+ * with FP32 accumulation; weights are kept in FP32 and copied to BF16 after each update; the
+ * latent Z is BF16 (48 values = 96 bytes per element, 64x fewer than 1536 FP32 values) and the
+ * decoder and training graph see the BF16 latent (its gradient passes through the rounding).
+ *
+ * Parameter arrays on the host are FP32, flattened in the order W1 (512 x 1536, row-major),
+ * b1 (512), W2 (48 x 512), b2 (48), W3 (512 x 48), b3 (512), W4 (1536 x 512), b4 (1536):
+ * sem_ae_param_count() values.  A sample is one element's 1536 values [u(512) | v(512) |
+ * w(512)] (node order i + 8 j + 64 k), FP32; training reads samples from a device array
+ * samples[n][1536] at the rows a device int64 array idx[B] names (the caller draws them).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct sem_ae sem_ae;
+
+/* Number of FP32 values in the flattened parameter arrays (1,624,624). */
+SEM_API int64_t sem_ae_param_count(void);
+
+/* Create an autoencoder on ctx's device with all parameters zero, for training batches of at
+ * most `batch` samples (a multiple of 128; encode/decode work in chunks of `batch`).
+ * Allocates its parameters, Adam moments, gradients and activations (about 28 KB per batch
+ * row plus 26 MB).  Free with sem_ae_destroy. */
+SEM_API sem_status sem_ae_create(sem_ctx *ctx, int batch, sem_ae **out);
+SEM_API void sem_ae_destroy(sem_ae *ae);
+
+/* Parameters (and the Adam moments with the step count, for checkpoints) from/to HOST
+ * arrays of sem_ae_param_count() FP32 values.  Synchronous. */
+SEM_API sem_status sem_ae_set_params(sem_ae *ae, const float *host, int64_t n);
+SEM_API sem_status sem_ae_get_params(sem_ae *ae, float *host, int64_t n);
+SEM_API sem_status sem_ae_get_state(sem_ae *ae, float *m_host, float *v_host, int64_t n, int64_t *step);
+SEM_API sem_status sem_ae_set_state(sem_ae *ae, const float *m_host, const float *v_host, int64_t n, int64_t step);
+
+/* Normalisation X = (value - mean[c]) / std[c] per component c.  sem_ae_fit_normalization
+ * takes per-component means and one common scale (root of the mean per-component variance)
+ * over device samples[n][1536] (FP64 sums; synchronous). */
+SEM_API sem_status sem_ae_set_normalization(sem_ae *ae, const float mean[3], const float stdv[3]);
+SEM_API sem_status sem_ae_get_normalization(sem_ae *ae, float mean[3], float stdv[3]);
+SEM_API sem_status sem_ae_fit_normalization(sem_ae *ae, const float *samples, int64_t n);
+
+/* Loss and gradients for the batch samples[idx[0..B-1]] (samples: n_samples rows) without
+ * updating: *loss_host = the mean squared error; grad_host (HOST, flattened like the
+ * parameters, or NULL) the gradient.  1 <= B <= batch.  An index outside [0, n_samples) is
+ * read as the component means and raises SEM_ERR_ARG on the device flag (reported by
+ * sem_synchronize).  Synchronous. */
+SEM_API sem_status sem_ae_loss_grad(sem_ae *ae, const float *samples, int64_t n_samples, const int64_t *idx, int B,
+                                    float *loss_host, float *grad_host, int64_t n);
+
+/* One AdamW training step on the batch samples[idx[0..B-1]] (indices checked as in
+ * sem_ae_loss_grad; asynchronous on the context's
+ * stream; may be captured in a CUDA graph once the step count is fixed by the caller).
+ * loss_dev (device float, or NULL) receives the batch's SUM of squared errors (divide by
+ * 1536 B for the mean).  Bias corrections use the object's step count (incremented here). */
+SEM_API sem_status sem_ae_train_step(sem_ae *ae, const float *samples, int64_t n_samples, const int64_t *idx, int B,
+                                     float lr, float beta1, float beta2, float eps, float weight_decay,
+                                     float *loss_dev);
+
+/* Encode E elements of the device fields u, v, w ([E][512] FP32 each) to the device latent
+ * [E][48] (BF16 bit patterns, 16-byte aligned); decode a latent back to u, v, w (16-byte
+ * aligned).  Asynchronous. */
+SEM_API sem_status sem_ae_encode(sem_ae *ae, const float *u, const float *v, const float *w, int64_t E,
+                                 uint16_t *latent);
+SEM_API sem_status sem_ae_decode(sem_ae *ae, const uint16_t *latent, int64_t E, float *u, float *v, float *w);
+
+/* The library's tensor-core GEMM: C[M][N] = A[M][K] B[N][K]^T, A and B row-major BF16 bit
+ * patterns (device, 16-byte aligned), C FP32 (device).  M % 128 == 0, N % 64 == 0,
+ * K % 64 == 0 (else SEM_ERR_ARG).  FP32 accumulation.  Asynchronous. */
+SEM_API sem_status sem_gemm_bf16(sem_ctx *ctx, const uint16_t *A, const uint16_t *B, int64_t M, int N, int K,
+                                 float *C);
+
 /* Host-only queries (no device needed). */
 
 /* The library's marching-cubes case table: ntri[256] triangles per case and

@@ -200,3 +200,17 @@ def hausdorff(P: np.ndarray, Q: np.ndarray, chunk: int = 2048) -> float:
         return math.sqrt(worst)
 
     return max(directed(P, Q), directed(Q, P))
+
+
+def hausdorff_kd(P: np.ndarray, Q: np.ndarray) -> float:
+    """hausdorff() for large point sets: the nearest-neighbour distances come from a k-d tree
+    (scipy.spatial.cKDTree) instead of all pairs; same definition, pinned against the brute
+    force in the tests."""
+    from scipy.spatial import cKDTree
+    P = np.asarray(P, np.float64)
+    Q = np.asarray(Q, np.float64)
+    if P.size == 0 or Q.size == 0:
+        return 0.0 if P.size == Q.size else math.inf
+    d_pq = cKDTree(Q).query(P)[0].max()
+    d_qp = cKDTree(P).query(Q)[0].max()
+    return float(max(d_pq, d_qp))

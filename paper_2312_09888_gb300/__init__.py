@@ -77,6 +77,23 @@ def _declare(L):
     L.sem_mc_table.argtypes = [vp, vp]
     L.sem_mc_table.restype = i32
     L.sem_gll.argtypes = [i32, vp, vp]
+    L.sem_ae_param_count.restype = i64
+    L.sem_ae_param_count.argtypes = []
+    L.sem_ae_create.argtypes = [vp, i32, C.POINTER(vp)]
+    L.sem_ae_destroy.argtypes = [vp]
+    L.sem_ae_destroy.restype = None
+    L.sem_ae_set_params.argtypes = [vp, vp, i64]
+    L.sem_ae_get_params.argtypes = [vp, vp, i64]
+    L.sem_ae_get_state.argtypes = [vp, vp, vp, i64, C.POINTER(i64)]
+    L.sem_ae_set_state.argtypes = [vp, vp, vp, i64, i64]
+    L.sem_ae_set_normalization.argtypes = [vp, vp, vp]
+    L.sem_ae_get_normalization.argtypes = [vp, vp, vp]
+    L.sem_ae_fit_normalization.argtypes = [vp, vp, i64]
+    L.sem_ae_loss_grad.argtypes = [vp, vp, i64, vp, i32, C.POINTER(f32), vp, i64]
+    L.sem_ae_train_step.argtypes = [vp, vp, i64, vp, i32, f32, f32, f32, f32, f32, vp]
+    L.sem_ae_encode.argtypes = [vp, vp, vp, vp, i64, vp]
+    L.sem_ae_decode.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.sem_gemm_bf16.argtypes = [vp, vp, vp, i64, i32, i32, vp]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
@@ -354,6 +371,131 @@ def sem_gll(N: int):
     if st:
         raise SemError(st, f"sem_gll({N})")
     return xi, D
+
+
+# ------------------------------------------------------------------------ learned compression
+
+AE_LAYER_SHAPES = [("W1", (512, 1536)), ("b1", (512,)), ("W2", (48, 512)), ("b2", (48,)),
+                   ("W3", (512, 48)), ("b3", (512,)), ("W4", (1536, 512)), ("b4", (1536,))]
+
+
+def ae_flatten(params: dict) -> np.ndarray:
+    """{name: array} -> the flat FP32 host array of the C ABI (order W1 b1 W2 b2 W3 b3 W4 b4)."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                                                for k, _ in AE_LAYER_SHAPES]))
+
+
+def ae_unflatten(flat) -> dict:
+    out, at = {}, 0
+    for k, shp in AE_LAYER_SHAPES:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[at:at + n]).reshape(shp)
+        at += n
+    return out
+
+
+def sem_ae_param_count() -> int:
+    return int(get_lib().sem_ae_param_count())
+
+
+def sem_ae_create(ctx, batch: int):
+    h = C.c_void_p()
+    _check(ctx, get_lib().sem_ae_create(ctx, int(batch), C.byref(h)))
+    return h
+
+
+def sem_ae_destroy(ae) -> None:
+    if ae:
+        get_lib().sem_ae_destroy(ae)
+
+
+def sem_ae_set_params(ctx, ae, params) -> None:
+    flat = ae_flatten(params) if isinstance(params, dict) else np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, get_lib().sem_ae_set_params(ae, flat.ctypes.data_as(C.c_void_p), int(flat.size)))
+
+
+def sem_ae_get_params(ctx, ae) -> dict:
+    flat = np.zeros(sem_ae_param_count(), dtype=np.float32)
+    _check(ctx, get_lib().sem_ae_get_params(ae, flat.ctypes.data_as(C.c_void_p), int(flat.size)))
+    return ae_unflatten(flat)
+
+
+def sem_ae_get_state(ctx, ae):
+    n = sem_ae_param_count()
+    m, v, st = np.zeros(n, np.float32), np.zeros(n, np.float32), C.c_int64(0)
+    _check(ctx, get_lib().sem_ae_get_state(ae, m.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p), n,
+                                           C.byref(st)))
+    return m, v, st.value
+
+
+def sem_ae_set_state(ctx, ae, m, v, step: int) -> None:
+    m = np.ascontiguousarray(m, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    _check(ctx, get_lib().sem_ae_set_state(ae, m.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                                           int(m.size), int(step)))
+
+
+def sem_ae_set_normalization(ctx, ae, mean, std) -> None:
+    mu = np.ascontiguousarray(mean, np.float32)
+    sd = np.ascontiguousarray(std, np.float32)
+    _check(ctx, get_lib().sem_ae_set_normalization(ae, mu.ctypes.data_as(C.c_void_p), sd.ctypes.data_as(C.c_void_p)))
+
+
+def sem_ae_get_normalization(ctx, ae):
+    mu, sd = np.zeros(3, np.float32), np.zeros(3, np.float32)
+    _check(ctx, get_lib().sem_ae_get_normalization(ae, mu.ctypes.data_as(C.c_void_p), sd.ctypes.data_as(C.c_void_p)))
+    return mu, sd
+
+
+def sem_ae_fit_normalization(ctx, ae, samples) -> None:
+    import torch
+    _check(ctx, get_lib().sem_ae_fit_normalization(ae, _dev(samples, "samples", torch.float32),
+                                                   int(samples.shape[0])))
+
+
+def sem_ae_loss_grad(ctx, ae, samples, idx, want_grad: bool = True):
+    """(loss, {name: gradient}) of the batch samples[idx] (idx: device int64)."""
+    import torch
+    loss = C.c_float(0)
+    g = np.zeros(sem_ae_param_count(), np.float32) if want_grad else None
+    _check(ctx, get_lib().sem_ae_loss_grad(ae, _dev(samples, "samples", torch.float32), int(samples.shape[0]),
+                                           _dev(idx, "idx", torch.int64),
+                                           int(idx.numel()), C.byref(loss),
+                                           g.ctypes.data_as(C.c_void_p) if g is not None else None,
+                                           sem_ae_param_count()))
+    return loss.value, (ae_unflatten(g) if g is not None else None)
+
+
+def sem_ae_train_step(ctx, ae, samples, idx, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                      eps: float = 1e-8, weight_decay: float = 0.0, loss_dev=None) -> None:
+    import torch
+    _check(ctx, get_lib().sem_ae_train_step(ae, _dev(samples, "samples", torch.float32), int(samples.shape[0]),
+                                            _dev(idx, "idx", torch.int64), int(idx.numel()), float(lr), float(beta1),
+                                            float(beta2), float(eps), float(weight_decay),
+                                            _dev(loss_dev, "loss_dev", torch.float32, allow_none=True)))
+
+
+def sem_ae_encode(ctx, ae, u, v, w, latent) -> None:
+    """latent: device int16/uint16-sized tensor of E*48 BF16 values (torch.bfloat16 works)."""
+    import torch
+    E = u.numel() // 512
+    _check(ctx, get_lib().sem_ae_encode(ae, _dev(u, "u", torch.float32), _dev(v, "v", torch.float32),
+                                        _dev(w, "w", torch.float32), int(E), _dev(latent, "latent")))
+
+
+def sem_ae_decode(ctx, ae, latent, E: int, u, v, w) -> None:
+    import torch
+    _check(ctx, get_lib().sem_ae_decode(ae, _dev(latent, "latent"), int(E), _dev(u, "u", torch.float32),
+                                        _dev(v, "v", torch.float32), _dev(w, "w", torch.float32)))
+
+
+def sem_gemm_bf16(ctx, A, B, C_out) -> None:
+    """C_out[M][N] = A[M][K] B[N][K]^T (torch.bfloat16 A, B; float32 C) on the tensor cores."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    _check(ctx, get_lib().sem_gemm_bf16(ctx, _dev(A, "A", torch.bfloat16), _dev(B, "B", torch.bfloat16), int(M),
+                                        int(N), int(K), _dev(C_out, "C", torch.float32)))
 
 
 def exported_symbols():

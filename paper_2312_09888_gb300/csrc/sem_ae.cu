@@ -1,0 +1,1038 @@
+// sem_ae.cu -- the learned per-element compression: an MLP autoencoder trained and run on the
+// 5th-generation tensor cores in BF16 with FP32 accumulation.
+//
+// Method (the per-element compression for in-transit transfer, Sec. 4.2's motivation): per
+// element of order N = 7 the 3 x 512 nodal velocity values, z-scored per component, go
+// through
+//     encoder  H1 = X W1^T + b1, A1 = gelu(H1), Z = A1 W2^T + b2     (1536 -> 512 -> 48)
+//     decoder  H3 = Z W3^T + b3, A3 = gelu(H3), Y = A3 W4^T + b4     (48 -> 512 -> 1536)
+// gelu(x) = x Phi(x) (exact, via erff), loss = mean (Y - X)^2, AdamW updates (Loshchilov &
+// Hutter 2019).  The latent Z is stored in BF16: the decoder and the training graph both see
+// the BF16 latent, whose gradient passes through the rounding unchanged.
+//
+// Design (GB300): every product is one tcgen05 GEMM D[M][N] = A[M][K] B[N][K]^T with both
+// operands K-major BF16 tiles brought into shared memory by TMA (2-D tensor maps, 128-byte
+// swizzle), the accumulator in TMEM (128 lanes x BN FP32 columns), one elected thread issuing
+// the MMAs, and four epilogue warps reading TMEM back and applying the layer's fused tail
+// (bias, gelu, gelu', loss and its gradient, de-normalisation) before storing.  Products that
+// need a transposed operand (dW = dH^T A) take a transposed copy that the producing epilogue
+// wrote alongside the row-major one, so no GEMM needs an MN-major operand.  Widths are padded
+// to multiples of 64 (the 48-wide latent to 64 with zero weights, which stay zero).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "sem_internal.cuh"
+#include "sem_tc.cuh"
+
+typedef __nv_bfloat16 bf16;
+
+namespace {
+
+constexpr int BM = 128, BK = 64, STAGES = 4, GEMM_THREADS = 192;
+
+enum EpiMode : int {
+    EPI_F32 = 0,        // C32 = acc                                    (weight gradients)
+    EPI_BIAS_GELU = 1,  // H = acc + b -> out (H), aux (gelu H), out_t (gelu H)^T
+    EPI_BIAS = 2,       // Z = acc + b -> out, out_t                     (latent)
+    EPI_LOSS = 3,       // Y = acc + b; R = Y - X -> out (dY = scale R), out_t, loss += R^2
+    EPI_DGELU = 4,      // dH = acc * gelu'(H_in) -> out, out_t
+    EPI_PLAIN = 5,      // acc -> out, out_t
+    EPI_DECODE = 6,     // Y = acc + b -> fields[c][row][node] = Y std_c + mean_c
+    EPI_LATENT = 7,     // Z = acc + b -> out[row][0..47] (the transmitted latent)
+};
+
+struct EpiArgs {
+    int mode;
+    int64_t m_valid;     // rows >= m_valid are padding: nothing is stored for them
+    const float *bias;   // [N]
+    bf16 *out;           // row-major, leading dimension ld_out
+    int ld_out;
+    bf16 *out_t;         // transposed [N][ld_t]
+    int ld_t;
+    bf16 *aux;           // EPI_BIAS_GELU: gelu(H), leading dimension ld_out
+    const bf16 *in;      // EPI_DGELU: H; EPI_LOSS: target X (leading dimension ld_in)
+    int ld_in;
+    float *c32;          // EPI_F32, leading dimension ld_out
+    float *loss;         // EPI_LOSS accumulator
+    float scale;         // EPI_LOSS: 2 / (B D)
+    float *fields[3];    // EPI_DECODE
+    float mean[3], stdv[3];
+    int np3;
+};
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float x)
+{
+    return 0.5f * (1.f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void store8_bf16(bf16 *p, const float (&v)[8])
+{
+    __align__(16) bf16 t[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) t[c] = __float2bfloat16_rn(v[c]);
+    *reinterpret_cast<uint4 *>(p) = *reinterpret_cast<const uint4 *>(t);
+}
+
+__device__ __forceinline__ void load8_bf16(const bf16 *p, float (&v)[8])
+{
+    const uint4 raw = *reinterpret_cast<const uint4 *>(p);
+    const bf16 *t = reinterpret_cast<const bf16 *>(&raw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __bfloat162float(t[c]);
+}
+
+// The fused tail of one row's 8 consecutive output columns n .. n+7.
+__device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, float (&v)[8], float &loss_acc)
+{
+    if (row >= P.m_valid) {
+        if (P.mode == EPI_LOSS) {
+            // padding rows of a partial batch carry no gradient (their stale values would
+            // otherwise reach the weight gradients)
+            const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            store8_bf16(P.out + row * P.ld_out + n, z);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(0.f);
+        }
+        return;
+    }
+    switch (P.mode) {
+    case EPI_F32: {
+        float4 *dst = reinterpret_cast<float4 *>(P.c32 + row * P.ld_out + n);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        return;
+    }
+    case EPI_BIAS_GELU: {
+        float a[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            v[c] += P.bias[n + c];
+            // gelu of the BF16-rounded pre-activation, the value the backward pass sees
+            a[c] = gelu_f(__bfloat162float(__float2bfloat16_rn(v[c])));
+        }
+        store8_bf16(P.out + row * P.ld_out + n, v);
+        store8_bf16(P.aux + row * P.ld_out + n, a);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(a[c]);
+        return;
+    }
+    case EPI_BIAS:
+    case EPI_PLAIN: {
+        if (P.mode == EPI_BIAS)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] += P.bias[n + c];
+        store8_bf16(P.out + row * P.ld_out + n, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        return;
+    }
+    case EPI_LOSS: {
+        float x[8];
+        load8_bf16(P.in + row * P.ld_in + n, x);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float r = v[c] + P.bias[n + c] - x[c];
+            loss_acc = fmaf(r, r, loss_acc);
+            v[c] = P.scale * r;
+        }
+        store8_bf16(P.out + row * P.ld_out + n, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        return;
+    }
+    case EPI_DGELU: {
+        float h[8];
+        load8_bf16(P.in + row * P.ld_in + n, h);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] *= gelu_grad_f(h[c]);
+        store8_bf16(P.out + row * P.ld_out + n, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        return;
+    }
+    case EPI_DECODE: {
+        const int comp = n / P.np3, node = n % P.np3;
+        float4 *dst = reinterpret_cast<float4 *>(P.fields[comp] + row * P.np3 + node);
+        float y[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c] = fmaf(v[c] + P.bias[n + c], P.stdv[comp], P.mean[comp]);
+        dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+        dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+        return;
+    }
+    case EPI_LATENT: {
+        if (n >= 48) return;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] += P.bias[n + c];
+        store8_bf16(P.out + row * 48 + n, v);
+        return;
+    }
+    default: return;
+    }
+}
+
+// D[M][N] = A[M][K] B[N][K]^T for one BM x BN output tile per CTA.  Warp 0: TMA producer;
+// warp 1: TMEM owner and MMA issuer; warps 2..5: epilogue (warp w reads TMEM lanes
+// 32 (w % 4) .. + 31).  STAGES-deep ring of (A, B) K-slices of BK = 64 BF16 (one 128-byte
+// swizzle atom row).  Every wait is bounded: on a time-out the kernel records SEM_ERR_TIMEOUT,
+// stops issuing, waits (bounded) for its copies in flight, frees TMEM and returns.
+template <int BN>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
+                const __grid_constant__ EpiArgs P, int *err)
+{
+    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    __shared__ int s_consumed[STAGES];
+    // SW128 tiles need 1024-byte alignment
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K / BK;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            s_consumed[s] = 0;
+        }
+        mbar_init(&accf, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_base, BN);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    int issued[STAGES] = {0, 0, 0, 0};
+    if (warp == 0 && lane == 0) {
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, err)) {
+                s_abort = 1;
+                break;
+            }
+            if (*(volatile int *)&s_abort) break;
+            uint8_t *a = smem + s * STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(a, &tmA, kb * BK, blockIdx.x * BM, &full[s]);
+            tma_load_2d(a + A_BYTES, &tmB, kb * BK, blockIdx.y * BN, &full[s]);
+            ++issued[s];
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t IDESC = tc::idesc_f16(BM, BN, true);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES, round = kb / STAGES;
+            if (*(volatile int *)&s_abort || !mbar_wait_bounded(&full[s], round & 1, err)) {
+                s_abort = 1;
+                break;
+            }
+            s_consumed[s] = round + 1;
+            tc::fence_after_sync();
+            const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+                tc::mma_f16(tmem, tc::desc_k_sw128(a + kk * 32), tc::desc_k_sw128(b + kk * 32), IDESC,
+                            (kb | kk) != 0 ? 1u : 0u);
+            tc::commit(&empty[s]);
+        }
+        tc::commit(&accf);  // also on an abort: the epilogue's wait then covers the issued MMAs
+    } else if (warp >= 2) {
+        // warp-uniform: the TMEM loads below are collective over the warp
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&accf, 0, err));
+        if (!ok) s_abort = 1;
+        tc::fence_after_sync();
+        if (ok && !*(volatile int *)&s_abort) {
+            const int q = warp & 3;
+            const int64_t row = (int64_t)blockIdx.x * BM + q * 32 + lane;
+            float loss_acc = 0.f;
+            for (int c0 = 0; c0 < BN; c0 += 8) {
+                uint32_t r[8];
+                tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tc::tmem_wait_ld();
+                float v[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+                epilogue8(P, row, blockIdx.y * BN + c0, v, loss_acc);
+            }
+            if (P.mode == EPI_LOSS) {
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, d);
+                if (lane == 0) atomicAdd(P.loss, loss_acc);
+            }
+        }
+    }
+    // on an abort: wait (bounded) for this CTA's copies still in flight
+    if (warp == 0 && lane == 0 && *(volatile int *)&s_abort) {
+        for (int s = 0; s < STAGES; ++s)
+            if (issued[s] > s_consumed[s]) mbar_wait_bounded(&full[s], s_consumed[s] & 1, nullptr);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, BN);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// element-wise kernels
+// ------------------------------------------------------------------------------------------
+
+// X[r][c] = (sample(r)[c] - mean) / std (BF16), and X^T; rows >= B are zero.  A sample is
+// either row idx[r] of samples[n][3*np3] or element e0 + r of the fields u, v, w.  One block
+// per 32 x 32 tile (rows r0.., columns c0..), transposed through shared memory so both X and
+// X^T are written with coalesced stores.
+__global__ void __launch_bounds__(256) k_pack(const float *__restrict__ samples, const int64_t *__restrict__ idx,
+                                              int64_t n_samples, const float *__restrict__ f0,
+                                              const float *__restrict__ f1, const float *__restrict__ f2, int64_t e0,
+                                              int B, int Bp, int np3, float m0, float m1, float m2, float r0,
+                                              float r1, float r2, bf16 *__restrict__ X, bf16 *__restrict__ XT,
+                                              int *err)
+{
+    __shared__ bf16 tile[32][34];
+    const int D = 3 * np3;
+    const int c0 = blockIdx.x * 32, rbase = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    const int c = c0 + tx, comp = c / np3, node = c % np3;
+    const float mean = comp == 0 ? m0 : comp == 1 ? m1 : m2, rs = comp == 0 ? r0 : comp == 1 ? r1 : r2;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int r = rbase + rr;
+        float x = 0.f;
+        if (r < B) {
+            float raw = 0.f;
+            if (samples) {
+                const int64_t j = idx[r];
+                if (j >= 0 && j < n_samples) {
+                    raw = samples[j * D + c];
+                } else {
+                    // an index outside the sample array: flagged, and read as the mean
+                    if (err) atomicOr(err, 1 << SEM_ERR_ARG);
+                    raw = mean;
+                }
+            } else {
+                raw = (comp == 0 ? f0 : comp == 1 ? f1 : f2)[(e0 + r) * np3 + node];
+            }
+            x = (raw - mean) * rs;
+        }
+        const bf16 b = __float2bfloat16_rn(x);
+        X[(int64_t)r * D + c] = b;
+        tile[rr][tx] = b;
+    }
+    if (!XT) return;
+    __syncthreads();
+    for (int cc = ty; cc < 32; cc += 8) XT[(int64_t)(c0 + cc) * Bp + rbase + tx] = tile[tx][cc];
+}
+
+// latent [E][48] (BF16) rows e0 .. e0 + B - 1 -> Z [Bp][64] with zero padding
+__global__ void k_latent_in(const bf16 *__restrict__ lat, int64_t e0, int B, int Bp, bf16 *__restrict__ Z)
+{
+    const int64_t total = (int64_t)Bp * 64;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / 64), c = (int)(t % 64);
+        Z[t] = (r < B && c < 48) ? lat[(e0 + r) * 48 + c] : __float2bfloat16_rn(0.f);
+    }
+}
+
+// out[n] = sum_{r < B} M^T[n][r]: one warp per row of a transposed BF16 matrix [N][ld]
+// (16-byte loads, fixed summation order, so the result is deterministic)
+__global__ void k_rowsum(const bf16 *__restrict__ MT, int N, int B, int ld, float *__restrict__ out)
+{
+    const int n = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (n >= N) return;
+    const bf16 *row = MT + (int64_t)n * ld;
+    float s = 0.f;
+    const int B8 = B & ~7;
+    for (int r = lane * 8; r < B8; r += 256) {
+        float v[8];
+        load8_bf16(row + r, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s += v[c];
+    }
+    for (int r = B8 + lane; r < B; r += 32) s += __bfloat162float(row[r]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) out[n] = s;
+}
+
+struct TensorDesc {
+    int64_t off;      // offset of the tensor in the flat FP32 arrays
+    int rows, cols;   // padded shape (rows x cols), row-major
+    int64_t wb_off;   // BF16 copy [rows][cols], -1 if none (biases)
+    int64_t wt_off;   // BF16 transpose [cols][rows], -1 if none
+};
+constexpr int NT = 8;
+struct AdamTable {
+    TensorDesc t[NT];
+};
+
+// AdamW over every parameter (FP32 master, moments m and v), then the BF16 copies the GEMMs
+// read: W [rows][cols] and W^T [cols][rows].
+__global__ void k_adamw(const __grid_constant__ AdamTable T, int64_t n_total, float *__restrict__ w,
+                        float *__restrict__ m, float *__restrict__ v, const float *__restrict__ g, float lr, float b1,
+                        float b2, float eps, float wd, float bc1, float bc2, bf16 *__restrict__ wb,
+                        bf16 *__restrict__ wt, int update)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_total; t += (int64_t)gridDim.x * blockDim.x) {
+        float p = w[t];
+        if (update) {
+            const float gt = g[t];
+            const float mt = b1 * m[t] + (1.f - b1) * gt;
+            const float vt = b2 * v[t] + (1.f - b2) * gt * gt;
+            m[t] = mt;
+            v[t] = vt;
+            const float mhat = mt / bc1, vhat = vt / bc2;
+            p = p - lr * (mhat / (sqrtf(vhat) + eps) + wd * p);
+            w[t] = p;
+        }
+        int k = 0;
+        while (k < NT - 1 && t >= T.t[k + 1].off) ++k;
+        const TensorDesc &d = T.t[k];
+        if (d.wb_off >= 0) {
+            const int64_t local = t - d.off;
+            const int r = (int)(local / d.cols), c = (int)(local % d.cols);
+            const bf16 b = __float2bfloat16_rn(p);
+            wb[d.wb_off + local] = b;
+            if (d.wt_off >= 0) wt[d.wt_off + (int64_t)c * d.rows + r] = b;
+        }
+    }
+}
+
+// per component sum and sum of squares (FP64) of samples[n][3*np3]
+__global__ void k_moments(const float *__restrict__ samples, int64_t n, int np3, double *__restrict__ acc)
+{
+    __shared__ double s[6][256];
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t total = n * 3 * np3;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)((t % (3 * np3)) / np3);
+        const double x = samples[t];
+        a[comp] += x;
+        a[3 + comp] += x * x;
+    }
+    for (int q = 0; q < 6; ++q) s[q][threadIdx.x] = a[q];
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int q = 0; q < 6; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 6; ++q) atomicAdd(acc + q, s[q][0]);
+}
+
+// ------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][cols] (cols = K, contiguous), box 64 x box_rows
+sem_status make_map(sem_ctx *ctx, CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return sem_fail(ctx, SEM_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) != 0 || cols % 64 != 0)
+        return sem_fail(ctx, SEM_ERR_ARG, "GEMM operand not 16-byte aligned or K not a multiple of 64");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return sem_fail(ctx, SEM_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return SEM_OK;
+}
+
+template <int BN>
+size_t gemm_smem() { return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024; }
+
+// D = A B^T with A [M][K], B [N][K] (BF16, row-major), M % 128 == 0, N % BN == 0, K % 64 == 0
+sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, int K, const EpiArgs &P,
+                const char *name = "k_gemm_bf16")
+{
+    if (M % BM != 0 || K % BK != 0 || N % 64 != 0 || M <= 0 || N <= 0 || K <= 0)
+        return sem_fail(ctx, SEM_ERR_ARG, "GEMM shape %lld x %d x %d not tileable", (long long)M, N, K);
+    CUtensorMap ta, tb;
+    const int bn = (N % 128 == 0) ? 128 : 64;
+    SEM_TRY(make_map(ctx, &ta, A, M, K, BM));
+    SEM_TRY(make_map(ctx, &tb, B, N, K, bn));
+    const dim3 grid((unsigned)(M / BM), (unsigned)(N / bn));
+    if (bn == 128) {
+        static bool set = false;
+        const size_t sm = gemm_smem<128>();
+        if (!set) {
+            SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            set = true;
+        }
+        SEM_TRACED(ctx, name, k_gemm_bf16<128><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
+    } else {
+        static bool set = false;
+        const size_t sm = gemm_smem<64>();
+        if (!set) {
+            SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            set = true;
+        }
+        SEM_TRACED(ctx, name, k_gemm_bf16<64><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
+    }
+    return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16 launch");
+}
+
+EpiArgs epi(int mode, int64_t m_valid)
+{
+    EpiArgs e;
+    memset(&e, 0, sizeof e);
+    e.mode = mode;
+    e.m_valid = m_valid;
+    return e;
+}
+
+unsigned grid_for(int64_t n, int threads, int sm) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 8LL * sm)); }
+
+}  // namespace
+
+// ==========================================================================================
+// the autoencoder object
+// ==========================================================================================
+struct sem_ae {
+    sem_ctx *ctx = nullptr;
+    int Bp = 0;  // batch rows (multiple of 128)
+    // flat FP32 arrays of the padded parameters: W1 [512][1536], b1 [512], W2 [64][512],
+    // b2 [64], W3 [512][64], b3 [512], W4 [1536][512], b4 [1536]
+    AdamTable tab;
+    int64_t n_param = 0;
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;
+    bf16 *wb = nullptr, *wt = nullptr;
+    int64_t n_wb = 0;
+    float mean[3] = {0, 0, 0}, stdv[3] = {1, 1, 1};
+    int64_t step = 0;
+    float *loss = nullptr;  // device
+    // activations (BF16): rows Bp
+    bf16 *X = nullptr, *XT = nullptr, *H1 = nullptr, *A1 = nullptr, *A1T = nullptr, *Z = nullptr, *ZT = nullptr;
+    bf16 *H3 = nullptr, *A3 = nullptr, *A3T = nullptr, *dY = nullptr, *dYT = nullptr, *dH3 = nullptr, *dH3T = nullptr;
+    bf16 *dZ = nullptr, *dZT = nullptr, *dH1 = nullptr, *dH1T = nullptr;
+    void *arena = nullptr;
+};
+
+namespace {
+constexpr int D_IN = 1536, D_H = 512, D_ZP = 64, NP3_AE = 512;  // widths (latent 48 padded to 64)
+// unpadded parameter shapes, in the order of the flat host arrays
+const int kShape[8][2] = {{512, 1536}, {512, 1}, {48, 512}, {48, 1}, {512, 48}, {512, 1}, {1536, 512}, {1536, 1}};
+// padded shapes on the device
+const int kPad[8][2] = {{512, 1536}, {512, 1}, {64, 512}, {64, 1}, {512, 64}, {512, 1}, {1536, 512}, {1536, 1}};
+
+int64_t host_param_count()
+{
+    int64_t n = 0;
+    for (auto &s : kShape) n += (int64_t)s[0] * s[1];
+    return n;
+}
+
+sem_status ae_forward(sem_ae *ae, int B, bool want_loss, bool training)
+{
+    sem_ctx *ctx = ae->ctx;
+    const int Bp = ae->Bp;
+    const TensorDesc *T = ae->tab.t;
+    const bf16 *W1 = ae->wb + T[0].wb_off, *W2 = ae->wb + T[2].wb_off, *W3 = ae->wb + T[4].wb_off,
+               *W4 = ae->wb + T[6].wb_off;
+    EpiArgs e = epi(EPI_BIAS_GELU, Bp);
+    e.bias = ae->w + T[1].off;
+    e.out = ae->H1;
+    e.aux = ae->A1;
+    e.ld_out = D_H;
+    e.out_t = ae->A1T;
+    e.ld_t = Bp;
+    SEM_TRY(gemm(ctx, ae->X, W1, Bp, D_H, D_IN, e, "k_gemm_bf16 fwd1"));
+    e = epi(EPI_BIAS, Bp);
+    e.bias = ae->w + T[3].off;
+    e.out = ae->Z;
+    e.ld_out = D_ZP;
+    e.out_t = ae->ZT;
+    e.ld_t = Bp;
+    SEM_TRY(gemm(ctx, ae->A1, W2, Bp, D_ZP, D_H, e, "k_gemm_bf16 fwd2"));
+    e = epi(EPI_BIAS_GELU, Bp);
+    e.bias = ae->w + T[5].off;
+    e.out = ae->H3;
+    e.aux = ae->A3;
+    e.ld_out = D_H;
+    e.out_t = ae->A3T;
+    e.ld_t = Bp;
+    SEM_TRY(gemm(ctx, ae->Z, W3, Bp, D_H, D_ZP, e, "k_gemm_bf16 fwd3"));
+    if (!want_loss) return SEM_OK;
+    e = epi(EPI_LOSS, B);
+    e.bias = ae->w + T[7].off;
+    e.out = ae->dY;
+    e.ld_out = D_IN;
+    e.out_t = ae->dYT;
+    e.ld_t = Bp;
+    e.in = ae->X;
+    e.ld_in = D_IN;
+    e.loss = ae->loss;
+    e.scale = 2.0f / ((float)B * (float)D_IN);
+    SEM_CU(ctx, cudaMemsetAsync(ae->loss, 0, sizeof(float), ctx->stream));
+    SEM_TRY(gemm(ctx, ae->A3, W4, Bp, D_IN, D_H, e, "k_gemm_bf16 fwd4"));
+    (void)training;
+    return SEM_OK;
+}
+
+sem_status ae_backward(sem_ae *ae, int B)
+{
+    sem_ctx *ctx = ae->ctx;
+    const int Bp = ae->Bp;
+    const TensorDesc *T = ae->tab.t;
+    const bf16 *W2t = ae->wt + T[2].wt_off, *W3t = ae->wt + T[4].wt_off, *W4t = ae->wt + T[6].wt_off;
+    float *g = ae->g;
+    // layer 4: dA3 = dY W4 -> dH3 = dA3 gelu'(H3); dW4 = dY^T A3
+    EpiArgs e = epi(EPI_DGELU, Bp);
+    e.out = ae->dH3;
+    e.ld_out = D_H;
+    e.out_t = ae->dH3T;
+    e.ld_t = Bp;
+    e.in = ae->H3;
+    e.ld_in = D_H;
+    SEM_TRY(gemm(ctx, ae->dY, W4t, Bp, D_H, D_IN, e, "k_gemm_bf16 dx4"));
+    e = epi(EPI_F32, D_IN);
+    e.c32 = g + T[6].off;
+    e.ld_out = D_H;
+    SEM_TRY(gemm(ctx, ae->dYT, ae->A3T, D_IN, D_H, Bp, e, "k_gemm_bf16 dw4"));
+    // layer 3: dZ = dH3 W3; dW3 = dH3^T Z
+    e = epi(EPI_PLAIN, Bp);
+    e.out = ae->dZ;
+    e.ld_out = D_ZP;
+    e.out_t = ae->dZT;
+    e.ld_t = Bp;
+    SEM_TRY(gemm(ctx, ae->dH3, W3t, Bp, D_ZP, D_H, e, "k_gemm_bf16 dx3"));
+    e = epi(EPI_F32, D_H);
+    e.c32 = g + T[4].off;
+    e.ld_out = D_ZP;
+    SEM_TRY(gemm(ctx, ae->dH3T, ae->ZT, D_H, D_ZP, Bp, e, "k_gemm_bf16 dw3"));
+    // layer 2: dA1 = dZ W2 -> dH1 = dA1 gelu'(H1); dW2 = dZ^T A1 (dZ^T padded to 128 rows)
+    e = epi(EPI_DGELU, Bp);
+    e.out = ae->dH1;
+    e.ld_out = D_H;
+    e.out_t = ae->dH1T;
+    e.ld_t = Bp;
+    e.in = ae->H1;
+    e.ld_in = D_H;
+    SEM_TRY(gemm(ctx, ae->dZ, W2t, Bp, D_H, D_ZP, e, "k_gemm_bf16 dx2"));
+    e = epi(EPI_F32, D_ZP);
+    e.c32 = g + T[2].off;
+    e.ld_out = D_H;
+    SEM_TRY(gemm(ctx, ae->dZT, ae->A1T, 128, D_H, Bp, e, "k_gemm_bf16 dw2"));
+    // layer 1: dW1 = dH1^T X
+    e = epi(EPI_F32, D_H);
+    e.c32 = g + T[0].off;
+    e.ld_out = D_IN;
+    SEM_TRY(gemm(ctx, ae->dH1T, ae->XT, D_H, D_IN, Bp, e, "k_gemm_bf16 dw1"));
+    // bias gradients: row sums of the transposed gradients (the padding columns are zero)
+    SEM_TRACED(ctx, "k_rowsum", k_rowsum<<<(D_IN + 7) / 8, 256, 0, ctx->stream>>>(ae->dYT, D_IN, B, Bp, g + T[7].off));
+    SEM_TRACED(ctx, "k_rowsum", k_rowsum<<<(D_H + 7) / 8, 256, 0, ctx->stream>>>(ae->dH3T, D_H, B, Bp, g + T[5].off));
+    SEM_TRACED(ctx, "k_rowsum", k_rowsum<<<(D_ZP + 7) / 8, 256, 0, ctx->stream>>>(ae->dZT, D_ZP, B, Bp, g + T[3].off));
+    SEM_TRACED(ctx, "k_rowsum", k_rowsum<<<(D_H + 7) / 8, 256, 0, ctx->stream>>>(ae->dH1T, D_H, B, Bp, g + T[1].off));
+    return sem_cuda(ctx, cudaGetLastError(), "k_rowsum launch");
+}
+
+sem_status ae_refresh_copies(sem_ae *ae, bool update, float lr, float b1, float b2, float eps, float wd)
+{
+    sem_ctx *ctx = ae->ctx;
+    float bc1 = 1.f, bc2 = 1.f;
+    if (update) {
+        ae->step += 1;
+        bc1 = (float)(1.0 - pow((double)b1, (double)ae->step));
+        bc2 = (float)(1.0 - pow((double)b2, (double)ae->step));
+    }
+    SEM_TRACED(ctx, "k_adamw", k_adamw<<<grid_for(ae->n_param, 256, ctx->sm_count), 256, 0, ctx->stream>>>(
+                                   ae->tab, ae->n_param, ae->w, ae->m, ae->v, ae->g, lr, b1, b2, eps, wd, bc1, bc2,
+                                   ae->wb, ae->wt, update ? 1 : 0));
+    return sem_cuda(ctx, cudaGetLastError(), "k_adamw launch");
+}
+
+sem_status ae_pack_samples(sem_ae *ae, const float *samples, int64_t n_samples, const int64_t *idx, int B)
+{
+    sem_ctx *ctx = ae->ctx;
+    const dim3 pg(D_IN / 32, ae->Bp / 32);
+    SEM_TRACED(ctx, "k_pack", k_pack<<<pg, 256, 0, ctx->stream>>>(
+                                  samples, idx, n_samples, nullptr, nullptr, nullptr, 0, B, ae->Bp, NP3_AE, ae->mean[0],
+                                  ae->mean[1], ae->mean[2], 1.f / ae->stdv[0], 1.f / ae->stdv[1], 1.f / ae->stdv[2],
+                                  ae->X, ae->XT, ctx->d_flag));
+    return sem_cuda(ctx, cudaGetLastError(), "k_pack launch");
+}
+
+sem_status check_ae(sem_ae *ae, const char *fn)
+{
+    if (!ae) return SEM_ERR_ARG;
+    SEM_CU(ae->ctx, cudaSetDevice(ae->ctx->device));
+    (void)fn;
+    return SEM_OK;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+sem_status sem_ae_create(sem_ctx *ctx, int batch, sem_ae **out)
+{
+    if (!ctx || !out) return SEM_ERR_ARG;
+    *out = nullptr;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (batch < 128 || batch % 128 != 0 || batch > (1 << 20))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_create: batch %d is not a positive multiple of 128", batch);
+    sem_ae *ae = new sem_ae();
+    ae->ctx = ctx;
+    ae->Bp = batch;
+    // parameter table (padded shapes)
+    int64_t off = 0, wboff = 0;
+    for (int k = 0; k < NT; ++k) {
+        TensorDesc &d = ae->tab.t[k];
+        d.off = off;
+        d.rows = kPad[k][0];
+        d.cols = kPad[k][1];
+        off += (int64_t)d.rows * d.cols;
+        if (kPad[k][1] > 1) {
+            d.wb_off = wboff;
+            wboff += (int64_t)d.rows * d.cols;
+        } else {
+            d.wb_off = -1;
+        }
+    }
+    ae->n_param = off;
+    ae->n_wb = wboff;
+    for (int k = 0; k < NT; ++k) ae->tab.t[k].wt_off = ae->tab.t[k].wb_off;  // same offsets in the transpose array
+    // one arena: params, moments, gradients, BF16 copies, activations
+    const int Bp = batch;
+    const size_t fbytes = sizeof(float) * (size_t)ae->n_param;
+    const size_t wbytes = sizeof(bf16) * (size_t)ae->n_wb;
+    struct Piece {
+        void **dst;
+        size_t bytes;
+    };
+    const size_t r = sizeof(bf16) * (size_t)Bp;
+    std::vector<Piece> pieces = {
+        {(void **)&ae->w, fbytes}, {(void **)&ae->m, fbytes}, {(void **)&ae->v, fbytes}, {(void **)&ae->g, fbytes},
+        {(void **)&ae->wb, wbytes}, {(void **)&ae->wt, wbytes}, {(void **)&ae->loss, 256},
+        {(void **)&ae->X, r * D_IN}, {(void **)&ae->XT, r * D_IN}, {(void **)&ae->H1, r * D_H},
+        {(void **)&ae->A1, r * D_H}, {(void **)&ae->A1T, r * D_H}, {(void **)&ae->Z, r * D_ZP},
+        {(void **)&ae->ZT, r * D_ZP}, {(void **)&ae->H3, r * D_H}, {(void **)&ae->A3, r * D_H},
+        {(void **)&ae->A3T, r * D_H}, {(void **)&ae->dY, r * D_IN}, {(void **)&ae->dYT, r * D_IN},
+        {(void **)&ae->dH3, r * D_H}, {(void **)&ae->dH3T, r * D_H}, {(void **)&ae->dZ, r * D_ZP},
+        {(void **)&ae->dZT, r * 128}, {(void **)&ae->dH1, r * D_H}, {(void **)&ae->dH1T, r * D_H}};
+    size_t total = 0;
+    for (auto &p : pieces) total += (p.bytes + 1023) / 1024 * 1024;
+    cudaError_t e = cudaMalloc(&ae->arena, total);
+    if (e != cudaSuccess) {
+        delete ae;
+        return sem_cuda(ctx, e, "sem_ae_create: cudaMalloc");
+    }
+    size_t at = 0;
+    for (auto &p : pieces) {
+        *p.dst = static_cast<char *>(ae->arena) + at;
+        at += (p.bytes + 1023) / 1024 * 1024;
+    }
+    // everything starts at zero (padding rows/columns of weights and dZ^T stay zero)
+    e = cudaMemsetAsync(ae->arena, 0, total, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(ae->arena);
+        delete ae;
+        return sem_cuda(ctx, e, "sem_ae_create: memset");
+    }
+    *out = ae;
+    return SEM_OK;
+}
+
+void sem_ae_destroy(sem_ae *ae)
+{
+    if (!ae) return;
+    cudaSetDevice(ae->ctx->device);
+    cudaStreamSynchronize(ae->ctx->stream);
+    if (ae->arena) cudaFree(ae->arena);
+    delete ae;
+}
+
+int64_t sem_ae_param_count(void) { return host_param_count(); }
+
+// host flat unpadded <-> device padded
+static void scatter_params(const float *host, std::vector<float> &dev, const AdamTable &tab)
+{
+    int64_t h = 0;
+    for (int k = 0; k < NT; ++k) {
+        const TensorDesc &d = tab.t[k];
+        for (int rr = 0; rr < kShape[k][0]; ++rr)
+            for (int cc = 0; cc < kShape[k][1]; ++cc) dev[d.off + (int64_t)rr * d.cols + cc] = host[h++];
+    }
+}
+
+static void gather_params(const std::vector<float> &dev, float *host, const AdamTable &tab)
+{
+    int64_t h = 0;
+    for (int k = 0; k < NT; ++k) {
+        const TensorDesc &d = tab.t[k];
+        for (int rr = 0; rr < kShape[k][0]; ++rr)
+            for (int cc = 0; cc < kShape[k][1]; ++cc) host[h++] = dev[d.off + (int64_t)rr * d.cols + cc];
+    }
+}
+
+static sem_status copy_flat(sem_ae *ae, float *dev_arr, const float *host, int64_t n, bool to_dev, float *host_out)
+{
+    sem_ctx *ctx = ae->ctx;
+    if (n != host_param_count())
+        return sem_fail(ctx, SEM_ERR_ARG, "autoencoder arrays hold %lld values, got %lld", (long long)host_param_count(),
+                        (long long)n);
+    std::vector<float> buf((size_t)ae->n_param, 0.f);
+    if (to_dev) {
+        scatter_params(host, buf, ae->tab);
+        SEM_CU(ctx, cudaMemcpyAsync(dev_arr, buf.data(), sizeof(float) * buf.size(), cudaMemcpyHostToDevice, ctx->stream));
+        SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    } else {
+        SEM_CU(ctx, cudaMemcpyAsync(buf.data(), dev_arr, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost, ctx->stream));
+        SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        gather_params(buf, host_out, ae->tab);
+    }
+    return SEM_OK;
+}
+
+sem_status sem_ae_set_params(sem_ae *ae, const float *host, int64_t n)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_set_params"));
+    if (!host) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_set_params: host is NULL");
+    SEM_TRY(copy_flat(ae, ae->w, host, n, true, nullptr));
+    return ae_refresh_copies(ae, false, 0.f, 0.f, 0.f, 0.f, 0.f);
+}
+
+sem_status sem_ae_get_params(sem_ae *ae, float *host, int64_t n)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_get_params"));
+    if (!host) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_get_params: host is NULL");
+    return copy_flat(ae, ae->w, nullptr, n, false, host);
+}
+
+sem_status sem_ae_get_state(sem_ae *ae, float *m_host, float *v_host, int64_t n, int64_t *step)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_get_state"));
+    if (!m_host || !v_host || !step) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_get_state: NULL argument");
+    SEM_TRY(copy_flat(ae, ae->m, nullptr, n, false, m_host));
+    SEM_TRY(copy_flat(ae, ae->v, nullptr, n, false, v_host));
+    *step = ae->step;
+    return SEM_OK;
+}
+
+sem_status sem_ae_set_state(sem_ae *ae, const float *m_host, const float *v_host, int64_t n, int64_t step)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_set_state"));
+    if (!m_host || !v_host || step < 0) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_set_state: bad argument");
+    SEM_TRY(copy_flat(ae, ae->m, m_host, n, true, nullptr));
+    SEM_TRY(copy_flat(ae, ae->v, v_host, n, true, nullptr));
+    ae->step = step;
+    return SEM_OK;
+}
+
+sem_status sem_ae_set_normalization(sem_ae *ae, const float mean[3], const float stdv[3])
+{
+    SEM_TRY(check_ae(ae, "sem_ae_set_normalization"));
+    if (!mean || !stdv) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_set_normalization: NULL");
+    for (int c = 0; c < 3; ++c) {
+        if (!(stdv[c] > 0.f) || !isfinite(mean[c]))
+            return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_set_normalization: std must be positive");
+        ae->mean[c] = mean[c];
+        ae->stdv[c] = stdv[c];
+    }
+    return SEM_OK;
+}
+
+sem_status sem_ae_get_normalization(sem_ae *ae, float mean[3], float stdv[3])
+{
+    SEM_TRY(check_ae(ae, "sem_ae_get_normalization"));
+    if (!mean || !stdv) return sem_fail(ae->ctx, SEM_ERR_ARG, "sem_ae_get_normalization: NULL");
+    for (int c = 0; c < 3; ++c) {
+        mean[c] = ae->mean[c];
+        stdv[c] = ae->stdv[c];
+    }
+    return SEM_OK;
+}
+
+sem_status sem_ae_fit_normalization(sem_ae *ae, const float *samples, int64_t n)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_fit_normalization"));
+    sem_ctx *ctx = ae->ctx;
+    if (!samples || n < 2) return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_fit_normalization: need >= 2 samples");
+    void *scr;
+    SEM_TRY(sem_scratch(ctx, SCR_MISC, 6 * sizeof(double), &scr));
+    double *acc = static_cast<double *>(scr);
+    SEM_CU(ctx, cudaMemsetAsync(acc, 0, 6 * sizeof(double), ctx->stream));
+    SEM_TRACED(ctx, "k_moments", k_moments<<<grid_for(n * 3 * NP3_AE, 256, ctx->sm_count), 256, 0, ctx->stream>>>(
+                                     samples, n, NP3_AE, acc));
+    SEM_CU(ctx, cudaGetLastError());
+    double h[6];
+    SEM_CU(ctx, cudaMemcpyAsync(h, acc, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+    SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+    // per-component means; one common scale, the root of the mean per-component variance, so a
+    // component that carries only noise (w of a Taylor-Green field) is not blown up to unit
+    // variance
+    const double cnt = (double)n * NP3_AE;
+    double var = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        const double mu = h[c] / cnt;
+        var += (h[3 + c] / cnt - mu * mu) / 3.0;
+        ae->mean[c] = (float)mu;
+    }
+    const float sd = (float)sqrt(var > 1e-30 ? var : 1e-30);
+    for (int c = 0; c < 3; ++c) ae->stdv[c] = sd;
+    return SEM_OK;
+}
+
+sem_status sem_ae_loss_grad(sem_ae *ae, const float *samples, int64_t n_samples, const int64_t *idx, int B,
+                            float *loss_host, float *grad_host, int64_t n)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_loss_grad"));
+    sem_ctx *ctx = ae->ctx;
+    if (!samples || !idx || B < 1 || B > ae->Bp || n_samples < 1)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_loss_grad: need samples, idx and 1 <= B <= %d", ae->Bp);
+    SEM_TRY(ae_pack_samples(ae, samples, n_samples, idx, B));
+    SEM_TRY(ae_forward(ae, B, true, true));
+    SEM_TRY(ae_backward(ae, B));
+    if (loss_host) {
+        float l = 0.f;
+        SEM_CU(ctx, cudaMemcpyAsync(&l, ae->loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
+        *loss_host = l / ((float)B * (float)D_IN);
+    }
+    if (grad_host) SEM_TRY(copy_flat(ae, ae->g, nullptr, n, false, grad_host));
+    return SEM_OK;
+}
+
+sem_status sem_ae_train_step(sem_ae *ae, const float *samples, int64_t n_samples, const int64_t *idx, int B,
+                             float lr, float beta1, float beta2, float eps, float weight_decay, float *loss_dev)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_train_step"));
+    sem_ctx *ctx = ae->ctx;
+    if (!samples || !idx || B < 1 || B > ae->Bp || n_samples < 1)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_train_step: need samples, idx and 1 <= B <= %d", ae->Bp);
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_train_step: bad hyper-parameters");
+    SEM_TRY(ae_pack_samples(ae, samples, n_samples, idx, B));
+    SEM_TRY(ae_forward(ae, B, true, true));
+    SEM_TRY(ae_backward(ae, B));
+    if (loss_dev)
+        SEM_CU(ctx, cudaMemcpyAsync(loss_dev, ae->loss, sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+    return ae_refresh_copies(ae, true, lr, beta1, beta2, eps, weight_decay);
+}
+
+sem_status sem_ae_encode(sem_ae *ae, const float *u, const float *v, const float *w, int64_t E, uint16_t *latent)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_encode"));
+    sem_ctx *ctx = ae->ctx;
+    if (E < 0 || (E > 0 && (!u || !v || !w || !latent))) return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_encode: bad arguments");
+    if ((reinterpret_cast<uintptr_t>(latent) & 15u) != 0)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_encode: latent must be 16-byte aligned");
+    const int Bp = ae->Bp;
+    for (int64_t e0 = 0; e0 < E; e0 += Bp) {
+        const int B = (int)std::min<int64_t>(Bp, E - e0);
+        const dim3 pg(D_IN / 32, Bp / 32);
+        SEM_TRACED(ctx, "k_pack", k_pack<<<pg, 256, 0, ctx->stream>>>(
+                                      nullptr, nullptr, 0, u, v, w, e0, B, Bp, NP3_AE, ae->mean[0], ae->mean[1],
+                                      ae->mean[2], 1.f / ae->stdv[0], 1.f / ae->stdv[1], 1.f / ae->stdv[2], ae->X,
+                                      nullptr, nullptr));
+        SEM_CU(ctx, cudaGetLastError());
+        const TensorDesc *T = ae->tab.t;
+        EpiArgs e = epi(EPI_BIAS_GELU, Bp);
+        e.bias = ae->w + T[1].off;
+        e.out = ae->H1;
+        e.aux = ae->A1;
+        e.ld_out = D_H;
+        e.out_t = ae->A1T;
+        e.ld_t = Bp;
+        SEM_TRY(gemm(ctx, ae->X, ae->wb + T[0].wb_off, Bp, D_H, D_IN, e));
+        e = epi(EPI_LATENT, B);
+        e.bias = ae->w + T[3].off;
+        e.out = reinterpret_cast<bf16 *>(latent) + e0 * 48;
+        SEM_TRY(gemm(ctx, ae->A1, ae->wb + T[2].wb_off, Bp, D_ZP, D_H, e));
+    }
+    return SEM_OK;
+}
+
+sem_status sem_ae_decode(sem_ae *ae, const uint16_t *latent, int64_t E, float *u, float *v, float *w)
+{
+    SEM_TRY(check_ae(ae, "sem_ae_decode"));
+    sem_ctx *ctx = ae->ctx;
+    if (E < 0 || (E > 0 && (!u || !v || !w || !latent))) return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_decode: bad arguments");
+    for (const float *p : {u, v, w})
+        if (E > 0 && (reinterpret_cast<uintptr_t>(p) & 15u) != 0)
+            return sem_fail(ctx, SEM_ERR_ARG, "sem_ae_decode: fields must be 16-byte aligned");
+    const int Bp = ae->Bp;
+    const TensorDesc *T = ae->tab.t;
+    for (int64_t e0 = 0; e0 < E; e0 += Bp) {
+        const int B = (int)std::min<int64_t>(Bp, E - e0);
+        SEM_TRACED(ctx, "k_latent_in", k_latent_in<<<grid_for((int64_t)Bp * 64, 256, ctx->sm_count), 256, 0, ctx->stream>>>(
+                                           reinterpret_cast<const bf16 *>(latent), e0, B, Bp, ae->Z));
+        SEM_CU(ctx, cudaGetLastError());
+        EpiArgs e = epi(EPI_BIAS_GELU, Bp);
+        e.bias = ae->w + T[5].off;
+        e.out = ae->H3;
+        e.aux = ae->A3;
+        e.ld_out = D_H;
+        e.out_t = ae->A3T;
+        e.ld_t = Bp;
+        SEM_TRY(gemm(ctx, ae->Z, ae->wb + T[4].wb_off, Bp, D_H, D_ZP, e));
+        e = epi(EPI_DECODE, B);
+        e.bias = ae->w + T[7].off;
+        e.fields[0] = u + e0 * NP3_AE;
+        e.fields[1] = v + e0 * NP3_AE;
+        e.fields[2] = w + e0 * NP3_AE;
+        e.np3 = NP3_AE;
+        for (int c = 0; c < 3; ++c) {
+            e.mean[c] = ae->mean[c];
+            e.stdv[c] = ae->stdv[c];
+        }
+        SEM_TRY(gemm(ctx, ae->A3, ae->wb + T[6].wb_off, Bp, D_IN, D_H, e));
+    }
+    return SEM_OK;
+}
+
+sem_status sem_gemm_bf16(sem_ctx *ctx, const uint16_t *A, const uint16_t *B, int64_t M, int N, int K, float *C)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (!A || !B || !C) return sem_fail(ctx, SEM_ERR_ARG, "sem_gemm_bf16: NULL operand");
+    if ((reinterpret_cast<uintptr_t>(C) & 15u) != 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_gemm_bf16: C not 16-byte aligned");
+    EpiArgs e = epi(EPI_F32, M);
+    e.c32 = C;
+    e.ld_out = N;
+    return gemm(ctx, A, B, M, N, K, e);
+}

@@ -412,6 +412,9 @@ sem_status sem_synchronize(sem_ctx *ctx)
         SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
         if (flag & (1 << SEM_ERR_TIMEOUT))
             return sem_fail(ctx, SEM_ERR_TIMEOUT, "a bounded device-side wait ran out (flag 0x%x)", flag);
+        if (flag & (1 << SEM_ERR_ARG))
+            return sem_fail(ctx, SEM_ERR_ARG, "a kernel found an argument out of range, e.g. a sample index (flag 0x%x)",
+                            flag);
         if (flag & (1 << SEM_ERR_CAPACITY))
             return sem_fail(ctx, SEM_ERR_CAPACITY,
                             "an asynchronous call found more triangles than its buffer holds (flag 0x%x)", flag);

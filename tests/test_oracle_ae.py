@@ -183,3 +183,11 @@ def test_hausdorff_brute_force():
     d = np.sqrt(((A[:50, None] - B[None]) ** 2).sum(-1))
     ref = max(d.min(axis=1).max(), d.min(axis=0).max())
     assert abs(ae.hausdorff(A[:50], B, chunk=7) - ref) < 1e-12
+
+
+def test_hausdorff_kd_equals_brute_force():
+    rng = np.random.default_rng(9)
+    A = rng.normal(size=(700, 3))
+    B = rng.normal(size=(500, 3)) * 1.3 + 0.2
+    assert abs(ae.hausdorff_kd(A, B) - ae.hausdorff(A, B)) < 1e-12
+    assert ae.hausdorff_kd(A, A) == 0.0
