@@ -253,6 +253,94 @@ class Pipeline:
         return off
 
 
+# GEMM shapes (M, N, K as executed, padded) of the autoencoder's training step at batch B
+def _ae_gemm_shapes(B):
+    return {"fwd1": (B, 512, 1536), "fwd2": (B, 64, 512), "fwd3": (B, 512, 64), "fwd4": (B, 1536, 512),
+            "dx4": (B, 512, 1536), "dw4": (1536, 512, B), "dx3": (B, 64, 512), "dw3": (512, 64, B),
+            "dx2": (B, 512, 64), "dw2": (128, 512, B), "dw1": (512, 1536, B)}
+
+
+def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
+    """The learned per-element compression on the benchmark's scale: AdamW steps of the
+    1536-512-48-512-1536 BF16 autoencoder at batch 8192 on samples of 8 Taylor-Green snapshots
+    of 32^3 elements (not part of the timed frame step), and encode/decode of one snapshot."""
+    import torch
+    import sem_inputs as si
+    B = 8192
+    train = torch.cat([si.ae_samples(si.ae_snapshot(s, nel=32, device="cuda")) for s in range(0, 200, 25)])
+    ae = S.sem_ae_create(ctx, B)
+    stream = torch.cuda.current_stream()
+    try:
+        S.sem_ae_set_params(ctx, ae, si.ae_init_params())
+        S.sem_ae_fit_normalization(ctx, ae, train[:32768])
+        g = torch.Generator(device="cuda")
+        g.manual_seed(si.seed_for(5, 2000))
+        idx = torch.randint(0, train.shape[0], (steps + warmup, B), generator=g, device="cuda")
+        for i in range(warmup):
+            S.sem_ae_train_step(ctx, ae, train, idx[i], lr=1e-4)
+        torch.cuda.synchronize()
+        S.sem_trace_enable(ctx, True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for i in range(warmup, warmup + steps):
+            S.sem_ae_train_step(ctx, ae, train, idx[i], lr=1e-4)
+        b.record(stream)
+        torch.cuda.synchronize()
+        trace = S.sem_trace_collect(ctx)
+        S.sem_trace_enable(ctx, False)
+        step_ms = a.elapsed_time(b) / steps
+        shapes = _ae_gemm_shapes(B)
+        gemm = {}
+        for name, (M, N, K) in shapes.items():
+            ms, n = trace.get("k_gemm_bf16 " + name, (0.0, 0))
+            if n:
+                t = ms / n
+                gemm[name] = {"ms": round(t, 5), "tflops": round(2.0 * M * N * K / (t * 1e-3) / 1e12, 1)}
+        gemm_ms = sum(v["ms"] for v in gemm.values())
+        gemm_flops = sum(2.0 * M * N * K for M, N, K in shapes.values())
+        dims = [(1536, 512), (512, 48), (48, 512), (512, 1536)]
+        model_flops = 2.0 * B * (2 * sum(i * o for i, o in dims) + sum(i * o for i, o in dims[1:]))
+        best = max(gemm, key=lambda k: gemm[k]["tflops"])
+        # encode + decode of one snapshot (32768 elements)
+        f = si.ae_snapshot(201, nel=32, device="cuda")
+        E = f.shape[1]
+        lat = torch.empty(E * 48, dtype=torch.bfloat16, device="cuda")
+        out = [torch.empty(E, 512, device="cuda") for _ in range(3)]
+        uvw = [f[c].contiguous() for c in range(3)]
+        for _ in range(3):
+            S.sem_ae_encode(ctx, ae, *uvw, lat)
+            S.sem_ae_decode(ctx, ae, lat, E, *out)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        for _ in range(10):
+            S.sem_ae_encode(ctx, ae, *uvw, lat)
+        e1.record(stream)
+        for _ in range(10):
+            S.sem_ae_decode(ctx, ae, lat, E, *out)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        enc_ms, dec_ms = e0.elapsed_time(e1) / 10, e1.elapsed_time(e2) / 10
+        return {"model": "per-element autoencoder 1536-512-48-512-1536, BF16 tensor cores, FP32 accumulation",
+                "train_batch": B, "train_ms_per_step": round(step_ms, 4),
+                "train_samples_per_s": round(B / (step_ms * 1e-3), 1),
+                "train_model_tflops": round(model_flops / (step_ms * 1e-3) / 1e12, 1),
+                "gemm_share_of_step": round(gemm_ms / step_ms, 3),
+                "gemm_tflops_all": round(gemm_flops / (gemm_ms * 1e-3) / 1e12, 1),
+                "roofline": {"kernel": "k_gemm_bf16 " + best, "bound": "tensor",
+                             "achieved": gemm[best]["tflops"], "peak": bf16_peak, "peak_source": peak_src,
+                             "unit": "TFLOP/s", "frac": round(gemm[best]["tflops"] / bf16_peak, 4)},
+                "gemms": gemm,
+                "encode_elements_per_s": round(E / (enc_ms * 1e-3), 1),
+                "decode_elements_per_s": round(E / (dec_ms * 1e-3), 1),
+                "latent_bytes_per_element": 96}
+    finally:
+        S.sem_ae_destroy(ae)
+        del train
+        torch.cuda.empty_cache()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -373,6 +461,31 @@ def run_ours(args):
             "launch_ms": round(dom_ms, 5)}
     launches_per_step = sum(n for _, n in trace.values()) / K
 
+    qprec = None
+    if args.q_precisions:
+        # sem_qcriterion alone at each arithmetic (CUDA events, 50 launches after 5 warm-up)
+        qprec = {}
+        for name in ("FP32", "BF16", "FP16", "BF16X2"):
+            prec = getattr(S, "SEM_" + name)
+            for _ in range(5):
+                S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q, prec)
+            qa, qb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            qa.record(P.stream)
+            for _ in range(50):
+                S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q, prec)
+            qb.record(P.stream)
+            torch.cuda.synchronize()
+            us = qa.elapsed_time(qb) / 50 * 1e3
+            qprec[name] = {"us": round(us, 2), "gbs": round(16 * P.npts / (us * 1e-6) / 1e9, 1)}
+        S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q)
+
+    mem_now, mem_peak = S.sem_memory(P.ctx)
+    torch_peak = int(torch.cuda.max_memory_allocated())  # the caller's buffers (torch allocator)
+    learned = None
+    if not args.no_learned:
+        bpk = peaks.get("bf16_tflops")
+        learned = measure_learned(S, P.ctx, bpk or 1900.0, "measured" if bpk else "fallback")
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, P.isos, budget_s=args.cpu_seconds)
@@ -391,7 +504,12 @@ def run_ours(args):
                         "isosurface_all": round(float(mean_stage[1]), 4),
                         "render": round(float(mean_stage[2]), 4), "eager_step": round(eager_ms, 4)},
            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-           "kernels": kernels, "gpu_launches": int(round(launches_per_step * K))}
+           "kernels": kernels, "gpu_launches": int(round(launches_per_step * K)),
+           "memory": {"library_bytes_in_use": mem_now, "library_bytes_peak": mem_peak,
+                      "caller_buffers_bytes_peak": torch_peak},
+           "learned": learned}
+    if qprec is not None:
+        out["q_precisions"] = qprec
     P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -486,6 +604,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of the captured graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the autoencoder measurement")
+    ap.add_argument("--q-precisions", action="store_true",
+                    help="also time sem_qcriterion at FP32, BF16, FP16 and split BF16 (q_precisions)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-elements", type=int, default=512)
     args = ap.parse_args()

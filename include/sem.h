@@ -115,6 +115,11 @@ SEM_API sem_status sem_set_stream(sem_ctx *ctx, void *stream);
  * (SEM_ERR_TIMEOUT) and clear it. */
 SEM_API sem_status sem_synchronize(sem_ctx *ctx);
 
+/* Device memory the library holds for ctx (scratch arenas, tables, meshes loaded with ctx,
+ * autoencoders created on ctx; caller-owned buffers are not counted): *in_use now and *peak,
+ * the high-water mark since sem_create.  Free meshes and autoencoders before their context. */
+SEM_API sem_status sem_memory(sem_ctx *ctx, int64_t *in_use, int64_t *peak);
+
 /* Kernel trace (instrumentation; no counterpart in the paper).  While on, every kernel the
  * library launches on the context's stream outside a stream capture is bracketed by a pair of
  * CUDA events on that stream.  sem_trace_collect waits for the recorded launches, sums their

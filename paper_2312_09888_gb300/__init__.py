@@ -58,6 +58,7 @@ def _declare(L):
     L.sem_set_stream.argtypes = [vp, vp]
     L.sem_synchronize.argtypes = [vp]
     L.sem_trace_enable.argtypes = [vp, i32]
+    L.sem_memory.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.sem_trace_collect.argtypes = [vp, C.POINTER(i32)]
     L.sem_trace_entry.argtypes = [vp, i32, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64)]
     L.sem_load_mesh.argtypes = [vp, i32, i64, vp, C.POINTER(vp)]
@@ -181,6 +182,13 @@ def sem_set_stream(ctx, stream) -> None:
 
 def sem_synchronize(ctx) -> None:
     _check(ctx, get_lib().sem_synchronize(ctx))
+
+
+def sem_memory(ctx):
+    """(bytes in use, high-water mark) of the device memory the library holds for ctx."""
+    a, b = C.c_int64(0), C.c_int64(0)
+    _check(ctx, get_lib().sem_memory(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def sem_trace_enable(ctx, on: bool = True) -> None:

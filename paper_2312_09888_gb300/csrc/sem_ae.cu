@@ -548,6 +548,7 @@ struct sem_ae {
     bf16 *H3 = nullptr, *A3 = nullptr, *A3T = nullptr, *dY = nullptr, *dYT = nullptr, *dH3 = nullptr, *dH3T = nullptr;
     bf16 *dZ = nullptr, *dZT = nullptr, *dH1 = nullptr, *dH1T = nullptr;
     void *arena = nullptr;
+    int64_t bytes = 0;
 };
 
 namespace {
@@ -760,6 +761,8 @@ sem_status sem_ae_create(sem_ctx *ctx, int batch, sem_ae **out)
         delete ae;
         return sem_cuda(ctx, e, "sem_ae_create: cudaMalloc");
     }
+    ctx->mem_add((int64_t)total);
+    ae->bytes = (int64_t)total;
     size_t at = 0;
     for (auto &p : pieces) {
         *p.dst = static_cast<char *>(ae->arena) + at;
@@ -770,6 +773,7 @@ sem_status sem_ae_create(sem_ctx *ctx, int batch, sem_ae **out)
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         cudaFree(ae->arena);
+        ctx->mem_add(-(int64_t)total);
         delete ae;
         return sem_cuda(ctx, e, "sem_ae_create: memset");
     }
@@ -783,6 +787,7 @@ void sem_ae_destroy(sem_ae *ae)
     cudaSetDevice(ae->ctx->device);
     cudaStreamSynchronize(ae->ctx->stream);
     if (ae->arena) cudaFree(ae->arena);
+    ae->ctx->mem_add(-ae->bytes);
     delete ae;
 }
 

@@ -44,11 +44,13 @@ sem_status sem_scratch(sem_ctx *ctx, int slot, size_t bytes, void **out)
         if (ctx->scratch[slot]) {
             SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
             SEM_CU(ctx, cudaFree(ctx->scratch[slot]));
+            ctx->mem_add(-(int64_t)ctx->scratch_bytes[slot]);
             ctx->scratch[slot] = nullptr;
             ctx->scratch_bytes[slot] = 0;
         }
         SEM_CU(ctx, cudaMalloc(&ctx->scratch[slot], nb));
         ctx->scratch_bytes[slot] = nb;
+        ctx->mem_add((int64_t)nb);
     }
     *out = ctx->scratch[slot];
     return SEM_OK;
@@ -289,6 +291,7 @@ sem_status sem_create(int device, void *stream, sem_ctx **out)
         }
         ctx->sm_count = prop.multiProcessorCount;
         if ((st = sem_cuda(ctx, cudaMalloc(&ctx->d_flag, 64), "cudaMalloc(flag)")) != SEM_OK) break;
+        ctx->mem_add(64);
         if ((st = sem_cuda(ctx, cudaMemset(ctx->d_flag, 0, 64), "cudaMemset(flag)")) != SEM_OK) break;
         if ((st = sem_cuda(ctx, cudaMallocHost(&ctx->h_pinned, 16 * sizeof(int64_t)), "cudaMallocHost")) != SEM_OK)
             break;
@@ -351,6 +354,14 @@ TraceScope::TraceScope(sem_ctx *c, const char *name) : ctx(c)
 TraceScope::~TraceScope()
 {
     if (idx >= 0) cudaEventRecord(ctx->trace[idx].b, ctx->stream);
+}
+
+sem_status sem_memory(sem_ctx *ctx, int64_t *in_use, int64_t *peak)
+{
+    if (!ctx || !in_use || !peak) return SEM_ERR_ARG;
+    *in_use = ctx->mem_now;
+    *peak = ctx->mem_peak;
+    return SEM_OK;
 }
 
 sem_status sem_trace_enable(sem_ctx *ctx, int on)
@@ -475,6 +486,9 @@ sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz, sem_
         if ((st = sem_cuda(ctx, cudaMalloc(&m->lo, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
         if ((st = sem_cuda(ctx, cudaMalloc(&m->hi, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
         if ((st = sem_cuda(ctx, cudaMalloc(&m->g, bytes), "cudaMalloc(mesh)")) != SEM_OK) break;
+        m->owner = ctx;
+        m->bytes = 3 * (int64_t)bytes;
+        ctx->mem_add(m->bytes);
         if (E > 0) {
             if ((st = sem_cuda(ctx, cudaMemcpy(m->lo, lo.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
             if ((st = sem_cuda(ctx, cudaMemcpy(m->hi, hi.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
@@ -493,6 +507,7 @@ void sem_mesh_free(sem_mesh *m)
 {
     if (!m) return;
     cudaSetDevice(m->device);
+    if (m->owner) m->owner->mem_add(-m->bytes);
     if (m->lo) cudaFree(m->lo);
     if (m->hi) cudaFree(m->hi);
     if (m->g) cudaFree(m->g);

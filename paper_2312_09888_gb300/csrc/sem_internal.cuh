@@ -29,6 +29,14 @@ struct sem_ctx {
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
     void *tc_A[2] = {nullptr, nullptr};
+    // device bytes the library holds for this context (scratch arenas, tables, meshes,
+    // autoencoders) and their high-water mark
+    int64_t mem_now = 0, mem_peak = 0;
+    void mem_add(int64_t b)
+    {
+        mem_now += b;
+        if (mem_now > mem_peak) mem_peak = mem_now;
+    }
     // kernel trace: an event pair around every launch while tracing is on (not while the
     // stream is being captured); collected per kernel name by sem_trace_collect
     bool trace_on = false;
@@ -63,6 +71,8 @@ struct sem_mesh {
     int N = 0;
     int64_t E = 0;
     int device = 0;
+    sem_ctx *owner = nullptr;  // the context whose memory count holds this mesh's bytes
+    int64_t bytes = 0;
     float4 *lo = nullptr;   // element box lower corner (x0, y0, z0, 0)
     float4 *hi = nullptr;   // element box upper corner (x1, y1, z1, 0)
     float4 *g = nullptr;    // 2/(x1-x0), 2/(y1-y0), 2/(z1-z0), 0

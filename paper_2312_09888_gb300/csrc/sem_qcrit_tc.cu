@@ -394,6 +394,7 @@ sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, cons
         both.insert(both.end(), lo.begin(), lo.end());
         void *d = nullptr;
         SEM_CU(ctx, cudaMalloc(&d, both.size()));
+        ctx->mem_add((int64_t)both.size());
         SEM_CU(ctx, cudaMemcpy(d, both.data(), both.size(), cudaMemcpyHostToDevice));
         ctx->tc_A[slot] = d;
         float Df[64];

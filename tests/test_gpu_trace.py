@@ -39,3 +39,24 @@ def test_trace_counts_the_frame_kernels(gpu, sess):
     S.sem_trace_enable(sess.ctx, False)
     S.sem_qcriterion(sess.ctx, m, *vel, Q)
     assert S.sem_trace_collect(sess.ctx) == {}
+
+
+def test_memory_in_use_and_high_water_mark(gpu):
+    S = gpu
+    s = S.Session(0)
+    try:
+        base, peak0 = S.sem_memory(s.ctx)
+        assert base > 0 and peak0 >= base
+        w = si.tgv_box(nel=4)
+        m = S.sem_load_mesh(s.ctx, w.mesh.N, w.mesh.xyz().numpy())
+        with_mesh, _ = S.sem_memory(s.ctx)
+        assert with_mesh == base + 3 * 16 * w.E  # three float4 per element
+        ae = S.sem_ae_create(s.ctx, 128)
+        with_ae, peak1 = S.sem_memory(s.ctx)
+        assert with_ae > with_mesh + 26 * 2 ** 20 and peak1 >= with_ae
+        S.sem_ae_destroy(ae)
+        S.sem_mesh_free(m)
+        after, peak2 = S.sem_memory(s.ctx)
+        assert after == base and peak2 == peak1
+    finally:
+        s.close()
