@@ -98,11 +98,36 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t *__re
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
+// One block for small inputs: thread t scans its contiguous chunk of ceil(n / 1024) entries
+// (sum, block-wide scan of the sums, then the chunk's offsets), so the whole scan is a single
+// launch; used up to SCAN_SINGLE_MAX entries.
+#define SCAN_SINGLE_MAX (SCAN_THREADS * 256)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t *__restrict__ in, int64_t n,
+                                                              int64_t *__restrict__ out)
+{
+    __shared__ int64_t s_w[33];
+    const int64_t per = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int64_t lo = min(n, (int64_t)threadIdx.x * per), hi = min(n, lo + per);
+    int64_t v = 0;
+    for (int64_t i = lo; i < hi; ++i) v += in[i];
+    int64_t tot;
+    int64_t run = block_excl_scan(v, s_w, tot);
+    for (int64_t i = lo; i < hi; ++i) {
+        out[i] = run;
+        run += in[i];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp)
 {
     if (n <= 0) {
         SEM_CU(ctx, cudaMemsetAsync(out, 0, sizeof(int64_t), ctx->stream));
         return SEM_OK;
+    }
+    if (n <= SCAN_SINGLE_MAX) {
+        SEM_TRACED(ctx, "k_scan_single", k_scan_single<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, out));
+        return sem_cuda(ctx, cudaGetLastError(), "scan launch");
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     int64_t *bsum = reinterpret_cast<int64_t *>(tmp);

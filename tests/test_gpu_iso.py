@@ -190,3 +190,26 @@ def test_channel_full_size_sampled(gpu, sess, orc):
         tri_h = tris.view(-1, 3, 3)
         got = np.concatenate([tri_h[starts[e]:starts[e + 1]].double().cpu().numpy() for e in sample])
         assert np.abs(got - ref["tris"]).max() <= 1e-5 * 2 * math.pi
+
+
+def test_many_elements_multi_isovalue_uses_the_multi_block_scan(gpu, sess, orc):
+    """64^3 elements of order 1 x 2 isovalues = 524288 counts: above the single-block scan's
+    limit (262144), so the three-kernel scan runs; counts and offsets against the oracle."""
+    mesh = si.uniform_box((64, 64, 64), (0, 0, 0), (1, 1, 1), 1)
+    xyz = mesh.xyz().numpy()
+    f32 = dev32(si.sphere_field(mesh, (0.5, 0.5, 0.5), 0.3).numpy())
+    m = sess.mesh(1, xyz)
+    isos = [0.0, 0.02]
+    counts = gpu.sem_isosurface_multi(sess.ctx, m, f32, isos, None)
+    tris = torch.empty(sum(counts) * 9, device="cuda")
+    te = torch.empty(sum(counts), dtype=torch.int32, device="cuda")
+    assert gpu.sem_isosurface_multi(sess.ctx, m, f32, isos, tris, te) == counts
+    torch.cuda.synchronize()
+    f64 = host64(f32)
+    off = 0
+    e_h = te.cpu().numpy()
+    for q, iso in enumerate(isos):
+        ref = orc.isosurface(1, xyz, f64, float(np.float32(iso)))
+        assert counts[q] == ref["ntri"]
+        np.testing.assert_array_equal(e_h[off:off + counts[q]], ref["tri_elem"])
+        off += counts[q]
