@@ -95,6 +95,8 @@ def _declare(L):
     L.sem_ae_encode.argtypes = [vp, vp, vp, vp, i64, vp]
     L.sem_ae_decode.argtypes = [vp, vp, i64, vp, vp, vp]
     L.sem_gemm_bf16.argtypes = [vp, vp, vp, i64, i32, i32, vp]
+    L.sem_autotune_set.argtypes = [vp, i32]
+    L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 6 + [C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
@@ -495,6 +497,25 @@ def sem_ae_decode(ctx, ae, latent, E: int, u, v, w) -> None:
     import torch
     _check(ctx, get_lib().sem_ae_decode(ae, _dev(latent, "latent"), int(E), _dev(u, "u", torch.float32),
                                         _dev(v, "v", torch.float32), _dev(w, "w", torch.float32)))
+
+
+def sem_autotune_set(ctx, on: bool) -> None:
+    _check(ctx, get_lib().sem_autotune_set(ctx, 1 if on else 0))
+
+
+def sem_autotune_choices(ctx) -> list:
+    """[(M, N, K, epilogue, BN, stages, split, ms)] of the tuned GEMM shapes."""
+    out, k = [], 0
+    L = get_lib()
+    while True:
+        M = C.c_int64(0)
+        v = [C.c_int32(0) for _ in range(6)]
+        ms = C.c_float(0)
+        st = L.sem_autotune_entry(ctx, k, C.byref(M), *[C.byref(x) for x in v], C.byref(ms))
+        if st != SEM_OK:
+            return out
+        out.append((M.value, *[x.value for x in v], ms.value))
+        k += 1
 
 
 def sem_gemm_bf16(ctx, A, B, C_out) -> None:

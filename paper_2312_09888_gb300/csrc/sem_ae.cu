@@ -35,7 +35,7 @@ typedef __nv_bfloat16 bf16;
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, GEMM_THREADS = 192;
+constexpr int BM = 128, BK = 64, GEMM_THREADS = 192;
 
 enum EpiMode : int {
     EPI_F32 = 0,        // C32 = acc                                    (weight gradients)
@@ -60,6 +60,7 @@ struct EpiArgs {
     const bf16 *in;      // EPI_DGELU: H; EPI_LOSS: target X (leading dimension ld_in)
     int ld_in;
     float *c32;          // EPI_F32, leading dimension ld_out
+    int64_t split_stride;  // EPI_F32 with a split K range: floats between the partial arrays
     float *loss;         // EPI_LOSS accumulator
     float scale;         // EPI_LOSS: 2 / (B D)
     float *fields[3];    // EPI_DECODE
@@ -99,7 +100,8 @@ __device__ __forceinline__ void load8_bf16(const bf16 *p, float (&v)[8])
 }
 
 // The fused tail of one row's 8 consecutive output columns n .. n+7.
-__device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, float (&v)[8], float &loss_acc)
+__device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, float (&v)[8], float &loss_acc,
+                                          float *__restrict__ c32)
 {
     if (row >= P.m_valid) {
         if (P.mode == EPI_LOSS) {
@@ -114,7 +116,7 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
     }
     switch (P.mode) {
     case EPI_F32: {
-        float4 *dst = reinterpret_cast<float4 *>(P.c32 + row * P.ld_out + n);
+        float4 *dst = reinterpret_cast<float4 *>(c32 + row * P.ld_out + n);
         dst[0] = make_float4(v[0], v[1], v[2], v[3]);
         dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         return;
@@ -190,27 +192,30 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
 
 // D[M][N] = A[M][K] B[N][K]^T for one BM x BN output tile per CTA.  Warp 0: TMA producer;
 // warp 1: TMEM owner and MMA issuer; warps 2..5: epilogue (warp w reads TMEM lanes
-// 32 (w % 4) .. + 31).  STAGES-deep ring of (A, B) K-slices of BK = 64 BF16 (one 128-byte
+// 32 (w % 4) .. + 31).  NST-deep ring of (A, B) K-slices of BK = 64 BF16 (one 128-byte
 // swizzle atom row).  Every wait is bounded: on a time-out the kernel records SEM_ERR_TIMEOUT,
 // stops issuing, waits (bounded) for its copies in flight, frees TMEM and returns.
-template <int BN>
+template <int BN, int NST>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
                 const __grid_constant__ EpiArgs P, int *err)
 {
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accf;
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], accf;
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    __shared__ int s_consumed[STAGES];
+    __shared__ int s_consumed[NST];
     // SW128 tiles need 1024-byte alignment
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = K / BK;
+    // this CTA's K slice (all of K unless split)
+    const int nk_all = K / BK;
+    const int kb0 = (int)((int64_t)blockIdx.z * nk_all / gridDim.z);
+    const int nk = (int)((int64_t)(blockIdx.z + 1) * nk_all / gridDim.z) - kb0;
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
             s_consumed[s] = 0;
@@ -223,10 +228,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
-    int issued[STAGES] = {0, 0, 0, 0};
+    int issued[NST] = {};
     if (warp == 0 && lane == 0) {
         for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES, round = kb / STAGES;
+            const int s = kb % NST, round = kb / NST;
             if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1, err)) {
                 s_abort = 1;
                 break;
@@ -234,14 +239,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             if (*(volatile int *)&s_abort) break;
             uint8_t *a = smem + s * STAGE_BYTES;
             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(a, &tmA, kb * BK, blockIdx.x * BM, &full[s]);
-            tma_load_2d(a + A_BYTES, &tmB, kb * BK, blockIdx.y * BN, &full[s]);
+            tma_load_2d(a, &tmA, (kb0 + kb) * BK, blockIdx.x * BM, &full[s]);
+            tma_load_2d(a + A_BYTES, &tmB, (kb0 + kb) * BK, blockIdx.y * BN, &full[s]);
             ++issued[s];
         }
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t IDESC = tc::idesc_f16(BM, BN, true);
         for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES, round = kb / STAGES;
+            const int s = kb % NST, round = kb / NST;
             if (*(volatile int *)&s_abort || !mbar_wait_bounded(&full[s], round & 1, err)) {
                 s_abort = 1;
                 break;
@@ -265,6 +270,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             const int q = warp & 3;
             const int64_t row = (int64_t)blockIdx.x * BM + q * 32 + lane;
             float loss_acc = 0.f;
+            float *c32 = P.c32 + (int64_t)blockIdx.z * P.split_stride;  // this K slice's partial array
             for (int c0 = 0; c0 < BN; c0 += 8) {
                 uint32_t r[8];
                 tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 float v[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
-                epilogue8(P, row, blockIdx.y * BN + c0, v, loss_acc);
+                epilogue8(P, row, blockIdx.y * BN + c0, v, loss_acc, c32);
             }
             if (P.mode == EPI_LOSS) {
 #pragma unroll
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     // on an abort: wait (bounded) for this CTA's copies still in flight
     if (warp == 0 && lane == 0 && *(volatile int *)&s_abort) {
-        for (int s = 0; s < STAGES; ++s)
+        for (int s = 0; s < NST; ++s)
             if (issued[s] > s_consumed[s]) mbar_wait_bounded(&full[s], s_consumed[s] & 1, nullptr);
     }
     tc::fence_before_sync();
@@ -480,38 +486,137 @@ sem_status make_map(sem_ctx *ctx, CUtensorMap *map, const void *base, int64_t ro
     return SEM_OK;
 }
 
-template <int BN>
-size_t gemm_smem() { return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024; }
+unsigned grid_for(int64_t n, int threads, int sm)
+{
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 8LL * sm));
+}
 
-// D = A B^T with A [M][K], B [N][K] (BF16, row-major), M % 128 == 0, N % BN == 0, K % 64 == 0
+// sum of the `splits` partial arrays (stride floats apart) of a K-split product, in split order
+// (deterministic), into out[0 .. n)
+__global__ void k_split_reduce(const float *__restrict__ part, int splits, int64_t stride, int64_t n,
+                               float *__restrict__ out)
+{
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        float a = part[t];
+        for (int z = 1; z < splits; ++z) a += part[z * stride + t];
+        out[t] = a;
+    }
+}
+
+struct GemmCfg {
+    int bn, nst, split;
+};
+
+template <int BN, int NST>
+sem_status launch_gemm(sem_ctx *ctx, const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K,
+                       const EpiArgs &P, int split, const char *name)
+{
+    const size_t sm = (size_t)NST * (BM * BK * 2 + BN * BK * 2) + 1024;
+    static bool set = false;  // per instantiation; the attribute is a property of the function
+    if (!set) {
+        SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        set = true;
+    }
+    const dim3 grid((unsigned)(M / BM), (unsigned)(N / BN), (unsigned)split);
+    SEM_TRACED(ctx, name, k_gemm_bf16<BN, NST><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
+    return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16 launch");
+}
+
+// One product in configuration c: tensor maps for its tile shape, the K-split partials (weight
+// gradients only) in the context's scratch and their ordered reduction.
+sem_status run_gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, int K, const EpiArgs &P,
+                    GemmCfg c, const char *name)
+{
+    CUtensorMap ta, tb;
+    SEM_TRY(make_map(ctx, &ta, A, M, K, BM));
+    SEM_TRY(make_map(ctx, &tb, B, N, K, c.bn));
+    EpiArgs Q = P;
+    float *part = nullptr;
+    const int64_t stride = M * (int64_t)P.ld_out;
+    if (c.split > 1) {
+        void *scr;
+        SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_MISC, sizeof(float) * (size_t)(stride * c.split), &scr));
+        part = static_cast<float *>(scr);
+        Q.c32 = part;
+        Q.split_stride = stride;
+    }
+    sem_status st;
+#define SEM_GEMM_CASE(BNV, NSTV) \
+    if (c.bn == BNV && c.nst == NSTV) st = launch_gemm<BNV, NSTV>(ctx, ta, tb, M, N, K, Q, c.split, name); else
+    SEM_GEMM_CASE(64, 3) SEM_GEMM_CASE(64, 4) SEM_GEMM_CASE(128, 3) SEM_GEMM_CASE(128, 4)
+    SEM_GEMM_CASE(256, 3) SEM_GEMM_CASE(256, 4)
+    return sem_fail(ctx, SEM_ERR_ARG, "no GEMM kernel for BN=%d, %d stages", c.bn, c.nst);
+#undef SEM_GEMM_CASE
+    SEM_TRY(st);
+    if (c.split > 1) {
+        const int64_t n = P.m_valid * (int64_t)P.ld_out;
+        SEM_TRACED(ctx, "k_split_reduce", k_split_reduce<<<grid_for(n, 256, ctx->sm_count), 256, 0, ctx->stream>>>(
+                                              part, c.split, stride, n, P.c32));
+        SEM_CU(ctx, cudaGetLastError());
+    }
+    return SEM_OK;
+}
+
+// D = A B^T with A [M][K], B [N][K] (BF16, row-major), M % 128 == 0, N % 64 == 0, K % 64 == 0.
+// The tile width, pipeline depth and (for FP32 weight gradients) K split come from the
+// context's autotuner: the first product of a given (M, N, K, epilogue) runs every candidate on
+// the call's own data (each twice, the second timed with CUDA events) and keeps the fastest;
+// the candidates compute identical tiles, so the outputs do not depend on which one ran, except
+// the order of the K-split partial sums.  Under stream capture, or with tuning off, the default
+// (BN 128 when N allows, 4 stages, no split) is used.
 sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, int K, const EpiArgs &P,
                 const char *name = "k_gemm_bf16")
 {
     if (M % BM != 0 || K % BK != 0 || N % 64 != 0 || M <= 0 || N <= 0 || K <= 0)
         return sem_fail(ctx, SEM_ERR_ARG, "GEMM shape %lld x %d x %d not tileable", (long long)M, N, K);
-    CUtensorMap ta, tb;
-    const int bn = (N % 128 == 0) ? 128 : 64;
-    SEM_TRY(make_map(ctx, &ta, A, M, K, BM));
-    SEM_TRY(make_map(ctx, &tb, B, N, K, bn));
-    const dim3 grid((unsigned)(M / BM), (unsigned)(N / bn));
-    if (bn == 128) {
-        static bool set = false;
-        const size_t sm = gemm_smem<128>();
-        if (!set) {
-            SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            set = true;
+    for (const auto &t : ctx->gemm_tune)
+        if (t.M == M && t.N == N && t.K == K && t.mode == P.mode)
+            return run_gemm(ctx, A, B, M, N, K, P, GemmCfg{t.bn, t.nst, t.split}, name);
+    const GemmCfg dflt{N % 128 == 0 ? 128 : 64, 4, 1};
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (!ctx->autotune || cs != cudaStreamCaptureStatusNone) return run_gemm(ctx, A, B, M, N, K, P, dflt, name);
+    std::vector<GemmCfg> cand;
+    const int nk = K / BK;
+    const int64_t tiles = (M / BM) * (int64_t)(N / 128 > 0 ? N / 128 : 1);
+    for (int bn : {64, 128, 256}) {
+        if (N % bn != 0) continue;
+        for (int nst : {3, 4}) {
+            cand.push_back(GemmCfg{bn, nst, 1});
+            if (P.mode == EPI_F32 && tiles < 2 * ctx->sm_count)
+                for (int sp : {2, 4, 8})
+                    if (nk / sp >= 4) cand.push_back(GemmCfg{bn, nst, sp});
         }
-        SEM_TRACED(ctx, name, k_gemm_bf16<128><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
-    } else {
-        static bool set = false;
-        const size_t sm = gemm_smem<64>();
-        if (!set) {
-            SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            set = true;
-        }
-        SEM_TRACED(ctx, name, k_gemm_bf16<64><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
     }
-    return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16 launch");
+    cudaEvent_t e0, e1;
+    SEM_CU(ctx, cudaEventCreate(&e0));
+    SEM_CU(ctx, cudaEventCreate(&e1));
+    GemmCfg best = dflt;
+    float best_ms = 1e30f;
+    sem_status st = SEM_OK;
+    for (const GemmCfg &c : cand) {
+        for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
+            if (P.mode == EPI_LOSS) st = sem_cuda(ctx, cudaMemsetAsync(P.loss, 0, sizeof(float), ctx->stream), "memset");
+            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
+            if (st == SEM_OK) st = run_gemm(ctx, A, B, M, N, K, P, c, name);
+            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+        }
+        if (st != SEM_OK) break;
+        float ms = 0.f;
+        if ((st = sem_cuda(ctx, cudaEventSynchronize(e1), "event")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event")) != SEM_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SEM_TRY(st);
+    ctx->gemm_tune.push_back({M, N, K, P.mode, best.bn, best.nst, best.split, best_ms});
+    // the outputs (and the loss) of the chosen configuration
+    if (P.mode == EPI_LOSS) SEM_CU(ctx, cudaMemsetAsync(P.loss, 0, sizeof(float), ctx->stream));
+    return run_gemm(ctx, A, B, M, N, K, P, best, name);
 }
 
 EpiArgs epi(int mode, int64_t m_valid)
@@ -523,7 +628,6 @@ EpiArgs epi(int mode, int64_t m_valid)
     return e;
 }
 
-unsigned grid_for(int64_t n, int threads, int sm) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 8LL * sm)); }
 
 }  // namespace
 
@@ -1040,4 +1144,30 @@ sem_status sem_gemm_bf16(sem_ctx *ctx, const uint16_t *A, const uint16_t *B, int
     e.c32 = C;
     e.ld_out = N;
     return gemm(ctx, A, B, M, N, K, e);
+}
+
+sem_status sem_autotune_set(sem_ctx *ctx, int on)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    ctx->autotune = on != 0;
+    if (!on) ctx->gemm_tune.clear();
+    return SEM_OK;
+}
+
+sem_status sem_autotune_entry(sem_ctx *ctx, int k, int64_t *M, int *N, int *K, int *mode, int *bn, int *stages,
+                              int *split, float *ms)
+{
+    if (!ctx || !M || !N || !K || !mode || !bn || !stages || !split || !ms) return SEM_ERR_ARG;
+    if (k < 0 || k >= (int)ctx->gemm_tune.size())
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_autotune_entry: index %d outside [0, %d)", k, (int)ctx->gemm_tune.size());
+    const auto &t = ctx->gemm_tune[k];
+    *M = t.M;
+    *N = t.N;
+    *K = t.K;
+    *mode = t.mode;
+    *bn = t.bn;
+    *stages = t.nst;
+    *split = t.split;
+    *ms = t.ms;
+    return SEM_OK;
 }

@@ -29,6 +29,14 @@ struct sem_ctx {
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
     void *tc_A[2] = {nullptr, nullptr};
+    // autotuner: tile shape chosen per (M, N, K, epilogue) of the tensor-core GEMM
+    bool autotune = true;
+    struct GemmTune {
+        int64_t M;
+        int N, K, mode, bn, nst, split;
+        float ms;
+    };
+    std::vector<GemmTune> gemm_tune;
     // device bytes the library holds for this context (scratch arenas, tables, meshes,
     // autoencoders) and their high-water mark
     int64_t mem_now = 0, mem_peak = 0;

@@ -43,6 +43,36 @@ def test_gemm_bf16_matches_fp64_product(gpu, sess, M, N, K):
     assert (err <= bound).all(), float((err / bound).max())
 
 
+def test_gemm_autotuner_choices_and_determinism(gpu, sess):
+    """The first product of a shape tunes (tile width, stages, K split); later products reuse the
+    choice bit for bit; with tuning off the default configuration agrees within the FP32 bound."""
+    S = gpu
+    rng = np.random.default_rng(5)
+    M, N, K = 512, 1536, 8192  # a weight-gradient shape: few tiles, long K -> split candidates
+    A = _bf(rng.normal(size=(M, K))).cuda()
+    B = _bf(rng.normal(size=(N, K))).cuda()
+    C1, C2, C3 = (torch.empty(M, N, device="cuda") for _ in range(3))
+    S.sem_autotune_set(sess.ctx, True)
+    S.sem_gemm_bf16(sess.ctx, A, B, C1)
+    S.sem_gemm_bf16(sess.ctx, A, B, C2)
+    torch.cuda.synchronize()
+    ch = [c for c in S.sem_autotune_choices(sess.ctx) if c[:3] == (M, N, K)]
+    assert len(ch) == 1
+    _, _, _, mode, bn, stages, split, ms = ch[0]
+    assert bn in (64, 128, 256) and stages in (3, 4) and split in (1, 2, 4, 8) and ms > 0
+    assert torch.equal(C1, C2)
+    S.sem_autotune_set(sess.ctx, False)
+    S.sem_gemm_bf16(sess.ctx, A, B, C3)
+    torch.cuda.synchronize()
+    S.sem_autotune_set(sess.ctx, True)
+    a, b = A.float().cpu().double().numpy(), B.float().cpu().double().numpy()
+    bound = 2.0 * K * 2.0 ** -24 * (np.abs(a) @ np.abs(b).T)
+    ref = a @ b.T
+    for Cx in (C1, C3):
+        assert (np.abs(Cx.cpu().double().numpy() - ref) <= bound).all()
+    print(f"\n{M}x{N}x{K}: BN {bn}, {stages} stages, K split {split}, {ms * 1e3:.1f} us")
+
+
 def test_gemm_rejects_untileable_shapes(gpu, sess):
     S = gpu
     A = torch.zeros(100, 64, dtype=torch.bfloat16, device="cuda")
