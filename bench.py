@@ -341,6 +341,114 @@ def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
         torch.cuda.empty_cache()
 
 
+def measure_batched(S, ctx, steps=20, warmup=3):
+    """Batching workload: 16 partitions of E_p ~ U{4096..40960} elements (seeded) and orders
+    N_p in {5, 7, 9}, each the first E_p elements of a ceil(E_p^(1/3))^3 lattice of [0, 2 pi]^3
+    with a phase-shifted Taylor-Green field; per step Q of every partition, 4 isovalues of Q and
+    of u per partition, one 1024x1024 frame per partition and field.  Three forms of the same
+    step: the plain path (one host-synchronised call after another), one CUDA graph with one Q
+    launch per partition, and one CUDA graph with the batched Q."""
+    import math as _m
+    import numpy as np
+    import torch
+    import sem_inputs as si
+    rng = np.random.default_rng(si.seed_for(4, 0))
+    parts = []
+    for p in range(16):
+        Ep, N = int(rng.integers(4096, 40961)), int(rng.choice([5, 7, 9]))
+        n = int(_m.ceil(Ep ** (1.0 / 3.0) - 1e-9))
+        mesh = si.uniform_box((n, n, n), (0.0,) * 3, (2 * _m.pi,) * 3, N)
+        xyz = mesh.xyz("cuda")[:, :Ep].contiguous()
+        vel = si.taylor_green(mesh, 0.0, 0, "cuda", phase=2 * _m.pi * p / 64)[:, :Ep].float().contiguous()
+        m = S.sem_load_mesh(ctx, N, xyz.cpu().numpy())
+        del xyz
+        cam = si.box_camera_persp((0.0,) * 3, (2 * _m.pi,) * 3, 1024, 1024)
+        q = torch.empty_like(vel[0])
+        parts.append(dict(m=m, E=Ep, N=N, vel=vel, Q=q, cam=cam))
+    E_total = sum(p["E"] for p in parts)
+    qmax = 1.0  # Taylor-Green: max Q = 1; u in [-1, 1]
+    qisos = [f * qmax for f in (0.05, 0.1, 0.2, 0.4)]
+    uisos = [-0.5, 0.0, 0.25, 0.5]
+    for p in parts:
+        S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
+        cq = S.sem_isosurface_multi(ctx, p["m"], p["Q"], qisos, None)
+        cu = S.sem_isosurface_multi(ctx, p["m"], p["vel"][0], uisos, None)
+        p["cap"] = [int(sum(cq) * 1.1) + 1024, int(sum(cu) * 1.1) + 1024]
+        p["tris"] = [torch.empty(c * 9, device="cuda") for c in p["cap"]]
+        p["cnt"] = [torch.zeros(5, dtype=torch.int64, device="cuda") for _ in range(2)]
+        p["img"] = [torch.empty(1024 * 1024 * 4, dtype=torch.uint8, device="cuda") for _ in range(2)]
+        p["counts"] = [cq, cu]
+
+    def plain():
+        for p in parts:
+            S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
+            for k, (fld, isos) in enumerate(((p["Q"], qisos), (p["vel"][0], uisos))):
+                c = S.sem_isosurface_multi(ctx, p["m"], fld, isos, p["tris"][k], cap=p["cap"][k])
+                S.sem_render(ctx, p["tris"][k], sum(c), c, None, p["cam"], 1024, 1024, p["img"][k], None)
+
+    def tail():
+        for p in parts:
+            for k, (fld, isos) in enumerate(((p["Q"], qisos), (p["vel"][0], uisos))):
+                S.sem_isosurface_multi_async(ctx, p["m"], fld, isos, p["tris"][k], p["cnt"][k], cap=p["cap"][k])
+                S.sem_render_async(ctx, p["tris"][k], p["cap"][k], p["cnt"][k], 4, None, p["cam"], 1024, 1024,
+                                   p["img"][k], None)
+
+    def per_partition():
+        for p in parts:
+            S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
+        tail()
+
+    def batched():
+        S.sem_qcriterion_batch(ctx, [p["m"] for p in parts], [p["vel"][0] for p in parts],
+                               [p["vel"][1] for p in parts], [p["vel"][2] for p in parts], [p["Q"] for p in parts])
+        tail()
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    def graph_of(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            S.sem_set_stream(ctx, torch.cuda.current_stream())
+            fn()
+        S.sem_set_stream(ctx, stream)
+        return g.replay
+
+    ms_plain = timed(plain)
+    ms_pp = timed(graph_of(per_partition))
+    ms_b = timed(graph_of(batched))
+    S.sem_synchronize(ctx)
+    # the Q stage alone, per partition vs batched (graphs)
+    qpp = graph_of(lambda: [S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"]) for p in parts])
+    qb = graph_of(lambda: S.sem_qcriterion_batch(ctx, [p["m"] for p in parts], [p["vel"][0] for p in parts],
+                                                 [p["vel"][1] for p in parts], [p["vel"][2] for p in parts],
+                                                 [p["Q"] for p in parts]))
+    ms_qpp, ms_qb = timed(qpp), timed(qb)
+    for p in parts:
+        S.sem_mesh_free(p["m"])
+    eps = lambda ms: round(E_total / (ms * 1e-3), 1)  # noqa: E731
+    return {"workload": "16 partitions, E_p ~ U{4096..40960}, N_p in {5,7,9}, Taylor-Green; Q + 4 isovalues "
+                        "of Q and of u + one 1024x1024 frame per partition and field",
+            "elements": E_total, "orders": [p["N"] for p in parts],
+            "plain_ms": round(ms_plain, 4), "plain_elements_per_s": eps(ms_plain),
+            "graph_per_partition_ms": round(ms_pp, 4), "graph_per_partition_elements_per_s": eps(ms_pp),
+            "graph_batched_ms": round(ms_b, 4), "graph_batched_elements_per_s": eps(ms_b),
+            "q_only_per_partition_ms": round(ms_qpp, 4), "q_only_batched_ms": round(ms_qb, 4)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -481,6 +589,7 @@ def run_ours(args):
 
     mem_now, mem_peak = S.sem_memory(P.ctx)
     torch_peak = int(torch.cuda.max_memory_allocated())  # the caller's buffers (torch allocator)
+    batched = measure_batched(S, P.ctx) if args.batched else None
     learned = None
     if not args.no_learned:
         bpk = peaks.get("bf16_tflops")
@@ -510,6 +619,8 @@ def run_ours(args):
            "learned": learned}
     if qprec is not None:
         out["q_precisions"] = qprec
+    if batched is not None:
+        out["batched"] = batched
     P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -605,6 +716,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of the captured graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the autoencoder measurement")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the batching workload: plain path vs CUDA graph vs batched Q (batched)")
     ap.add_argument("--q-precisions", action="store_true",
                     help="also time sem_qcriterion at FP32, BF16, FP16 and split BF16 (q_precisions)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -157,6 +157,14 @@ SEM_API sem_status sem_derivatives(sem_ctx *ctx, const sem_mesh *mesh, const flo
 SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const float *u, const float *v,
                           const float *w, float *Q, sem_prec prec);
 
+/* Q of n partitions in as few launches as possible (the batched form of sem_qcriterion, FP32):
+ * meshes[p] with fields u[p], v[p], w[p] -> Q[p] (device pointers, each as in sem_qcriterion;
+ * the pointer arrays are HOST arrays).  Partitions of one order share one persistent launch
+ * (up to 48 per launch), whatever their element counts; orders may be mixed.  Results equal
+ * sem_qcriterion's on each partition bit for bit.  Asynchronous; may be captured in a graph. */
+SEM_API sem_status sem_qcriterion_batch(sem_ctx *ctx, int n, const sem_mesh *const *meshes, const float *const *u,
+                                        const float *const *v, const float *const *w, float *const *Q);
+
 /* Marching-cubes isosurface (Lorensen & Cline 1987) of f = iso over the N^3 sub-hexes of each
  * element's GLL lattice.  Cell (i,j,k), corner v = a + 2b + 4c at node (i+a, j+b, k+c);
  * case = sum_v [f_v >= iso] 2^v (NaN counts as below).  The case table is the library's own,

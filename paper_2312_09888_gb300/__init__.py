@@ -67,6 +67,7 @@ def _declare(L):
     L.sem_mesh_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i64)]
     L.sem_derivatives.argtypes = [vp, vp, vp, vp, vp, vp, i32]
     L.sem_qcriterion.argtypes = [vp, vp, vp, vp, vp, vp, i32]
+    L.sem_qcriterion_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_isosurface_multi.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_multi_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
@@ -245,6 +246,15 @@ def sem_qcriterion(ctx, mesh, u, v, w, Q, prec: int = SEM_FP32) -> None:
     f = torch.float32
     _check(ctx, get_lib().sem_qcriterion(ctx, mesh, _dev(u, "u", f), _dev(v, "v", f), _dev(w, "w", f),
                                          _dev(Q, "Q", f), int(prec)))
+
+
+def sem_qcriterion_batch(ctx, meshes, us, vs, ws, Qs) -> None:
+    """Q of several partitions (lists of meshes and device tensors) in one launch per order."""
+    import torch
+    n = len(meshes)
+    arr = lambda xs, name: (C.c_void_p * max(n, 1))(*[_dev(x, name, torch.float32) for x in xs])  # noqa: E731
+    mp = (C.c_void_p * max(n, 1))(*meshes)
+    _check(ctx, get_lib().sem_qcriterion_batch(ctx, n, mp, arr(us, "u"), arr(vs, "v"), arr(ws, "w"), arr(Qs, "Q")))
 
 
 def sem_isosurface(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None, cap: Optional[int] = None) -> int:

@@ -575,6 +575,26 @@ sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *m, const float *u, const
                     "sem_qcriterion: precision %d not available", (int)prec);
 }
 
+sem_status sem_qcriterion_batch(sem_ctx *ctx, int n, const sem_mesh *const *meshes, const float *const *u,
+                                const float *const *v, const float *const *w, float *const *Q)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    SEM_CU(ctx, cudaSetDevice(ctx->device));
+    if (n < 0 || (n > 0 && (!meshes || !u || !v || !w || !Q)))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_batch: bad arrays");
+    for (int p = 0; p < n; ++p) {
+        SEM_TRY(check_common(ctx, meshes[p], "sem_qcriterion_batch"));
+        if (meshes[p]->E == 0) continue;
+        SEM_TRY(check_ptr(ctx, u[p], "sem_qcriterion_batch", "u[p]"));
+        SEM_TRY(check_ptr(ctx, v[p], "sem_qcriterion_batch", "v[p]"));
+        SEM_TRY(check_ptr(ctx, w[p], "sem_qcriterion_batch", "w[p]"));
+        SEM_TRY(check_ptr(ctx, Q[p], "sem_qcriterion_batch", "Q[p]"));
+        if (Q[p] == u[p] || Q[p] == v[p] || Q[p] == w[p])
+            return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_batch: Q[%d] aliases an input", p);
+    }
+    return qcrit_batch_launch(ctx, n, meshes, u, v, w, Q);
+}
+
 sem_status sem_isosurface(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
                           int64_t cap, int64_t *ntri_out, uint8_t *cases)
 {

@@ -121,6 +121,8 @@ sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const f
 sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q,
                            sem_prec prec, const double *D64);
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
+sem_status qcrit_batch_launch(sem_ctx *ctx, int n, const sem_mesh *const *m, const float *const *u,
+                              const float *const *v, const float *const *w, float *const *Q);
 sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris, int32_t *tri_elem,
                    int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso, float *tris,

@@ -19,6 +19,10 @@
 // transposed between the three directions, costing more shared-memory traffic than the
 // FFMA work they would replace.
 #include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "sem_internal.cuh"
 
@@ -259,12 +263,34 @@ struct QCfg {
     static constexpr int MINB = (NP == 8) ? SEM_Q_MINB : 1;
 };
 
+// The partitions one launch covers (one partition for sem_qcriterion / sem_derivatives, up to
+// QB_MAX of the same order for sem_qcriterion_batch).  Elements are taken in groups of EPB per
+// partition; gstart[p] is partition p's first group in the launch's group numbering.
+#define QB_MAX 48
+struct GBatch {
+    int n;
+    int64_t gstart[QB_MAX + 1];
+    int64_t E[QB_MAX];
+    const float *f[3][QB_MAX];
+    float *o[3][QB_MAX];
+    const float4 *g[QB_MAX];
+};
+
+// the partition holding group grp (largest p with gstart[p] <= grp)
+__device__ __forceinline__ int qb_find(const GBatch &B, int64_t grp)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.gstart[mid] <= grp) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // NC = 3: Q of (f0, f1, f2) -> out0.   NC = 1: gradient of f0 -> (out0, out1, out2).
 template <int NP, int NC>
-__global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const float *__restrict__ f0, const float *__restrict__ f1,
-                                                           const float *__restrict__ f2, float *__restrict__ out0,
-                                                           float *__restrict__ out1, float *__restrict__ out2,
-                                                           const float4 *__restrict__ gfac, int64_t E, int *err)
+__global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const __grid_constant__ GBatch B, int *err)
 {
     using C = QCfg<NP>;
     constexpr int NP3 = C::NP3, L = C::L, EPB = C::EPB;
@@ -277,9 +303,14 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
     const int tid = threadIdx.x;
     const bool active = tid < EPB * L;
     const int el = tid / L, line = tid % L, j = line % NP, k = line / NP;
-    const int64_t ngroups = (E + EPB - 1) / EPB;
-    const int64_t nfull = C::BULK ? E / EPB : 0;
-    const float *src[3] = {f0, f1, f2};
+    const int64_t ngroups = B.gstart[B.n];
+    // group -> (partition, its elements): a full group (EPB elements) can come by bulk copy
+    auto elems = [&](int64_t grp, int &p, int64_t &e0) {
+        p = qb_find(B, grp);
+        e0 = (grp - B.gstart[p]) * EPB;
+        const int64_t left = B.E[p] - e0;
+        return (int)(left < EPB ? left : EPB);
+    };
 
     float Dj[NP], Dk[NP];
 #pragma unroll
@@ -297,43 +328,51 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
     }
     __syncthreads();
 
+    auto full = [&](int64_t grp) {
+        int p;
+        int64_t e0;
+        return C::BULK && grp < ngroups && elems(grp, p, e0) == EPB;
+    };
     auto issue = [&](int64_t grp, int s) {
+        int p;
+        int64_t e0;
+        elems(grp, p, e0);
         float *dst = smem + s * STAGE;
         mbar_arrive_expect_tx(&bar[s], NC * BYTES);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) bulk_g2s(dst + c * EPB * NP3, src[c] + grp * EPB * NP3, BYTES, &bar[s]);
+        for (int c = 0; c < NC; ++c) bulk_g2s(dst + c * EPB * NP3, B.f[c][p] + e0 * NP3, BYTES, &bar[s]);
     };
     uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {false, false};
-    if (C::BULK && tid == 0) {
-        if ((int64_t)blockIdx.x < nfull) issue(blockIdx.x, 0);
-        if ((int64_t)blockIdx.x + gridDim.x < nfull) issue(blockIdx.x + gridDim.x, 1);
-    }
-    if (C::BULK) {
-        pending[0] = (int64_t)blockIdx.x < nfull;
-        pending[1] = (int64_t)blockIdx.x + gridDim.x < nfull;
+    bool pending[2] = {full(blockIdx.x), full((int64_t)blockIdx.x + gridDim.x)};
+    if (tid == 0) {
+        if (pending[0]) issue(blockIdx.x, 0);
+        if (pending[1]) issue((int64_t)blockIdx.x + gridDim.x, 1);
     }
 
     int it = 0;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
         const int s = C::BULK ? (it & 1) : 0;
         float *st = smem + s * STAGE;
-        if (C::BULK && grp < nfull) {
+        int p;
+        int64_t e0;
+        const int ne = elems(grp, p, e0);
+        if (C::BULK && ne == EPB) {
             if (!mbar_wait_bounded(&bar[s], phase[s], err)) s_abort = 1;
             phase[s] ^= 1u;
             pending[s] = false;
         } else {
-            const int64_t ne = E - grp * EPB < EPB ? E - grp * EPB : EPB;
             for (int c = 0; c < NC; ++c)
-                for (int64_t idx = tid; idx < ne * NP3; idx += blockDim.x) st[c * EPB * NP3 + idx] = src[c][grp * EPB * NP3 + idx];
+                for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x)
+                    st[c * EPB * NP3 + idx] = B.f[c][p][e0 * NP3 + idx];
         }
         __syncthreads();
         if (s_abort) break;
-        const int64_t e = grp * EPB + el;
-        if (active && e < E) {
-            const float4 g = gfac[e];
+        const int64_t e = e0 + el;
+        if (active && el < ne) {
+            const float4 g = B.g[p][e];
             float dr[NP], ds[NP], dt[NP];
             const int64_t off = e * NP3 + (k * NP + j) * NP;
+            float *out0 = B.o[0][p], *out1 = B.o[1][p], *out2 = B.o[2][p];
             if constexpr (NC == 1) {
                 line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
 #pragma unroll
@@ -405,8 +444,8 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
             }
         }
         __syncthreads();
-        if (C::BULK && tid == 0 && grp + 2 * (int64_t)gridDim.x < nfull) {
-            issue(grp + 2 * gridDim.x, s);
+        if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
+            issue(grp + 2 * (int64_t)gridDim.x, s);
             pending[s] = true;
         }
     }
@@ -455,9 +494,7 @@ constexpr int XS = 2 * CS;                                // exchange: s then t 
 constexpr size_t SMEM = sizeof(float) * (2 * STAGE + XS);
 }  // namespace q8
 
-__global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0, const float *__restrict__ f1,
-                                                   const float *__restrict__ f2, float *__restrict__ Q,
-                                                   const float4 *__restrict__ gfac, int64_t E, int *err)
+__global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatch B, int *err)
 {
     using namespace q8;
     extern __shared__ __align__(128) float smem[];
@@ -469,8 +506,19 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0,
     const int el = tid >> 6, k = (tid >> 3) & 7, j = tid & 7;
     // s-/t-line owner: element lane/8, node i = lane%8, slab k = warp (s), plane j = warp (t)
     const int oe = lane >> 3, oi = lane & 7;
-    const int64_t ngroups = (E + EPB - 1) / EPB, nfull = E / EPB;
-    const float *src[3] = {f0, f1, f2};
+    const int64_t ngroups = B.gstart[B.n];
+    // group -> (partition, its elements): a full group (EPB elements) comes by bulk copies
+    auto elems = [&](int64_t grp, int &p, int64_t &e0) {
+        p = qb_find(B, grp);
+        e0 = (grp - B.gstart[p]) * EPB;
+        const int64_t left = B.E[p] - e0;
+        return (int)(left < EPB ? left : EPB);
+    };
+    auto full = [&](int64_t grp) {
+        int p;
+        int64_t e0;
+        return grp < ngroups && elems(grp, p, e0) == EPB;
+    };
     if (tid == 0) {
         s_abort = 0;
         mbar_init(&bar[0], 1);
@@ -479,17 +527,20 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0,
     }
     __syncthreads();
     auto issue = [&](int64_t grp, int s) {
+        int p;
+        int64_t e0;
+        elems(grp, p, e0);
         float *dst = smem + s * STAGE;
         mbar_arrive_expect_tx(&bar[s], 3 * EPB * NP3 * 4);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int e = 0; e < EPB; ++e)
-                bulk_g2s(dst + c * CS + e * ES, src[c] + (grp * EPB + e) * NP3, NP3 * 4, &bar[s]);
+                bulk_g2s(dst + c * CS + e * ES, B.f[c][p] + (e0 + e) * NP3, NP3 * 4, &bar[s]);
     };
     // per stage s: bit s of `phase` is its mbarrier parity, bit s of `pending` a copy in flight
     uint32_t phase = 0u;
-    uint32_t pending = ((int64_t)blockIdx.x < nfull ? 1u : 0u) | ((int64_t)blockIdx.x + gridDim.x < nfull ? 2u : 0u);
+    uint32_t pending = (full(blockIdx.x) ? 1u : 0u) | (full((int64_t)blockIdx.x + gridDim.x) ? 2u : 0u);
     if (tid == 0) {
         if (pending & 1u) issue(blockIdx.x, 0);
         if (pending & 2u) issue(blockIdx.x + gridDim.x, 1);
@@ -499,20 +550,22 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0,
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
         const int s = it & 1;
         float *st = smem + s * STAGE;
-        if (grp < nfull) {
+        int p;
+        int64_t e0;
+        const int ne = elems(grp, p, e0);
+        if (ne == EPB) {
             if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err)) s_abort = 1;
             phase ^= 1u << s;
             pending &= ~(1u << s);
         } else {
-            const int ne = (int)(E - grp * EPB);
             for (int c = 0; c < 3; ++c)
                 for (int idx = tid; idx < ne * NP3; idx += 256)
-                    st[c * CS + (idx / NP3) * ES + idx % NP3] = src[c][grp * EPB * NP3 + idx];
+                    st[c * CS + (idx / NP3) * ES + idx % NP3] = B.f[c][p][e0 * NP3 + idx];
         }
         __syncthreads();
         if (s_abort) break;
-        const int64_t e = grp * EPB + el;
-        const float4 g = gfac[e < E ? e : E - 1];
+        const int64_t e = e0 + el;
+        const float4 g = B.g[p][el < ne ? e : e0];
         const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
         const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
         float q[8], su[8], tu[8], tv[8];
@@ -583,8 +636,8 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0,
             }
             __syncthreads();  // the exchange is free for the next component
         }
-        if (e < E) store_line<8>(Q + e * NP3 + (k * 8 + j) * 8, q);
-        if (tid == 0 && grp + 2 * (int64_t)gridDim.x < nfull) {
+        if (el < ne) store_line<8>(B.o[0][p] + e * NP3 + (k * 8 + j) * 8, q);
+        if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
             issue(grp + 2 * gridDim.x, s);
             pending |= 1u << s;
         }
@@ -595,59 +648,120 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const float *__restrict__ f0,
     }
 }
 
-static sem_status launch_q8(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
+// A batch table for partitions [first, first + n) of (meshes, fields); EPB elements per group.
+static void fill_batch(GBatch &B, int n, int epb, const sem_mesh *const *m, const float *const *f0,
+                       const float *const *f1, const float *const *f2, float *const *o0, float *const *o1,
+                       float *const *o2)
 {
-    SEM_CU(ctx, cudaFuncSetAttribute(k_sem_q8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q8::SMEM));
-    int per_sm = 0;
-    SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_q8, 256, q8::SMEM));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t ngroups = (m->E + q8::EPB - 1) / q8::EPB;
+    memset(&B, 0, sizeof B);
+    B.n = n;
+    int64_t g = 0;
+    for (int p = 0; p < n; ++p) {
+        B.gstart[p] = g;
+        B.E[p] = m[p]->E;
+        B.f[0][p] = f0[p];
+        B.f[1][p] = f1 ? f1[p] : nullptr;
+        B.f[2][p] = f2 ? f2[p] : nullptr;
+        B.o[0][p] = o0[p];
+        B.o[1][p] = o1 ? o1[p] : nullptr;
+        B.o[2][p] = o2 ? o2[p] : nullptr;
+        B.g[p] = m[p]->g;
+        g += (m[p]->E + epb - 1) / epb;
+    }
+    B.gstart[n] = g;
+}
+
+static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
+{
+    static int per_sm = 0;
+    if (!per_sm) {
+        SEM_CU(ctx, cudaFuncSetAttribute(k_sem_q8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q8::SMEM));
+        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_q8, 256, q8::SMEM));
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t ngroups = B.gstart[B.n];
+    if (ngroups == 0) return SEM_OK;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
     if (grid > ngroups) grid = ngroups;
-    SEM_TRACED(ctx, "k_sem_q8", k_sem_q8<<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(u, v, w, Q, m->g, m->E,
-                                                                                         ctx->d_flag));
+    SEM_TRACED(ctx, "k_sem_q8", k_sem_q8<<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(B, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_sem_q8 launch");
 }
 
 template <int NP, int NC>
-static sem_status launch_grad(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
-                              float *o0, float *o1, float *o2)
+static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
 {
     using C = QCfg<NP>;
     const size_t smem = sizeof(float) * (size_t)C::NSTAGE * NC * C::EPB * C::NP3;
     auto kern = k_sem_grad<NP, NC>;
-    SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, smem));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t ngroups = (m->E + C::EPB - 1) / C::EPB;
+    static int per_sm = 0;
+    if (!per_sm) {
+        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, smem));
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t ngroups = B.gstart[B.n];
+    if (ngroups == 0) return SEM_OK;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
     if (grid > ngroups) grid = ngroups;
-    SEM_TRACED(ctx, "k_sem_grad", kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(f0, f1, f2, o0, o1, o2, m->g, m->E, ctx->d_flag));
+    SEM_TRACED(ctx, "k_sem_grad", kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(B, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
 }
 
 template <int NC>
-static sem_status dispatch(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
-                           float *o0, float *o1, float *o2)
+static sem_status dispatch(sem_ctx *ctx, int N, int n, const sem_mesh *const *m, const float *const *f0,
+                           const float *const *f1, const float *const *f2, float *const *o0, float *const *o1,
+                           float *const *o2)
 {
-    switch (m->N + 1) {
-#define SEM_CASE(NPV) \
-    case NPV: return launch_grad<NPV, NC>(ctx, m, f0, f1, f2, o0, o1, o2);
+    GBatch B;
+    if (NC == 3 && N == 7) {
+        fill_batch(B, n, q8::EPB, m, f0, f1, f2, o0, o1, o2);
+        return launch_q8(ctx, B);
+    }
+    switch (N + 1) {
+#define SEM_CASE(NPV)                                                        \
+    case NPV:                                                                \
+        fill_batch(B, n, QCfg<NPV>::EPB, m, f0, f1, f2, o0, o1, o2);         \
+        return launch_grad<NPV, NC>(ctx, B);
         SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
         SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
 #undef SEM_CASE
-    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", N);
     }
 }
 
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
 {
-    if (m->N == 7) return launch_q8(ctx, m, u, v, w, Q);
-    return dispatch<3>(ctx, m, u, v, w, Q, nullptr, nullptr);
+    return dispatch<3>(ctx, m->N, 1, &m, &u, &v, &w, &Q, nullptr, nullptr);
 }
 
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz)
 {
-    return dispatch<1>(ctx, m, u, nullptr, nullptr, dx, dy, dz);
+    return dispatch<1>(ctx, m->N, 1, &m, &u, nullptr, nullptr, &dx, &dy, &dz);
+}
+
+// Q of several partitions: one persistent launch per order over all partitions of that order
+// (at most QB_MAX per launch), in the order the partitions first appear.
+sem_status qcrit_batch_launch(sem_ctx *ctx, int n, const sem_mesh *const *m, const float *const *u,
+                              const float *const *v, const float *const *w, float *const *Q)
+{
+    std::vector<char> done(n, 0);
+    std::vector<const sem_mesh *> mm;
+    std::vector<const float *> uu, vv, ww;
+    std::vector<float *> qq;
+    for (int a = 0; a < n; ++a) {
+        if (done[a]) continue;
+        const int N = m[a]->N;
+        mm.clear(), uu.clear(), vv.clear(), ww.clear(), qq.clear();
+        for (int b = a; b < n; ++b)
+            if (!done[b] && m[b]->N == N && m[b]->E > 0) {
+                done[b] = 1;
+                mm.push_back(m[b]), uu.push_back(u[b]), vv.push_back(v[b]), ww.push_back(w[b]), qq.push_back(Q[b]);
+            }
+        for (size_t c0 = 0; c0 < mm.size(); c0 += QB_MAX) {
+            const int k = (int)std::min<size_t>(QB_MAX, mm.size() - c0);
+            SEM_TRY(dispatch<3>(ctx, N, k, mm.data() + c0, uu.data() + c0, vv.data() + c0, ww.data() + c0,
+                                qq.data() + c0, nullptr, nullptr));
+        }
+    }
+    return SEM_OK;
 }

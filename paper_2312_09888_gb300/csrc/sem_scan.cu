@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t *__re
 
 // One block for small inputs: thread t scans its contiguous chunk of ceil(n / 1024) entries
 // (sum, block-wide scan of the sums, then the chunk's offsets), so the whole scan is a single
-// launch; used up to SCAN_SINGLE_MAX entries.
-#define SCAN_SINGLE_MAX (SCAN_THREADS * 256)
+// launch; used up to SCAN_SINGLE_MAX entries (8 per thread: beyond that one SM's serial chunks
+// cost more than the three-kernel scan, measured 194 us against 20 us at 98304 entries).
+#define SCAN_SINGLE_MAX (SCAN_THREADS * 8)
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t *__restrict__ in, int64_t n,
                                                               int64_t *__restrict__ out)
 {

@@ -188,3 +188,45 @@ def test_batched_partitions_mixed_orders_one_graph(gpu, sess, orc):
                 ref = orc.isosurface(mesh.N, xyz, field, float(np.float32(iso)), want_tris=False)
                 assert c[q + 1] - c[q] == ref["ntri"], (mesh.N, q)
         S.sem_mesh_free(f.mesh)
+
+
+def test_qcriterion_batch_equals_per_partition_calls(gpu, sess):
+    """12 partitions of uneven element counts (including counts that leave partial 4-element
+    groups) and mixed orders in one batch call: Q bit-identical to one call per partition,
+    also when the batch call is captured in a CUDA graph."""
+    S = gpu
+    rng = np.random.default_rng(si.seed_for(4, 77))
+    parts = []
+    for p in range(12):
+        N = int(rng.choice([5, 7, 9]))
+        nel = (int(rng.integers(1, 6)), int(rng.integers(1, 6)), int(rng.integers(1, 5)))
+        lo = np.array([p * 1.1, 0.3, 0.0])
+        mesh = si.uniform_box(nel, lo, lo + np.array([1.0, 1.3, 0.9]), N)
+        vel = si.taylor_green(mesh, 1e-3, si.seed_for(4, 100 + p), phase=0.1 * p)
+        m = sess.mesh(N, mesh.xyz().numpy())
+        f = [vel[c].float().cuda().contiguous() for c in range(3)]
+        parts.append((m, f))
+    metas = [m for m, _ in parts]
+    us, vs, ws = ([f[c] for _, f in parts] for c in range(3))
+    ref = []
+    for m, f in parts:
+        q = torch.empty_like(f[0])
+        S.sem_qcriterion(sess.ctx, m, *f, q)
+        ref.append(q)
+    got = [torch.full_like(f[0], float("nan")) for _, f in parts]
+    S.sem_qcriterion_batch(sess.ctx, metas, us, vs, ws, got)
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        assert torch.equal(a, b)
+    # captured
+    got2 = [torch.full_like(f[0], float("nan")) for _, f in parts]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        S.sem_qcriterion_batch(sess.ctx, metas, us, vs, ws, got2)
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    S.sem_synchronize(sess.ctx)
+    for a, b in zip(got2, ref):
+        assert torch.equal(a, b)

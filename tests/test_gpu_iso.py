@@ -193,8 +193,8 @@ def test_channel_full_size_sampled(gpu, sess, orc):
 
 
 def test_many_elements_multi_isovalue_uses_the_multi_block_scan(gpu, sess, orc):
-    """64^3 elements of order 1 x 2 isovalues = 524288 counts: above the single-block scan's
-    limit (262144), so the three-kernel scan runs; counts and offsets against the oracle."""
+    """64^3 elements of order 1 x 2 isovalues = 524288 counts: the three-kernel scan (the
+    single-block scan takes at most 8192); counts and offsets against the oracle."""
     mesh = si.uniform_box((64, 64, 64), (0, 0, 0), (1, 1, 1), 1)
     xyz = mesh.xyz().numpy()
     f32 = dev32(si.sphere_field(mesh, (0.5, 0.5, 0.5), 0.3).numpy())
