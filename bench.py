@@ -269,6 +269,117 @@ def _ae_gemm_shapes(B):
             "dx2": (B, 512, 64), "dw2": (128, 512, B), "dw1": (512, 1536, B)}
 
 
+def measure_in_transit(S, ctx, ae, steps=50, warmup=4):
+    """The in-transit use of the learned compression, end to end on the Taylor-Green snapshot of
+    32^3 elements (N = 7): per step either the velocity (201 MB FP32) or its latent (3.1 MB BF16)
+    comes from pinned host memory, the latent is decoded on the device, then Q, the isosurface at
+    0.1 max Q and a 1920x1080 frame, read back to pinned host memory.  Both forms are one CUDA
+    graph per step, pipelined over two device slots."""
+    import math as _m
+    import torch
+    import sem_inputs as si
+    f = si.ae_snapshot(203, nel=32, device="cuda")
+    E = f.shape[1]
+    mesh = si.uniform_box((32,) * 3, (0.0,) * 3, (2 * _m.pi,) * 3, 7)
+    m = S.sem_load_mesh(ctx, 7, mesh.xyz().numpy())
+    cam = si.box_camera_persp((0.0,) * 3, (2 * _m.pi,) * 3, 1920, 1080)
+    W, H = 1920, 1080
+    Q = torch.empty_like(f[0])
+    S.sem_qcriterion(ctx, m, f[0].contiguous(), f[1].contiguous(), f[2].contiguous(), Q)
+    iso = [float(0.1 * S.sem_field_max(ctx, Q))]
+    n = S.sem_isosurface_multi(ctx, m, Q, iso, None)
+    cap = int(sum(n) * 1.5) + 4096
+    tris = torch.empty(cap * 9, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    lat_host = torch.empty(E * 48, dtype=torch.bfloat16)
+    lat_dev = torch.empty(E * 48, dtype=torch.bfloat16, device="cuda")
+    S.sem_ae_encode(ctx, ae, f[0].contiguous(), f[1].contiguous(), f[2].contiguous(), lat_dev)
+    lat_host.copy_(lat_dev.cpu())
+    lat_host = lat_host.pin_memory()
+    vel_host = [f[c].cpu().pin_memory() for c in range(3)]
+
+    def make_slot(from_latent):
+        sl = dict(vel=[torch.empty_like(f[c]) for c in range(3)], rgba=torch.empty(W * H * 4, dtype=torch.uint8,
+                                                                                     device="cuda"),
+                  depth=torch.empty(W * H, device="cuda"), lat=torch.empty_like(lat_dev))
+        if from_latent:
+            sl["lat"].copy_(lat_dev)
+        else:
+            for c in range(3):
+                sl["vel"][c].copy_(f[c])
+
+        def step():
+            if from_latent:
+                S.sem_ae_decode(ctx, ae, sl["lat"], E, *sl["vel"])
+            S.sem_qcriterion(ctx, m, *sl["vel"], Q)
+            S.sem_isosurface_multi_async(ctx, m, Q, iso, tris, cnt, cap=cap)
+            S.sem_render_async(ctx, tris, cap, cnt, 1, None, cam, W, H, sl["rgba"], sl["depth"])
+
+        step()
+        S.sem_synchronize(ctx)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            S.sem_set_stream(ctx, torch.cuda.current_stream())
+            step()
+        S.sem_set_stream(ctx, stream)
+        sl["replay"] = g.replay
+        sl["graph"] = g
+        return sl
+
+    img_host = torch.empty(W * H * 4, dtype=torch.uint8).pin_memory()
+    dep_host = torch.empty(W * H, dtype=torch.float32).pin_memory()
+
+    def timed(from_latent):
+        slots = [make_slot(from_latent), make_slot(from_latent)]
+        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in, ev_done, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+        used = [False, False]
+
+        def one(k):
+            sl = slots[k % 2]
+            i = k % 2
+            with torch.cuda.stream(h2d):
+                if used[i]:
+                    h2d.wait_event(ev_out[i])
+                if from_latent:
+                    sl["lat"].copy_(lat_host, non_blocking=True)
+                else:
+                    for c in range(3):
+                        sl["vel"][c].copy_(vel_host[c], non_blocking=True)
+                ev_in[i].record(h2d)
+            stream.wait_event(ev_in[i])
+            sl["replay"]()
+            ev_done[i].record(stream)
+            with torch.cuda.stream(d2h):
+                d2h.wait_event(ev_done[i])
+                img_host.copy_(sl["rgba"], non_blocking=True)
+                dep_host.copy_(sl["depth"], non_blocking=True)
+                ev_out[i].record(d2h)
+            used[i] = True
+
+        for k in range(warmup):
+            one(k)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(h2d)
+        for k in range(steps):
+            one(k)
+        b.record(d2h)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    ms_plain, ms_lat = timed(False), timed(True)
+    S.sem_synchronize(ctx)
+    S.sem_mesh_free(m)
+    eps = lambda ms: round(E / (ms * 1e-3), 1)  # noqa: E731
+    return {"workload": "Taylor-Green 32^3 elements, N=7, Q-isosurface at 0.1 max Q, 1920x1080, end to end",
+            "velocity_in": {"h2d_bytes_per_step": int(E * 1536 * 4), "ms_per_step": round(ms_plain, 4),
+                            "elements_per_s": eps(ms_plain)},
+            "latent_in": {"h2d_bytes_per_step": int(E * 96), "ms_per_step": round(ms_lat, 4),
+                          "elements_per_s": eps(ms_lat)}}
+
+
 def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
     """The learned per-element compression on the benchmark's scale: AdamW steps of the
     1536-512-48-512-1536 BF16 autoencoder at batch 8192 on samples of 8 Taylor-Green snapshots
@@ -331,6 +442,10 @@ def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
         e2.record(stream)
         torch.cuda.synchronize()
         enc_ms, dec_ms = e0.elapsed_time(e1) / 10, e1.elapsed_time(e2) / 10
+        # a short training run so the decoded field looks like the data, then the in-transit form
+        for i in range(3000):
+            S.sem_ae_train_step(ctx, ae, train, idx[i % (steps + warmup)], lr=1e-3 * (1.0 - i / 3000.0) + 1e-5)
+        in_transit = measure_in_transit(S, ctx, ae)
         return {"model": "per-element autoencoder 1536-512-48-512-1536, BF16 tensor cores, FP32 accumulation",
                 "train_batch": B, "train_ms_per_step": round(step_ms, 4),
                 "train_samples_per_s": round(B / (step_ms * 1e-3), 1),
@@ -343,7 +458,7 @@ def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
                 "gemms": gemm,
                 "encode_elements_per_s": round(E / (enc_ms * 1e-3), 1),
                 "decode_elements_per_s": round(E / (dec_ms * 1e-3), 1),
-                "latent_bytes_per_element": 96}
+                "latent_bytes_per_element": 96, "in_transit": in_transit}
     finally:
         S.sem_ae_destroy(ae)
         del train
