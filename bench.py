@@ -690,10 +690,23 @@ def run_ours(args):
         b.record(d2h)
         barrier()
         es = max_over_ranks(a.elapsed_time(b) / 1e3, "cuda")
+        h2d_bytes = int(sum(h.numel() * 4 for h in host_vel))
+        # the host link's ceiling: the same copy-in alone, back to back on the copy stream
+        for _ in range(2):
+            a.record(h2d)
+            for _ in range(10):
+                for d, h in zip(slots[1][0], host_vel):
+                    d.copy_(h, non_blocking=True)
+            b.record(h2d)
+            b.synchronize()
+        link = 10 * h2d_bytes / (a.elapsed_time(b) / 1e3) / 1e9
+        step_gbs = h2d_bytes / (es / K) / 1e9
         e2e = {"value": aggregate([total_elems], [es]), "unit": UNIT,
-               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in host_vel)),
+               "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4),
                "ms_per_step": es * 1e3 / K,
+               "h2d_gbs": round(step_gbs, 1), "h2d_link_gbs": round(link, 1),
+               "frac_of_link": round(step_gbs / link, 3),
                "pipelining": "two device slots; copy-in of step k+1 and read-back of step k-1 overlap step k"}
 
     # roofline of the dominant kernel: its CUDA-event launch time from the library's kernel trace

@@ -141,35 +141,55 @@ __device__ __forceinline__ void shade_pixel(const Setup &S, int px, int py, int 
     atomicMin(&keys[(int64_t)py * W + px], key);
 }
 
-// Compact per-triangle setup kept in shared memory for the warp's pixel work: four 16-byte
-// words per triangle, each in its own array (a lane's four stores are contiguous with its
-// neighbours'), read with four vector loads per pixel test.
-//   a: x0 y0 x1 y1   b: x2 y2 z0 z1   c: z2, 1/area, 1/nx, top-left flags   d: px0 py0 nx -
-struct SmallRec {
-    float4 a, b, c;
-    int4 d;
+// Compact per-triangle setup kept in shared memory for the warp's pixel work: the three edge
+// functions and the depth as planes over the triangle's box, e(kx, ky) = e(0, 0) + A kx + B ky
+// for candidate (px0 + kx, py0 + ky), so a test is eight FMAs.  The values at the box's first
+// pixel centre are evaluated exactly as shade_pixel does; the increments are the edges'
+// coordinate differences.  Per triangle, in four arrays (a lane's stores are contiguous with
+// its neighbours'):
+//   a: e0 e1 e2 z at (px0 + .5, py0 + .5)   b: de/dx (3), dz/dx   c: de/dy (3), dz/dy
+//   d: pixel index py0 W + px0,  ceil(1024 / nx),  nx,  top-left flags (one per byte)
+// Box row of candidate k (0 <= k < nx ny <= 32): ky = (k ceil(1024/nx)) >> 10 is floor(k/nx)
+// exactly, since k (ceil(1024/nx) - 1024/nx) / 1024 < k / 1024 < 1/nx for nx < 32, and the
+// multiplier is exact for nx = 32.
+//
+// Coverage test on the float bits: for a float e that is neither -0 nor NaN,
+// "e > 0, or e == 0 on a top-left edge" is exactly int_bits(e) + tl > 0 (positive floats have
+// positive integer bits, +0 has 0, negative floats negative ones).  The box-origin values are
+// stored with -0 turned into +0 (x + 0 = +0 for x = -0), and an FMA chain of such a value with
+// non-negative candidate offsets rounds an exact zero to +0, never -0.  Triangles whose planes
+// could overflow over the 32-pixel box (|e| + 32 (|A| + |B|) not finite) are not drawn, so no
+// test sees an infinity or NaN.
+struct SmallRecs {
+    float4 a[256], b[256], c[256];
+    int4 d[256];
 };
 
-__device__ __forceinline__ void test_pixel(const SmallRec &R, int k, int W, unsigned t,
-                                           unsigned long long *__restrict__ keys)
+__device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, int W)
 {
-    const float4 a = R.a, b = R.b, c = R.c;
-    const int4 d = R.d;
-    // box row of candidate k: floor((k + .5) / nx), exact for k, nx <= 32
-    const int ky = (int)(((float)k + 0.5f) * c.z), kx = k - ky * d.z;
-    const int px = d.x + kx, py = d.y + ky;
-    const int flags = __float_as_int(c.w);
-    const float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
-    const float e0 = (a.z - a.x) * (cy - a.y) - (a.w - a.y) * (cx - a.x);
-    const float e1 = (b.x - a.z) * (cy - a.w) - (b.y - a.w) * (cx - a.z);
-    const float e2 = (a.x - b.x) * (cy - b.y) - (a.y - b.y) * (cx - b.x);
-    const bool in = (e0 > 0.f || (e0 == 0.f && (flags & 1))) && (e1 > 0.f || (e1 == 0.f && (flags & 2))) &&
-                    (e2 > 0.f || (e2 == 0.f && (flags & 4)));
-    if (!in) return;
-    float z = (e1 * b.z + e2 * b.w + e0 * c.x) * c.y;
-    z = fminf(fmaxf(z, 0.f), 1.f);
-    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | t;
-    atomicMin(&keys[(int64_t)py * W + px], key);
+    const float cx = (float)S.px0 + 0.5f, cy = (float)S.py0 + 0.5f;
+    const float e0 = (S.x[1] - S.x[0]) * (cy - S.y[0]) - (S.y[1] - S.y[0]) * (cx - S.x[0]) + 0.f;
+    const float e1 = (S.x[2] - S.x[1]) * (cy - S.y[1]) - (S.y[2] - S.y[1]) * (cx - S.x[1]) + 0.f;
+    const float e2 = (S.x[0] - S.x[2]) * (cy - S.y[2]) - (S.y[0] - S.y[2]) * (cx - S.x[2]) + 0.f;
+    const float A0 = S.y[0] - S.y[1], A1 = S.y[1] - S.y[2], A2 = S.y[2] - S.y[0];
+    const float B0 = S.x[1] - S.x[0], B1 = S.x[2] - S.x[1], B2 = S.x[0] - S.x[2];
+    const float z = (e1 * S.z[0] + e2 * S.z[1] + e0 * S.z[2]) * S.inv_area;
+    const float dzdx = (A1 * S.z[0] + A2 * S.z[1] + A0 * S.z[2]) * S.inv_area;
+    const float dzdy = (B1 * S.z[0] + B2 * S.z[1] + B0 * S.z[2]) * S.inv_area;
+    const float reach = fabsf(e0) + fabsf(e1) + fabsf(e2) + fabsf(z) +
+                        32.f * (fabsf(A0) + fabsf(A1) + fabsf(A2) + fabsf(B0) + fabsf(B1) + fabsf(B2) +
+                                fabsf(dzdx) + fabsf(dzdy));
+    if (!(reach <= 3.0e38f)) return false;
+    const int nx = S.px1 - S.px0 + 1;
+    const int tl = (S.tl0 ? 1 : 0) | (S.tl1 ? 0x100 : 0) | (S.tl2 ? 0x10000 : 0);
+    // ceil(1024 / nx): 1024/nx is an integer or at least 1/32 above one, far beyond the
+    // approximate quotient's error
+    const int mul = (int)(__fdividef(1024.f, (float)nx) - 0.00390625f) + 1;
+    R.a[i] = make_float4(e0, e1, e2, z);
+    R.b[i] = make_float4(A0, A1, A2, dzdx);
+    R.c[i] = make_float4(B0, B1, B2, dzdy);
+    R.d[i] = make_int4(S.py0 * W + S.px0, mul, nx, tl);
+    return true;
 }
 
 // Flat headlight shade of triangle t (colour of its segment times 0.15 + 0.85 |n.l|, l the view
@@ -208,9 +228,8 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
                                                       uint32_t *__restrict__ colors)
 {
     __shared__ __align__(16) float s_tri[256 * 9];
-    __shared__ float4 s_ra[256], s_rb[256], s_rc[256];
-    __shared__ int4 s_rd[256];
-    __shared__ uint8_t s_own[8][32 * SMALL_PX];
+    __shared__ SmallRecs s_rec;
+    __shared__ __align__(16) uint8_t s_own[8][32 * SMALL_PX];
     if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
     const int t0 = blockIdx.x * 256;
     // blocks past the (device-clamped) triangle count have no work; the whole block leaves
@@ -239,12 +258,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
             colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, t);
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
-                npx = nx * ny;
-                const int flags = (S.tl0 ? 1 : 0) | (S.tl1 ? 2 : 0) | (S.tl2 ? 4 : 0);
-                s_ra[threadIdx.x] = make_float4(S.x[0], S.y[0], S.x[1], S.y[1]);
-                s_rb[threadIdx.x] = make_float4(S.x[2], S.y[2], S.z[0], S.z[1]);
-                s_rc[threadIdx.x] = make_float4(S.z[2], S.inv_area, 1.f / (float)nx, __int_as_float(flags));
-                s_rd[threadIdx.x] = make_int4(S.px0, S.py0, nx, 0);
+                if (store_rec(s_rec, threadIdx.x, S, P.W)) npx = nx * ny;
             } else {
                 is_large = true;
             }
@@ -269,16 +283,37 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     const int wbase = threadIdx.x & ~31;
     const int excl = incl - npx;
     uint8_t *own = s_own[threadIdx.x >> 5];
-    for (int q = 0; q < npx; ++q) own[excl + q] = (uint8_t)lane;
+    {
+        // the lane's byte over its candidates' slots: single bytes up to a word boundary, then
+        // whole words, then the tail
+        int q = excl;
+        const int end = excl + npx;
+        for (; q < end && (q & 3); ++q) own[q] = (uint8_t)lane;
+        for (; q + 4 <= end; q += 4) *reinterpret_cast<uint32_t *>(own + q) = (uint32_t)lane * 0x01010101u;
+        for (; q < end; ++q) own[q] = (uint8_t)lane;
+    }
     __syncwarp();
+    // each round: lane `lane` takes candidate r + lane of the warp's list.  Branch-free up to
+    // the atomic: past the list's end the owner byte is clamped to the row and masked to a
+    // lane, and the candidate is switched off in the coverage predicate.
+    const int W = P.W;
     for (int r = 0; r < total; r += 32) {
         const int idx = r + lane;
-        const int L = idx < total ? own[idx] : 31;
+        const int L = own[min(idx, 32 * SMALL_PX - 1)] & 31;
         const int first = __shfl_sync(0xffffffffu, excl, L);
-        if (idx < total) {
-            const int r8 = wbase + L;
-            const SmallRec R{s_ra[r8], s_rb[r8], s_rc[r8], s_rd[r8]};
-            test_pixel(R, idx - first, P.W, (unsigned)(t0 + r8), keys);
+        const int i = wbase + L;
+        const float4 a = s_rec.a[i], b = s_rec.b[i], c = s_rec.c[i];
+        const int4 d = s_rec.d[i];
+        const int k = idx - first;
+        const int ky = (k * d.y) >> 10, kx = k - ky * d.z;
+        const float fx = (float)kx, fy = (float)ky;
+        const int v0 = __float_as_int(fmaf(c.x, fy, fmaf(b.x, fx, a.x))) + (int)__byte_perm(d.w, 0, 0x4440);
+        const int v1 = __float_as_int(fmaf(c.y, fy, fmaf(b.y, fx, a.y))) + (int)__byte_perm(d.w, 0, 0x4441);
+        const int v2 = __float_as_int(fmaf(c.z, fy, fmaf(b.z, fx, a.z))) + (int)__byte_perm(d.w, 0, 0x4442);
+        if (min(v0, min(v1, v2)) > 0 && idx < total) {
+            const float z = fminf(fmaxf(fmaf(c.w, fy, fmaf(b.w, fx, a.w)), 0.f), 1.f);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)(t0 + i);
+            atomicMin(keys + (unsigned)(d.x + ky * W + kx), key);
         }
     }
 }
