@@ -743,7 +743,7 @@ def run_ours(args):
     if args.q_precisions:
         # sem_qcriterion alone at each arithmetic (CUDA events, 50 launches after 5 warm-up)
         qprec = {}
-        for name in ("FP32", "BF16", "FP16", "BF16X2"):
+        for name in ("FP32", "BF16", "FP16", "BF16X2", "TF32"):
             prec = getattr(S, "SEM_" + name)
             for _ in range(5):
                 S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q, prec)
@@ -889,7 +889,7 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="also time the batching workload: plain path vs CUDA graph vs batched Q (batched)")
     ap.add_argument("--q-precisions", action="store_true",
-                    help="also time sem_qcriterion at FP32, BF16, FP16 and split BF16 (q_precisions)")
+                    help="also time sem_qcriterion at FP32, BF16, FP16, split BF16 and TF32 (q_precisions)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-elements", type=int, default=512)
     args = ap.parse_args()

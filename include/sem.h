@@ -153,7 +153,10 @@ SEM_API sem_status sem_derivatives(sem_ctx *ctx, const sem_mesh *mesh, const flo
 
 /* Q-criterion (Hunt, Wray & Moin 1988) of the velocity (u, v, w) at every node:
  *   J_ij = du_i/dx_j (as in sem_derivatives),  Q = 1/2(|Omega|^2 - |S|^2) = -1/2 sum_ij J_ij J_ji.
- * u, v, w, Q: device, E*(N+1)^3 floats each; Q must not alias the inputs. */
+ * u, v, w, Q: device, E*(N+1)^3 floats each; Q must not alias the inputs.
+ * prec: SEM_FP32 at every order; SEM_TF32, SEM_FP16, SEM_BF16 and SEM_BF16X2 run the s- and
+ * t-contractions on the tensor cores (the r-contraction and Q stay FP32) and exist for N = 7
+ * only (SEM_ERR_UNSUPPORTED otherwise). */
 SEM_API sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *mesh, const float *u, const float *v,
                           const float *w, float *Q, sem_prec prec);
 

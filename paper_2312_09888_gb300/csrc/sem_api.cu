@@ -322,7 +322,7 @@ void sem_destroy(sem_ctx *ctx)
     for (int s = 0; s < 4; ++s)
         if (ctx->scratch[s]) cudaFree(ctx->scratch[s]);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < 3; ++s)
         if (ctx->tc_A[s]) cudaFree(ctx->tc_A[s]);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_pinned_d) cudaFreeHost(ctx->h_pinned_d);
@@ -565,14 +565,13 @@ sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *m, const float *u, const
     SEM_TRY(check_ptr(ctx, Q, "sem_qcriterion", "Q"));
     if (Q == u || Q == v || Q == w) return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion: Q aliases an input");
     if (prec == SEM_FP32) return qcrit_launch(ctx, m, u, v, w, Q);
-    if (prec == SEM_BF16 || prec == SEM_FP16 || prec == SEM_BF16X2) {
+    if (prec == SEM_BF16 || prec == SEM_FP16 || prec == SEM_BF16X2 || prec == SEM_TF32) {
         double xi[SEM_MAX_ORDER + 1], D[(SEM_MAX_ORDER + 1) * (SEM_MAX_ORDER + 1)];
         gll_nodes(m->N, xi);
         gll_dmat(m->N, xi, D);
         return qcrit_tc_launch(ctx, m, u, v, w, Q, prec, D);
     }
-    return sem_fail(ctx, prec == SEM_TF32 ? SEM_ERR_UNSUPPORTED : SEM_ERR_ARG,
-                    "sem_qcriterion: precision %d not available", (int)prec);
+    return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion: precision %d not available", (int)prec);
 }
 
 sem_status sem_qcriterion_batch(sem_ctx *ctx, int n, const sem_mesh *const *meshes, const float *const *u,

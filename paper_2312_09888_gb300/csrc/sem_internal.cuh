@@ -28,7 +28,7 @@ struct sem_ctx {
     // the render key buffer must read "empty" (all ones) at the start of a frame
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
-    void *tc_A[2] = {nullptr, nullptr};
+    void *tc_A[3] = {nullptr, nullptr, nullptr};  // tensor-core D tables: bf16, fp16, tf32
     // autotuner: tile shape chosen per (M, N, K, epilogue) of the tensor-core GEMM
     bool autotune = true;
     struct GemmTune {

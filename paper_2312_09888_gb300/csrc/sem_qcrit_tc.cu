@@ -1,5 +1,5 @@
 // sem_qcrit_tc.cu -- Q-criterion with the s- and t-contractions on the tensor cores (tcgen05),
-// in BF16, FP16 or split BF16 (hi + lo), FP32 accumulation; N = 7 elements.
+// in BF16, FP16, split BF16 (hi + lo) or TF32, FP32 accumulation; N = 7 elements.
 //
 // For one element component U (64 node rows (k, j) x 8 columns i) the two contractions are
 //   S[(k,j), i] = sum_m D[j][m] U[(k,m), i],   T[(k,j), i] = sum_m D[k][m] U[(m,j), i],
@@ -8,8 +8,11 @@
 // A = [I8(x)D ; D(x)I8 ; I8(x)D] read from row 64 puts S and T in every TMEM lane quarter, so all
 // eight warps find S and T of their node lines in their own lanes and run the Q epilogue; the
 // r-contraction (K = 8) stays on FP32 FFMA from the FP32 copy of the element in shared memory.
-// The element data is staged by the TMA engine (cp.async.bulk), converted to the 16-bit type and
-// transposed into the K-major 128-byte-swizzled operand layout by the CUDA cores.
+// The element data is staged by the TMA engine (cp.async.bulk), converted to the operand type and
+// transposed into the K-major 128-byte-swizzled operand layout by the CUDA cores.  A 16-bit row
+// of K = 64 fills one 128-byte swizzle atom; a TF32 row fills two, stored as two K blocks (K 0-31
+// and 32-63) each laid out like the 16-bit tile, and an MMA (32 bytes of K: 16 16-bit or 8 TF32
+// values) never crosses from one block into the other.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -28,19 +31,23 @@ constexpr int NS = 3 * NE;            // element components (slots) per tile
 constexpr int NCOL = 8 * NS;          // MMA N = 96
 constexpr int SLOT_F = 520;           // floats per staged slot (512 + 8 padding: conflict-free transpose)
 constexpr int A_ROWS = 192;           // [I(x)D ; D(x)I ; I(x)D]
-constexpr int A_BYTES = A_ROWS * 128;
-constexpr int B_BYTES = NS * 1024;     // NCOL rows x 128 B
 constexpr int STAGE_BYTES = NS * SLOT_F * 4;
+// operand arithmetic of the s- and t-contractions
+constexpr int P_FP16 = 0, P_BF16 = 1, P_BF16X2 = 2, P_TF32 = 3;
 constexpr int TMEM_COLS = 512;
 // warp roles: 0-7 epilogue (warp w reads TMEM lane quarter w % 4), 8-11 convert, 12 TMA, 13 MMA
 constexpr int EPI_WARPS = 8, CVT_WARPS = 4;
 constexpr int TMA_WARP = EPI_WARPS + CVT_WARPS, MMA_WARP = TMA_WARP + 1;
 constexpr int THREADS = 32 * (MMA_WARP + 1);
 
-template <bool SPLIT>
+template <int PREC>
 struct Smem {
+    static constexpr bool SPLIT = PREC == P_BF16X2, TF32 = PREC == P_TF32;
+    static constexpr int KB = TF32 ? 2 : 1;               // K blocks of 128-byte rows
+    static constexpr int A_BYTES = KB * A_ROWS * 128;
+    static constexpr int B_BYTES = KB * NCOL * 128;
     static constexpr int NA = SPLIT ? 2 : 1;
-    static constexpr int NSTAGE = SPLIT ? 4 : 5;  // TMA ring of FP32 element tiles
+    static constexpr int NSTAGE = (SPLIT || TF32) ? 4 : 5;  // TMA ring of FP32 element tiles
     static constexpr int A_OFF = 0;
     static constexpr int B_OFF = A_OFF + NA * A_BYTES;                 // 2 buffers x NA
     static constexpr int ST_OFF = B_OFF + 2 * NA * B_BYTES;
@@ -71,6 +78,15 @@ __device__ __forceinline__ float round16(float a)
 {
     if constexpr (BF16) return __bfloat162float(__float2bfloat16_rn(a));
     else return __half2float(__float2half_rn(a));
+}
+
+// FP32 -> TF32 (10 explicit mantissa bits), round to nearest with ties away from zero, in a
+// 32-bit container whose low 13 bits are zero
+__device__ __forceinline__ uint32_t to_tf32(float a)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(a));
+    return r;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
@@ -104,14 +120,16 @@ __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool pred)
 //   MMA issuer (warp 13, lane 0): 2 x 4 MMAs (x3 products when split) into a free TMEM set;
 //   epilogue (warps 0-7): S and T from TMEM, r by FFMA from the stage, Q, 16-byte stores.
 // Every hand-off is an mbarrier; every wait is bounded and raises the error flag on expiry.
-template <bool BF16, bool SPLIT>
+template <int PREC>
 __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict__ f0, const float *__restrict__ f1,
                                                          const float *__restrict__ f2, float *__restrict__ Q,
                                                          const float4 *__restrict__ gfac, int64_t E,
                                                          const uint8_t *__restrict__ A_glob, int *err)
 {
-    using L = Smem<SPLIT>;
+    using L = Smem<PREC>;
     constexpr int NSTAGE = L::NSTAGE;
+    constexpr bool SPLIT = L::SPLIT, TF32 = L::TF32, BF16 = PREC == P_BF16 || PREC == P_BF16X2;
+    constexpr int A_BYTES = L::A_BYTES, B_BYTES = L::B_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
@@ -174,7 +192,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issuer: one thread
         if (lane == 0) {
-            constexpr uint32_t IDESC = tc::idesc_f16(128, NCOL, BF16);
+            constexpr uint32_t IDESC = TF32 ? tc::idesc_tf32(128, NCOL) : tc::idesc_f16(128, NCOL, BF16);
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
             if (!mbar_wait_bounded(abar, 0, err)) *s_abort = 1;
             int it_m = 0;
@@ -188,16 +206,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
                 const uint32_t bb0 = b0 + b * L::NA * B_BYTES;
                 for (int half = 0; half < 2; ++half) {
                     const uint32_t d = tmem + t * 2 * NCOL + half * NCOL;
-                    const uint32_t aoff = half * 64 * 128;
+                    const uint32_t aoff = half * 64 * 128;  // A rows 64.. within each K block
                     int acc = 0;
                     const int nterm = SPLIT ? 3 : 1;
                     for (int term = 0; term < nterm; ++term) {
                         // split: hi*hi, hi*lo (B lo), lo*hi (A lo)
                         const uint32_t aa = a0 + aoff + (term == 2 ? A_BYTES : 0);
                         const uint32_t bb = bb0 + (term == 1 ? B_BYTES : 0);
-                        for (int kk = 0; kk < 4; ++kk) {
-                            tc::mma_f16(d, tc::desc_k_sw128(aa + kk * 32), tc::desc_k_sw128(bb + kk * 32), IDESC,
-                                        acc);
+                        // 32 bytes of K per MMA; K block kk / 4 of the operands
+                        for (int kk = 0; kk < 4 * L::KB; ++kk) {
+                            const uint32_t ka = (kk >> 2) * (A_ROWS * 128) + (kk & 3) * 32;
+                            const uint32_t kb = (kk >> 2) * (NCOL * 128) + (kk & 3) * 32;
+                            if constexpr (TF32)
+                                tc::mma_tf32(d, tc::desc_k_sw128(aa + ka), tc::desc_k_sw128(bb + kb), IDESC, acc);
+                            else
+                                tc::mma_f16(d, tc::desc_k_sw128(aa + ka), tc::desc_k_sw128(bb + kb), IDESC, acc);
                             acc = 1;
                         }
                     }
@@ -231,6 +254,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
                     float v[8];
 #pragma unroll
                     for (int t = 0; t < 8; ++t) v[t] = live ? col[(kc * 8 + t) * 8] : 0.f;
+                    if constexpr (TF32) {
+                        // K = 8 kc + t: block kc / 4, 16-byte chunks 2 (kc % 4) and 2 (kc % 4) + 1
+                        uint8_t *rb = rowB + (kc >> 2) * (NCOL * 128);
+                        const int c0 = 2 * (kc & 3);
+                        *reinterpret_cast<uint4 *>(rb + ((c0 ^ i) * 16)) =
+                            make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+                        *reinterpret_cast<uint4 *>(rb + (((c0 + 1) ^ i) * 16)) =
+                            make_uint4(to_tf32(v[4]), to_tf32(v[5]), to_tf32(v[6]), to_tf32(v[7]));
+                        continue;
+                    }
                     uint4 hi;
                     hi.x = pack2<BF16>(v[0], v[1]);
                     hi.y = pack2<BF16>(v[2], v[3]);
@@ -332,12 +365,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
 
 // ------------------------------------------------------------------------------------------ host
 
-// A stack [I(x)D ; D(x)I ; I(x)D] in the swizzled K-major layout, 16-bit, for N = 7:
-// A_S[(k,j),(k',m)] = d(k,k') D[j][m];  A_T[(k,j),(m,j')] = D[k][m] d(j,j')
-static void build_A(const double *D, bool bf16, std::vector<uint8_t> &out_hi, std::vector<uint8_t> &out_lo)
+// Nearest TF32 (10 explicit mantissa bits, ties to even) of a finite float, in a 32-bit container
+static float host_tf32(float x)
 {
-    out_hi.assign(A_BYTES, 0);
-    out_lo.assign(A_BYTES, 0);
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= ~0x1FFFu;
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+// A stack [I(x)D ; D(x)I ; I(x)D] in the swizzled K-major layout, for N = 7:
+// A_S[(k,j),(k',m)] = d(k,k') D[j][m];  A_T[(k,j),(m,j')] = D[k][m] d(j,j').
+// 16-bit (bf16 or fp16, hi and the lo remainder) or TF32 (two K blocks, out_lo unused).
+static void build_A(const double *D, int prec, std::vector<uint8_t> &out_hi, std::vector<uint8_t> &out_lo)
+{
+    const bool tf32 = prec == P_TF32, bf16 = prec == P_BF16 || prec == P_BF16X2;
+    const size_t bytes = (size_t)(tf32 ? 2 : 1) * A_ROWS * 128;
+    out_hi.assign(bytes, 0);
+    out_lo.assign(bytes, 0);
     for (int r = 0; r < A_ROWS; ++r) {
         const int rr = r % 128, part = (r < 64 || r >= 128) ? 0 : 1;  // 0: S rows, 1: T rows
         const int k = (rr % 64) / 8, j = (rr % 64) % 8;
@@ -346,6 +393,14 @@ static void build_A(const double *D, bool bf16, std::vector<uint8_t> &out_hi, st
             double v = 0.0;
             if (part == 0) v = (a == k) ? D[j * 8 + b] : 0.0;
             else v = (b == j) ? D[k * 8 + a] : 0.0;
+            if (tf32) {
+                const int blk = kc / 32, e = kc % 32;
+                const size_t off = (size_t)blk * A_ROWS * 128 + (size_t)(r / 8) * 1024 + (r % 8) * 128 +
+                                   (((e / 4) ^ (r % 8)) * 16) + (e % 4) * 4;
+                const float t = host_tf32((float)v);
+                memcpy(&out_hi[off], &t, 4);
+                continue;
+            }
             const size_t off = (size_t)(r / 8) * 1024 + (r % 8) * 128 + (((kc / 8) ^ (r % 8)) * 16) + (kc % 8) * 2;
             uint16_t h, l;
             if (bf16) {
@@ -365,12 +420,13 @@ static void build_A(const double *D, bool bf16, std::vector<uint8_t> &out_hi, st
     }
 }
 
-template <bool BF16, bool SPLIT>
+template <int PREC>
 static sem_status launch_tc(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q,
                             const uint8_t *A)
 {
-    using L = Smem<SPLIT>;
-    auto kern = k_sem_q_tc<BF16, SPLIT>;
+    using L = Smem<PREC>;
+    static_assert(L::ALLOC <= 232448, "shared memory per CTA");
+    auto kern = k_sem_q_tc<PREC>;
     SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
     // one CTA per SM: it allocates all 512 TMEM columns (two accumulator sets)
     const int64_t ntiles = (m->E + NE - 1) / NE;
@@ -385,11 +441,12 @@ sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, cons
 {
     if (m->N != 7)
         return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "tensor-core precisions are built for N = 7 only (N=%d)", m->N);
-    const bool bf16 = prec != SEM_FP16;
-    const int slot = bf16 ? 0 : 1;
+    // operand tables: 0 bf16 (hi + lo), 1 fp16 (hi + lo), 2 tf32
+    const int slot = prec == SEM_FP16 ? 1 : (prec == SEM_TF32 ? 2 : 0);
+    const int tprec = slot == 0 ? P_BF16 : (slot == 1 ? P_FP16 : P_TF32);
     if (!ctx->tc_A[slot]) {
         std::vector<uint8_t> hi, lo;
-        build_A(D64, bf16, hi, lo);
+        build_A(D64, tprec, hi, lo);
         std::vector<uint8_t> both(hi);
         both.insert(both.end(), lo.begin(), lo.end());
         void *d = nullptr;
@@ -403,9 +460,10 @@ sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, cons
     }
     const uint8_t *A = static_cast<const uint8_t *>(ctx->tc_A[slot]);
     switch (prec) {
-    case SEM_BF16: return launch_tc<true, false>(ctx, m, u, v, w, Q, A);
-    case SEM_FP16: return launch_tc<false, false>(ctx, m, u, v, w, Q, A);
-    case SEM_BF16X2: return launch_tc<true, true>(ctx, m, u, v, w, Q, A);
+    case SEM_BF16: return launch_tc<P_BF16>(ctx, m, u, v, w, Q, A);
+    case SEM_FP16: return launch_tc<P_FP16>(ctx, m, u, v, w, Q, A);
+    case SEM_BF16X2: return launch_tc<P_BF16X2>(ctx, m, u, v, w, Q, A);
+    case SEM_TF32: return launch_tc<P_TF32>(ctx, m, u, v, w, Q, A);
     default: return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "precision %d has no tensor-core kernel", (int)prec);
     }
 }

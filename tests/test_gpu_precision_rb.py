@@ -1,7 +1,8 @@
 """The precision workload at full size: 64^3 = 262144 elements of order 7 (134M nodes), a
 Rayleigh-Benard-like field (convection rolls + 64 seeded modes, amplitude 0.1) with velocity
 and temperature (2.15 GB of FP32), Q at every arithmetic of sem_qcriterion against the FP64
-oracle on sampled elements (per-node bounds from the arithmetic, errors printed per result),
+oracle on sampled elements (per-node bounds from the arithmetic, errors printed per result: FP32, BF16,
+FP16, split BF16, TF32),
 the temperature isosurface T = 0.5 next to the Q isosurface (cases bit-exact on sampled
 elements) and one 3840x2160 frame holding both fields' surfaces."""
 import numpy as np
@@ -13,8 +14,8 @@ from _helpers import box_factors, grad_bounds, grad_bounds_prec, host64, q_bound
 
 pytestmark = pytest.mark.gpu
 
-EPS = {"BF16": 2.0 ** -9, "FP16": 2.0 ** -11, "BF16X2": 4.0 * 2.0 ** -17}
-ABS = {"BF16": 0.0, "FP16": 2.0 ** -25, "BF16X2": 0.0}
+EPS = {"BF16": 2.0 ** -9, "FP16": 2.0 ** -11, "BF16X2": 4.0 * 2.0 ** -17, "TF32": 2.0 ** -11}
+ABS = {"BF16": 0.0, "FP16": 2.0 ** -25, "BF16X2": 0.0, "TF32": 0.0}
 
 
 @pytest.fixture(scope="module")
@@ -42,7 +43,7 @@ def test_q_every_precision_full_size_sampled(gpu, sess, orc, rb):
     D, g = orc.dmat(7), box_factors(xs)
     Q = torch.empty_like(f[0])
     report = {}
-    for name in ("FP32", "BF16", "FP16", "BF16X2"):
+    for name in ("FP32", "BF16", "FP16", "BF16X2", "TF32"):
         Q.fill_(float("nan"))
         S.sem_qcriterion(sess.ctx, m, f[0], f[1], f[2], Q, getattr(S, "SEM_" + name))
         S.sem_synchronize(sess.ctx)
@@ -66,7 +67,7 @@ def test_q_every_precision_full_size_sampled(gpu, sess, orc, rb):
     drel = derr.max() / np.abs(J[0]).max()
     print("\n64^3 precision workload, sampled elements:", f"du/dx_j FP32 {drel:.3e};",
           "; ".join(f"Q {k} {v:.3e}" for k, v in report.items()), "(max error / max |Q_fp64|)")
-    assert report["FP32"] < report["BF16X2"] < report["BF16"] and report["FP16"] < report["BF16"]
+    assert report["FP32"] < report["BF16X2"] < report["TF32"] < report["BF16"] and report["FP16"] < report["BF16"]
 
 
 def test_temperature_and_q_isosurfaces_and_one_frame(gpu, sess, orc, rb):

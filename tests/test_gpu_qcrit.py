@@ -134,9 +134,6 @@ def test_argument_errors(gpu, sess):
         gpu.sem_qcriterion(sess.ctx, m, u, u, u, u)
     assert ex.value.status == gpu.SEM_ERR_ARG
     with pytest.raises(gpu.SemError) as ex:
-        gpu.sem_qcriterion(sess.ctx, m, u, u, u, Q, gpu.SEM_TF32)
-    assert ex.value.status == gpu.SEM_ERR_UNSUPPORTED
-    with pytest.raises(gpu.SemError) as ex:
         gpu.sem_qcriterion(sess.ctx, m, u, u, u, Q, 17)
     assert ex.value.status == gpu.SEM_ERR_ARG
     with pytest.raises(gpu.SemError) as ex:

@@ -1,9 +1,10 @@
 """Tensor-core precision variants of sem_qcriterion (s- and t-contractions on tcgen05 in BF16,
-FP16 or split BF16 hi+lo; r in FP32) against the FP64 oracle.
+FP16, split BF16 hi+lo or TF32; r in FP32) against the FP64 oracle.
 
 Bound per node: the FP32 bound of the plain path plus the rounding of the element data and of
-D to the 16-bit type on the s/t contractions (unit roundoff 2^-9 BF16, 2^-11 FP16, 2^-17 for
-the hi+lo pair); FP16 subnormals round with absolute error 2^-25.  The measured maximum
+D to the operand type on the s/t contractions (unit roundoff 2^-9 BF16, 2^-11 FP16 and TF32,
+2^-17 for the hi+lo pair); FP16 subnormals round with absolute error 2^-25 (TF32 keeps the
+FP32 exponent range).  The measured maximum
 errors are printed (pytest -s) per precision.
 """
 import numpy as np
@@ -15,13 +16,13 @@ from _helpers import box_factors, dev32, grad_bounds_prec, host64, q_bound
 
 pytestmark = pytest.mark.gpu
 
-EPS = {"BF16": 2.0 ** -9, "FP16": 2.0 ** -11, "BF16X2": 4.0 * 2.0 ** -17}
+EPS = {"BF16": 2.0 ** -9, "FP16": 2.0 ** -11, "BF16X2": 4.0 * 2.0 ** -17, "TF32": 2.0 ** -11}
 # FP16 subnormals (|x| < 2^-14, e.g. the velocity near a no-slip wall) round with absolute error
-ABS = {"BF16": 0.0, "FP16": 2.0 ** -25, "BF16X2": 0.0}
+ABS = {"BF16": 0.0, "FP16": 2.0 ** -25, "BF16X2": 0.0, "TF32": 0.0}
 
 
 def _prec(S, name):
-    return {"BF16": S.SEM_BF16, "FP16": S.SEM_FP16, "BF16X2": S.SEM_BF16X2}[name]
+    return {"BF16": S.SEM_BF16, "FP16": S.SEM_FP16, "BF16X2": S.SEM_BF16X2, "TF32": S.SEM_TF32}[name]
 
 
 def _check(S, sess, orc, xyz, uvw64, name, sample=None):
@@ -47,13 +48,13 @@ def _check(S, sess, orc, xyz, uvw64, name, sample=None):
     return rel
 
 
-@pytest.mark.parametrize("name", ["BF16", "FP16", "BF16X2"])
+@pytest.mark.parametrize("name", ["BF16", "FP16", "BF16X2", "TF32"])
 def test_tc_taylor_green_box(gpu, sess, orc, name):
     w = si.tgv_box()
     _check(gpu, sess, orc, w.mesh.xyz().numpy(), w.fields.numpy(), name)
 
 
-@pytest.mark.parametrize("name", ["BF16", "BF16X2"])
+@pytest.mark.parametrize("name", ["BF16", "BF16X2", "TF32"])
 @pytest.mark.parametrize("E", [1, 3, 4, 5, 9, 37])
 def test_tc_ragged_counts(gpu, sess, orc, name, E):
     mesh = si.stretched_box((E, 1, 1), 7, seed=E)
@@ -61,7 +62,7 @@ def test_tc_ragged_counts(gpu, sess, orc, name, E):
     _check(gpu, sess, orc, mesh.xyz().numpy(), uvw, name)
 
 
-@pytest.mark.parametrize("name", ["BF16", "FP16", "BF16X2"])
+@pytest.mark.parametrize("name", ["BF16", "FP16", "BF16X2", "TF32"])
 def test_tc_channel_full_size_sampled(gpu, sess, orc, name):
     w = si.channel(device="cuda")
     xyz = w.mesh.xyz("cuda").cpu().numpy()
@@ -78,10 +79,21 @@ def test_tc_split_is_more_accurate_than_single(gpu, sess, orc):
     assert split < single / 20
 
 
-def test_tc_rejects_other_orders(gpu, sess):
+def test_tc_tf32_between_bf16_and_split(gpu, sess, orc):
+    """TF32 operands (11 significant bits) against BF16 (8) and the hi+lo pair (16)."""
+    w = si.tgv_box()
+    xyz, f = w.mesh.xyz().numpy(), w.fields.numpy()
+    single = _check(gpu, sess, orc, xyz, f, "BF16")
+    tf32 = _check(gpu, sess, orc, xyz, f, "TF32")
+    split = _check(gpu, sess, orc, xyz, f, "BF16X2")
+    assert split < tf32 < single / 4
+
+
+@pytest.mark.parametrize("prec", ["SEM_BF16", "SEM_TF32"])
+def test_tc_rejects_other_orders(gpu, sess, prec):
     mesh = si.uniform_box((2, 2, 2), (0, 0, 0), (1, 1, 1), 5)
     m = sess.mesh(5, mesh.xyz().numpy())
     t = torch.zeros(8 * 216, device="cuda")
     with pytest.raises(gpu.SemError) as ex:
-        gpu.sem_qcriterion(sess.ctx, m, t, t.clone(), t.clone(), torch.zeros_like(t), gpu.SEM_BF16)
+        gpu.sem_qcriterion(sess.ctx, m, t, t.clone(), t.clone(), torch.zeros_like(t), getattr(gpu, prec))
     assert ex.value.status == gpu.SEM_ERR_UNSUPPORTED
