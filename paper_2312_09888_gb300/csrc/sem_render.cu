@@ -41,6 +41,8 @@ struct RenderParams {
     float za, zb;        // depth: ortho (zv - znear)*za ; perspective zb*(1 - znear/zv)
     int ortho;
     int W, H;
+    float hw, hh;        // W / 2, H / 2 (viewport: sx = hw (xn + 1), sy = hh (1 - yn))
+    float wmax, hmax;    // W - 1, H - 1
     int nseg;
     int seg_end[16];
     float rgb[16][3];
@@ -54,32 +56,34 @@ __device__ __forceinline__ bool top_left(float ax, float ay, float bx, float by)
 }
 
 // Screen position of one vertex; the NDC depth is finished in setup_tri only for triangles that
-// cover a pixel centre.  Perspective: one reciprocal of the view depth per vertex (__frcp_rn,
-// correctly rounded) instead of three divisions.
-__device__ __forceinline__ bool project(const RenderParams &P, const float *p, float &sx, float &sy, float &zv)
+// cover a pixel centre, from zw: the view depth (orthographic) or its reciprocal (perspective:
+// one __frcp_rn, correctly rounded, per vertex, shared by the position and the depth).
+__device__ __forceinline__ bool project(const RenderParams &P, const float *p, float &sx, float &sy, float &zw)
 {
     const float dx = p[0] - P.eye[0], dy = p[1] - P.eye[1], dz = p[2] - P.eye[2];
     const float xv = P.s[0] * dx + P.s[1] * dy + P.s[2] * dz;
     const float yv = P.u[0] * dx + P.u[1] * dy + P.u[2] * dz;
-    zv = P.f[0] * dx + P.f[1] * dy + P.f[2] * dz;
+    const float zv = P.f[0] * dx + P.f[1] * dy + P.f[2] * dz;
     if (!(zv > P.znear && zv < P.zfar)) return false;
     float xn, yn;
     if (P.ortho) {
         xn = xv * P.ax;
         yn = yv * P.ay;
+        zw = zv;
     } else {
         const float rz = __frcp_rn(zv);
         xn = xv * rz * P.ax;
         yn = yv * rz * P.ay;
+        zw = rz;
     }
-    sx = (xn + 1.f) * 0.5f * (float)P.W;
-    sy = (1.f - yn) * 0.5f * (float)P.H;
+    sx = fmaf(xn, P.hw, P.hw);
+    sy = fmaf(-yn, P.hh, P.hh);
     return true;
 }
 
-__device__ __forceinline__ float ndc_depth(const RenderParams &P, float zv)
+__device__ __forceinline__ float ndc_depth(const RenderParams &P, float zw)
 {
-    return P.ortho ? (zv - P.znear) * P.za : P.zb * (1.f - P.znear * __frcp_rn(zv));
+    return P.ortho ? (zw - P.znear) * P.za : P.zb * (1.f - P.znear * zw);
 }
 
 // Screen-space setup of one triangle; false if it is dropped or contains no pixel centre.
@@ -87,8 +91,14 @@ struct Setup {
     float x[3], y[3], z[3];
     float inv_area;
     int px0, px1, py0, py1;
-    bool tl0, tl1, tl2;
 };
+
+// top-left fill-rule flags of the three edges (v0 v1, v1 v2, v2 v0), one bit each
+__device__ __forceinline__ int tl_flags(const Setup &S)
+{
+    return (top_left(S.x[0], S.y[0], S.x[1], S.y[1]) ? 1 : 0) | (top_left(S.x[1], S.y[1], S.x[2], S.y[2]) ? 2 : 0) |
+           (top_left(S.x[2], S.y[2], S.x[0], S.y[0]) ? 4 : 0);
+}
 
 __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__restrict__ p, Setup &S)
 {
@@ -100,8 +110,8 @@ __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__
     // small triangles contain none and stop here
     const float mnx = fminf(S.x[0], fminf(S.x[1], S.x[2])), mxx = fmaxf(S.x[0], fmaxf(S.x[1], S.x[2]));
     const float mny = fminf(S.y[0], fminf(S.y[1], S.y[2])), mxy = fmaxf(S.y[0], fmaxf(S.y[1], S.y[2]));
-    const float fx0 = fmaxf(0.f, ceilf(mnx - 0.5f)), fx1 = fminf((float)(P.W - 1), floorf(mxx - 0.5f));
-    const float fy0 = fmaxf(0.f, ceilf(mny - 0.5f)), fy1 = fminf((float)(P.H - 1), floorf(mxy - 0.5f));
+    const float fx0 = fmaxf(0.f, ceilf(mnx - 0.5f)), fx1 = fminf(P.wmax, floorf(mxx - 0.5f));
+    const float fy0 = fmaxf(0.f, ceilf(mny - 0.5f)), fy1 = fminf(P.hmax, floorf(mxy - 0.5f));
     if (!(fx0 <= fx1 && fy0 <= fy1)) return false;
     float area = (S.x[1] - S.x[0]) * (S.y[2] - S.y[0]) - (S.x[2] - S.x[0]) * (S.y[1] - S.y[0]);
     if (!(area != 0.f) || isnan(area)) return false;
@@ -119,21 +129,18 @@ __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__
     S.py0 = (int)fy0;
     S.py1 = (int)fy1;
     S.inv_area = 1.f / area;
-    S.tl0 = top_left(S.x[0], S.y[0], S.x[1], S.y[1]);
-    S.tl1 = top_left(S.x[1], S.y[1], S.x[2], S.y[2]);
-    S.tl2 = top_left(S.x[2], S.y[2], S.x[0], S.y[0]);
     return true;
 }
 
-__device__ __forceinline__ void shade_pixel(const Setup &S, int px, int py, int W, unsigned t,
+__device__ __forceinline__ void shade_pixel(const Setup &S, int tl, int px, int py, int W, unsigned t,
                                             unsigned long long *__restrict__ keys)
 {
     const float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
     const float e0 = (S.x[1] - S.x[0]) * (cy - S.y[0]) - (S.y[1] - S.y[0]) * (cx - S.x[0]);
     const float e1 = (S.x[2] - S.x[1]) * (cy - S.y[1]) - (S.y[2] - S.y[1]) * (cx - S.x[1]);
     const float e2 = (S.x[0] - S.x[2]) * (cy - S.y[2]) - (S.y[0] - S.y[2]) * (cx - S.x[2]);
-    const bool in = (e0 > 0.f || (e0 == 0.f && S.tl0)) && (e1 > 0.f || (e1 == 0.f && S.tl1)) &&
-                    (e2 > 0.f || (e2 == 0.f && S.tl2));
+    const bool in = (e0 > 0.f || (e0 == 0.f && (tl & 1))) && (e1 > 0.f || (e1 == 0.f && (tl & 2))) &&
+                    (e2 > 0.f || (e2 == 0.f && (tl & 4)));
     if (!in) return;
     float z = (e1 * S.z[0] + e2 * S.z[1] + e0 * S.z[2]) * S.inv_area;
     z = fminf(fmaxf(z, 0.f), 1.f);
@@ -181,7 +188,9 @@ __device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, i
                                 fabsf(dzdx) + fabsf(dzdy));
     if (!(reach <= 3.0e38f)) return false;
     const int nx = S.px1 - S.px0 + 1;
-    const int tl = (S.tl0 ? 1 : 0) | (S.tl1 ? 0x100 : 0) | (S.tl2 ? 0x10000 : 0);
+    // top-left: dy < 0, or dy == 0 and dx > 0, with dy = -A_i and dx = B_i of edge i (exact)
+    const int tl = ((A0 > 0.f || (A0 == 0.f && B0 > 0.f)) ? 1 : 0) | ((A1 > 0.f || (A1 == 0.f && B1 > 0.f)) ? 0x100 : 0) |
+                   ((A2 > 0.f || (A2 == 0.f && B2 > 0.f)) ? 0x10000 : 0);
     // ceil(1024 / nx): 1024/nx is an integer or at least 1/32 above one, far beyond the
     // approximate quotient's error
     const int mul = (int)(__fdividef(1024.f, (float)nx) - 0.00390625f) + 1;
@@ -194,33 +203,41 @@ __device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, i
 
 // Flat headlight shade of triangle t (colour of its segment times 0.15 + 0.85 |n.l|, l the view
 // direction), packed as RGBA8 with alpha 255.
-__device__ __forceinline__ uint32_t shade_rgba(const RenderParams &P, const float *__restrict__ p, int t)
+__device__ __forceinline__ uint32_t shade_rgba(const RenderParams &P, const float *__restrict__ p, int sg)
 {
     const float ax = p[3] - p[0], ay = p[4] - p[1], az = p[5] - p[2];
     const float bx = p[6] - p[0], by = p[7] - p[1], bz = p[8] - p[2];
     const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
     const float n2 = nx * nx + ny * ny + nz * nz;
     const float shade = n2 > 0.f ? 0.15f + 0.85f * fabsf(nx * P.f[0] + ny * P.f[1] + nz * P.f[2]) * rsqrtf(n2) : 0.15f;
-    int sg = 0;
-    if (P.seg_dev) {
-        while (sg < P.nseg - 1 && (int64_t)t >= __ldg(P.seg_dev + sg + 1)) ++sg;
-    } else {
-        while (sg < P.nseg - 1 && t >= P.seg_end[sg]) ++sg;
-    }
     uint32_t c = 0xff000000u;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float v = fminf(fmaxf(P.rgb[sg][k] * shade, 0.f), 1.f);
-        c |= (uint32_t)(unsigned char)floorf(v * 255.f + 0.5f) << (8 * k);
+        // floor(v 255 + .5) of v = clamp(rgb shade, 0, 1): a value in [.5, 255.5]
+        const float v = __saturatef(P.rgb[sg][k] * shade);
+        c |= __float2uint_rd(fmaf(v, 255.f, 0.5f)) << (8 * k);
     }
     return c;
 }
 
+// start of segment k (k <= nseg): device table (asynchronous render) or the parameter ends
+__device__ __forceinline__ int64_t seg_start(const RenderParams &P, int k)
+{
+    if (P.seg_dev) return __ldg(P.seg_dev + k);
+    return k == 0 ? 0 : (int64_t)P.seg_end[k - 1];
+}
+
+// segment of triangle t, searched upwards from segment sg
+__device__ __forceinline__ int seg_of(const RenderParams &P, int64_t t, int sg)
+{
+    while (sg < P.nseg - 1 && t >= seg_start(P, sg + 1)) ++sg;
+    return sg;
+}
+
 // One thread per triangle for the setup (its 36 bytes staged through shared memory with
 // coalesced loads); then each warp spreads the pixel-centre tests of its 32 triangles evenly
-// over its lanes, so a lane never idles while a neighbour walks a bigger box.  Each lane
-// writes its own lane number over its candidates' slots of a per-warp owner map, so a pixel
-// test finds its triangle with one shared-memory byte load.
+// over its lanes, so a lane never idles while a neighbour walks a bigger box; a pixel test
+// finds its triangle from one warp OR of the list starts in its round and a rank -> lane table.
 __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
                                                       const __grid_constant__ RenderParams P,
                                                       unsigned long long *__restrict__ keys,
@@ -229,7 +246,9 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
 {
     __shared__ __align__(16) float s_tri[256 * 9];
     __shared__ SmallRecs s_rec;
-    __shared__ __align__(16) uint8_t s_own[8][32 * SMALL_PX];
+    __shared__ uint8_t s_lane_of[8][32];
+    __shared__ int s_sg0;        // segment of the block's first triangle
+    __shared__ int64_t s_next;   // start of the segment after it
     if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
     const int t0 = blockIdx.x * 256;
     // blocks past the (device-clamped) triangle count have no work; the whole block leaves
@@ -246,6 +265,11 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     } else {
         for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = __ldcs(src + q);
     }
+    if (threadIdx.x == 0) {
+        const int sg = seg_of(P, t0, 0);
+        s_sg0 = sg;
+        s_next = sg < P.nseg - 1 ? seg_start(P, sg + 1) : INT64_MAX;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
@@ -255,7 +279,8 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
             // only triangles that cover a pixel centre can win a pixel: their colour, once
-            colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, t);
+            const int sg = t < s_next ? s_sg0 : seg_of(P, t, s_sg0);
+            colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, sg);
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
                 if (store_rec(s_rec, threadIdx.x, S, P.W)) npx = nx * ny;
@@ -282,24 +307,26 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int wbase = threadIdx.x & ~31;
     const int excl = incl - npx;
-    uint8_t *own = s_own[threadIdx.x >> 5];
-    {
-        // the lane's byte over its candidates' slots: single bytes up to a word boundary, then
-        // whole words, then the tail
-        int q = excl;
-        const int end = excl + npx;
-        for (; q < end && (q & 3); ++q) own[q] = (uint8_t)lane;
-        for (; q + 4 <= end; q += 4) *reinterpret_cast<uint32_t *>(own + q) = (uint32_t)lane * 0x01010101u;
-        for (; q < end; ++q) own[q] = (uint8_t)lane;
-    }
+    // owners: the lanes with candidates, in lane order; their lists start at excl, increasing.
+    // Owner rank -> lane in a 32-byte table.
+    const unsigned owners = __ballot_sync(0xffffffffu, npx > 0);
+    uint8_t *lane_of = s_lane_of[threadIdx.x >> 5];
+    if (npx > 0) lane_of[__popc(owners & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
-    // each round: lane `lane` takes candidate r + lane of the warp's list.  Branch-free up to
-    // the atomic: past the list's end the owner byte is clamped to the row and masked to a
-    // lane, and the candidate is switched off in the coverage predicate.
+    // each round: lane `lane` takes candidate r + lane of the warp's list.  The owners whose
+    // lists start in [r, r + 32) set one bit each (warp OR); the candidate's owner has rank
+    // (starts before r) + (starts at or below it in the window) - 1.  Branch-free up to the
+    // atomic: past the list's end the rank is the last owner's, and the candidate is switched
+    // off in the coverage predicate.
     const int W = P.W;
+    int before = 0;
     for (int r = 0; r < total; r += 32) {
         const int idx = r + lane;
-        const int L = own[min(idx, 32 * SMALL_PX - 1)] & 31;
+        const unsigned starts =
+            __reduce_or_sync(0xffffffffu, (npx > 0 && (unsigned)(excl - r) < 32u) ? 1u << (excl - r) : 0u);
+        const int rank = before + __popc(starts & ((2u << lane) - 1u)) - 1;
+        before += __popc(starts);
+        const int L = lane_of[rank & 31];
         const int first = __shfl_sync(0xffffffffu, excl, L);
         const int i = wbase + L;
         const float4 a = s_rec.a[i], b = s_rec.b[i], c = s_rec.c[i];
@@ -333,10 +360,11 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_raster_large(const float *__r
         const int t = large[q];
         Setup S;
         if (!setup_tri(P, tris + (int64_t)t * 9, S)) continue;
+        const int tl = tl_flags(S);
         const int nx = S.px1 - S.px0 + 1;
         const int64_t npx = (int64_t)nx * (S.py1 - S.py0 + 1);
         for (int64_t k = lane; k < npx; k += 32)
-            shade_pixel(S, S.px0 + (int)(k % nx), S.py0 + (int)(k / nx), P.W, (unsigned)t, keys);
+            shade_pixel(S, tl, S.px0 + (int)(k % nx), S.py0 + (int)(k / nx), P.W, (unsigned)t, keys);
     }
 }
 
@@ -447,6 +475,10 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     P.zfar = cam->zfar;
     P.W = W;
     P.H = H;
+    P.hw = 0.5f * (float)W;
+    P.hh = 0.5f * (float)H;
+    P.wmax = (float)(W - 1);
+    P.hmax = (float)(H - 1);
     P.nseg = nseg;
     P.seg_dev = seg_start_dev;
     int64_t acc = 0;
