@@ -98,6 +98,48 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t *__re
     if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = bsum[nb];
 }
 
+// One launch for up to SCAN_SELF_MAX_TILES tiles: block b sums the counts of the tiles before
+// its own by itself (16-byte loads of at most (SCAN_SELF_MAX_TILES - 1) * 16 KB, just written by
+// the producer and still in L2), then scans its tile -- no tile-sum pass, no inter-block wait.
+#define SCAN_SELF_MAX_TILES 32
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_self(const int32_t *__restrict__ in, int64_t n, int64_t nb,
+                                                            int64_t *__restrict__ out)
+{
+    __shared__ int64_t s_w[33];
+    // counts before this tile: b * SCAN_TILE of them, a multiple of 4 (in is 16-byte aligned)
+    const int4 *in4 = reinterpret_cast<const int4 *>(in);
+    // (SCAN_TILE / 4) / SCAN_THREADS = 1 vector per thread and tile: eight tiles' loads in flight
+    static_assert(SCAN_TILE / 4 == SCAN_THREADS, "one 16-byte load per thread and tile");
+    int64_t pre = 0;
+    const int nbefore = (int)blockIdx.x;
+    for (int t0 = 0; t0 < nbefore; t0 += 8) {
+        int4 c[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            c[k] = t0 + k < nbefore ? in4[(int64_t)(t0 + k) * SCAN_THREADS + threadIdx.x] : make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) pre += (int64_t)c[k].x + c[k].y + c[k].z + c[k].w;
+    }
+    int64_t before;
+    block_excl_scan(pre, s_w, before);
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int64_t x[SCAN_ITEMS];
+    int64_t v = 0;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        x[q] = base + q < n ? in[base + q] : 0;
+        v += x[q];
+    }
+    int64_t tot;
+    int64_t run = block_excl_scan(v, s_w, tot) + before;
+#pragma unroll
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        if (base + q < n) out[base + q] = run;
+        run += x[q];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = before + tot;
+}
+
 // One block for small inputs: thread t scans its contiguous chunk of ceil(n / 1024) entries
 // (sum, block-wide scan of the sums, then the chunk's offsets), so the whole scan is a single
 // launch; used up to SCAN_SINGLE_MAX entries (8 per thread: beyond that one SM's serial chunks
@@ -131,6 +173,10 @@ sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n
         return sem_cuda(ctx, cudaGetLastError(), "scan launch");
     }
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb <= SCAN_SELF_MAX_TILES && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
+        SEM_TRACED(ctx, "k_scan_self", k_scan_self<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, nb, out));
+        return sem_cuda(ctx, cudaGetLastError(), "scan launch");
+    }
     int64_t *bsum = reinterpret_cast<int64_t *>(tmp);
     SEM_TRACED(ctx, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum));
     SEM_TRACED(ctx, "k_scan_blocks", k_scan_blocks<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb));

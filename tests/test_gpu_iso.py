@@ -192,9 +192,36 @@ def test_channel_full_size_sampled(gpu, sess, orc):
         assert np.abs(got - ref["tris"]).max() <= 1e-5 * 2 * math.pi
 
 
+@pytest.mark.parametrize("shape", [(64, 32, 32), (65537, 1, 1)])
+def test_scan_at_the_one_launch_limit(gpu, sess, orc, shape):
+    """2 isovalues x 65536 elements = 131072 counts (32 tiles of 4096: the one-launch scan, each
+    block summing the tiles before its own) and x 65537 = 131074 counts (33 tiles: the
+    three-kernel scan); counts and the triangles' elements against the oracle.  Per-node
+    random values, so nearly every element holds triangles."""
+    mesh = si.uniform_box(shape, (0, 0, 0), (1, 1, 1), 1)
+    xyz = mesh.xyz().numpy()
+    f32 = dev32(si.random_nodal(mesh, 1, seed=shape[0])[0].numpy())  # (E, 8)
+    m = sess.mesh(1, xyz)
+    isos = [0.0, 0.5]
+    counts = gpu.sem_isosurface_multi(sess.ctx, m, f32, isos, None)
+    tris = torch.empty(sum(counts) * 9, device="cuda")
+    te = torch.empty(sum(counts), dtype=torch.int32, device="cuda")
+    assert gpu.sem_isosurface_multi(sess.ctx, m, f32, isos, tris, te) == counts
+    torch.cuda.synchronize()
+    f64 = host64(f32)
+    off = 0
+    e_h = te.cpu().numpy()
+    for q, iso in enumerate(isos):
+        ref = orc.isosurface(1, xyz, f64, float(np.float32(iso)), want_tris=False)
+        assert counts[q] == ref["ntri"]
+        np.testing.assert_array_equal(e_h[off:off + counts[q]], np.repeat(np.arange(mesh.E), ref["elem_ntri"]))
+        off += counts[q]
+
+
 def test_many_elements_multi_isovalue_uses_the_multi_block_scan(gpu, sess, orc):
     """64^3 elements of order 1 x 2 isovalues = 524288 counts: the three-kernel scan (the
-    single-block scan takes at most 8192); counts and offsets against the oracle."""
+    single-block scan takes at most 8192, the one-launch tile scan 32 tiles of 4096); counts and
+    offsets against the oracle."""
     mesh = si.uniform_box((64, 64, 64), (0, 0, 0), (1, 1, 1), 1)
     xyz = mesh.xyz().numpy()
     f32 = dev32(si.sphere_field(mesh, (0.5, 0.5, 0.5), 0.3).numpy())
