@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *_
 }
 
 // per-warp dynamic shared memory of the emit kernel: the element's field, a window of the
-// triangle map, the mask of one isovalue, the element's node coordinates and a store staging
-// area; warps per block: up to 8 within ~96 KB
+// triangle map, the mask of one isovalue, the element's node coordinates, a store staging
+// area and the list of cut cells; warps per block: up to 8 within ~96 KB
 #define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
 #define EMIT_CHUNK 4     // (element, isovalue) units a warp takes per atomic
 template <int NP>
@@ -428,7 +428,8 @@ struct EmitW {
     static constexpr int M_BYTES = r16(4 * G::MW);
     static constexpr int X_BYTES = r16(4 * 3 * NP);
     static constexpr int STG_BYTES = 32 * 9 * 4;
-    static constexpr int B = F_BYTES + MAP_BYTES + M_BYTES + X_BYTES + STG_BYTES;
+    static constexpr int LIST_BYTES = r16(4 * G::N3);  // the element's cut cells: cell | case << 16
+    static constexpr int B = F_BYTES + MAP_BYTES + M_BYTES + X_BYTES + STG_BYTES + LIST_BYTES;
     static constexpr int R = 98304 / B;
     static constexpr int V = R < 1 ? 1 : (R > 8 ? 8 : R);
 };
@@ -442,11 +443,13 @@ __device__ __forceinline__ int corner_off(int v)
 
 // Persistent warps over (element, isovalue) units u = q E + e, EMIT_CHUNK units per atomic
 // on a counter the host zeroes before the launch.  For a unit with triangles: load the element
-// and its mask, then per window of EMIT_MAPCAP triangles (1) lane per row pair, find the cut
-// cells, warp-scan their triangle counts and write each triangle's packed (case, cell, index
-// in cell) into the map, in cell order; (2) lane per output triangle: interpolate its three
-// vertices, stage them, and store each round of 32 triangles (1152 contiguous bytes) with
-// coalesced 4-byte stores.
+// and its mask; (1a) lane per row pair, list the cut cells with their cases in cell order (a
+// warp scan of the per-lane counts places each lane's run; N uniform passes over the cells of
+// a row, each cut cell stored at its rank, so no lane walks its cells alone); then per window of
+// EMIT_MAPCAP triangles (1b) lane per listed cell, warp-scan the triangle counts and write each
+// triangle's packed (case, cell, index in cell) into the map, in cell order; (2) lane per
+// output triangle: interpolate its three vertices, stage them, and store each round of 32
+// triangles (1152 contiguous bytes) with coalesced 4-byte stores.
 template <int NP>
 __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
@@ -481,7 +484,8 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
     uint32_t *m = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES + EW::MAP_BYTES);
     float *X = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES);
     float *Y = X + NP, *Z = X + 2 * NP;
-    float *stg = reinterpret_cast<float *>(mine + EW::B - EW::STG_BYTES);
+    float *stg = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES + EW::X_BYTES);
+    uint32_t *list = reinterpret_cast<uint32_t *>(mine + EW::B - EW::LIST_BYTES);
     IsoSet S1;  // the unit's isovalue alone, for load_masks
     S1.niso = 1;
     for (;;) {
@@ -508,23 +512,43 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                 Z[lane] = fmaf(s, H.z, (1.f - s) * L.z);
             }
             __syncwarp();
+            // (1a) the cut cells of the element, in cell order, with their cases
+            int ncells = 0;
+            for (int rp0 = 0; rp0 < G::NRP; rp0 += 32) {
+                const int rp = rp0 + lane;
+                uint32_t act = 0, r00 = 0, r01 = 0, r10 = 0, r11 = 0;
+                if (rp < G::NRP) {
+                    const int j = rp % N, k = rp / N;
+                    r00 = row_bits<NP>(m, k, j);
+                    r01 = row_bits<NP>(m, k, j + 1);
+                    r10 = row_bits<NP>(m, k + 1, j);
+                    r11 = row_bits<NP>(m, k + 1, j + 1);
+                    act = cut_cells<NP>(r00, r01, r10, r11);
+                }
+                const int na = __popc(act);
+                int incl = na;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                    if (lane >= d) incl += y;
+                }
+                const int at = ncells + incl - na;
+#pragma unroll
+                for (int i = 0; i < N; ++i)
+                    if ((act >> i) & 1u)
+                        list[at + __popc(act & ((1u << i) - 1u))] =
+                            (uint32_t)(rp * N + i) | ((uint32_t)pair_case(r00, r01, r10, r11, i) << 16);
+                ncells += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            __syncwarp();
             for (int64_t win = 0; win < n; win += EMIT_MAPCAP) {
-                // (1) the map entries of triangles win .. win + EMIT_MAPCAP - 1, in cell order
+                // (1b) the map entries of triangles win .. win + EMIT_MAPCAP - 1, in cell order
                 int running = 0;
-                for (int rp0 = 0; rp0 < G::NRP && running < win + EMIT_MAPCAP; rp0 += 32) {
-                    const int rp = rp0 + lane;
-                    uint32_t act = 0, r00 = 0, r01 = 0, r10 = 0, r11 = 0;
-                    int nt = 0, j = 0, k = 0;
-                    if (rp < G::NRP) {
-                        j = rp % N;
-                        k = rp / N;
-                        r00 = row_bits<NP>(m, k, j);
-                        r01 = row_bits<NP>(m, k, j + 1);
-                        r10 = row_bits<NP>(m, k + 1, j);
-                        r11 = row_bits<NP>(m, k + 1, j + 1);
-                        act = cut_cells<NP>(r00, r01, r10, r11);
-                        for (uint32_t a = act; a; a &= a - 1u) nt += s_nt[pair_case(r00, r01, r10, r11, __ffs(a) - 1)];
-                    }
+                for (int c0 = 0; c0 < ncells && running < win + EMIT_MAPCAP; c0 += 32) {
+                    const int c = c0 + lane;
+                    const uint32_t ent = c < ncells ? list[c] : 0u;
+                    const int cs = (int)(ent >> 16);
+                    const int nt = c < ncells ? s_nt[cs] : 0;
                     int incl = nt;
 #pragma unroll
                     for (int d = 1; d < 32; d <<= 1) {
@@ -532,12 +556,11 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                         if (lane >= d) incl += y;
                     }
                     int slot = running + incl - nt - (int)win;
-                    for (uint32_t a = act; a; a &= a - 1u) {
-                        const int i = __ffs(a) - 1;
-                        const int cs = pair_case(r00, r01, r10, r11, i);
-                        const uint32_t key = ((uint32_t)cs << 16) | ((uint32_t)k << 12) | ((uint32_t)j << 8) | ((uint32_t)i << 4);
-                        const int nc = s_nt[cs];
-                        for (int t = 0; t < nc; ++t, ++slot)
+                    if (nt > 0) {
+                        const int cell = (int)(ent & 0xFFFFu), i = cell % N, rp = cell / N;
+                        const uint32_t key = ((uint32_t)cs << 16) | ((uint32_t)(rp / N) << 12) |
+                                             ((uint32_t)(rp % N) << 8) | ((uint32_t)i << 4);
+                        for (int t = 0; t < nt; ++t, ++slot)
                             if (slot >= 0 && slot < EMIT_MAPCAP) map[slot] = key | (uint32_t)t;
                     }
                     running += __shfl_sync(0xffffffffu, incl, 31);
