@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *_
 // triangle map, the mask of one isovalue, the element's node coordinates, a store staging
 // area and the list of cut cells; warps per block: up to 8 within ~96 KB
 #define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
-#define EMIT_CHUNK 4     // (element, isovalue) units a warp takes per atomic
+#define EMIT_CHUNK 2     // (element, isovalue) units a warp takes per atomic (swept: 1, 2, 4, 8)
 template <int NP>
 struct EmitW {
     using G = MaskGeo<NP>;
