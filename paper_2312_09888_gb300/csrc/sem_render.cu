@@ -49,12 +49,6 @@ struct RenderParams {
     const int64_t *seg_dev;  // device segment starts [nseg + 1] (asynchronous render), or null
 };
 
-__device__ __forceinline__ bool top_left(float ax, float ay, float bx, float by)
-{
-    const float dx = bx - ax, dy = by - ay;
-    return (dy < 0.f) || (dy == 0.f && dx > 0.f);
-}
-
 // Screen position of one vertex; the NDC depth is finished in setup_tri only for triangles that
 // cover a pixel centre, from zw: the view depth (orthographic) or its reciprocal (perspective:
 // one __frcp_rn, correctly rounded, per vertex, shared by the position and the depth).
@@ -93,13 +87,6 @@ struct Setup {
     int px0, px1, py0, py1;
 };
 
-// top-left fill-rule flags of the three edges (v0 v1, v1 v2, v2 v0), one bit each
-__device__ __forceinline__ int tl_flags(const Setup &S)
-{
-    return (top_left(S.x[0], S.y[0], S.x[1], S.y[1]) ? 1 : 0) | (top_left(S.x[1], S.y[1], S.x[2], S.y[2]) ? 2 : 0) |
-           (top_left(S.x[2], S.y[2], S.x[0], S.y[0]) ? 4 : 0);
-}
-
 __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__restrict__ p, Setup &S)
 {
     float zv0, zv1, zv2;
@@ -132,27 +119,11 @@ __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__
     return true;
 }
 
-__device__ __forceinline__ void shade_pixel(const Setup &S, int tl, int px, int py, int W, unsigned t,
-                                            unsigned long long *__restrict__ keys)
-{
-    const float cx = (float)px + 0.5f, cy = (float)py + 0.5f;
-    const float e0 = (S.x[1] - S.x[0]) * (cy - S.y[0]) - (S.y[1] - S.y[0]) * (cx - S.x[0]);
-    const float e1 = (S.x[2] - S.x[1]) * (cy - S.y[1]) - (S.y[2] - S.y[1]) * (cx - S.x[1]);
-    const float e2 = (S.x[0] - S.x[2]) * (cy - S.y[2]) - (S.y[0] - S.y[2]) * (cx - S.x[2]);
-    const bool in = (e0 > 0.f || (e0 == 0.f && (tl & 1))) && (e1 > 0.f || (e1 == 0.f && (tl & 2))) &&
-                    (e2 > 0.f || (e2 == 0.f && (tl & 4)));
-    if (!in) return;
-    float z = (e1 * S.z[0] + e2 * S.z[1] + e0 * S.z[2]) * S.inv_area;
-    z = fminf(fmaxf(z, 0.f), 1.f);
-    const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | t;
-    atomicMin(&keys[(int64_t)py * W + px], key);
-}
-
 // Compact per-triangle setup kept in shared memory for the warp's pixel work: the three edge
 // functions and the depth as planes over the triangle's box, e(kx, ky) = e(0, 0) + A kx + B ky
 // for candidate (px0 + kx, py0 + ky), so a test is eight FMAs.  The values at the box's first
-// pixel centre are evaluated exactly as shade_pixel does; the increments are the edges'
-// coordinate differences.  Per triangle, in four arrays (a lane's stores are contiguous with
+// pixel centre are the edge functions (x_i+1 - x_i)(cy - y_i) - (y_i+1 - y_i)(cx - x_i) of the
+// edges v0 v1, v1 v2, v2 v0; the increments are the edges' coordinate differences.  Per triangle, in four arrays (a lane's stores are contiguous with
 // its neighbours'):
 //   a: e0 e1 e2 z at (px0 + .5, py0 + .5)   b: de/dx (3), dz/dx   c: de/dy (3), dz/dy
 //   d: pixel index py0 W + px0,  ceil(1024 / nx),  nx,  top-left flags (one per byte)
@@ -172,7 +143,9 @@ struct SmallRecs {
     int4 d[256];
 };
 
-__device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, int W)
+// The planes of triangle S over its box (see above); false if they could overflow within
+// `span` pixels of the box origin.  tl: the top-left flags, one per byte.
+__device__ __forceinline__ bool make_planes(const Setup &S, float span, float4 &pa, float4 &pb, float4 &pc, int &tl)
 {
     const float cx = (float)S.px0 + 0.5f, cy = (float)S.py0 + 0.5f;
     const float e0 = (S.x[1] - S.x[0]) * (cy - S.y[0]) - (S.y[1] - S.y[0]) * (cx - S.x[0]) + 0.f;
@@ -184,19 +157,42 @@ __device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, i
     const float dzdx = (A1 * S.z[0] + A2 * S.z[1] + A0 * S.z[2]) * S.inv_area;
     const float dzdy = (B1 * S.z[0] + B2 * S.z[1] + B0 * S.z[2]) * S.inv_area;
     const float reach = fabsf(e0) + fabsf(e1) + fabsf(e2) + fabsf(z) +
-                        32.f * (fabsf(A0) + fabsf(A1) + fabsf(A2) + fabsf(B0) + fabsf(B1) + fabsf(B2) +
+                        span * (fabsf(A0) + fabsf(A1) + fabsf(A2) + fabsf(B0) + fabsf(B1) + fabsf(B2) +
                                 fabsf(dzdx) + fabsf(dzdy));
     if (!(reach <= 3.0e38f)) return false;
-    const int nx = S.px1 - S.px0 + 1;
     // top-left: dy < 0, or dy == 0 and dx > 0, with dy = -A_i and dx = B_i of edge i (exact)
-    const int tl = ((A0 > 0.f || (A0 == 0.f && B0 > 0.f)) ? 1 : 0) | ((A1 > 0.f || (A1 == 0.f && B1 > 0.f)) ? 0x100 : 0) |
-                   ((A2 > 0.f || (A2 == 0.f && B2 > 0.f)) ? 0x10000 : 0);
+    tl = ((A0 > 0.f || (A0 == 0.f && B0 > 0.f)) ? 1 : 0) | ((A1 > 0.f || (A1 == 0.f && B1 > 0.f)) ? 0x100 : 0) |
+         ((A2 > 0.f || (A2 == 0.f && B2 > 0.f)) ? 0x10000 : 0);
+    pa = make_float4(e0, e1, e2, z);
+    pb = make_float4(A0, A1, A2, dzdx);
+    pc = make_float4(B0, B1, B2, dzdy);
+    return true;
+}
+
+// Coverage of candidate (kx, ky) >= 0 of the box and its depth, from the planes; see above
+// for why the integer test equals the top-left rule.
+__device__ __forceinline__ bool plane_test(const float4 &a, const float4 &b, const float4 &c, int tl, float fx, float fy,
+                                           float &z)
+{
+    const int v0 = __float_as_int(fmaf(c.x, fy, fmaf(b.x, fx, a.x))) + (int)__byte_perm(tl, 0, 0x4440);
+    const int v1 = __float_as_int(fmaf(c.y, fy, fmaf(b.y, fx, a.y))) + (int)__byte_perm(tl, 0, 0x4441);
+    const int v2 = __float_as_int(fmaf(c.z, fy, fmaf(b.z, fx, a.z))) + (int)__byte_perm(tl, 0, 0x4442);
+    z = fminf(fmaxf(fmaf(c.w, fy, fmaf(b.w, fx, a.w)), 0.f), 1.f);
+    return min(v0, min(v1, v2)) > 0;
+}
+
+__device__ __forceinline__ bool store_rec(SmallRecs &R, int i, const Setup &S, int W)
+{
+    float4 a, b, c;
+    int tl;
+    if (!make_planes(S, 32.f, a, b, c, tl)) return false;
+    const int nx = S.px1 - S.px0 + 1;
     // ceil(1024 / nx): 1024/nx is an integer or at least 1/32 above one, far beyond the
     // approximate quotient's error
     const int mul = (int)(__fdividef(1024.f, (float)nx) - 0.00390625f) + 1;
-    R.a[i] = make_float4(e0, e1, e2, z);
-    R.b[i] = make_float4(A0, A1, A2, dzdx);
-    R.c[i] = make_float4(B0, B1, B2, dzdy);
+    R.a[i] = a;
+    R.b[i] = b;
+    R.c[i] = c;
     R.d[i] = make_int4(S.py0 * W + S.px0, mul, nx, tl);
     return true;
 }
@@ -333,20 +329,17 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         const int4 d = s_rec.d[i];
         const int k = idx - first;
         const int ky = (k * d.y) >> 10, kx = k - ky * d.z;
-        const float fx = (float)kx, fy = (float)ky;
-        const int v0 = __float_as_int(fmaf(c.x, fy, fmaf(b.x, fx, a.x))) + (int)__byte_perm(d.w, 0, 0x4440);
-        const int v1 = __float_as_int(fmaf(c.y, fy, fmaf(b.y, fx, a.y))) + (int)__byte_perm(d.w, 0, 0x4441);
-        const int v2 = __float_as_int(fmaf(c.z, fy, fmaf(b.z, fx, a.z))) + (int)__byte_perm(d.w, 0, 0x4442);
-        if (min(v0, min(v1, v2)) > 0 && idx < total) {
-            const float z = fminf(fmaxf(fmaf(c.w, fy, fmaf(b.w, fx, a.w)), 0.f), 1.f);
+        float z;
+        if (plane_test(a, b, c, d.w, (float)kx, (float)ky, z) && idx < total) {
             const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)(t0 + i);
             atomicMin(keys + (unsigned)(d.x + ky * W + kx), key);
         }
     }
 }
 
-// Triangles with more than SMALL_PX candidate pixels: one warp per triangle, lanes striding
-// over its box.
+// Triangles with more than SMALL_PX candidate pixels: one warp per triangle, lane l taking
+// candidates l, l + 32, ... of the box in row order (one division per triangle, then each
+// step of 32 candidates is q rows and r columns), tested on the triangle's planes.
 __global__ void __launch_bounds__(LARGE_THREADS) k_raster_large(const float *__restrict__ tris,
                                                                 const int32_t *__restrict__ large,
                                                                 const int32_t *__restrict__ nlarge,
@@ -360,11 +353,25 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_raster_large(const float *__r
         const int t = large[q];
         Setup S;
         if (!setup_tri(P, tris + (int64_t)t * 9, S)) continue;
-        const int tl = tl_flags(S);
-        const int nx = S.px1 - S.px0 + 1;
-        const int64_t npx = (int64_t)nx * (S.py1 - S.py0 + 1);
-        for (int64_t k = lane; k < npx; k += 32)
-            shade_pixel(S, tl, S.px0 + (int)(k % nx), S.py0 + (int)(k / nx), P.W, (unsigned)t, keys);
+        const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
+        float4 a, b, c;
+        int tl;
+        if (!make_planes(S, (float)max(nx, ny), a, b, c, tl)) continue;
+        const int dq = 32 / nx, dr = 32 - dq * nx;
+        int ky = lane / nx, kx = lane - ky * nx;
+        while (ky < ny) {
+            float z;
+            if (plane_test(a, b, c, tl, (float)kx, (float)ky, z)) {
+                const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)t;
+                atomicMin(keys + (unsigned)((S.py0 + ky) * P.W + S.px0 + kx), key);
+            }
+            kx += dr;
+            ky += dq;
+            if (kx >= nx) {
+                kx -= nx;
+                ++ky;
+            }
+        }
     }
 }
 
