@@ -524,7 +524,7 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
         SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge,
                                                                                             colors));
         SEM_CU(ctx, cudaGetLastError());
-        SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<4 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys));
+        SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<6 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys));
         SEM_CU(ctx, cudaGetLastError());
     }
     SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((npx / 4 + 255) / 256,

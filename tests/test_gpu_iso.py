@@ -74,7 +74,7 @@ def test_taylor_green_q_isosurface(gpu, sess, orc):
 
 
 @pytest.mark.parametrize("N,nel", [(2, (3, 4, 2)), (3, (5, 2, 3)), (5, (3, 3, 3)), (7, (5, 3, 3)), (9, (2, 3, 2)),
-                                   (10, (2, 2, 2))])
+                                   (10, (2, 2, 2)), (12, (2, 1, 2)), (15, (2, 2, 1))])
 def test_sphere_orders(gpu, sess, orc, N, nel):
     mesh = si.stretched_box(nel, N, seed=N)
     xyz = mesh.xyz().numpy()
