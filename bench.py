@@ -787,6 +787,9 @@ def run_ours(args):
            "memory": {"library_bytes_in_use": mem_now, "library_bytes_peak": mem_peak,
                       "caller_buffers_bytes_peak": torch_peak},
            "learned": learned}
+    emit_units = [c for c in S.sem_autotune_emit_choices(P.ctx) if c[:3] == (w.mesh.N, P.E, len(P.isos))]
+    out["autotune"] = {"emit_units_per_atomic": emit_units[0][3] if emit_units else None,
+                       "gemm_shapes_tuned": len(S.sem_autotune_choices(P.ctx))}
     if qprec is not None:
         out["q_precisions"] = qprec
     if batched is not None:

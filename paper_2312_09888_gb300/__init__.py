@@ -98,6 +98,8 @@ def _declare(L):
     L.sem_gemm_bf16.argtypes = [vp, vp, vp, i64, i32, i32, vp]
     L.sem_autotune_set.argtypes = [vp, i32]
     L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 6 + [C.POINTER(f32)]
+    L.sem_autotune_emit_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
+                                          C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
@@ -511,6 +513,19 @@ def sem_ae_decode(ctx, ae, latent, E: int, u, v, w) -> None:
 
 def sem_autotune_set(ctx, on: bool) -> None:
     _check(ctx, get_lib().sem_autotune_set(ctx, 1 if on else 0))
+
+
+def sem_autotune_emit_choices(ctx) -> list:
+    """[(N, E, isovalues, units per atomic, ms)] of the tuned isosurface emit launches."""
+    out, k = [], 0
+    L = get_lib()
+    while True:
+        N, E, nq, units, ms = C.c_int32(0), C.c_int64(0), C.c_int32(0), C.c_int32(0), C.c_float(0)
+        st = L.sem_autotune_emit_entry(ctx, k, C.byref(N), C.byref(E), C.byref(nq), C.byref(units), C.byref(ms))
+        if st != SEM_OK:
+            return out
+        out.append((N.value, E.value, nq.value, units.value, ms.value))
+        k += 1
 
 
 def sem_autotune_choices(ctx) -> list:

@@ -1150,7 +1150,25 @@ sem_status sem_autotune_set(sem_ctx *ctx, int on)
 {
     if (!ctx) return SEM_ERR_ARG;
     ctx->autotune = on != 0;
-    if (!on) ctx->gemm_tune.clear();
+    if (!on) {
+        ctx->gemm_tune.clear();
+        ctx->emit_tune.clear();
+    }
+    return SEM_OK;
+}
+
+sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t *E, int *niso, int *units, float *ms)
+{
+    if (!ctx || !N || !E || !niso || !units || !ms) return SEM_ERR_ARG;
+    if (k < 0 || k >= (int)ctx->emit_tune.size())
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_autotune_emit_entry: index %d outside [0, %d)", k,
+                        (int)ctx->emit_tune.size());
+    const auto &t = ctx->emit_tune[k];
+    *N = t.N;
+    *E = t.E;
+    *niso = t.niso;
+    *units = t.units;
+    *ms = t.ms;
     return SEM_OK;
 }
 

@@ -37,6 +37,15 @@ struct sem_ctx {
         float ms;
     };
     std::vector<GemmTune> gemm_tune;
+    // and the isosurface emit kernel's (element, isovalue) units per work-counter atomic, per
+    // (order, elements, isovalues)
+    struct EmitTune {
+        int N, niso;
+        int64_t E;
+        int units;
+        float ms;
+    };
+    std::vector<EmitTune> emit_tune;
     // device bytes the library holds for this context (scratch arenas, tables, meshes,
     // autoencoders) and their high-water mark
     int64_t mem_now = 0, mem_peak = 0;

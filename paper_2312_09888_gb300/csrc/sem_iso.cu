@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *_
 // triangle map, the mask of one isovalue, the element's node coordinates, a store staging
 // area and the list of cut cells; warps per block: up to 8 within ~96 KB
 #define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
-#define EMIT_CHUNK 2     // (element, isovalue) units a warp takes per atomic (swept: 1, 2, 4, 8)
+#define EMIT_UNITS_DEFAULT 2  // (element, isovalue) units a warp takes per atomic, untuned
 template <int NP>
 struct EmitW {
     using G = MaskGeo<NP>;
@@ -441,8 +441,8 @@ __device__ __forceinline__ int corner_off(int v)
     return (v & 1) + ((v >> 1) & 1) * NP + (v >> 2) * NP * NP;
 }
 
-// Persistent warps over (element, isovalue) units u = q E + e, EMIT_CHUNK units per atomic
-// on a counter the host zeroes before the launch.  For a unit with triangles: load the element
+// Persistent warps over (element, isovalue) units u = q E + e, `units` of them per atomic on a
+// counter the host zeroes before the launch.  For a unit with triangles: load the element
 // and its mask; (1a) lane per row pair, list the cut cells with their cases in cell order (a
 // warp scan of the per-lane counts places each lane's run; N uniform passes over the cells of
 // a row, each cut cell stored at its rank, so no lane walks its cells alone); then per window of
@@ -458,7 +458,8 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                                                                  const float4 *__restrict__ bhi,
                                                                  float *__restrict__ tris,
                                                                  int32_t *__restrict__ tri_elem, int64_t cap,
-                                                                 int *flag, unsigned long long *__restrict__ next)
+                                                                 int *flag, unsigned long long *__restrict__ next,
+                                                                 int units)
 {
     using EW = EmitW<NP>;
     using G = MaskGeo<NP>;
@@ -490,10 +491,10 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
     S1.niso = 1;
     for (;;) {
         unsigned long long u0 = 0;
-        if (lane == 0) u0 = atomicAdd(next, (unsigned long long)EMIT_CHUNK);
+        if (lane == 0) u0 = atomicAdd(next, (unsigned long long)units);
         u0 = __shfl_sync(0xffffffffu, u0, 0);
         if (u0 >= (unsigned long long)U) break;
-        const int64_t u1 = min((int64_t)u0 + EMIT_CHUNK, U);
+        const int64_t u1 = min((int64_t)u0 + units, U);
         for (int64_t u = (int64_t)u0; u < u1; ++u) {
             const int64_t o = offs[u], n = offs[u + 1] - o;
             if (n <= 0 || o + n > cap) continue;
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
 // `next` zeroed first.
 template <int NP>
 static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next)
+                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
 {
     constexpr int EV = EmitW<NP>::V;
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
@@ -622,8 +623,52 @@ static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, c
     SEM_CU(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
     const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
     SEM_TRACED(ctx, "k_iso_emit_m", k_iso_emit_m<NP><<<grid, 32 * EV, dyn, ctx->stream>>>(
-                                        f, S, m->E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag, next));
+                                        f, S, m->E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag, next, units));
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+}
+
+// The emit launch with the context's autotuner: the first emitting call of a given (order,
+// elements, isovalues) runs 1, 2, 4 and 8 units per work-counter atomic, each twice (the
+// second timed with CUDA events), and keeps the fastest; later calls reuse it.  Every
+// candidate writes the same triangles to the same places, so the output does not depend on the
+// choice.  Under stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
+template <int NP>
+static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
+                       float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next)
+{
+    for (const auto &t : ctx->emit_tune)
+        if (t.N == m->N && t.E == m->E && t.niso == S.niso)
+            return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, t.units);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (!ctx->autotune || cs != cudaStreamCaptureStatusNone)
+        return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, EMIT_UNITS_DEFAULT);
+    cudaEvent_t e0, e1;
+    SEM_CU(ctx, cudaEventCreate(&e0));
+    SEM_CU(ctx, cudaEventCreate(&e1));
+    int best = EMIT_UNITS_DEFAULT;
+    float best_ms = 1e30f;
+    sem_status st = SEM_OK;
+    for (int units : {1, 2, 4, 8}) {
+        for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
+            if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
+            if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
+            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+        }
+        if (st != SEM_OK) break;
+        float ms = 0.f;
+        if ((st = sem_cuda(ctx, cudaEventSynchronize(e1), "event")) != SEM_OK) break;
+        if ((st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event")) != SEM_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = units;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SEM_TRY(st);
+    ctx->emit_tune.push_back({m->N, S.niso, m->E, best, best_ms});
+    return SEM_OK;  // the triangles of the last candidate, the same as every other's
 }
 
 template <int NP>
@@ -654,7 +699,7 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
         return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface: %lld triangles exceed capacity %lld", (long long)total,
                         (long long)cap);
     if (total == 0) return SEM_OK;
-    return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
+    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
 }
 
 // No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
@@ -679,7 +724,7 @@ static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const floa
     SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t), S.niso + 1,
                                   cudaMemcpyDeviceToDevice, ctx->stream));
     if (!tris) return SEM_OK;
-    return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
+    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
 }
 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,

@@ -218,6 +218,36 @@ def test_scan_at_the_one_launch_limit(gpu, sess, orc, shape):
         off += counts[q]
 
 
+def test_emit_autotuner_choice_does_not_change_the_triangles(gpu, sess):
+    """The first emitting call of an (order, elements, isovalues) picks the units per work
+    atomic; the triangles are bit-identical to the untuned launch's."""
+    S = gpu
+    w = si.tgv_box(nel=6)
+    m = sess.mesh(7, w.mesh.xyz().numpy())
+    u, v, ww = (dev32(w.fields[c].numpy()) for c in range(3))
+    Q = torch.empty_like(u)
+    S.sem_qcriterion(sess.ctx, m, u, v, ww, Q)
+    qmax = S.sem_field_max(sess.ctx, Q)
+    isos = [float(np.float32(f * qmax)) for f in (0.05, 0.1, 0.2, 0.3)]
+    S.sem_autotune_set(sess.ctx, True)
+    counts = S.sem_isosurface_multi(sess.ctx, m, Q, isos, None)
+    tuned = torch.empty(sum(counts) * 9, device="cuda")
+    S.sem_isosurface_multi(sess.ctx, m, Q, isos, tuned)
+    mine = [c for c in S.sem_autotune_emit_choices(sess.ctx) if c[:3] == (7, w.E, 4)]
+    assert len(mine) == 1 and mine[0][3] in (1, 2, 4, 8) and mine[0][4] > 0
+    again = torch.empty_like(tuned)
+    S.sem_isosurface_multi(sess.ctx, m, Q, isos, again)
+    assert len([c for c in S.sem_autotune_emit_choices(sess.ctx) if c[:3] == (7, w.E, 4)]) == 1
+    S.sem_autotune_set(sess.ctx, False)
+    assert S.sem_autotune_emit_choices(sess.ctx) == []
+    plain = torch.empty_like(tuned)
+    S.sem_isosurface_multi(sess.ctx, m, Q, isos, plain)
+    S.sem_autotune_set(sess.ctx, True)
+    torch.cuda.synchronize()
+    assert torch.equal(tuned.view(torch.int32), plain.view(torch.int32))
+    assert torch.equal(again.view(torch.int32), plain.view(torch.int32))
+
+
 def test_many_elements_multi_isovalue_uses_the_multi_block_scan(gpu, sess, orc):
     """64^3 elements of order 1 x 2 isovalues = 524288 counts: the three-kernel scan (the
     single-block scan takes at most 8192, the one-launch tile scan 32 tiles of 4096); counts and
