@@ -66,14 +66,16 @@ def test_random_triangles_ortho_large_and_clipped(gpu, sess, orc):
 
 
 def test_every_box_size_class(gpu, sess, orc):
-    """Triangles whose boxes hold <= 32, 33..1024 and > 1024 pixel centres (the three ways the
-    rasteriser walks a box), overlapping at random depths, one pixel per world unit."""
+    """Triangles whose boxes (clamped to the image) hold <= 32 pixel centres (the warps' balanced
+    lists) and more (the large-triangle pass: a warp per triangle, its lanes stepping 32
+    candidates at a time), from 33 up to well over 4096 centres, overlapping at random depths,
+    one pixel per world unit."""
     rng = np.random.default_rng(6)
     W, H = 160, 128
     cam = si.camera(True, (W / 2, H / 2, 10.0), (W / 2, H / 2, 0), (0, 1, 0), W, H, half_h=H / 2, znear=1.0,
                     zfar=19.0)
     tris, classes = [], []
-    for size, count in ((4.0, 600), (12.0, 200), (40.0, 60), (90.0, 8)):
+    for size, count in ((4.0, 600), (12.0, 200), (40.0, 60), (90.0, 24)):
         for _ in range(count):
             c = rng.uniform((0, 0), (W, H))
             ang = rng.uniform(0, 2 * np.pi) + np.array([0.0, 2.1, 4.2]) + rng.uniform(-0.4, 0.4, 3)
@@ -81,13 +83,13 @@ def test_every_box_size_class(gpu, sess, orc):
             z = rng.uniform(-3, 3, 3)
             v = np.stack([c[0] + r * np.cos(ang), c[1] + r * np.sin(ang), z], axis=1)
             tris.append(v)
-            # candidate centres of the box (one pixel per unit, y flipped does not change counts)
-            nx = np.floor(v[:, 0].max() - 0.5) - np.ceil(v[:, 0].min() - 0.5) + 1
-            ny = np.floor(v[:, 1].max() - 0.5) - np.ceil(v[:, 1].min() - 0.5) + 1
-            classes.append(nx * ny)
+            # pixel centres of the box clamped to the image (the y flip does not change counts)
+            x0, x1 = max(0, np.ceil(v[:, 0].min() - 0.5)), min(W - 1, np.floor(v[:, 0].max() - 0.5))
+            y0, y1 = max(0, np.ceil(v[:, 1].min() - 0.5)), min(H - 1, np.floor(v[:, 1].max() - 0.5))
+            classes.append(max(0, x1 - x0 + 1) * max(0, y1 - y0 + 1))
     classes = np.array(classes)
-    assert (classes <= 32).sum() > 100 and ((classes > 32) & (classes <= 1024)).sum() > 100
-    assert (classes > 1024).sum() > 10
+    assert (classes <= 32).sum() > 100 and ((classes > 32) & (classes <= 4096)).sum() > 100
+    assert (classes > 4096).sum() >= 10
     t32 = dev32(np.array(tris).reshape(-1))
     n = len(tris)
     seg, rgb = [n // 2, n - n // 2], [[0.9, 0.3, 0.2], [0.2, 0.6, 0.9]]
