@@ -96,8 +96,14 @@ def sum_over_ranks(x: float, device) -> float:
 
 
 def _file_sha(path):
-    with open(os.path.join(ROOT, path), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of a source file's code: comments and whitespace removed, so that a counter capture
+    stays matched to its kernel through comment edits and is dropped by any code change."""
+    import re
+    with open(os.path.join(ROOT, path)) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
 
 
 def _traffic_for(kernel):

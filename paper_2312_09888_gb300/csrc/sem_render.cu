@@ -16,8 +16,10 @@
 //                   most SMALL_PX centres, the warp spreads all its triangles' centre tests
 //                   evenly over its lanes and atomicMins the keys.  Larger triangles are
 //                   appended to a list.
-//   k_raster_large  one warp per listed triangle, its lanes striding over the box.
-//   k_resolve       one thread per pixel: read the key, reset it for the next frame, shade.
+//   k_raster_large  one warp per listed triangle, its lanes stepping 32 candidates at a time
+//                   on the triangle's planes.
+//   k_resolve       grid-stride over groups of four pixels: read the key, reset it for the next
+//                   frame, look up the winner's colour (computed by the raster pass).
 //
 // Why not per-tile shared-memory z-buffers: the isosurface frames consist of millions of
 // triangles a few pixels or less in size, and binning them into tile lists costs two extra
@@ -31,7 +33,7 @@
 
 #include "sem_internal.cuh"
 
-#define SMALL_PX 32        // boxes with at most this many pixel centres are rasterised per thread
+#define SMALL_PX 32        // boxes with at most this many pixel centres: the warp's candidate list
 #define LARGE_THREADS 256
 
 struct RenderParams {
@@ -123,8 +125,8 @@ __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__
 // functions and the depth as planes over the triangle's box, e(kx, ky) = e(0, 0) + A kx + B ky
 // for candidate (px0 + kx, py0 + ky), so a test is eight FMAs.  The values at the box's first
 // pixel centre are the edge functions (x_i+1 - x_i)(cy - y_i) - (y_i+1 - y_i)(cx - x_i) of the
-// edges v0 v1, v1 v2, v2 v0; the increments are the edges' coordinate differences.  Per triangle, in four arrays (a lane's stores are contiguous with
-// its neighbours'):
+// edges v0 v1, v1 v2, v2 v0; the increments are the edges' coordinate differences.  Per
+// triangle, in four arrays (a lane's stores are contiguous with its neighbours'):
 //   a: e0 e1 e2 z at (px0 + .5, py0 + .5)   b: de/dx (3), dz/dx   c: de/dy (3), dz/dy
 //   d: pixel index py0 W + px0,  ceil(1024 / nx),  nx,  top-left flags (one per byte)
 // Box row of candidate k (0 <= k < nx ny <= 32): ky = (k ceil(1024/nx)) >> 10 is floor(k/nx)
@@ -136,8 +138,8 @@ __device__ __forceinline__ bool setup_tri(const RenderParams &P, const float *__
 // positive integer bits, +0 has 0, negative floats negative ones).  The box-origin values are
 // stored with -0 turned into +0 (x + 0 = +0 for x = -0), and an FMA chain of such a value with
 // non-negative candidate offsets rounds an exact zero to +0, never -0.  Triangles whose planes
-// could overflow over the 32-pixel box (|e| + 32 (|A| + |B|) not finite) are not drawn, so no
-// test sees an infinity or NaN.
+// could overflow within their box (|e| + span (|A| + |B|) not finite, span 32 for the small
+// boxes and the longer side for the others) are not drawn, so no test sees an infinity or NaN.
 struct SmallRecs {
     float4 a[256], b[256], c[256];
     int4 d[256];
