@@ -133,18 +133,26 @@ SEM_API sem_status sem_trace_entry(sem_ctx *ctx, int k, const char **name, doubl
 
 /* Load a mesh of E hexahedral elements of order N (1 <= N <= SEM_MAX_ORDER).
  * xyz_host: HOST array of 3*E*(N+1)^3 doubles, SoA x | y | z, node order as above; copied.
- * Each element must be an axis-aligned affine box (x depends only on i, y on j, z on k, with
- * the GLL spacing): this covers every box/channel mesh, stretched or not.  Curved
- * (non-affine) elements return SEM_ERR_UNSUPPORTED.  The element map x = x0 + (xi+1)/2 (x1-x0)
- * is Nek's isoparametric map restricted to boxes (Deville, Fischer & Mund, Sec. 4.5).
- * Synchronous.  Free with sem_mesh_free. */
+ * When every element is an axis-aligned affine box (x depends only on i, y on j, z on k, with
+ * the GLL spacing, x = x0 + (xi+1)/2 (x1-x0)), the mesh keeps six numbers per element and the
+ * derivative uses the per-axis factors 2/(x1-x0).  Otherwise the mesh is general (curved): the
+ * library computes at every node, in FP64 on the host, the Jacobian d x_c / d r_d of the
+ * isoparametric map (D applied to the node coordinates) and keeps its inverse d r_d / d x_j
+ * (9 floats per node) and the node coordinates (3 floats per node) on the device; derivatives
+ * then follow the chain rule d u / d x_j = sum_d (d u / d r_d)(d r_d / d x_j) (Deville, Fischer
+ * & Mund, Sec. 4.5) and isosurface vertices lie between the nodes' own coordinates.  On general
+ * meshes the tensor-core precisions, sem_qcriterion_batch and sem_isosurface_noalloc return
+ * SEM_ERR_UNSUPPORTED.  Errors: SEM_ERR_ARG for a non-finite coordinate or a node whose Jacobian
+ * determinant is not positive (an inverted or degenerate element).  Synchronous; the general
+ * case costs O(E (N+1)^4) host work.  Free with sem_mesh_free. */
 SEM_API sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz_host, sem_mesh **out);
 SEM_API void sem_mesh_free(sem_mesh *mesh);
 SEM_API sem_status sem_mesh_info(const sem_mesh *mesh, int *N, int64_t *E);
 
 /* Spectral derivative of one field u (device, E*(N+1)^3 floats):
  *   du/dr[k][j][i] = sum_m D[i][m] u[k][j][m]  (likewise s over j, t over k),
- *   du/dx = 2/(x1-x0) du/dr, du/dy = 2/(y1-y0) du/ds, du/dz = 2/(z1-z0) du/dt,
+ *   du/dx = 2/(x1-x0) du/dr, du/dy = 2/(y1-y0) du/ds, du/dz = 2/(z1-z0) du/dt on box meshes,
+ *   du/dx_j = sum_d du/dr_d dr_d/dx_j on general meshes (see sem_load_mesh),
  * with D the GLL collocation derivative matrix (Canuto et al., Spectral Methods, Sec. 2.3).
  * Derivatives are element-local (no averaging across element faces).
  * dudx, dudy, dudz: device, E*(N+1)^3 floats each, must not alias u. */

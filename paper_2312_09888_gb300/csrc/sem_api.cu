@@ -443,37 +443,91 @@ sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz, sem_
     if (E < 0 || E > (int64_t)1 << 31) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: bad E=%lld", (long long)E);
     if (E > 0 && !xyz) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: xyz is NULL");
     const int NP = N + 1, NP3 = NP * NP * NP;
-    double xi[SEM_MAX_ORDER + 1];
+    double xi[SEM_MAX_ORDER + 1], D[(SEM_MAX_ORDER + 1) * (SEM_MAX_ORDER + 1)];
     gll_nodes(N, xi);
+    gll_dmat(N, xi, D);
     std::vector<float4> lo(E), hi(E), g(E);
     const int64_t tot = E * NP3;
-    for (int64_t e = 0; e < E; ++e) {
+    for (int64_t q = 0; q < 3 * tot; ++q)
+        if (!isfinite(xyz[q])) return sem_fail(ctx, SEM_ERR_ARG, "sem_load_mesh: coordinate %lld is not finite", (long long)q);
+    // axis-aligned affine boxes (x = x0 + (xi + 1)/2 (x1 - x0) along each axis, to 1e-9
+    // relative) take the fast path; any other element makes the whole mesh general
+    bool curved = false;
+    for (int64_t e = 0; e < E && !curved; ++e) {
         const double *X = xyz + e * NP3, *Y = xyz + tot + e * NP3, *Z = xyz + 2 * tot + e * NP3;
-        double a[3] = {X[0], Y[0], Z[0]};
-        double b[3] = {X[N], Y[N * NP], Z[N * NP * NP]};
-        for (int d = 0; d < 3; ++d)
-            if (!(b[d] != a[d]) || !isfinite(a[d]) || !isfinite(b[d]))
-                return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "sem_load_mesh: element %lld is degenerate", (long long)e);
-        for (int k = 0; k < NP; ++k)
-            for (int j = 0; j < NP; ++j)
-                for (int i = 0; i < NP; ++i) {
-                    int n = (k * NP + j) * NP + i;
-                    int idx[3] = {i, j, k};
-                    const double *P[3] = {X, Y, Z};
+        const double a[3] = {X[0], Y[0], Z[0]};
+        const double b[3] = {X[N], Y[N * NP], Z[N * NP * NP]};
+        for (int d = 0; d < 3 && !curved; ++d) curved = !(b[d] != a[d]);  // zero extent: degenerate
+        for (int n = 0; n < NP3 && !curved; ++n) {
+            const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
+            const double *P[3] = {X, Y, Z};
+            for (int d = 0; d < 3 && !curved; ++d) {
+                const double expect = a[d] + (xi[idx[d]] + 1.0) * 0.5 * (b[d] - a[d]);
+                curved = !(fabs(P[d][n] - expect) <= 1e-9 * (fabs(b[d] - a[d]) + fabs(a[d])));
+            }
+        }
+    }
+    std::vector<float> geo, xyzn;
+    if (curved) {
+        // per node: Jacobian J[c][d] = d x_c / d r_d = sum_m D[idx_d][m] x_c(node with idx_d = m),
+        // its inverse G[d][j] = d r_d / d x_j (FP64, cofactors); a non-positive or non-finite
+        // determinant is an inverted or degenerate element
+        geo.resize(9 * (size_t)tot);
+        xyzn.resize(3 * (size_t)tot);
+        const int stride[3] = {1, NP, NP * NP};
+        for (int64_t e = 0; e < E; ++e) {
+            double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int n = 0; n < NP3; ++n) {
+                const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
+                double J[3][3];
+                for (int c = 0; c < 3; ++c) {
+                    const double *Xc = xyz + c * tot + e * NP3;
                     for (int d = 0; d < 3; ++d) {
-                        double s = (xi[idx[d]] + 1.0) * 0.5;
-                        double expect = a[d] + s * (b[d] - a[d]);
-                        double tol = 1e-9 * (fabs(b[d] - a[d]) + fabs(a[d]));
-                        if (!(fabs(P[d][n] - expect) <= tol))
-                            return sem_fail(ctx, SEM_ERR_UNSUPPORTED,
-                                            "sem_load_mesh: element %lld is not an axis-aligned affine box "
-                                            "(node %d, axis %d: %.17g vs %.17g); curved meshes are not supported",
-                                            (long long)e, n, d, P[d][n], expect);
+                        const int base = n - idx[d] * stride[d];
+                        double acc = 0.0;
+                        for (int m2 = 0; m2 < NP; ++m2) acc += D[idx[d] * NP + m2] * Xc[base + m2 * stride[d]];
+                        J[c][d] = acc;
                     }
+                    mn[c] = fmin(mn[c], Xc[n]);
+                    mx[c] = fmax(mx[c], Xc[n]);
+                    xyzn[c * tot + e * NP3 + n] = (float)Xc[n];
                 }
-        lo[e] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.f);
-        hi[e] = make_float4((float)b[0], (float)b[1], (float)b[2], 0.f);
-        g[e] = make_float4((float)(2.0 / (b[0] - a[0])), (float)(2.0 / (b[1] - a[1])), (float)(2.0 / (b[2] - a[2])), 0.f);
+                const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+                const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+                const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+                const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+                if (!(det > 0.0) || !isfinite(det))
+                    return sem_fail(ctx, SEM_ERR_ARG,
+                                    "sem_load_mesh: element %lld is inverted or degenerate at node %d (det J = %g)",
+                                    (long long)e, n, det);
+                // G = J^-1 = adj(J) / det, G[d][j]
+                double G[3][3];
+                G[0][0] = c00 / det;
+                G[1][0] = c01 / det;
+                G[2][0] = c02 / det;
+                G[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+                G[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+                G[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+                G[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+                G[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+                G[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+                for (int d = 0; d < 3; ++d)
+                    for (int j = 0; j < 3; ++j) geo[(size_t)(3 * d + j) * tot + e * NP3 + n] = (float)G[d][j];
+            }
+            lo[e] = make_float4((float)mn[0], (float)mn[1], (float)mn[2], 0.f);
+            hi[e] = make_float4((float)mx[0], (float)mx[1], (float)mx[2], 0.f);
+            g[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int64_t e = 0; e < E; ++e) {
+            const double *X = xyz + e * NP3, *Y = xyz + tot + e * NP3, *Z = xyz + 2 * tot + e * NP3;
+            const double a[3] = {X[0], Y[0], Z[0]};
+            const double b[3] = {X[N], Y[N * NP], Z[N * NP * NP]};
+            lo[e] = make_float4((float)a[0], (float)a[1], (float)a[2], 0.f);
+            hi[e] = make_float4((float)b[0], (float)b[1], (float)b[2], 0.f);
+            g[e] = make_float4((float)(2.0 / (b[0] - a[0])), (float)(2.0 / (b[1] - a[1])), (float)(2.0 / (b[2] - a[2])),
+                               0.f);
+        }
     }
     SEM_CU(ctx, cudaSetDevice(ctx->device));
     sem_mesh *m = new sem_mesh();
@@ -489,6 +543,17 @@ sem_status sem_load_mesh(sem_ctx *ctx, int N, int64_t E, const double *xyz, sem_
         m->owner = ctx;
         m->bytes = 3 * (int64_t)bytes;
         ctx->mem_add(m->bytes);
+        if (curved) {
+            m->curved = true;
+            if ((st = sem_cuda(ctx, cudaMalloc(&m->geo, sizeof(float) * geo.size()), "cudaMalloc(mesh)")) != SEM_OK) break;
+            m->bytes += (int64_t)(sizeof(float) * geo.size());
+            ctx->mem_add((int64_t)(sizeof(float) * geo.size()));
+            if ((st = sem_cuda(ctx, cudaMalloc(&m->xyzn, sizeof(float) * xyzn.size()), "cudaMalloc(mesh)")) != SEM_OK) break;
+            m->bytes += (int64_t)(sizeof(float) * xyzn.size());
+            ctx->mem_add((int64_t)(sizeof(float) * xyzn.size()));
+            if ((st = sem_cuda(ctx, cudaMemcpy(m->geo, geo.data(), sizeof(float) * geo.size(), cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
+            if ((st = sem_cuda(ctx, cudaMemcpy(m->xyzn, xyzn.data(), sizeof(float) * xyzn.size(), cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
+        }
         if (E > 0) {
             if ((st = sem_cuda(ctx, cudaMemcpy(m->lo, lo.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
             if ((st = sem_cuda(ctx, cudaMemcpy(m->hi, hi.data(), sizeof(float4) * E, cudaMemcpyHostToDevice), "copy")) != SEM_OK) break;
@@ -511,6 +576,8 @@ void sem_mesh_free(sem_mesh *m)
     if (m->lo) cudaFree(m->lo);
     if (m->hi) cudaFree(m->hi);
     if (m->g) cudaFree(m->g);
+    if (m->geo) cudaFree(m->geo);
+    if (m->xyzn) cudaFree(m->xyzn);
     delete m;
 }
 
@@ -566,6 +633,9 @@ sem_status sem_qcriterion(sem_ctx *ctx, const sem_mesh *m, const float *u, const
     if (Q == u || Q == v || Q == w) return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion: Q aliases an input");
     if (prec == SEM_FP32) return qcrit_launch(ctx, m, u, v, w, Q);
     if (prec == SEM_BF16 || prec == SEM_FP16 || prec == SEM_BF16X2 || prec == SEM_TF32) {
+        if (m->curved)
+            return sem_fail(ctx, SEM_ERR_UNSUPPORTED,
+                            "sem_qcriterion: tensor-core precisions need axis-aligned box elements (general mesh)");
         double xi[SEM_MAX_ORDER + 1], D[(SEM_MAX_ORDER + 1) * (SEM_MAX_ORDER + 1)];
         gll_nodes(m->N, xi);
         gll_dmat(m->N, xi, D);
@@ -590,6 +660,9 @@ sem_status sem_qcriterion_batch(sem_ctx *ctx, int n, const sem_mesh *const *mesh
         SEM_TRY(check_ptr(ctx, Q[p], "sem_qcriterion_batch", "Q[p]"));
         if (Q[p] == u[p] || Q[p] == v[p] || Q[p] == w[p])
             return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_batch: Q[%d] aliases an input", p);
+        if (meshes[p]->curved)
+            return sem_fail(ctx, SEM_ERR_UNSUPPORTED,
+                            "sem_qcriterion_batch: partition %d has a general (curved) mesh; use sem_qcriterion", p);
     }
     return qcrit_batch_launch(ctx, n, meshes, u, v, w, Q);
 }
@@ -687,6 +760,8 @@ sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *
                         "holds; use sem_isosurface",
                         (long long)m->E, SEM_NOALLOC_MAX_ELEMENTS);
     if (m->E == 0) return SEM_OK;
+    if (m->curved)
+        return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "sem_isosurface_noalloc: general (curved) mesh; use sem_isosurface");
     SEM_TRY(check_ptr(ctx, f, "sem_isosurface_noalloc", "f"));
     SEM_TRY(check_ptr(ctx, tris, "sem_isosurface_noalloc", "tris", true, 4));
     SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_noalloc", "tri_elem", true, 4));

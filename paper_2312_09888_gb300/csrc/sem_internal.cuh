@@ -93,6 +93,12 @@ struct sem_mesh {
     float4 *lo = nullptr;   // element box lower corner (x0, y0, z0, 0)
     float4 *hi = nullptr;   // element box upper corner (x1, y1, z1, 0)
     float4 *g = nullptr;    // 2/(x1-x0), 2/(y1-y0), 2/(z1-z0), 0
+    // general (curved) meshes: some element is not an axis-aligned affine box.  Then per node
+    // the inverse Jacobian d r_d / d x_j (9 planes of E (N+1)^3 floats, plane 3 d + j) and the
+    // node coordinates (3 planes); lo/hi hold each element's bounding box and g is zero.
+    bool curved = false;
+    float *geo = nullptr;
+    float *xyzn = nullptr;
 };
 
 // scratch arenas (each call uses its own so calls never overlap in scratch)

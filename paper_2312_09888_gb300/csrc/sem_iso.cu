@@ -448,9 +448,10 @@ __device__ __forceinline__ int corner_off(int v)
 // a row, each cut cell stored at its rank, so no lane walks its cells alone); then per window of
 // EMIT_MAPCAP triangles (1b) lane per listed cell, warp-scan the triangle counts and write each
 // triangle's packed (case, cell, index in cell) into the map, in cell order; (2) lane per
-// output triangle: interpolate its three vertices, stage them, and store each round of 32
+// output triangle: interpolate its three vertices (between the element box's node coordinates,
+// or the nodes' own coordinates on a general mesh), stage them, and store each round of 32
 // triangles (1152 contiguous bytes) with coalesced 4-byte stores.
-template <int NP>
+template <int NP, bool GENERAL>
 __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
                                                                  const int64_t *__restrict__ offs,
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                                                                  float *__restrict__ tris,
                                                                  int32_t *__restrict__ tri_elem, int64_t cap,
                                                                  int *flag, unsigned long long *__restrict__ next,
-                                                                 int units)
+                                                                 int units, const float *__restrict__ xyzn)
 {
     using EW = EmitW<NP>;
     using G = MaskGeo<NP>;
@@ -580,13 +581,24 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
 #pragma unroll
                         for (int sv = 0; sv < 3; ++sv) {
                             const int la = (pairs >> (6 * sv)) & 7, lb = (pairs >> (6 * sv + 3)) & 7;
-                            const float fa = sf[c0 + corner_off<NP>(la)], fb = sf[c0 + corner_off<NP>(lb)];
+                            const int na = c0 + corner_off<NP>(la), nb = c0 + corner_off<NP>(lb);
+                            const float fa = sf[na], fb = sf[nb];
                             const float tt = __fdividef(iso - fa, fb - fa);
-                            const int ia = i + (la & 1), ja = j + ((la >> 1) & 1), ka = k + (la >> 2);
-                            const int ib = i + (lb & 1), jb = j + ((lb >> 1) & 1), kb = k + (lb >> 2);
-                            stg[lane * 9 + sv * 3 + 0] = fmaf(tt, X[ib] - X[ia], X[ia]);
-                            stg[lane * 9 + sv * 3 + 1] = fmaf(tt, Y[jb] - Y[ja], Y[ja]);
-                            stg[lane * 9 + sv * 3 + 2] = fmaf(tt, Z[kb] - Z[ka], Z[ka]);
+                            if constexpr (GENERAL) {
+                                // general mesh: between the two nodes' own coordinates
+                                const int64_t tot = E * G::NP3, ga = e * G::NP3 + na, gb = e * G::NP3 + nb;
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) {
+                                    const float pa = __ldg(xyzn + c * tot + ga), pb = __ldg(xyzn + c * tot + gb);
+                                    stg[lane * 9 + sv * 3 + c] = fmaf(tt, pb - pa, pa);
+                                }
+                            } else {
+                                const int ia = i + (la & 1), ja = j + ((la >> 1) & 1), ka = k + (la >> 2);
+                                const int ib = i + (lb & 1), jb = j + ((lb >> 1) & 1), kb = k + (lb >> 2);
+                                stg[lane * 9 + sv * 3 + 0] = fmaf(tt, X[ib] - X[ia], X[ia]);
+                                stg[lane * 9 + sv * 3 + 1] = fmaf(tt, Y[jb] - Y[ja], Y[ja]);
+                                stg[lane * 9 + sv * 3 + 2] = fmaf(tt, Z[kb] - Z[ka], Z[ka]);
+                            }
                         }
                         if (tri_elem) tri_elem[o + win + idx] = (int32_t)e;
                     }
@@ -605,26 +617,36 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
     }
 }
 
-// Launch the persistent emit kernel: one resident wave (SMs x blocks per SM), work counter
-// `next` zeroed first.
-template <int NP>
-static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
+template <int NP, bool GENERAL>
+static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
+                                float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
 {
     constexpr int EV = EmitW<NP>::V;
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
-    static int blocks_per_sm = 0;  // per order; the same on every device of one architecture
+    auto kern = k_iso_emit_m<NP, GENERAL>;
+    static int blocks_per_sm = 0;  // per instantiation; the same on every device of one architecture
     if (!blocks_per_sm) {
-        SEM_CU(ctx, cudaFuncSetAttribute(k_iso_emit_m<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
         int nb = 0;
-        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_iso_emit_m<NP>, 32 * EV, dyn));
+        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * EV, dyn));
         blocks_per_sm = nb > 0 ? nb : 1;
     }
     SEM_CU(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
     const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
-    SEM_TRACED(ctx, "k_iso_emit_m", k_iso_emit_m<NP><<<grid, 32 * EV, dyn, ctx->stream>>>(
-                                        f, S, m->E, offs, m->lo, m->hi, tris, tri_elem, cap, ctx->d_flag, next, units));
+    SEM_TRACED(ctx, "k_iso_emit_m", kern<<<grid, 32 * EV, dyn, ctx->stream>>>(f, S, m->E, offs, m->lo, m->hi, tris,
+                                                                             tri_elem, cap, ctx->d_flag, next, units,
+                                                                             m->xyzn));
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
+}
+
+// Launch the persistent emit kernel: one resident wave (SMs x blocks per SM), work counter
+// `next` zeroed first; box meshes and general meshes have their own instantiation.
+template <int NP>
+static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
+                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
+{
+    if (m->curved) return launch_emit_k<NP, true>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
+    return launch_emit_k<NP, false>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
 }
 
 // The emit launch with the context's autotuner: the first emitting call of a given (order,

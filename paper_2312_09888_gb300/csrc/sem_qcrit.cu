@@ -729,13 +729,97 @@ static sem_status dispatch(sem_ctx *ctx, int N, int n, const sem_mesh *const *m,
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// General (curved) elements: the isoparametric chain rule at every node,
+//   d u / d x_j = sum_d (d u / d r_d) (d r_d / d x_j),
+// with the reference derivatives d u / d r_d = sum_m D[idx_d][m] u(idx_d -> m) and the inverse
+// Jacobian d r_d / d x_j of each node precomputed by sem_load_mesh (plane 3 d + j of geo).
+// A block takes one element at a time (grid-stride): its NC components and D in shared
+// memory, one thread per node.  NC = 1: the three derivatives; NC = 3: Q = -1/2 sum_ij J_ij J_ji.
+// ------------------------------------------------------------------------------------------
+#define GEN_THREADS 256
+template <int NP, int NC>
+__global__ void __launch_bounds__(GEN_THREADS) k_sem_grad_gen(const float *__restrict__ f0, const float *__restrict__ f1,
+                                                             const float *__restrict__ f2, const float *__restrict__ geo,
+                                                             int64_t E, float *__restrict__ o0, float *__restrict__ o1,
+                                                             float *__restrict__ o2)
+{
+    constexpr int NP3 = NP * NP * NP;
+    extern __shared__ float s_u[];  // NC * NP3
+    __shared__ float s_D[NP * NP];
+    for (int q = threadIdx.x; q < NP * NP; q += blockDim.x) s_D[q] = Dc<NP>(q / NP, q % NP);
+    const int64_t tot = E * NP3;
+    const float *src[3] = {f0, f1, f2};
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        __syncthreads();  // the previous element's readers are done (and D is in place)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            for (int n = threadIdx.x; n < NP3; n += blockDim.x) s_u[c * NP3 + n] = __ldg(src[c] + e * NP3 + n);
+        __syncthreads();
+        for (int n = threadIdx.x; n < NP3; n += blockDim.x) {
+            const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
+            const int64_t node = e * NP3 + n;
+            float G[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) G[q] = __ldg(geo + q * tot + node);
+            float J[NC][3];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float *U = s_u + c * NP3;
+                float dr = 0.f, ds = 0.f, dt = 0.f;
+#pragma unroll
+                for (int m = 0; m < NP; ++m) {
+                    dr = fmaf(s_D[i * NP + m], U[(k * NP + j) * NP + m], dr);
+                    ds = fmaf(s_D[j * NP + m], U[(k * NP + m) * NP + i], ds);
+                    dt = fmaf(s_D[k * NP + m], U[(m * NP + j) * NP + i], dt);
+                }
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) J[c][jj] = fmaf(dt, G[6 + jj], fmaf(ds, G[3 + jj], dr * G[jj]));
+            }
+            if constexpr (NC == 1) {
+                o0[node] = J[0][0];
+                o1[node] = J[0][1];
+                o2[node] = J[0][2];
+            } else {
+                const float d = fmaf(J[0][0], J[0][0], fmaf(J[1][1], J[1][1], J[2][2] * J[2][2]));
+                const float o = fmaf(J[0][1], J[1][0], fmaf(J[0][2], J[2][0], J[1][2] * J[2][1]));
+                o0[node] = -0.5f * fmaf(2.f, o, d);
+            }
+        }
+    }
+}
+
+template <int NC>
+static sem_status launch_gen(sem_ctx *ctx, const sem_mesh *m, const float *f0, const float *f1, const float *f2,
+                             float *o0, float *o1, float *o2)
+{
+    switch (m->N + 1) {
+#define SEM_CASE(NPV)                                                                                          \
+    case NPV: {                                                                                                \
+        auto kern = k_sem_grad_gen<NPV, NC>;                                                                   \
+        const size_t smem = sizeof(float) * NC * NPV * NPV * NPV;                                              \
+        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+        const int64_t grid = std::min<int64_t>(m->E, (int64_t)ctx->sm_count * 8);                             \
+        SEM_TRACED(ctx, "k_sem_grad_gen",                                                                      \
+                   kern<<<(unsigned)grid, GEN_THREADS, smem, ctx->stream>>>(f0, f1, f2, m->geo, m->E, o0, o1, o2)); \
+        return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad_gen launch");                                    \
+    }
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
+}
+
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)
 {
+    if (m->curved) return launch_gen<3>(ctx, m, u, v, w, Q, nullptr, nullptr);
     return dispatch<3>(ctx, m->N, 1, &m, &u, &v, &w, &Q, nullptr, nullptr);
 }
 
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz)
 {
+    if (m->curved) return launch_gen<1>(ctx, m, u, nullptr, nullptr, dx, dy, dz);
     return dispatch<1>(ctx, m->N, 1, &m, &u, nullptr, nullptr, &dx, &dy, &dz);
 }
 

@@ -142,6 +142,38 @@ class BoxMesh:
         return gx[None, None, :], gy[None, :, None], gz[:, None, None]
 
 
+def perturbed_box(n: Sequence[int], lo: Sequence[float], hi: Sequence[float], N: int, amp: float = 0.2,
+                  seed: int = 0) -> np.ndarray:
+    """(3, E, NP^3) float64 node coordinates of a conforming curved mesh: the uniform grid of
+    element corners with every interior corner moved by up to amp times the element size per
+    axis (seeded; a grid with a single element along some axis has no interior corner and stays
+    a box), each element the trilinear map of its eight corners sampled at the GLL points.  Element order e = ex + nx (ey + ny ez), node order i + NP (j + NP k), as in
+    BoxMesh."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = n
+    h = [(hi[d] - lo[d]) / n[d] for d in range(3)]
+    cx, cy, cz = (np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3))
+    C = np.stack(np.meshgrid(cx, cy, cz, indexing="ij"), axis=-1)  # (nx+1, ny+1, nz+1, 3)
+    inner = (slice(1, nx), slice(1, ny), slice(1, nz))
+    C[inner] += rng.uniform(-amp, amp, size=C[inner].shape) * np.array(h)
+    xi = gll_points(N)
+    NP = N + 1
+    r = np.broadcast_to(xi[None, None, :], (NP, NP, NP)).reshape(-1)
+    s_ = np.broadcast_to(xi[None, :, None], (NP, NP, NP)).reshape(-1)
+    t = np.broadcast_to(xi[:, None, None], (NP, NP, NP)).reshape(-1)
+    xyz = np.zeros((3, nx * ny * nz, NP ** 3))
+    for ez in range(nz):
+        for ey in range(ny):
+            for ex in range(nx):
+                e = ex + nx * (ey + ny * ez)
+                for v in range(8):
+                    a, b, c = v & 1, (v >> 1) & 1, (v >> 2) & 1
+                    wgt = ((1 + r) / 2 if a else (1 - r) / 2) * ((1 + s_) / 2 if b else (1 - s_) / 2) * \
+                          ((1 + t) / 2 if c else (1 - t) / 2)
+                    xyz[:, e] += C[ex + a, ey + b, ez + c][:, None] * wgt[None, :]
+    return xyz
+
+
 def uniform_box(n: Sequence[int], lo: Sequence[float], hi: Sequence[float], N: int) -> BoxMesh:
     f = [np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3)]
     return BoxMesh(N, f[0], f[1], f[2])

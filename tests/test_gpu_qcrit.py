@@ -139,10 +139,12 @@ def test_argument_errors(gpu, sess):
     with pytest.raises(gpu.SemError) as ex:
         gpu.sem_load_mesh(sess.ctx, 16, np.zeros((3, 1, 17 ** 3)))
     assert ex.value.status == gpu.SEM_ERR_ARG
-    # a curved element is refused (no silent wrong answer)
+    # a non-box element makes the mesh general (isoparametric path); an inverted one is refused
     xyz = mesh.xyz().numpy().copy()
     xyz[0, 0, 100] += 0.01
+    gpu.sem_mesh_free(gpu.sem_load_mesh(sess.ctx, 7, xyz))
+    xyz[0] = -xyz[0]  # mirrored: every Jacobian determinant of the general mesh is negative
     with pytest.raises(gpu.SemError) as ex:
         gpu.sem_load_mesh(sess.ctx, 7, xyz)
-    assert ex.value.status == gpu.SEM_ERR_UNSUPPORTED
+    assert ex.value.status == gpu.SEM_ERR_ARG
     gpu.sem_synchronize(sess.ctx)
