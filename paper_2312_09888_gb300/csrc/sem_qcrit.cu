@@ -798,7 +798,11 @@ static sem_status launch_gen(sem_ctx *ctx, const sem_mesh *m, const float *f0, c
     case NPV: {                                                                                                \
         auto kern = k_sem_grad_gen<NPV, NC>;                                                                   \
         const size_t smem = sizeof(float) * NC * NPV * NPV * NPV;                                              \
-        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+        static bool attr_set = false; /* once per instantiation, before any capture needs it */               \
+        if (!attr_set) {                                                                                       \
+            SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));  \
+            attr_set = true;                                                                                   \
+        }                                                                                                      \
         const int64_t grid = std::min<int64_t>(m->E, (int64_t)ctx->sm_count * 8);                             \
         SEM_TRACED(ctx, "k_sem_grad_gen",                                                                      \
                    kern<<<(unsigned)grid, GEN_THREADS, smem, ctx->stream>>>(f0, f1, f2, m->geo, m->E, o0, o1, o2)); \

@@ -427,7 +427,11 @@ static sem_status launch_tc(sem_ctx *ctx, const sem_mesh *m, const float *u, con
     using L = Smem<PREC>;
     static_assert(L::ALLOC <= 232448, "shared memory per CTA");
     auto kern = k_sem_q_tc<PREC>;
-    SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
+    static bool attr_set = false;  // per instantiation; the attribute is a property of the function
+    if (!attr_set) {
+        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
+        attr_set = true;
+    }
     // one CTA per SM: it allocates all 512 TMEM columns (two accumulator sets)
     const int64_t ntiles = (m->E + NE - 1) / NE;
     int64_t grid = (int64_t)ctx->sm_count;
