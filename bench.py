@@ -471,6 +471,37 @@ def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
         torch.cuda.empty_cache()
 
 
+def measure_curved(S, ctx, vel, box_mesh, steps=20, warmup=3):
+    """sem_qcriterion on a general (curved) mesh of the benchmark's size: 32^3 elements, N = 7,
+    interior element corners moved by up to 0.15 element sizes (sem_inputs.perturbed_box), the
+    benchmark's velocity values; against the same call on the box mesh.  Algorithmic bytes:
+    16 B per node (u, v, w in, Q out) plus 36 B per node of inverse Jacobian on the curved mesh."""
+    import time
+    import torch
+    import sem_inputs as si
+    xyz = si.perturbed_box((32, 32, 32), (0.0, -1.0, 0.0), (2 * 3.141592653589793, 1.0, 3.141592653589793), 7,
+                           amp=0.15, seed=si.seed_for(2, 99))
+    t0 = time.perf_counter()
+    m = S.sem_load_mesh(ctx, 7, xyz)
+    load_s = time.perf_counter() - t0
+    Q = torch.empty_like(vel[0])
+    nodes = vel[0].numel()
+    out = {"mesh": "32^3 elements, N=7, interior corners moved up to 0.15 element sizes", "load_s": round(load_s, 2)}
+    for name, mesh, per_node in (("curved", m, 52), ("box", box_mesh, 16)):
+        for _ in range(warmup):
+            S.sem_qcriterion(ctx, mesh, *vel, Q)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            S.sem_qcriterion(ctx, mesh, *vel, Q)
+        b.record()
+        torch.cuda.synchronize()
+        us = a.elapsed_time(b) / steps * 1e3
+        out[name] = {"us": round(us, 1), "gbs": round(per_node * nodes / (us * 1e-6) / 1e9, 1)}
+    S.sem_mesh_free(m)
+    return out
+
+
 def measure_batched(S, ctx, steps=20, warmup=3):
     """Batching workload: 16 partitions of E_p ~ U{4096..40960} elements (seeded) and orders
     N_p in {5, 7, 9}, each the first E_p elements of a ceil(E_p^(1/3))^3 lattice of [0, 2 pi]^3
@@ -766,6 +797,7 @@ def run_ours(args):
     mem_now, mem_peak = S.sem_memory(P.ctx)
     torch_peak = int(torch.cuda.max_memory_allocated())  # the caller's buffers (torch allocator)
     batched = measure_batched(S, P.ctx) if args.batched else None
+    curved = measure_curved(S, P.ctx, P.vel, P.mesh) if args.curved else None
     learned = None
     if not args.no_learned:
         bpk = peaks.get("bf16_tflops")
@@ -800,6 +832,8 @@ def run_ours(args):
         out["q_precisions"] = qprec
     if batched is not None:
         out["batched"] = batched
+    if curved is not None:
+        out["curved"] = curved
     P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -895,6 +929,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of the captured graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the autoencoder measurement")
+    ap.add_argument("--curved", action="store_true",
+                    help="also time sem_qcriterion on a general (curved) mesh of the same size (curved)")
     ap.add_argument("--batched", action="store_true",
                     help="also time the batching workload: plain path vs CUDA graph vs batched Q (batched)")
     ap.add_argument("--q-precisions", action="store_true",
