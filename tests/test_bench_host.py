@@ -1,0 +1,37 @@
+"""bench.py's host-side contract, on the CPU: the reference arm's JSON line (the FP64 oracle
+timed on a bounded sample of the benchmark workload) and the source hash that keeps a counter
+capture matched to its kernel."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                        "--ref-elements", "4"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["impl"] == "reference"
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("channel 32x32x32")
+
+
+def test_source_hash_ignores_comments_only(tmp_path):
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "a.cu"
+    a.write_text("// header\n__global__ void k(int *x) { x[0] = 1; /* one */ }\n")
+    b = tmp_path / "b.cu"
+    b.write_text("// another header\n\n__global__ void k(int *x)\n{\n    x[0] = 1;  // one\n}\n")
+    c = tmp_path / "c.cu"
+    c.write_text("// header\n__global__ void k(int *x) { x[0] = 2; }\n")
+    assert bench._file_sha(str(a)) == bench._file_sha(str(b))
+    assert bench._file_sha(str(a)) != bench._file_sha(str(c))
