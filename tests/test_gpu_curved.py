@@ -6,8 +6,9 @@ trilinear map of its corners (conforming, non-affine).  Bound per node for the d
 the reference derivative along direction d is an FP32 sum of NP products with FP32 D, error
 <= (NP + 1) u A_d with A_d = sum_m |D||u| along d; the inverse Jacobian G = d r / d x is
 rounded to FP32 (u |G|), and the three-term sum d u / d x_j = sum_d (d u / d r_d) G_dj adds
-3 u sum_d |d u / d r_d| |G_dj|; together (NP + 5) u sum_d |G_dj| A_d, u = 2^-24.  Q's bound
-follows from the derivatives' (q_bound).
+3 u sum_d |d u / d r_d| |G_dj|; together (NP + 5) u sum_d |G_dj| A_d to first order, u = 2^-24
+(the test takes NP + 6 for the second-order terms).  Q's bound follows from the derivatives'
+(q_bound).
 """
 import numpy as np
 import pytest
