@@ -1,14 +1,20 @@
 """Benchmark of the SEM Q-isosurface render path on GB300.
 
-One step = one snapshot through the whole path: sem_qcriterion on all elements, sem_isosurface
-for each isovalue (triangles of all isovalues packed into one buffer), and one sem_render of
-the frame.  Workload: the 32x32x32-element channel, N = 7 (16.8M GLL nodes, 201 MB of FP32
-velocity), three Q isovalues {0.05, 0.1, 0.2} * max Q, 1920x1080 perspective frame.
+One step = one snapshot through the whole path, as one CUDA graph: sem_qcriterion on all
+elements, the isosurfaces of every field and isovalue (triangles of all of them packed into one
+buffer, no host synchronisation) and one sem_render of the frame.
 
-Prints one JSON line (rank 0).  ``value`` is elements/s with the velocity already resident in
-HBM; ``e2e`` is the same metric with the velocity copied from pinned host memory and the frame
-read back inside the timed region.  ``roofline`` reports the dominant kernel against the
-measured HBM bandwidth; ``cpu_baseline`` times the FP64 CPU oracle on a bounded sample.
+Headline workload (the largest single-GPU configuration): the Rayleigh-Benard-like box of
+64x64x64 elements, N = 7 (134M GLL nodes), velocity and temperature (2.15 GB of FP32), the
+Q-isosurface at 0.1 max Q and the temperature isosurface T = 0.5, one 3840x2160 perspective
+frame.  The 32^3-element channel (16.8M nodes, three Q isovalues, 1920x1080) is measured the
+same way and reported under ``extra``.
+
+Prints one JSON line (rank 0).  ``value`` is elements/s with the inputs already resident in
+HBM; ``e2e`` is the same metric with every step's inputs copied from pinned host memory and the
+frame read back inside the timed region.  ``roofline`` reports the dominant kernel against the
+measured HBM bandwidth; ``cpu_baseline`` times the FP64 CPU oracle on bounded samples, on one
+host thread and on all host cores.
 
 ``--impl reference`` times the CPU oracle alone (the reference arm) on the same workload.
 Under torchrun each rank runs an independent replica on its own GPU (weak scaling).
@@ -32,7 +38,15 @@ if ROOT not in sys.path:
 
 METRIC = "SEM elements/s through Q-isosurface render; frames/s; fraction of HBM roofline"
 UNIT = "elements/s"
-WORKLOAD = "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, 1920x1080 perspective"
+WORKLOADS = {
+    "rb64": "RB-like 64x64x64 elements, N=7 (134M GLL nodes), velocity + temperature (2.15 GB FP32), "
+            "Q-isosurface at 0.1 max Q + temperature isosurface T=0.5, one 3840x2160 perspective frame",
+    "channel32": "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, "
+                 "1920x1080 perspective",
+}
+HEADLINE = "rb64"
+# segment colours of the two-field frame: Q red, temperature blue
+RB_COLOURS = [[0.9, 0.3, 0.2], [0.2, 0.5, 0.9]]
 KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_sem_q8": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_iso_count_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
@@ -41,23 +55,23 @@ KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_resolve": "paper_2312_09888_gb300/csrc/sem_render.cu"}
 
 
-def algorithmic_bytes(name, P):
-    """Bytes a kernel must move per launch at the least (each input read once, each output
-    written once), for the roofline of the step's kernels."""
-    NP3 = (P.w.mesh.N + 1) ** 3
-    niso = len(P.isos)
+def algorithmic_bytes_per_step(name, P):
+    """Bytes a kernel must move per step at the least (each input read once, each output
+    written once), summed over its launches in the step."""
+    NP3 = (P.N + 1) ** 3
+    surf = P.surface_stats
     table = {
         # u, v, w read (12 B/node) + Q written (4 B/node)
         "k_sem_grad": 16 * P.npts,
         "k_sem_q8": 16 * P.npts,
-        # the field read once for all isovalues + one int32 count per element and isovalue
-        "k_iso_count_m": 4 * P.npts + 4 * P.E * niso,
-        # the active elements' field read + 36 B per triangle written + the offsets read
-        "k_iso_emit_m": 4 * NP3 * P.active_elems + 36 * P.last_ntri + 8 * (niso * P.E + 1),
+        # per field: read once for all its isovalues + one int32 count per element and isovalue
+        "k_iso_count_m": sum(4 * P.npts + 4 * P.E * s["niso"] for s in surf),
+        # per field: its active elements read + 36 B per triangle written + the offsets read
+        "k_iso_emit_m": sum(4 * NP3 * s["active_elems"] + 36 * s["ntri"] + 8 * (s["niso"] * P.E + 1) for s in surf),
         # 36 B per triangle read (the 64-bit depth keys live in L2)
         "k_raster_small": 36 * P.last_ntri,
-        # key read 8 B + RGBA 4 B + depth 4 B per pixel, and the winner's 36 B triangle per covered pixel
-        "k_resolve": 16 * P.W * P.H + 36 * P.covered,
+        # key read 8 B + RGBA 4 B + depth 4 B per pixel, and the winner's colour per covered pixel
+        "k_resolve": 16 * P.W * P.H + 4 * P.covered,
     }
     return table.get(name)
 
@@ -106,13 +120,13 @@ def _file_sha(path):
     return hashlib.sha256(" ".join(src.split()).encode()).hexdigest()[:16]
 
 
-def _traffic_for(kernel):
+def _traffic_for(kernel, workload):
     """DRAM bytes per launch from a committed ncu summary, or None if absent or stale."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p)).get(kernel)
+        d = json.load(open(p)).get(f"{workload}:{kernel}")
         if d and d.get("source_sha") == _file_sha(KERNEL_SOURCES[kernel]):
             return d.get("bytes_per_launch_full")
     except Exception:
@@ -180,13 +194,20 @@ class Clocks:
 
 # ------------------------------------------------------------------------------------ workload
 
-def make_workload(device):
+def make_workload(name, device):
     import sem_inputs as si
+    if name == "rb64":
+        return si.rb_box(device=device)
     return si.channel(device=device)
 
 
 class Pipeline:
-    """Device buffers and the per-step call sequence through the C ABI."""
+    """Device buffers and the per-step call sequence through the C ABI.
+
+    Inputs: the velocity (and, on the Rayleigh-Benard-like box, the temperature), FP32 on the
+    device.  Surfaces: Q at the workload's fractions of max Q (fixed once at setup from the GPU's
+    Q), then the temperature at its isovalue; their triangles share one buffer, one colour
+    segment per (field, isovalue)."""
 
     def __init__(self, S, w, device_index=0):
         import numpy as np
@@ -197,71 +218,95 @@ class Pipeline:
         self.ctx = self.sess.ctx
         xyz = w.mesh.xyz(w.fields.device).cpu().numpy()
         self.mesh = self.sess.mesh(w.mesh.N, xyz)
+        del xyz
+        self.N = w.mesh.N
         self.E = w.E
         self.npts = w.E * w.mesh.NP ** 3
-        self.vel = [w.fields[c].float().contiguous() for c in range(3)]
-        self.Q = torch.empty_like(self.vel[0])
-        S.sem_qcriterion(self.ctx, self.mesh, *self.vel, self.Q)
+        self.inputs = [w.fields[c].float().contiguous() for c in range(w.fields.shape[0])]
+        w.fields = None  # the FP64 originals are not needed past this point
+        torch.cuda.empty_cache()
+        self.Q = torch.empty_like(self.inputs[0])
+        S.sem_qcriterion(self.ctx, self.mesh, *self.inputs[:3], self.Q)
         qmax = S.sem_field_max(self.ctx, self.Q)
-        self.isos = [float(np.float32(f * qmax)) for f in w.iso_fracs]
-        counts = S.sem_isosurface_multi(self.ctx, self.mesh, self.Q, self.isos, None)
-        self.cap = int(sum(counts) * 1.05) + 1024
+        self.surfaces = [("Q", [float(np.float32(f * qmax)) for f in w.iso_fracs])]
+        if "t_iso" in w.extra:
+            self.surfaces.append((3, [float(np.float32(w.extra["t_iso"]))]))
+        self.colours = RB_COLOURS if len(self.surfaces) > 1 else None
+        self.nseg = sum(len(isos) for _, isos in self.surfaces)
+        counts = [S.sem_isosurface_multi(self.ctx, self.mesh, self.field(src), isos, None)
+                  for src, isos in self.surfaces]
+        total = sum(sum(c) for c in counts)
+        self.cap = int(total * 1.05) + 1024
         self.tris = torch.empty(self.cap * 9, device="cuda")
         self.W, self.H = w.camera["W"], w.camera["H"]
         self.rgba = torch.empty(self.W * self.H * 4, dtype=torch.uint8, device="cuda")
         self.depth = torch.empty(self.W * self.H, device="cuda")
-        self.counts = counts
-        self.ev = None
-        self.counts_dev = torch.zeros(len(self.isos) + 1, dtype=torch.int64, device="cuda")
+        self.counts_dev = torch.zeros(self.nseg + 1, dtype=torch.int64, device="cuda")
         self.graph = None
-        # elements holding a triangle of some isovalue (the emit pass reads only those)
+        # per field: isovalues, triangles, and the elements holding a triangle (the emit pass
+        # reads only those)
+        self.surface_stats = []
         te = torch.empty(self.cap, dtype=torch.int32, device="cuda")
-        S.sem_isosurface_multi(self.ctx, self.mesh, self.Q, self.isos, self.tris, tri_elem=te, cap=self.cap)
-        self.active_elems = int(torch.unique(te[:sum(counts)]).numel())
+        for (src, isos), c in zip(self.surfaces, counts):
+            S.sem_isosurface_multi(self.ctx, self.mesh, self.field(src), isos, self.tris, tri_elem=te, cap=self.cap)
+            n = sum(c)
+            self.surface_stats.append({"field": "Q" if src == "Q" else "T", "niso": len(isos), "isovalues": isos,
+                                       "ntri": n, "active_elems": int(torch.unique(te[:n]).numel()) if n else 0})
         del te
         self.covered = 0
-        self.last_ntri = sum(counts)
+        self.last_ntri = total
 
-    def step_async(self):
-        """The same step without host synchronisation (device-side triangle counts)."""
+    def field(self, src, inputs=None):
+        return self.Q if src == "Q" else (inputs or self.inputs)[src]
+
+    def step_async(self, inputs=None, rgba=None, depth=None):
+        """The step without host synchronisation (device-side triangle counts; the second
+        field's triangles are appended behind the first's on the device)."""
         S, ctx, m = self.S, self.ctx, self.mesh
-        S.sem_qcriterion(ctx, m, *self.vel, self.Q)
-        S.sem_isosurface_multi_async(ctx, m, self.Q, self.isos, self.tris, self.counts_dev, cap=self.cap)
-        S.sem_render_async(ctx, self.tris, self.cap, self.counts_dev, len(self.isos), None, self.w.camera, self.W,
-                           self.H, self.rgba, self.depth)
+        inputs = inputs or self.inputs
+        S.sem_qcriterion(ctx, m, *inputs[:3], self.Q)
+        pos = 0
+        for k, (src, isos) in enumerate(self.surfaces):
+            cd = self.counts_dev[pos:pos + len(isos) + 1]
+            fn = S.sem_isosurface_multi_async if k == 0 else S.sem_isosurface_multi_append_async
+            fn(ctx, m, self.field(src, inputs), isos, self.tris, cd, cap=self.cap)
+            pos += len(isos)
+        S.sem_render_async(ctx, self.tris, self.cap, self.counts_dev, self.nseg, self.colours, self.w.camera, self.W,
+                           self.H, self.rgba if rgba is None else rgba, self.depth if depth is None else depth)
 
     def capture(self):
         """One CUDA graph per step: Q -> isosurfaces -> frame."""
-        self.graph = self.capture_with(self.vel, self.rgba, self.depth)
+        self.graph = self.capture_with(self.inputs, self.rgba, self.depth)
 
-    def capture_with(self, vel, rgba, depth):
-        """A graph of the step reading `vel` and writing `rgba`, `depth` (Q, triangles and
+    def capture_with(self, inputs, rgba, depth):
+        """A graph of the step reading `inputs` and writing `rgba`, `depth` (Q, triangles and
         counts are shared: the steps run one after another on one stream)."""
         torch = self.torch
-        keep = (self.vel, self.rgba, self.depth)
-        self.vel, self.rgba, self.depth = vel, rgba, depth
-        self.step_async()  # sizes the library scratch outside the capture
+        self.step_async(inputs, rgba, depth)  # sizes the library scratch outside the capture
         self.S.sem_synchronize(self.ctx)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             self.S.sem_set_stream(self.ctx, torch.cuda.current_stream())
-            self.step_async()
+            self.step_async(inputs, rgba, depth)
         self.S.sem_set_stream(self.ctx, self.stream)
-        self.vel, self.rgba, self.depth = keep
         return g
 
     def step(self, events=None):
+        """The host-synchronised step (exact triangle counts back on the host)."""
         S, ctx, m = self.S, self.ctx, self.mesh
         if events is not None:
             events[0].record(self.stream)
-        S.sem_qcriterion(ctx, m, *self.vel, self.Q)
+        S.sem_qcriterion(ctx, m, *self.inputs[:3], self.Q)
         if events is not None:
             events[1].record(self.stream)
-        seg = S.sem_isosurface_multi(ctx, m, self.Q, self.isos, self.tris, cap=self.cap)
-        off = sum(seg)
+        off, segs = 0, []
+        for src, isos in self.surfaces:
+            c = S.sem_isosurface_multi(ctx, m, self.field(src), isos, self.tris[off * 9:], cap=self.cap - off)
+            segs += c
+            off += sum(c)
         if events is not None:
             events[2].record(self.stream)
-        S.sem_render(ctx, self.tris, off, seg, None, self.w.camera, self.W, self.H, self.rgba, self.depth)
+        S.sem_render(ctx, self.tris, off, segs, self.colours, self.w.camera, self.W, self.H, self.rgba, self.depth)
         if events is not None:
             events[3].record(self.stream)
         self.last_ntri = off
@@ -610,30 +655,18 @@ def measure_batched(S, ctx, steps=20, warmup=3):
             "q_only_per_partition_ms": round(ms_qpp, 4), "q_only_batched_ms": round(ms_qb, 4)}
 
 
-def run_ours(args):
+def _peaks():
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(pp)) if os.path.exists(pp) else {}
+
+
+def time_workload(S, P, K, warmup, local, barrier, use_graph=True):
+    """Per-stage and per-kernel times from K eager traced steps, then the headline: K steps
+    replayed as one CUDA graph each, between a barrier + synchronize on both sides, with the
+    clocks sampled during the timed region."""
     import numpy as np
     import torch
-    import paper_2312_09888_gb300 as S
-
-    rank, world, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    S.get_lib()
-    w = make_workload("cuda")
-    P = Pipeline(S, w, local)
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    K = args.steps
-    # per-stage breakdown (and the roofline kernel's launch time): eager steps, CUDA events on
-    # the library's stream around each call
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         P.step()
     stage_ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
     barrier()
@@ -645,12 +678,9 @@ def run_ours(args):
     S.sem_trace_enable(P.ctx, False)
     P.covered = int((P.rgba.view(-1, 4)[:, 3] > 0).sum())
     stage_ms = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(3)] for e in stage_ev])
-    eager_ms = float(stage_ms.sum(axis=1).mean())
-    # headline: the whole step as one CUDA graph, replayed K times (device-resident inputs)
-    use_graph = not args.no_graph
     if use_graph:
         P.capture()
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             P.graph.replay()
     run_step = P.graph.replay if use_graph else P.step
     clocks = Clocks(local)
@@ -659,182 +689,227 @@ def run_ours(args):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(P.stream)
-    for k in range(K):
+    for _ in range(K):
         run_step()
     t1.record(P.stream)
     barrier()
     clk = clocks.stop()
-    P.S.sem_synchronize(P.ctx)
-    ms = t0.elapsed_time(t1)
-    secs = max_over_ranks(ms / 1e3, "cuda")
+    P.S.sem_synchronize(P.ctx)  # raises if a capacity or timeout flag was set in the graph
+    secs = max_over_ranks(t0.elapsed_time(t1) / 1e3, "cuda")
     total_elems = sum_over_ranks(P.E * K, "cuda")
-    value = aggregate([total_elems], [secs])
-
-    # end to end: every step's velocity from pinned host memory and its frame back to pinned
-    # host memory, pipelined: two device slots; while step k computes (graph replay), a copy
-    # stream brings step k+1's velocity in and another reads step k-1's frame back
-    e2e = None
-    if not args.no_e2e:
-        host_vel = [v.cpu().pin_memory() for v in P.vel]
-        host_img = torch.empty(P.rgba.numel(), dtype=torch.uint8).pin_memory()
-        host_dep = torch.empty(P.depth.numel(), dtype=torch.float32).pin_memory()
-        slots = [(P.vel, P.rgba, P.depth), ([v.clone() for v in P.vel], torch.empty_like(P.rgba),
-                                            torch.empty_like(P.depth))]
-        if use_graph:
-            runs = [P.graph.replay, P.capture_with(*slots[1]).replay]
-        else:
-            def eager_on(slot):
-                def f():
-                    keep = (P.vel, P.rgba, P.depth)
-                    P.vel, P.rgba, P.depth = slot
-                    P.step()
-                    P.vel, P.rgba, P.depth = keep
-                return f
-            runs = [eager_on(slots[0]), eager_on(slots[1])]
-        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        issued = [False, False]
-
-        def e2e_step(k):
-            sl = k % 2
-            vel, rgba, dep = slots[sl]
-            with torch.cuda.stream(h2d):
-                if issued[sl]:
-                    h2d.wait_event(ev_out[sl])  # the slot's previous frame has been read back
-                for d, h in zip(vel, host_vel):
-                    d.copy_(h, non_blocking=True)
-                ev_in[sl].record(h2d)
-            P.stream.wait_event(ev_in[sl])
-            runs[sl]()
-            ev_done[sl].record(P.stream)
-            with torch.cuda.stream(d2h):
-                d2h.wait_event(ev_done[sl])
-                host_img.copy_(rgba, non_blocking=True)
-                host_dep.copy_(dep, non_blocking=True)
-                ev_out[sl].record(d2h)
-            issued[sl] = True
-
-        for k in range(max(2, args.warmup // 2)):
-            e2e_step(k)
-        barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(h2d)
-        for k in range(K):
-            e2e_step(k)
-        b.record(d2h)
-        barrier()
-        es = max_over_ranks(a.elapsed_time(b) / 1e3, "cuda")
-        h2d_bytes = int(sum(h.numel() * 4 for h in host_vel))
-        # the host link's ceiling: the same copy-in alone, back to back on the copy stream
-        for _ in range(2):
-            a.record(h2d)
-            for _ in range(10):
-                for d, h in zip(slots[1][0], host_vel):
-                    d.copy_(h, non_blocking=True)
-            b.record(h2d)
-            b.synchronize()
-        link = 10 * h2d_bytes / (a.elapsed_time(b) / 1e3) / 1e9
-        step_gbs = h2d_bytes / (es / K) / 1e9
-        e2e = {"value": aggregate([total_elems], [es]), "unit": UNIT,
-               "h2d_bytes_per_step": h2d_bytes,
-               "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4),
-               "ms_per_step": es * 1e3 / K,
-               "h2d_gbs": round(step_gbs, 1), "h2d_link_gbs": round(link, 1),
-               "frac_of_link": round(step_gbs / link, 3),
-               "pipelining": "two device slots; copy-in of step k+1 and read-back of step k-1 overlap step k"}
-
-    # roofline of the dominant kernel: its CUDA-event launch time from the library's kernel trace
-    # (events on the library's stream around each launch, eager steps above)
     mean_stage = stage_ms.mean(axis=0)
-    peaks = {}
-    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pp):
-        peaks = json.load(open(pp))
-    hbm_peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm_peak else "fallback"
-    hbm_peak = hbm_peak or 6800.0
+    return {"value": aggregate([total_elems], [secs]), "secs": secs, "trace": trace, "clocks": clk,
+            "stage_ms": {"qcriterion": round(float(mean_stage[0]), 4),
+                         "isosurface_all": round(float(mean_stage[1]), 4),
+                         "render": round(float(mean_stage[2]), 4),
+                         "eager_step": round(float(stage_ms.sum(axis=1).mean()), 4)}}
+
+
+def kernel_table(P, trace, K, hbm_peak, workload):
+    """Per-kernel CUDA-event times (library trace) with algorithmic bytes and the fraction of
+    the HBM peak, and the roofline object of the dominant kernel."""
     kernels = {}
     for name, (tot_ms, n) in trace.items():
-        kb = algorithmic_bytes(name, P)
+        per_step = algorithmic_bytes_per_step(name, P)
         ent = {"ms_per_step": round(tot_ms / K, 5), "launches_per_step": n / K}
-        if kb is not None and n:
-            gbs = kb / (tot_ms / n * 1e-3) / 1e9
-            ent.update({"algorithmic_bytes_per_launch": int(kb), "achieved_gbs": round(gbs, 1),
+        if per_step is not None and n:
+            per_launch = per_step * K / n
+            gbs = per_launch / (tot_ms / n * 1e-3) / 1e9
+            ent.update({"algorithmic_bytes_per_launch": int(per_launch), "achieved_gbs": round(gbs, 1),
                         "frac": round(gbs / hbm_peak, 4)})
         kernels[name] = ent
     dom = max(trace, key=lambda k: trace[k][0])
     dom_ms = trace[dom][0] / trace[dom][1]
-    dom_bytes = algorithmic_bytes(dom, P)
+    per_step = algorithmic_bytes_per_step(dom, P)
+    dom_bytes = per_step * K / trace[dom][1] if per_step is not None else None
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
-            "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-            "frac": round(achieved / hbm_peak, 4) if achieved else None,
-            "traffic": _traffic_for(dom), "algorithmic_bytes_per_launch": dom_bytes,
-            "launch_ms": round(dom_ms, 5)}
-    launches_per_step = sum(n for _, n in trace.values()) / K
+    return kernels, {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4) if achieved else None,
+                     "traffic": _traffic_for(dom, workload),
+                     "algorithmic_bytes_per_launch": int(dom_bytes) if dom_bytes else None,
+                     "launch_ms": round(dom_ms, 5)}
+
+
+def measure_e2e(P, K, warmup, barrier):
+    """End to end through the C ABI: every step's inputs (velocity, and temperature where the
+    workload has it) from pinned host memory and its frame (RGBA + depth) back to pinned host
+    memory, pipelined over two device slots: while step k computes (graph replay), a copy stream
+    brings step k+1's inputs in and another reads step k-1's frame back."""
+    import torch
+    host_in = [v.cpu().pin_memory() for v in P.inputs]
+    host_img = torch.empty(P.rgba.numel(), dtype=torch.uint8).pin_memory()
+    host_dep = torch.empty(P.depth.numel(), dtype=torch.float32).pin_memory()
+    slots = [(P.inputs, P.rgba, P.depth),
+             ([v.clone() for v in P.inputs], torch.empty_like(P.rgba), torch.empty_like(P.depth))]
+    runs = [P.graph.replay, P.capture_with(*slots[1]).replay]
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in, ev_done, ev_out = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    issued = [False, False]
+
+    def e2e_step(k):
+        sl = k % 2
+        ins, rgba, dep = slots[sl]
+        with torch.cuda.stream(h2d):
+            if issued[sl]:
+                h2d.wait_event(ev_out[sl])  # the slot's previous frame has been read back
+            for d, h in zip(ins, host_in):
+                d.copy_(h, non_blocking=True)
+            ev_in[sl].record(h2d)
+        P.stream.wait_event(ev_in[sl])
+        runs[sl]()
+        ev_done[sl].record(P.stream)
+        with torch.cuda.stream(d2h):
+            d2h.wait_event(ev_done[sl])
+            host_img.copy_(rgba, non_blocking=True)
+            host_dep.copy_(dep, non_blocking=True)
+            ev_out[sl].record(d2h)
+        issued[sl] = True
+
+    for k in range(max(2, warmup // 2)):
+        e2e_step(k)
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(h2d)
+    for k in range(K):
+        e2e_step(k)
+    b.record(d2h)
+    barrier()
+    es = max_over_ranks(a.elapsed_time(b) / 1e3, "cuda")
+    h2d_bytes = int(sum(h.numel() * 4 for h in host_in))
+    # the host link's ceiling: the same copy-in alone, back to back on the copy stream
+    for _ in range(2):
+        a.record(h2d)
+        for _ in range(3):
+            for d, h in zip(slots[1][0], host_in):
+                d.copy_(h, non_blocking=True)
+        b.record(h2d)
+        b.synchronize()
+    link = 3 * h2d_bytes / (a.elapsed_time(b) / 1e3) / 1e9
+    step_gbs = h2d_bytes / (es / K) / 1e9
+    total_elems = sum_over_ranks(P.E * K, "cuda")
+    P.S.sem_synchronize(P.ctx)
+    del slots
+    return {"value": aggregate([total_elems], [es]), "unit": UNIT, "h2d_bytes_per_step": h2d_bytes,
+            "d2h_bytes_per_step": int(host_img.numel() + host_dep.numel() * 4), "ms_per_step": es * 1e3 / K,
+            "h2d_gbs": round(step_gbs, 1), "h2d_link_gbs": round(link, 1), "frac_of_link": round(step_gbs / link, 3),
+            "pipelining": "two device slots; copy-in of step k+1 and read-back of step k-1 overlap step k"}
+
+
+def run_ours(args):
+    import torch
+    import paper_2312_09888_gb300 as S
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    S.get_lib()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    K = args.steps
+    w = make_workload(args.workload, "cuda")
+    mesh_cpu = w.mesh
+    camera = w.camera
+    P = Pipeline(S, w, local)
+    del w
+    head = time_workload(S, P, K, args.warmup, local, barrier, use_graph=not args.no_graph)
+    kernels, roof = kernel_table(P, head["trace"], K, hbm_peak, args.workload)
+    roof["peak_source"] = peak_src
+    launches_per_step = sum(n for _, n in head["trace"].values()) / K
+    e2e = None
+    if not args.no_e2e and not args.no_graph:
+        e2e = measure_e2e(P, K, args.warmup, barrier)
 
     qprec = None
     if args.q_precisions:
-        # sem_qcriterion alone at each arithmetic (CUDA events, 50 launches after 5 warm-up)
+        # sem_qcriterion alone at each arithmetic (CUDA events, 20 launches after 3 warm-up)
         qprec = {}
         for name in ("FP32", "BF16", "FP16", "BF16X2", "TF32"):
             prec = getattr(S, "SEM_" + name)
-            for _ in range(5):
-                S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q, prec)
+            for _ in range(3):
+                S.sem_qcriterion(P.ctx, P.mesh, *P.inputs[:3], P.Q, prec)
             qa, qb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             qa.record(P.stream)
-            for _ in range(50):
-                S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q, prec)
+            for _ in range(20):
+                S.sem_qcriterion(P.ctx, P.mesh, *P.inputs[:3], P.Q, prec)
             qb.record(P.stream)
             torch.cuda.synchronize()
-            us = qa.elapsed_time(qb) / 50 * 1e3
+            us = qa.elapsed_time(qb) / 20 * 1e3
             qprec[name] = {"us": round(us, 2), "gbs": round(16 * P.npts / (us * 1e-6) / 1e9, 1)}
-        S.sem_qcriterion(P.ctx, P.mesh, *P.vel, P.Q)
+        S.sem_qcriterion(P.ctx, P.mesh, *P.inputs[:3], P.Q)
 
     mem_now, mem_peak = S.sem_memory(P.ctx)
     torch_peak = int(torch.cuda.max_memory_allocated())  # the caller's buffers (torch allocator)
-    batched = measure_batched(S, P.ctx) if args.batched else None
-    curved = measure_curved(S, P.ctx, P.vel, P.mesh) if args.curved else None
-    learned = None
-    if not args.no_learned:
-        bpk = peaks.get("bf16_tflops")
-        learned = measure_learned(S, P.ctx, bpk or 1900.0, "measured" if bpk else "fallback")
-
+    emit_units = [c for c in S.sem_autotune_emit_choices(P.ctx) if c[:2] == (P.N, P.E)]
+    surfaces = P.surface_stats
+    W, H, ntri, npts, E, N = P.W, P.H, int(P.last_ntri), P.npts, P.E, P.N
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, P.isos, budget_s=args.cpu_seconds)
+        cpu = cpu_baseline(mesh_cpu, P, camera, budget_s=args.cpu_seconds)
+    # the headline's buffers are released before the secondary measurements
+    P.sess.close()
+    del P
+    torch.cuda.empty_cache()
 
-    n_iso = len(P.isos)
+    extra = {}
+    if not args.no_extra and args.workload != "channel32":
+        w2 = make_workload("channel32", "cuda")
+        P2 = Pipeline(S, w2, local)
+        del w2
+        r2 = time_workload(S, P2, K, args.warmup, local, barrier, use_graph=not args.no_graph)
+        k2, roof2 = kernel_table(P2, r2["trace"], K, hbm_peak, "channel32")
+        extra["channel32"] = {"workload": WORKLOADS["channel32"], "value": round(r2["value"], 1), "unit": UNIT,
+                              "ms_per_step": round(r2["secs"] * 1e3 / K, 4),
+                              "frames_per_s": round(K * world / r2["secs"], 2), "triangles": int(P2.last_ntri),
+                              "stage_ms": r2["stage_ms"], "kernels": k2, "roofline": roof2, "clocks": r2["clocks"]}
+        if args.curved:
+            extra["channel32"]["curved"] = measure_curved(S, P2.ctx, P2.inputs[:3], P2.mesh)
+        P2.sess.close()
+        del P2
+        torch.cuda.empty_cache()
+
+    ctx2 = S.sem_create(local, torch.cuda.current_stream())
+    try:
+        batched = measure_batched(S, ctx2) if args.batched else None
+        learned = None
+        if not args.no_learned:
+            bpk = peaks.get("bf16_tflops")
+            learned = measure_learned(S, ctx2, bpk or 1900.0, "measured" if bpk else "fallback")
+    finally:
+        S.sem_destroy(ctx2)
+
+    value, secs = head["value"], head["secs"]
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / K, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "frames_per_s": round(K * world / secs, 2),
-           "config": {"workload": WORKLOAD, "elements": P.E, "order": w.mesh.N, "nodes": P.npts,
-                      "isovalues": w.iso_fracs, "image": [P.W, P.H], "triangles": int(P.last_ntri),
-                      "l2": "inputs 201 MB of velocity > 129 MB L2 (no flush)",
+           "config": {"workload": WORKLOADS[args.workload], "elements": E, "order": N, "nodes": npts,
+                      "surfaces": surfaces, "image": [W, H], "triangles": ntri,
+                      "l2": f"inputs {sum(4 * npts for _ in range(3 + (len(surfaces) > 1))) / 1e9:.2f} GB "
+                            "> 129 MB L2 (no flush)",
                       "parallelism": f"replicas x{world}"},
-           "step_mode": "cuda_graph" if use_graph else "eager",
-           "stage_ms": {"qcriterion": round(float(mean_stage[0]), 4),
-                        "isosurface_all": round(float(mean_stage[1]), 4),
-                        "render": round(float(mean_stage[2]), 4), "eager_step": round(eager_ms, 4)},
-           "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+           "step_mode": "eager" if args.no_graph else "cuda_graph",
+           "stage_ms": head["stage_ms"], "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": head["clocks"],
            "kernels": kernels, "gpu_launches": int(round(launches_per_step * K)),
            "memory": {"library_bytes_in_use": mem_now, "library_bytes_peak": mem_peak,
                       "caller_buffers_bytes_peak": torch_peak},
-           "learned": learned}
-    emit_units = [c for c in S.sem_autotune_emit_choices(P.ctx) if c[:3] == (w.mesh.N, P.E, len(P.isos))]
-    out["autotune"] = {"emit_units_per_atomic": emit_units[0][3] if emit_units else None,
-                       "gemm_shapes_tuned": len(S.sem_autotune_choices(P.ctx))}
+           "autotune": {"emit_units_per_atomic": sorted({c[3] for c in emit_units}) or None},
+           "extra": extra or None, "learned": learned}
     if qprec is not None:
         out["q_precisions"] = qprec
     if batched is not None:
         out["batched"] = batched
-    if curved is not None:
-        out["curved"] = curved
-    P.sess.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -843,51 +918,85 @@ def run_ours(args):
 
 # ------------------------------------------------------------------------------------ CPU oracle
 
-def _oracle_sample(w, isos, nelem, seed=0):
-    import numpy as np
+def _slab(mesh, inputs, e0, nelem):
+    """Host FP64 copies of elements [e0, e0 + nelem): node coordinates and the FP32 inputs the
+    GPU reads (velocity, and temperature where present), promoted exactly."""
     import torch
-    rng = np.random.default_rng(seed)
-    E = w.E
-    e0 = int(rng.integers(0, max(1, E - nelem)))
-    idx = torch.arange(e0, e0 + nelem, device=w.fields.device)
-    xyz = w.mesh.xyz(w.fields.device)[:, idx].cpu().numpy()
-    vel = w.fields[:, idx].float().double().cpu().numpy()
-    return xyz, vel
+    idx = torch.arange(e0, e0 + nelem, device=inputs[0].device)
+    return mesh.xyz_range(e0, e0 + nelem), [t.view(-1, (mesh.N + 1) ** 3)[idx].double().cpu().numpy()
+                                            for t in inputs]
 
 
-def _oracle_step(oracle, N, xyz, vel, isos, cam):
+def _oracle_step(oracle, N, xyz, fields, surfaces, colours, cam):
+    """One step of the oracle on a slab: Q from the velocity, every surface's isosurfaces, and
+    one full-size frame of the slab's triangles."""
     import numpy as np
-    Q = oracle.qcriterion(N, xyz, vel)
+    Q = oracle.qcriterion(N, xyz, np.stack(fields[:3]))
     tris, seg = [], []
-    for iso in isos:
-        r = oracle.isosurface(N, xyz, Q, iso)
-        tris.append(r["tris"])
-        seg.append(r["ntri"])
+    for src, isos in surfaces:
+        f = Q if src == "Q" else fields[src]
+        for iso in isos:
+            r = oracle.isosurface(N, xyz, f, iso)
+            tris.append(r["tris"])
+            seg.append(r["ntri"])
     allt = np.concatenate(tris) if tris else np.zeros((0, 3, 3))
-    oracle.render(allt, seg, [[0.9, 0.35, 0.25], [0.25, 0.6, 0.9], [0.35, 0.85, 0.4]][:len(seg)], cam)
+    oracle.render(allt, seg, colours[:len(seg)], cam)
 
 
-def cpu_baseline(w, isos, budget_s=15.0, nelem=1024):
-    """Times the FP64 oracle (single thread) on a contiguous slab of ``nelem`` elements of the
-    same workload -- Q, all isovalues, and a full-size frame of the slab's triangles --
-    repeating until ``budget_s`` of CPU time; elements/s = elements processed / seconds."""
+_PALETTE = [[0.9, 0.35, 0.25], [0.25, 0.6, 0.9], [0.35, 0.85, 0.4]]
+
+
+def _oracle_run(slabs, N, surfaces, colours, cam, threads, budget_s=None, reps=None):
+    """Runs the oracle step on every slab, one slab per thread, repeated until `budget_s` seconds
+    (or `reps` times); the ctypes calls release the GIL, so the threads run on separate host
+    cores.  Returns (elements processed, seconds)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import oracle
+
+    def worker(slab):
+        xyz, fields = slab
+        done, t0 = 0, time.perf_counter()
+        while True:
+            _oracle_step(oracle, N, xyz, fields, surfaces, colours, cam)
+            done += xyz.shape[1]
+            if (reps is not None and done >= reps * xyz.shape[1]) or \
+                    (budget_s is not None and time.perf_counter() - t0 >= budget_s):
+                return done
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        done = sum(ex.map(worker, slabs[:threads]))
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(mesh, P, cam, budget_s=15.0):
+    """Times the FP64 oracle on slabs of 1/64 of the elements (contiguous, spread over the mesh) of
+    the same workload -- Q, every isosurface, and a full-size frame of the slab's triangles --
+    once on one thread and once with one thread per host core, each for about `budget_s`
+    seconds; elements/s = elements processed / wall seconds."""
     import oracle
     oracle.lib()
-    xyz, vel = _oracle_sample(w, isos, nelem)
-    done, t0 = 0, time.perf_counter()
-    while True:
-        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
-        done += nelem
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return {"value": round(done / el, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nelem} contiguous elements of the workload (Q + {len(isos)} isosurfaces + "
-                      f"{w.camera['W']}x{w.camera['H']} frame), repeated {done // nelem}x in {el:.1f} s"}
+    cores = os.cpu_count() or 1
+    nelem = max(64, P.E // 64)
+    colours = P.colours or _PALETTE
+    starts = [(t * (P.E // cores)) // nelem * nelem for t in range(cores)]
+    slabs = [_slab(mesh, P.inputs, min(e0, P.E - nelem), nelem) for e0 in starts]
+    _oracle_step(oracle, P.N, *slabs[0], P.surfaces, colours, cam)  # builds the oracle's case table once
+    d1, s1 = _oracle_run(slabs, P.N, P.surfaces, colours, cam, 1, budget_s=budget_s)
+    dn, sn = _oracle_run(slabs, P.N, P.surfaces, colours, cam, cores, budget_s=budget_s)
+    what = (f"slabs of {nelem} contiguous elements (1/64 of the mesh) of the workload: Q + "
+            f"{sum(len(i) for _, i in P.surfaces)} isosurfaces + a {P.W}x{P.H} frame of the slab's triangles")
+    single = {"value": round(d1 / s1, 2), "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{what}; one thread, {d1 // nelem} slab steps in {s1:.1f} s"}
+    return {"value": round(dn / sn, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what}; one thread per core on {cores} cores (nproc), each on its own slab, "
+                      f"{dn // nelem} slab steps in {sn:.1f} s",
+            "single_thread": single}
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    """The reference arm: the FP64 CPU oracle, as it stands, on all host cores (one thread per
+    core, each on its own slab of the workload); each step is one slab per thread."""
     import numpy as np
     import torch
     rank, world, _ = _dist()
@@ -896,25 +1005,37 @@ def run_reference(args):
     import oracle
     oracle.lib()
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    w = make_workload(dev)
-    import paper_2312_09888_gb300  # noqa: F401  (isovalues come from the oracle's own Q below)
-    nelem = args.ref_elements
-    xyz, vel = _oracle_sample(w, None, nelem)
-    Q = oracle.qcriterion(w.mesh.N, xyz, vel)
-    isos = [float(np.float32(f * Q.max())) for f in w.iso_fracs]
-    for _ in range(args.warmup):
-        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        _oracle_step(oracle, w.mesh.N, xyz, vel, isos, w.camera)
-    el = time.perf_counter() - t0
-    value = nelem * args.steps / el
-    sample = f"each step: {nelem} contiguous elements of the workload (Q + {len(isos)} isosurfaces + frame)"
+    w = make_workload(args.workload, dev)
+    N, E = w.mesh.N, w.E
+    inputs = [w.fields[c].float().contiguous() for c in range(w.fields.shape[0])]
+    cam, mesh, fracs, extra = w.camera, w.mesh, w.iso_fracs, dict(w.extra)
+    del w
+    cores = os.cpu_count() or 1
+    nelem = args.ref_elements if args.ref_elements else max(64, E // 64)
+    starts = [(t * (E // cores)) // nelem * nelem for t in range(cores)]
+    slabs = [_slab(mesh, inputs, min(e0, E - nelem), nelem) for e0 in starts]
+    del inputs
+    # isovalues from the oracle's own Q on the first slab (the full field's max would need the
+    # oracle on every element)
+    Q0 = oracle.qcriterion(N, slabs[0][0], np.stack(slabs[0][1][:3]))
+    surfaces = [("Q", [float(np.float32(f * Q0.max())) for f in fracs])]
+    if "t_iso" in extra:
+        surfaces.append((3, [float(np.float32(extra["t_iso"]))]))
+    colours = RB_COLOURS if len(surfaces) > 1 else _PALETTE
+    _oracle_step(oracle, N, *slabs[0], surfaces, colours, cam)  # builds the oracle's case table once
+    if args.warmup:
+        _oracle_run(slabs, N, surfaces, colours, cam, cores, reps=args.warmup)
+    done, el = _oracle_run(slabs, N, surfaces, colours, cam, cores, reps=args.steps)
+    value = done / el
+    sample = (f"each step: one slab of {nelem} contiguous elements per thread, {cores} threads on {cores} cores "
+              f"(nproc), slabs spread over the mesh (Q + {sum(len(i) for _, i in surfaces)} isosurfaces + "
+              f"a {cam['W']}x{cam['H']} frame of the slab's triangles); Q isovalue from the first slab's max Q")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD},
-           "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOADS[args.workload]},
+           "cpu_baseline": {"value": round(value, 2), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -922,21 +1043,25 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(WORKLOADS),
+                    help="rb64: the 64^3-element two-field 3840x2160 workload (headline); channel32: 32^3 channel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of the captured graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary 32^3 channel measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the autoencoder measurement")
     ap.add_argument("--curved", action="store_true",
-                    help="also time sem_qcriterion on a general (curved) mesh of the same size (curved)")
+                    help="also time sem_qcriterion on a general (curved) 32^3 mesh (extra.channel32.curved)")
     ap.add_argument("--batched", action="store_true",
                     help="also time the batching workload: plain path vs CUDA graph vs batched Q (batched)")
     ap.add_argument("--q-precisions", action="store_true",
                     help="also time sem_qcriterion at FP32, BF16, FP16, split BF16 and TF32 (q_precisions)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-elements", type=int, default=512)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-elements", type=int, default=0,
+                    help="reference arm: elements per slab (default 1/64 of the mesh)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

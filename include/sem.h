@@ -218,6 +218,22 @@ SEM_API sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *mesh
                                               const float *isos_host, int niso, float *tris, int32_t *tri_elem,
                                               int64_t cap, int64_t *counts_dev, uint8_t *cases);
 
+/* sem_isosurface_multi_async appending behind triangles already in `tris`, so that the
+ * isosurfaces of several fields (e.g. Q and temperature) fill one buffer back to back and one
+ * sem_render_async draws them as consecutive segments, all without host synchronisation.
+ * counts_dev (device int64[niso + 1]) is read and written on the device: counts_dev[0] is an
+ * INPUT, the index in tris of this call's first triangle (typically the last entry an earlier
+ * sem_isosurface_multi_async or append call wrote, i.e. pass that call's counts_dev + its niso);
+ * the call writes counts_dev[q] = counts_dev[0] + (triangles of isovalues 0..q-1) for
+ * q = 1..niso.  cap is the capacity of the whole buffer from tris[0]; if counts_dev[0] plus this
+ * call's total exceeds it, no triangle is written and the device flag records
+ * SEM_ERR_CAPACITY (reported by sem_synchronize).  Triangle order and everything else as
+ * sem_isosurface_multi_async (same scratch rule under stream capture). */
+SEM_API sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mesh *mesh, const float *f,
+                                                     const float *isos_host, int niso, float *tris,
+                                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev,
+                                                     uint8_t *cases);
+
 /* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
 #define SEM_NOALLOC_MAX_ELEMENTS 262144
 

@@ -71,6 +71,7 @@ def _declare(L):
     L.sem_isosurface.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_isosurface_multi.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_multi_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
+    L.sem_isosurface_multi_append_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
@@ -101,7 +102,8 @@ def _declare(L):
     L.sem_autotune_emit_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                           C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
-                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async", "sem_render_async",
+                 "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
+                 "sem_isosurface_multi_append_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
@@ -304,6 +306,25 @@ def sem_isosurface_multi_async(ctx, mesh, f, isos, tris, counts_dev, tri_elem=No
                                               _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap),
                                               _dev(counts_dev, "counts_dev", torch.int64),
                                               _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st)
+
+
+def sem_isosurface_multi_append_async(ctx, mesh, f, isos, tris, counts_dev, tri_elem=None, cases=None,
+                                      cap: Optional[int] = None) -> None:
+    """As sem_isosurface_multi_async, appending behind triangles already in ``tris``:
+    counts_dev[0] (device) is read as the index of the first triangle written, counts_dev[1:]
+    receive the segment ends (counts_dev: int64 CUDA tensor of len(isos) + 1, e.g. a view
+    starting at an earlier call's last entry).  ``cap`` is the whole buffer's capacity."""
+    import torch
+    iv = np.ascontiguousarray(np.asarray(isos, dtype=np.float32).reshape(-1))
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    st = get_lib().sem_isosurface_multi_append_async(ctx, mesh, _dev(f, "f", torch.float32),
+                                                     iv.ctypes.data_as(C.c_void_p), len(iv),
+                                                     _dev(tris, "tris", torch.float32, allow_none=True),
+                                                     _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
+                                                     int(cap), _dev(counts_dev, "counts_dev", torch.int64),
+                                                     _dev(cases, "cases", torch.uint8, allow_none=True))
     _check(ctx, st)
 
 

@@ -726,6 +726,35 @@ sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *m, const flo
     return iso_run_multi_async(ctx, m, f, isos, niso, tris, tri_elem, cap, counts_dev, cases);
 }
 
+sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos,
+                                             int niso, float *tris, int32_t *tri_elem, int64_t cap,
+                                             int64_t *counts_dev, uint8_t *cases)
+{
+    SEM_TRY(check_common(ctx, m, "sem_isosurface_multi_append_async"));
+    if (!isos || niso < 1 || niso > SEM_MAX_ISO)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_append_async: need 1 <= niso <= %d isovalues",
+                        SEM_MAX_ISO);
+    for (int q = 0; q < niso; ++q)
+        if (isnan(isos[q]))
+            return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_append_async: isovalue %d is NaN", q);
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_append_async: negative cap");
+    SEM_TRY(check_ptr(ctx, counts_dev, "sem_isosurface_multi_append_async", "counts_dev", false, 8));
+    if (m->E * (int64_t)niso > ((int64_t)1 << 31))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_multi_append_async: E*niso too large");
+    SEM_TRY(check_ptr(ctx, f, "sem_isosurface_multi_append_async", "f", m->E == 0));
+    SEM_TRY(check_ptr(ctx, tris, "sem_isosurface_multi_append_async", "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, "sem_isosurface_multi_append_async", "tri_elem", true, 4));
+    SEM_TRY(check_ptr(ctx, cases, "sem_isosurface_multi_append_async", "cases", true));
+    if (m->E == 0) {
+        // no triangles: every segment end equals the start
+        for (int q = 1; q <= niso; ++q)
+            SEM_CU(ctx, cudaMemcpyAsync(counts_dev + q, counts_dev, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                                        ctx->stream));
+        return SEM_OK;
+    }
+    return iso_run_multi_async(ctx, m, f, isos, niso, tris, tri_elem, cap, counts_dev, cases, true);
+}
+
 sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
                             const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
 {

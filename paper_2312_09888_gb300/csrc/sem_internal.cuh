@@ -143,7 +143,8 @@ sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, f
 sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso, float *tris,
                          int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
-                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases);
+                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases,
+                               bool append = false);
 sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                            int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,

@@ -460,14 +460,18 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
                                                                  float *__restrict__ tris,
                                                                  int32_t *__restrict__ tri_elem, int64_t cap,
                                                                  int *flag, unsigned long long *__restrict__ next,
-                                                                 int units, const float *__restrict__ xyzn)
+                                                                 int units, const float *__restrict__ xyzn,
+                                                                 const int64_t *__restrict__ base)
 {
     using EW = EmitW<NP>;
     using G = MaskGeo<NP>;
     constexpr int N = G::N;
     const int64_t U = (int64_t)S.niso * E;
+    // index of the first triangle in `tris`: 0, or (appending behind an earlier call's
+    // segments) a value another kernel wrote on the device
+    const int64_t b0 = base ? *base : 0;
     // all-or-nothing capacity check (the host-synchronised path has checked already)
-    if (offs[U] > cap) {
+    if (b0 + offs[U] > cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicOr(flag, 1 << SEM_ERR_CAPACITY);
         return;
     }
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
         if (u0 >= (unsigned long long)U) break;
         const int64_t u1 = min((int64_t)u0 + units, U);
         for (int64_t u = (int64_t)u0; u < u1; ++u) {
-            const int64_t o = offs[u], n = offs[u + 1] - o;
+            const int64_t o = b0 + offs[u], n = offs[u + 1] - offs[u];
             if (n <= 0 || o + n > cap) continue;
             const int q = (int)(u / E);
             const int64_t e = u - (int64_t)q * E;
@@ -619,7 +623,8 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
 
 template <int NP, bool GENERAL>
 static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                                float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
+                                float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units,
+                                const int64_t *base)
 {
     constexpr int EV = EmitW<NP>::V;
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
@@ -635,7 +640,7 @@ static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f,
     const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
     SEM_TRACED(ctx, "k_iso_emit_m", kern<<<grid, 32 * EV, dyn, ctx->stream>>>(f, S, m->E, offs, m->lo, m->hi, tris,
                                                                              tri_elem, cap, ctx->d_flag, next, units,
-                                                                             m->xyzn));
+                                                                             m->xyzn, base));
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
 }
 
@@ -643,10 +648,11 @@ static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f,
 // `next` zeroed first; box meshes and general meshes have their own instantiation.
 template <int NP>
 static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units)
+                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units,
+                              const int64_t *base)
 {
-    if (m->curved) return launch_emit_k<NP, true>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
-    return launch_emit_k<NP, false>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
+    if (m->curved) return launch_emit_k<NP, true>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
+    return launch_emit_k<NP, false>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
 }
 
 // The emit launch with the context's autotuner: the first emitting call of a given (order,
@@ -656,15 +662,16 @@ static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, c
 // choice.  Under stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
 template <int NP>
 static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                       float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next)
+                       float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next,
+                       const int64_t *base = nullptr)
 {
     for (const auto &t : ctx->emit_tune)
         if (t.N == m->N && t.E == m->E && t.niso == S.niso)
-            return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, t.units);
+            return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, t.units, base);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
     if (!ctx->autotune || cs != cudaStreamCaptureStatusNone)
-        return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, EMIT_UNITS_DEFAULT);
+        return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, EMIT_UNITS_DEFAULT, base);
     cudaEvent_t e0, e1;
     SEM_CU(ctx, cudaEventCreate(&e0));
     SEM_CU(ctx, cudaEventCreate(&e1));
@@ -674,7 +681,7 @@ static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const Is
     for (int units : {1, 2, 4, 8}) {
         for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
             if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
-            if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units);
+            if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
             if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
         }
         if (st != SEM_OK) break;
@@ -724,11 +731,20 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
 }
 
+// Segment ends of an appending call: counts_dev[0] (written earlier on the device) is the first
+// triangle's index, counts_dev[q] = counts_dev[0] + offs[q E] for q = 1..niso.
+__global__ void k_seg_ends(const int64_t *__restrict__ offs, int64_t E, int niso, int64_t *__restrict__ counts_dev)
+{
+    const int q = threadIdx.x + 1;
+    if (q <= niso) counts_dev[q] = counts_dev[0] + offs[(int64_t)q * E];
+}
+
 // No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
-// raises the context's device flag and writes no triangle.
+// raises the context's device flag and writes no triangle.  With `append`, counts_dev[0] is an
+// input (the first triangle's index in tris) and only counts_dev[1..niso] are written.
 template <int NP>
 static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, float *tris,
-                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases)
+                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases, bool append)
 {
     const int64_t E = m->E, n = E * S.niso;
     const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
@@ -743,14 +759,20 @@ static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const floa
         f, S, E, cnt, cases));
     SEM_CU(ctx, cudaGetLastError());
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
-    SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t), S.niso + 1,
-                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    if (append) {
+        SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(offs, E, S.niso, counts_dev));
+        SEM_CU(ctx, cudaGetLastError());
+    } else {
+        SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t),
+                                      S.niso + 1, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     if (!tris) return SEM_OK;
-    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
+    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, append ? counts_dev : nullptr);
 }
 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
-                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases)
+                               float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases,
+                               bool append)
 {
     IsoSet S;
     memset(&S, 0, sizeof S);
@@ -758,7 +780,7 @@ sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     for (int q = 0; q < niso; ++q) S.iso[q] = isos[q];
     switch (m->N + 1) {
 #define SEM_CASE(NPV) \
-    case NPV: return iso_multi_async_np<NPV>(ctx, m, f, S, tris, tri_elem, cap, counts_dev, cases);
+    case NPV: return iso_multi_async_np<NPV>(ctx, m, f, S, tris, tri_elem, cap, counts_dev, cases, append);
         SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
         SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
 #undef SEM_CASE

@@ -136,6 +136,18 @@ class BoxMesh:
         return torch.stack([self.gather(X.contiguous(), idx), self.gather(Y.contiguous(), idx),
                             self.gather(Z.contiguous(), idx)])
 
+    def xyz_range(self, e0: int, e1: int) -> np.ndarray:
+        """(3, e1-e0, NP^3) float64 node coordinates of elements [e0, e1) only (the same values
+        as xyz()[:, e0:e1], without building the whole mesh)."""
+        gx, gy, gz = self.global_axes()
+        NP, N = self.NP, self.N
+        e = np.arange(e0, e1, dtype=np.int64)
+        ex, ey, ez = e % self.nex, (e // self.nex) % self.ney, e // (self.nex * self.ney)
+        n = np.arange(NP ** 3, dtype=np.int64)
+        i, j, k = n % NP, (n // NP) % NP, n // (NP * NP)
+        return np.stack([gx[ex[:, None] * N + i[None, :]], gy[ey[:, None] * N + j[None, :]],
+                         gz[ez[:, None] * N + k[None, :]]])
+
     def grids(self, device="cpu"):
         """Broadcastable global coordinate grids X[1,1,nx], Y[1,ny,1], Z[nz,1,1]."""
         gx, gy, gz = (torch.as_tensor(a, dtype=torch.float64, device=device) for a in self.global_axes())

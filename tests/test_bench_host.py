@@ -1,6 +1,6 @@
 """bench.py's host-side contract, on the CPU: the reference arm's JSON line (the FP64 oracle
-timed on a bounded sample of the benchmark workload) and the source hash that keeps a counter
-capture matched to its kernel."""
+timed on bounded samples of a benchmark workload, one thread per host core) and the source hash
+that keeps a counter capture matched to its kernel."""
 import json
 import os
 import subprocess
@@ -10,8 +10,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                        "--ref-elements", "4"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "channel32", "--steps", "1",
+                        "--warmup", "0", "--ref-elements", "4"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     d = json.loads(r.stdout.strip().splitlines()[-1])
     assert d["impl"] == "reference"
@@ -22,6 +23,8 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("channel 32x32x32")
+    # one oracle thread per host core, each on its own slab
+    assert d["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
 
 
 def test_source_hash_ignores_comments_only(tmp_path):

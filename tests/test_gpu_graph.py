@@ -230,3 +230,99 @@ def test_qcriterion_batch_equals_per_partition_calls(gpu, sess):
     S.sem_synchronize(sess.ctx)
     for a, b in zip(got2, ref):
         assert torch.equal(a, b)
+
+
+def _two_field_case(nel=5):
+    """The Rayleigh-Benard-like field on a small box: velocity (Q) and temperature."""
+    import math
+    mesh = si.BoxMesh(7, np.linspace(0, 2 * math.pi, nel + 1), np.linspace(0, 2 * math.pi, nel + 1),
+                      np.linspace(0, 1.0, nel + 1))
+    f = si.rayleigh_benard(mesh, 64, si.seed_for(3, 5))
+    cam = si.box_camera_persp((0.0, 0.0, 0.0), (2 * math.pi, 2 * math.pi, 1.0), 320, 180,
+                              direction=(1.0, -1.2, 0.8), up=(0.0, 0.0, 1.0))
+    return mesh, f, cam
+
+
+def test_append_second_field_in_one_graph(gpu, sess):
+    """Q isosurfaces then the temperature's appended behind them on the device (counts_dev[0] of
+    the second call is the first call's total), drawn by one sem_render_async as consecutive
+    segments, captured in one graph: triangles, segment starts and frame equal the
+    host-synchronised calls written back to back."""
+    S = gpu
+    mesh, f, cam = _two_field_case()
+    m = sess.mesh(7, mesh.xyz().numpy())
+    vel = [f[c].float().cuda().contiguous() for c in range(3)]
+    T = f[3].float().cuda().contiguous()
+    Q = torch.empty_like(vel[0])
+    S.sem_qcriterion(sess.ctx, m, *vel, Q)
+    qmax = S.sem_field_max(sess.ctx, Q)
+    qisos = [float(np.float32(0.1 * qmax)), float(np.float32(0.3 * qmax))]
+    tisos = [0.5]
+    cq = S.sem_isosurface_multi(sess.ctx, m, Q, qisos, None)
+    ct = S.sem_isosurface_multi(sess.ctx, m, T, tisos, None)
+    nq, nt = sum(cq), sum(ct)
+    assert nq > 0 and nt > 0
+    ref = torch.empty((nq + nt) * 9, device="cuda")
+    S.sem_isosurface_multi(sess.ctx, m, Q, qisos, ref[:nq * 9])
+    S.sem_isosurface_multi(sess.ctx, m, T, tisos, ref[nq * 9:])
+    W, H = cam["W"], cam["H"]
+    cols = [[0.9, 0.3, 0.2], [0.7, 0.2, 0.1], [0.2, 0.5, 0.9]]
+    r_rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+    r_depth = torch.zeros(H * W, device="cuda")
+    S.sem_render(sess.ctx, ref, nq + nt, cq + ct, cols, cam, W, H, r_rgba, r_depth)
+    cap = nq + nt + 100
+    tris = torch.full((cap * 9,), -1.0, device="cuda")
+    cnt = torch.full((4,), -7, dtype=torch.int64, device="cuda")
+    rgba = torch.zeros_like(r_rgba)
+    depth = torch.zeros_like(r_depth)
+
+    def step():
+        S.sem_isosurface_multi_async(sess.ctx, m, Q, qisos, tris, cnt[:3], cap=cap)
+        S.sem_isosurface_multi_append_async(sess.ctx, m, T, tisos, tris, cnt[2:], cap=cap)
+        S.sem_render_async(sess.ctx, tris, cap, cnt, 3, cols, cam, W, H, rgba, depth)
+
+    step()
+    S.sem_synchronize(sess.ctx)
+    assert cnt.cpu().tolist() == [0, cq[0], nq, nq + nt]
+    assert torch.equal(tris[:(nq + nt) * 9], ref)
+    assert (tris[(nq + nt) * 9:] == -1.0).all()
+    assert torch.equal(rgba, r_rgba) and torch.equal(depth, r_depth)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        step()
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    tris.fill_(-1.0)
+    rgba.zero_()
+    cnt.fill_(-7)
+    g.replay()
+    S.sem_synchronize(sess.ctx)
+    assert cnt.cpu().tolist() == [0, cq[0], nq, nq + nt]
+    assert torch.equal(tris[:(nq + nt) * 9], ref)
+    assert torch.equal(rgba, r_rgba) and torch.equal(depth, r_depth)
+
+
+def test_append_overflow_is_flagged_and_writes_nothing(gpu, sess):
+    """An append whose start plus its own total exceeds the buffer writes no triangle and raises
+    the capacity flag; the segment ends still report the required size."""
+    S = gpu
+    mesh, f, _ = _two_field_case(nel=3)
+    m = sess.mesh(7, mesh.xyz().numpy())
+    T = f[3].float().cuda().contiguous()
+    nt = S.sem_isosurface_multi(sess.ctx, m, T, [0.5], None)[0]
+    assert nt > 10
+    cap = nt + 5
+    tris = torch.full((cap * 9,), -1.0, device="cuda")
+    cnt = torch.tensor([10, -1], dtype=torch.int64, device="cuda")  # 10 + nt > cap
+    S.sem_isosurface_multi_append_async(sess.ctx, m, T, [0.5], tris, cnt, cap=cap)
+    with pytest.raises(S.SemError) as ex:
+        S.sem_synchronize(sess.ctx)
+    assert ex.value.status == S.SEM_ERR_CAPACITY
+    assert cnt.cpu().tolist() == [10, 10 + nt]
+    assert (tris == -1.0).all()
+    cnt = torch.tensor([5, -1], dtype=torch.int64, device="cuda")  # fits exactly
+    S.sem_isosurface_multi_append_async(sess.ctx, m, T, [0.5], tris, cnt, cap=cap)
+    S.sem_synchronize(sess.ctx)
+    ref = torch.empty(nt * 9, device="cuda")
+    S.sem_isosurface_multi(sess.ctx, m, T, [0.5], ref)
+    assert torch.equal(tris[5 * 9:], ref) and (tris[:5 * 9] == -1.0).all()
