@@ -115,6 +115,16 @@ SEM_API sem_status sem_set_stream(sem_ctx *ctx, void *stream);
  * (SEM_ERR_TIMEOUT) and clear it. */
 SEM_API sem_status sem_synchronize(sem_ctx *ctx);
 
+/* Failure-detection test hook (no counterpart in the paper).  The Q kernels of
+ * sem_qcriterion, sem_qcriterion_batch and sem_derivatives (FP32 path) wait on an mbarrier for
+ * each stage's input copies; every such wait gives up after a bounded number of polls, records
+ * SEM_ERR_TIMEOUT on the context's device flag, waits (with the default limit) for its copies
+ * still in flight and returns, leaving the outputs incomplete.  This call sets that limit for
+ * later launches on ctx: polls >= 0 (0 = give up at the first wait, so the timeout path runs
+ * deterministically), polls < 0 restores the default (about 2^24 polls, seconds).  Host only;
+ * takes effect at the next launch. */
+SEM_API sem_status sem_debug_set_wait_limit(sem_ctx *ctx, int64_t polls);
+
 /* Device memory the library holds for ctx (scratch arenas, tables, meshes loaded with ctx,
  * autoencoders created on ctx; caller-owned buffers are not counted): *in_use now and *peak,
  * the high-water mark since sem_create.  Free meshes and autoencoders before their context. */
@@ -250,8 +260,12 @@ SEM_API sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mes
  *     sem_load_mesh do allocate).
  *   - E may be at most SEM_NOALLOC_MAX_ELEMENTS; a larger mesh is rejected with SEM_ERR_ARG
  *     and a message naming the limit, and nothing is launched.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) and caches it; make that first call before any stream capture.
+ *   - sem_create does this entry point's set-up on its device: it looks up the array's device
+ *     address (cudaGetSymbolAddress; the host-side symbol is only a stand-in) and keeps it in
+ *     the context, and it makes the runtime load the array and every kernel this entry point
+ *     launches, so that under lazy module loading no call of it loads code or data (which
+ *     would allocate).  A context created after a cudaDeviceReset looks the address up again;
+ *     contexts that lived through a reset are invalid, as for every other call.
  *   - Every call on a device shares the one array and leaves its contents behind for the next
  *     call.  Calls whose work overlaps on the GPU (different streams or contexts, or several
  *     host threads) race on it and give wrong results: issue them one after another. */

@@ -57,6 +57,7 @@ def _declare(L):
     L.sem_last_error.restype = C.c_char_p
     L.sem_set_stream.argtypes = [vp, vp]
     L.sem_synchronize.argtypes = [vp]
+    L.sem_debug_set_wait_limit.argtypes = [vp, i64]
     L.sem_trace_enable.argtypes = [vp, i32]
     L.sem_memory.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.sem_trace_collect.argtypes = [vp, C.POINTER(i32)]
@@ -101,7 +102,7 @@ def _declare(L):
     L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 6 + [C.POINTER(f32)]
     L.sem_autotune_emit_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                           C.POINTER(f32)]
-    for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_load_mesh", "sem_mesh_info",
+    for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_debug_set_wait_limit", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
                  "sem_isosurface_multi_append_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
@@ -189,6 +190,12 @@ def sem_set_stream(ctx, stream) -> None:
 
 def sem_synchronize(ctx) -> None:
     _check(ctx, get_lib().sem_synchronize(ctx))
+
+
+def sem_debug_set_wait_limit(ctx, polls: int) -> None:
+    """Polls a Q-kernel wait for its input copies makes before it gives up and records
+    SEM_ERR_TIMEOUT (0: at once; negative: the default).  A failure-detection test hook."""
+    _check(ctx, get_lib().sem_debug_set_wait_limit(ctx, int(polls)))
 
 
 def sem_memory(ctx):

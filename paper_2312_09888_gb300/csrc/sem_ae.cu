@@ -512,11 +512,8 @@ sem_status launch_gemm(sem_ctx *ctx, const CUtensorMap &ta, const CUtensorMap &t
                        const EpiArgs &P, int split, const char *name)
 {
     const size_t sm = (size_t)NST * (BM * BK * 2 + BN * BK * 2) + 1024;
-    static bool set = false;  // per instantiation; the attribute is a property of the function
-    if (!set) {
-        SEM_CU(ctx, cudaFuncSetAttribute(k_gemm_bf16<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        set = true;
-    }
+    static KernelSetup ks;  // per instantiation and device
+    SEM_TRY(kernel_setup(ctx, ks, k_gemm_bf16<BN, NST>, 0, sm));
     const dim3 grid((unsigned)(M / BM), (unsigned)(N / BN), (unsigned)split);
     SEM_TRACED(ctx, name, k_gemm_bf16<BN, NST><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16 launch");

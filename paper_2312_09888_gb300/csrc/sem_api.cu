@@ -298,6 +298,7 @@ sem_status sem_create(int device, void *stream, sem_ctx **out)
         if ((st = sem_cuda(ctx, cudaMallocHost(&ctx->h_pinned_d, 4 * sizeof(double)), "cudaMallocHost")) != SEM_OK)
             break;
         if ((st = upload_tables(ctx)) != SEM_OK) break;
+        if ((st = iso_noalloc_prepare(ctx)) != SEM_OK) break;
         if ((st = sem_cuda(ctx, cudaDeviceSynchronize(), "cudaDeviceSynchronize")) != SEM_OK) break;
     } while (0);
     if (st != SEM_OK) {
@@ -408,6 +409,13 @@ sem_status sem_set_stream(sem_ctx *ctx, void *stream)
 {
     if (!ctx) return SEM_ERR_ARG;
     ctx->stream = (cudaStream_t)stream;
+    return SEM_OK;
+}
+
+sem_status sem_debug_set_wait_limit(sem_ctx *ctx, int64_t polls)
+{
+    if (!ctx) return SEM_ERR_ARG;
+    ctx->wait_limit = polls < 0 ? SEM_WAIT_LIMIT : (long long)polls;
     return SEM_OK;
 }
 

@@ -4,10 +4,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
 #include "../../include/sem.h"
+
+#define SEM_WAIT_LIMIT (1ll << 24)   // bounded spin on an mbarrier phase (~ seconds)
 
 // ------------------------------------------------------------------------------------------
 // Host-side objects
@@ -19,6 +22,12 @@ struct sem_ctx {
     int sm_count = 0;
     // device error word: kernels with bounded waits OR a code in here (SEM_ERR_TIMEOUT ...)
     int *d_flag = nullptr;
+    // iteration limit of the Q kernels' waits for their input copies (sem_debug_set_wait_limit);
+    // the waits that drain copies still in flight after an abort keep SEM_WAIT_LIMIT
+    long long wait_limit = SEM_WAIT_LIMIT;
+    // device address of sem_isosurface_noalloc's fixed scratch array on this device (resolved
+    // by sem_create, so a context made after a device reset looks it up again)
+    void *noalloc_scratch = nullptr;
     // pinned host words for small read-backs (counts, totals)
     int64_t *h_pinned = nullptr;   // 16 int64 slots
     double *h_pinned_d = nullptr;  // 4 double slots
@@ -121,6 +130,35 @@ sem_status sem_scratch_nogrow_in_capture(sem_ctx *ctx, int slot, size_t bytes, v
 
 #define SEM_CU(ctx, expr) SEM_TRY(sem_cuda((ctx), (expr), #expr))
 
+// Per-(kernel, device) launch set-up.  The max-dynamic-shared-memory attribute and the resident
+// blocks per SM belong to a kernel on one device, so they are set and computed once per device
+// (the context's device, current when this runs) and cached in the kernel's own table.  Two
+// host threads racing on a first call both set the same attribute and store the same value.
+#define SEM_MAX_DEVICES 64
+struct KernelSetup {
+    std::atomic<int> per_sm[SEM_MAX_DEVICES];
+};
+template <class K>
+inline sem_status kernel_setup(sem_ctx *ctx, KernelSetup &ks, K kern, int threads, size_t dyn, int *per_sm = nullptr)
+{
+    const int d = ctx->device;
+    if (d < 0 || d >= SEM_MAX_DEVICES)
+        return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "device index %d: at most %d devices", d, SEM_MAX_DEVICES);
+    int v = ks.per_sm[d].load(std::memory_order_acquire);
+    if (!v) {
+        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        int nb = 1;
+        if (threads > 0) {
+            SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, dyn));
+            if (nb < 1) nb = 1;
+        }
+        ks.per_sm[d].store(nb, std::memory_order_release);
+        v = nb;
+    }
+    if (per_sm) *per_sm = v;
+    return SEM_OK;
+}
+
 static inline bool sem_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // ------------------------------------------------------------------------------------------
@@ -147,6 +185,7 @@ sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, 
                                bool append = false);
 sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                            int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
+sem_status iso_noalloc_prepare(sem_ctx *ctx);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
                       const int64_t *seg_start_dev = nullptr);
@@ -157,11 +196,11 @@ sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host
 // scan_tmp_bytes(n) bytes.  Stream-ordered on ctx->stream.
 size_t scan_tmp_bytes(int64_t n);
 sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp);
+// makes the runtime load the scan kernels (lazy module loading), see iso_noalloc_prepare
+sem_status scan_load_kernels(sem_ctx *ctx);
 
 // ------------------------------------------------------------------------------------------
 // Device helpers: mbarrier + bulk async copy (TMA engine, non-tensor form)
-
-#define SEM_WAIT_LIMIT (1ll << 24)   // bounded spin on an mbarrier phase (~ seconds)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -211,10 +250,12 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait; returns false (and flags `err`) if the phase never completed
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err)
+// bounded wait; returns false (and flags `err`) if the phase did not complete within `limit`
+// polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  long long limit = SEM_WAIT_LIMIT)
 {
-    for (long long it = 0; it < SEM_WAIT_LIMIT; ++it)
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicOr(err, 1 << SEM_ERR_TIMEOUT);
     return false;

@@ -629,13 +629,9 @@ static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f,
     constexpr int EV = EmitW<NP>::V;
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
     auto kern = k_iso_emit_m<NP, GENERAL>;
-    static int blocks_per_sm = 0;  // per instantiation; the same on every device of one architecture
-    if (!blocks_per_sm) {
-        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-        int nb = 0;
-        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * EV, dyn));
-        blocks_per_sm = nb > 0 ? nb : 1;
-    }
+    static KernelSetup ks;  // per instantiation and device
+    int blocks_per_sm = 1;
+    SEM_TRY(kernel_setup(ctx, ks, kern, 32 * EV, dyn, &blocks_per_sm));
     SEM_CU(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
     const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
     SEM_TRACED(ctx, "k_iso_emit_m", kern<<<grid, 32 * EV, dyn, ctx->stream>>>(f, S, m->E, offs, m->lo, m->hi, tris,
@@ -816,40 +812,43 @@ sem_status iso_run(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, f
 // same scan; the per-element counts, offsets and scan partials live in one file-scope device
 // array instead of the context's grow-only arena, so a call never allocates.
 // ==========================================================================================
-#include <mutex>
-
 namespace {
 constexpr size_t al256(size_t b) { return ((b + 255) / 256) * 256; }
 constexpr int64_t kNaMaxE = SEM_NOALLOC_MAX_ELEMENTS;
 constexpr size_t kNaCnt = al256(sizeof(int32_t) * kNaMaxE);
 constexpr size_t kNaOff = al256(sizeof(int64_t) * (kNaMaxE + 1));
 constexpr size_t kNaTmp = al256(sizeof(int64_t) * ((kNaMaxE + 4095) / 4096 + 1));
-constexpr int kNaMaxDevices = 64;
 }  // namespace
 
 // Shared by every call on a device; holds the last call's contents until the next call.
 // Nothing in it needs to start at zero: every word is written before it is read.
 static __device__ __align__(256) unsigned char g_iso_noalloc_scratch[kNaCnt + kNaOff + kNaTmp];
 
-static std::mutex g_na_mu;
-static void *g_na_ptr[kNaMaxDevices] = {};
-
-// Device address of g_iso_noalloc_scratch on ctx->device (which the caller has made current).
-// The host-side symbol is only a stand-in, so the address is looked up once per device.
-static sem_status noalloc_scratch(sem_ctx *ctx, char **out)
+template <int NP>
+static cudaError_t noalloc_load_kernels()
 {
-    if (ctx->device < 0 || ctx->device >= kNaMaxDevices)
-        return sem_fail(ctx, SEM_ERR_UNSUPPORTED, "sem_isosurface_noalloc: device index %d >= %d", ctx->device,
-                        kNaMaxDevices);
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_iso_noalloc_scratch);
-        if (e != cudaSuccess || !p) return sem_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
-        g_na_ptr[ctx->device] = p;
-    }
-    *out = static_cast<char *>(g_na_ptr[ctx->device]);
-    return SEM_OK;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_iso_count<NP>);
+    return e != cudaSuccess ? e : cudaFuncGetAttributes(&a, k_iso_emit<NP>);
+}
+
+// Set-up of sem_isosurface_noalloc for ctx->device (current), run by sem_create: the device
+// address of g_iso_noalloc_scratch (in host code the symbol is only a stand-in), kept in the
+// context, and the kernels the entry point launches, so that with lazy module loading neither
+// the array nor any of its code is loaded -- which would allocate -- during a call.  Querying a
+// kernel's attributes takes its handle, which makes the runtime load it.
+sem_status iso_noalloc_prepare(sem_ctx *ctx)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_iso_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return sem_cuda(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    ctx->noalloc_scratch = p;
+#define SEM_CASE(NPV) if ((e = noalloc_load_kernels<NPV>()) != cudaSuccess) return sem_cuda(ctx, e, "cudaFuncGetAttributes");
+    SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+    SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    return scan_load_kernels(ctx);
 }
 
 template <int NP>
@@ -858,8 +857,8 @@ static sem_status iso_run_noalloc_np(sem_ctx *ctx, const sem_mesh *m, const floa
 {
     const int64_t E = m->E;
     if (scan_tmp_bytes(E) > kNaTmp) return sem_fail(ctx, SEM_ERR_ARG, "sem_isosurface_noalloc: scan scratch too small");
-    char *scr;
-    SEM_TRY(noalloc_scratch(ctx, &scr));
+    char *scr = static_cast<char *>(ctx->noalloc_scratch);
+    if (!scr) return sem_fail(ctx, SEM_ERR_CUDA, "sem_isosurface_noalloc: scratch address not resolved");
     int32_t *cnt = reinterpret_cast<int32_t *>(scr);
     int64_t *offs = reinterpret_cast<int64_t *>(scr + kNaCnt);
     void *tmp = scr + kNaCnt + kNaOff;

@@ -60,6 +60,122 @@ __device__ __forceinline__ float Dc(int i, int m)
     return c_D[((NP - 1) * MP + i) * MP + m];
 }
 
+// Every contraction below subtracts the line's first value from the line before the products
+// (the line's level shift): D's rows sum to zero (D 1 = 0), so the derivative is unchanged in
+// exact arithmetic, while the FP32 rounding then follows the field's variation along the line
+// instead of its magnitude -- a field with a large mean over thin elements would otherwise
+// lose most of its significant digits to cancellation.
+
+// (D row)_i for one r-line held in registers
+template <int NP>
+__device__ __forceinline__ void contract_row(float (&row)[NP], float (&dr)[NP])
+{
+#pragma unroll
+    for (int m = 1; m < NP; ++m) row[m] -= row[0];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        float a = 0.f;
+#pragma unroll
+        for (int m = 1; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
+        dr[i] = a;
+    }
+}
+
+// One direction at a time (the Q kernel folds each into Q before computing the next).
+template <int NP>
+__device__ __forceinline__ void deriv_r(const float *__restrict__ U, int k, int j, float (&dr)[NP])
+{
+    float row[NP];
+    if constexpr (NP == 8) {
+        const int sw = (j >> 2) & 1;
+        const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
+        float4 A = rp[sw], B = rp[sw ^ 1];
+        float4 lo = sw ? B : A, hi = sw ? A : B;
+        row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
+        row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
+    } else {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
+    }
+    contract_row<NP>(row, dr);
+}
+
+// d/ds at the nodes (i, j, k), i = 0..NP-1, of slab k: the s-line of node i is U[k][.][i], its
+// level U[k][0][i]
+template <int NP>
+__device__ __forceinline__ void deriv_s(const float *__restrict__ U, int k, int j, const float (&Dj)[NP], float (&ds)[NP])
+{
+    if constexpr (NP == 8) {
+        // rows in the order rotated by k (Dj pre-rotated to match); row 0 itself adds zero
+        const float4 *b0 = reinterpret_cast<const float4 *>(U + (k * 8) * 8);
+        const float4 LA = b0[0], LB = b0[1];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ds[i] = 0.f;
+#pragma unroll
+        for (int mm = 0; mm < 8; ++mm) {
+            const int m = (mm + k) & 7;
+            const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
+            const float4 A = sp[0], B = sp[1];
+            const float d = Dj[mm];
+            ds[0] = fmaf(d, A.x - LA.x, ds[0]); ds[1] = fmaf(d, A.y - LA.y, ds[1]);
+            ds[2] = fmaf(d, A.z - LA.z, ds[2]); ds[3] = fmaf(d, A.w - LA.w, ds[3]);
+            ds[4] = fmaf(d, B.x - LB.x, ds[4]); ds[5] = fmaf(d, B.y - LB.y, ds[5]);
+            ds[6] = fmaf(d, B.z - LB.z, ds[6]); ds[7] = fmaf(d, B.w - LB.w, ds[7]);
+        }
+    } else {
+        float lv[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            ds[i] = 0.f;
+            lv[i] = U[(k * NP) * NP + i];
+        }
+#pragma unroll
+        for (int m = 1; m < NP; ++m)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i] - lv[i], ds[i]);
+    }
+}
+
+// d/dt at the nodes (i, j, k), i = 0..NP-1, of column j: the t-line of node i is U[.][j][i],
+// its level U[0][j][i]
+template <int NP>
+__device__ __forceinline__ void deriv_t(const float *__restrict__ U, int j, const float (&Dk)[NP], float (&dt)[NP])
+{
+    if constexpr (NP == 8) {
+        // chunk order staggered by j; swap the two accumulator halves at the end
+        const int sw = (j >> 2) & 1;
+        const float4 *b0 = reinterpret_cast<const float4 *>(U + j * 8);
+        const float4 LA = b0[sw], LB = b0[sw ^ 1];
+        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int m = 1; m < 8; ++m) {
+            const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
+            const float4 A = tp[sw], B = tp[sw ^ 1];
+            const float d = Dk[m];
+            a0[0] = fmaf(d, A.x - LA.x, a0[0]); a0[1] = fmaf(d, A.y - LA.y, a0[1]);
+            a0[2] = fmaf(d, A.z - LA.z, a0[2]); a0[3] = fmaf(d, A.w - LA.w, a0[3]);
+            a1[0] = fmaf(d, B.x - LB.x, a1[0]); a1[1] = fmaf(d, B.y - LB.y, a1[1]);
+            a1[2] = fmaf(d, B.z - LB.z, a1[2]); a1[3] = fmaf(d, B.w - LB.w, a1[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            dt[i] = sw ? a1[i] : a0[i];
+            dt[i + 4] = sw ? a0[i] : a1[i];
+        }
+    } else {
+        float lv[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            dt[i] = 0.f;
+            lv[i] = U[j * NP + i];
+        }
+#pragma unroll
+        for (int m = 1; m < NP; ++m)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i] - lv[i], dt[i]);
+    }
+}
+
 // Derivatives of one component along the three directions for the r-line (k, j) of one
 // element held in shared memory U[k][j][i].  Dj[m] = D[j][(m + k) % NP] when NP == 8 (the
 // slab reads are rotated by k), else D[j][m]; Dk[m] = D[k][m].
@@ -79,159 +195,16 @@ __device__ __forceinline__ void line_derivs(const float *__restrict__ U, int k, 
             row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
             row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
         }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            float a = 0.f;
-#pragma unroll
-            for (int m = 0; m < 8; ++m) a = fmaf(Dc<8>(i, m), row[m], a);
-            dr[i] = a;
-        }
-        // --- s: slab k, row order rotated by k (Dj pre-rotated to match)
-        {
-            float acc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-#pragma unroll
-            for (int mm = 0; mm < 8; ++mm) {
-                const int m = (mm + k) & 7;
-                const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
-                float4 A = sp[0], B = sp[1];
-                const float d = Dj[mm];
-                acc[0] = fmaf(d, A.x, acc[0]); acc[1] = fmaf(d, A.y, acc[1]);
-                acc[2] = fmaf(d, A.z, acc[2]); acc[3] = fmaf(d, A.w, acc[3]);
-                acc[4] = fmaf(d, B.x, acc[4]); acc[5] = fmaf(d, B.y, acc[5]);
-                acc[6] = fmaf(d, B.z, acc[6]); acc[7] = fmaf(d, B.w, acc[7]);
-            }
-#pragma unroll
-            for (int i = 0; i < 8; ++i) ds[i] = acc[i];
-        }
-        // --- t: column j, chunk order staggered; swap the two accumulator halves at the end
-        {
-            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
-                float4 A = tp[sw], B = tp[sw ^ 1];
-                const float d = Dk[m];
-                a0[0] = fmaf(d, A.x, a0[0]); a0[1] = fmaf(d, A.y, a0[1]);
-                a0[2] = fmaf(d, A.z, a0[2]); a0[3] = fmaf(d, A.w, a0[3]);
-                a1[0] = fmaf(d, B.x, a1[0]); a1[1] = fmaf(d, B.y, a1[1]);
-                a1[2] = fmaf(d, B.z, a1[2]); a1[3] = fmaf(d, B.w, a1[3]);
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                dt[i] = sw ? a1[i] : a0[i];
-                dt[i + 4] = sw ? a0[i] : a1[i];
-            }
-        }
+        contract_row<8>(row, dr);
+        deriv_s<8>(U, k, j, Dj, ds);
+        deriv_t<8>(U, j, Dk, dt);
     } else {
         float row[NP];
 #pragma unroll
         for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            float a = 0.f;
-#pragma unroll
-            for (int m = 0; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
-            dr[i] = a;
-        }
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            ds[i] = 0.f;
-            dt[i] = 0.f;
-        }
-#pragma unroll
-        for (int m = 0; m < NP; ++m) {
-#pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i], ds[i]);
-                dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i], dt[i]);
-            }
-        }
-    }
-}
-
-// The three directions one at a time (same arithmetic and shared-memory order as
-// line_derivs), so the Q kernel can fold each into Q before computing the next.
-template <int NP>
-__device__ __forceinline__ void deriv_r(const float *__restrict__ U, int k, int j, float (&dr)[NP])
-{
-    float row[NP];
-    if constexpr (NP == 8) {
-        const int sw = (j >> 2) & 1;
-        const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
-        float4 A = rp[sw], B = rp[sw ^ 1];
-        float4 lo = sw ? B : A, hi = sw ? A : B;
-        row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
-        row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
-    } else {
-#pragma unroll
-        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
-    }
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        float a = 0.f;
-#pragma unroll
-        for (int m = 0; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
-        dr[i] = a;
-    }
-}
-
-template <int NP>
-__device__ __forceinline__ void deriv_s(const float *__restrict__ U, int k, int j, const float (&Dj)[NP], float (&ds)[NP])
-{
-    if constexpr (NP == 8) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) ds[i] = 0.f;
-#pragma unroll
-        for (int mm = 0; mm < 8; ++mm) {
-            const int m = (mm + k) & 7;
-            const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
-            const float4 A = sp[0], B = sp[1];
-            const float d = Dj[mm];
-            ds[0] = fmaf(d, A.x, ds[0]); ds[1] = fmaf(d, A.y, ds[1]);
-            ds[2] = fmaf(d, A.z, ds[2]); ds[3] = fmaf(d, A.w, ds[3]);
-            ds[4] = fmaf(d, B.x, ds[4]); ds[5] = fmaf(d, B.y, ds[5]);
-            ds[6] = fmaf(d, B.z, ds[6]); ds[7] = fmaf(d, B.w, ds[7]);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) ds[i] = 0.f;
-#pragma unroll
-        for (int m = 0; m < NP; ++m)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i], ds[i]);
-    }
-}
-
-template <int NP>
-__device__ __forceinline__ void deriv_t(const float *__restrict__ U, int j, const float (&Dk)[NP], float (&dt)[NP])
-{
-    if constexpr (NP == 8) {
-        const int sw = (j >> 2) & 1;
-        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {
-            const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
-            const float4 A = tp[sw], B = tp[sw ^ 1];
-            const float d = Dk[m];
-            a0[0] = fmaf(d, A.x, a0[0]); a0[1] = fmaf(d, A.y, a0[1]);
-            a0[2] = fmaf(d, A.z, a0[2]); a0[3] = fmaf(d, A.w, a0[3]);
-            a1[0] = fmaf(d, B.x, a1[0]); a1[1] = fmaf(d, B.y, a1[1]);
-            a1[2] = fmaf(d, B.z, a1[2]); a1[3] = fmaf(d, B.w, a1[3]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            dt[i] = sw ? a1[i] : a0[i];
-            dt[i + 4] = sw ? a0[i] : a1[i];
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < NP; ++i) dt[i] = 0.f;
-#pragma unroll
-        for (int m = 0; m < NP; ++m)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i], dt[i]);
+        contract_row<NP>(row, dr);
+        deriv_s<NP>(U, k, j, Dj, ds);
+        deriv_t<NP>(U, j, Dk, dt);
     }
 }
 
@@ -269,6 +242,7 @@ struct QCfg {
 #define QB_MAX 48
 struct GBatch {
     int n;
+    long long wait_limit;  // polls of a wait for the stage's input copies before giving up
     int64_t gstart[QB_MAX + 1];
     int64_t E[QB_MAX];
     const float *f[3][QB_MAX];
@@ -357,9 +331,13 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
         int64_t e0;
         const int ne = elems(grp, p, e0);
         if (C::BULK && ne == EPB) {
-            if (!mbar_wait_bounded(&bar[s], phase[s], err)) s_abort = 1;
-            phase[s] ^= 1u;
-            pending[s] = false;
+            // a wait that ran out leaves the stage pending, so the abort path drains its copy
+            if (mbar_wait_bounded(&bar[s], phase[s], err, B.wait_limit)) {
+                phase[s] ^= 1u;
+                pending[s] = false;
+            } else {
+                s_abort = 1;
+            }
         } else {
             for (int c = 0; c < NC; ++c)
                 for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x)
@@ -475,6 +453,12 @@ __device__ __forceinline__ void deriv8_eo(const float (&u)[8], float (&out)[8])
     float2 eo[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) eo[m] = make_float2(u[m] + u[7 - m], u[m] - u[7 - m]);
+    // the line's level shift: the even coefficients of a row sum to zero (D 1 = 0), so
+    // subtracting e_0 from every even part leaves the result unchanged in exact arithmetic and
+    // makes the rounding follow the field's variation along the line, not its magnitude
+#pragma unroll
+    for (int m = 1; m < 4; ++m) eo[m].x -= eo[0].x;
+    eo[0].x = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         float2 a = __ffma2_rn(c_Deo7[i * 4 + 0], eo[0], make_float2(0.f, 0.f));
@@ -554,9 +538,13 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
         int64_t e0;
         const int ne = elems(grp, p, e0);
         if (ne == EPB) {
-            if (!mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err)) s_abort = 1;
-            phase ^= 1u << s;
-            pending &= ~(1u << s);
+            // a wait that ran out leaves the stage pending, so the abort path drains its copy
+            if (mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err, B.wait_limit)) {
+                phase ^= 1u << s;
+                pending &= ~(1u << s);
+            } else {
+                s_abort = 1;
+            }
         } else {
             for (int c = 0; c < 3; ++c)
                 for (int idx = tid; idx < ne * NP3; idx += 256)
@@ -673,12 +661,9 @@ static void fill_batch(GBatch &B, int n, int epb, const sem_mesh *const *m, cons
 
 static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
 {
-    static int per_sm = 0;
-    if (!per_sm) {
-        SEM_CU(ctx, cudaFuncSetAttribute(k_sem_q8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q8::SMEM));
-        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sem_q8, 256, q8::SMEM));
-        if (per_sm < 1) per_sm = 1;
-    }
+    static KernelSetup ks;
+    int per_sm = 1;
+    SEM_TRY(kernel_setup(ctx, ks, k_sem_q8, 256, q8::SMEM, &per_sm));
     const int64_t ngroups = B.gstart[B.n];
     if (ngroups == 0) return SEM_OK;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
@@ -693,12 +678,9 @@ static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
     using C = QCfg<NP>;
     const size_t smem = sizeof(float) * (size_t)C::NSTAGE * NC * C::EPB * C::NP3;
     auto kern = k_sem_grad<NP, NC>;
-    static int per_sm = 0;
-    if (!per_sm) {
-        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        SEM_CU(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::NT, smem));
-        if (per_sm < 1) per_sm = 1;
-    }
+    static KernelSetup ks;  // per instantiation and device
+    int per_sm = 1;
+    SEM_TRY(kernel_setup(ctx, ks, kern, C::NT, smem, &per_sm));
     const int64_t ngroups = B.gstart[B.n];
     if (ngroups == 0) return SEM_OK;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
@@ -715,12 +697,14 @@ static sem_status dispatch(sem_ctx *ctx, int N, int n, const sem_mesh *const *m,
     GBatch B;
     if (NC == 3 && N == 7) {
         fill_batch(B, n, q8::EPB, m, f0, f1, f2, o0, o1, o2);
+        B.wait_limit = ctx->wait_limit;
         return launch_q8(ctx, B);
     }
     switch (N + 1) {
 #define SEM_CASE(NPV)                                                        \
     case NPV:                                                                \
         fill_batch(B, n, QCfg<NPV>::EPB, m, f0, f1, f2, o0, o1, o2);         \
+        B.wait_limit = ctx->wait_limit;                                      \
         return launch_grad<NPV, NC>(ctx, B);
         SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
         SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
@@ -766,12 +750,14 @@ __global__ void __launch_bounds__(GEN_THREADS) k_sem_grad_gen(const float *__res
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float *U = s_u + c * NP3;
+                // each line shifted by its first value (D 1 = 0; see contract_row)
+                const float lr = U[(k * NP + j) * NP], ls = U[(k * NP) * NP + i], lt = U[j * NP + i];
                 float dr = 0.f, ds = 0.f, dt = 0.f;
 #pragma unroll
-                for (int m = 0; m < NP; ++m) {
-                    dr = fmaf(s_D[i * NP + m], U[(k * NP + j) * NP + m], dr);
-                    ds = fmaf(s_D[j * NP + m], U[(k * NP + m) * NP + i], ds);
-                    dt = fmaf(s_D[k * NP + m], U[(m * NP + j) * NP + i], dt);
+                for (int m = 1; m < NP; ++m) {
+                    dr = fmaf(s_D[i * NP + m], U[(k * NP + j) * NP + m] - lr, dr);
+                    ds = fmaf(s_D[j * NP + m], U[(k * NP + m) * NP + i] - ls, ds);
+                    dt = fmaf(s_D[k * NP + m], U[(m * NP + j) * NP + i] - lt, dt);
                 }
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) J[c][jj] = fmaf(dt, G[6 + jj], fmaf(ds, G[3 + jj], dr * G[jj]));
@@ -798,11 +784,8 @@ static sem_status launch_gen(sem_ctx *ctx, const sem_mesh *m, const float *f0, c
     case NPV: {                                                                                                \
         auto kern = k_sem_grad_gen<NPV, NC>;                                                                   \
         const size_t smem = sizeof(float) * NC * NPV * NPV * NPV;                                              \
-        static bool attr_set = false; /* once per instantiation, before any capture needs it */               \
-        if (!attr_set) {                                                                                       \
-            SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));  \
-            attr_set = true;                                                                                   \
-        }                                                                                                      \
+        static KernelSetup ks; /* per instantiation and device */                                             \
+        SEM_TRY(kernel_setup(ctx, ks, kern, 0, smem));                                                         \
         const int64_t grid = std::min<int64_t>(m->E, (int64_t)ctx->sm_count * 8);                             \
         SEM_TRACED(ctx, "k_sem_grad_gen",                                                                      \
                    kern<<<(unsigned)grid, GEN_THREADS, smem, ctx->stream>>>(f0, f1, f2, m->geo, m->E, o0, o1, o2)); \

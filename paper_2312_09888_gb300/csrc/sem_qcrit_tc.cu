@@ -316,12 +316,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
                     const float4 *rp = reinterpret_cast<const float4 *>(st + (el * 3 + c) * SLOT_F + line * 8);
                     const float4 A = rp[sw], B = rp[sw ^ 1];
                     const float4 lo = sw ? B : A, hi = sw ? A : B;
-                    const float row[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+                    // the row shifted by its first value (D's rows sum to zero): the rounding
+                    // follows the variation along the row, not the values' magnitude
+                    const float row[8] = {0.f, lo.y - lo.x, lo.z - lo.x, lo.w - lo.x,
+                                          hi.x - lo.x, hi.y - lo.x, hi.z - lo.x, hi.w - lo.x};
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         float a = 0.f;
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) a = fmaf(c_Dtc[i * 8 + m], row[m], a);
+                        for (int m = 1; m < 8; ++m) a = fmaf(c_Dtc[i * 8 + m], row[m], a);
                         dr[c][i] = a;
                     }
                 }
@@ -427,11 +430,8 @@ static sem_status launch_tc(sem_ctx *ctx, const sem_mesh *m, const float *u, con
     using L = Smem<PREC>;
     static_assert(L::ALLOC <= 232448, "shared memory per CTA");
     auto kern = k_sem_q_tc<PREC>;
-    static bool attr_set = false;  // per instantiation; the attribute is a property of the function
-    if (!attr_set) {
-        SEM_CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::ALLOC));
-        attr_set = true;
-    }
+    static KernelSetup ks;  // per instantiation and device
+    SEM_TRY(kernel_setup(ctx, ks, kern, 0, L::ALLOC));
     // one CTA per SM: it allocates all 512 TMEM columns (two accumulator sets)
     const int64_t ntiles = (m->E + NE - 1) / NE;
     int64_t grid = (int64_t)ctx->sm_count;

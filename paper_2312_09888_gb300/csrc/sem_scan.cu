@@ -184,6 +184,17 @@ sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n
     return sem_cuda(ctx, cudaGetLastError(), "scan launch");
 }
 
+sem_status scan_load_kernels(sem_ctx *ctx)
+{
+    cudaFuncAttributes a;
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_single));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_self));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_reduce));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_blocks));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_apply));
+    return SEM_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // FP64 surface area and divergence-theorem volume: area = sum |(p1-p0)x(p2-p0)|/2,
 // volume = sum p0.(p1 x p2)/6.

@@ -25,17 +25,25 @@ def host64(t):
 
 
 def ref_abs_contractions(D, u, NP):
-    """sum_m M[i][m] |u| along r, s, t for u (E, NP^3) -> three (E, NP^3) arrays, with
-    M[i][m] = max(|D[i][m]|, |D[i][N-m]|).  D is centro-antisymmetric (GLL nodes are symmetric),
-    so a kernel may contract with the even/odd parts u_m +- u_{N-m} and the coefficients
-    (D[i][m] +- D[i][N-m])/2; their rounding error is bounded by the same sums with
-    |(x+y)/2| + |(x-y)/2| = max(|x|, |y|) in place of |D[i][m]|.  M >= |D|, so the bound also
-    covers the plain contraction."""
+    """sum_m M[i][m] (|u_m| + |u_0| + |u_N|) along r, s, t for u (E, NP^3) -> three (E, NP^3)
+    arrays, with M[i][m] = max(|D[i][m]|, |D[i][N-m]|) and u_0, u_N the ends of the line through
+    the node.  D is centro-antisymmetric (GLL nodes are symmetric), so a kernel may contract with
+    the even/odd parts u_m +- u_{N-m} and the coefficients (D[i][m] +- D[i][N-m])/2; their
+    rounding error is bounded by the same sums with |(x+y)/2| + |(x-y)/2| = max(|x|, |y|) in
+    place of |D[i][m]|.  M >= |D|, so the bound also covers the plain contraction.  The kernels
+    subtract the line's first value (or, in the even/odd form, the first even part u_0 + u_N)
+    from the line before the products (D's rows sum to zero, so the result is unchanged in exact
+    arithmetic); that subtraction rounds each operand with an error of at most
+    eps (|u_m| + |u_0| + |u_N|), hence the ends' term."""
     A = np.maximum(np.abs(D), np.abs(D[:, ::-1]))
+    rs = A.sum(axis=1)
     U = np.abs(u).reshape(-1, NP, NP, NP)  # [e][k][j][i]
-    br = np.einsum("im,ekjm->ekji", A, U)
-    bs = np.einsum("jm,ekmi->ekji", A, U)
-    bt = np.einsum("km,emji->ekji", A, U)
+    ends_r = U[:, :, :, :1] + U[:, :, :, -1:]
+    ends_s = U[:, :, :1, :] + U[:, :, -1:, :]
+    ends_t = U[:, :1, :, :] + U[:, -1:, :, :]
+    br = np.einsum("im,ekjm->ekji", A, U) + rs[None, None, None, :] * ends_r
+    bs = np.einsum("jm,ekmi->ekji", A, U) + rs[None, None, :, None] * ends_s
+    bt = np.einsum("km,emji->ekji", A, U) + rs[None, :, None, None] * ends_t
     return [b.reshape(u.shape) for b in (br, bs, bt)]
 
 
@@ -82,3 +90,25 @@ def box_factors(xyz):
     x0 = xyz[:, :, 0]
     x1 = np.stack([xyz[0, :, NP - 1], xyz[1, :, NP * (NP - 1)], xyz[2, :, NP * NP * (NP - 1)]])
     return (2.0 / (x1 - x0)).T
+
+
+def compare_images(img, dep, ref_img, ref_dep, min_frac=0.999):
+    """GPU frame against the oracle's from the same FP32 triangles.  Colour: every channel
+    within 1/255 on >= 99.9% of pixels; the pixels beyond are those whose centre lies within
+    FP32 rounding of a triangle edge, where the two sides can pick different winners (often on
+    different surfaces, at any depth).  Depth, where both sides cover the pixel with colours
+    within 1/255 (the same winner, or an adjacent one of the same surface): within 1e-5 on
+    >= 99.9% of those pixels (the rest are sliver triangles, whose FP32 depth plane has steep
+    gradients) and within 1e-3 on all of them.  Returns (fraction of pixels within 1/255,
+    fraction of the depth-compared pixels within 1e-5)."""
+    close = (np.abs(img.astype(int) - ref_img.astype(int)) <= 1).all(axis=2)
+    frac = close.mean()
+    assert frac >= min_frac, frac
+    both = (img[..., 3] > 0) & (ref_img[..., 3] > 0) & close
+    dfrac = 1.0
+    if both.any():
+        dz = np.abs(dep[both] - ref_dep[both])
+        dfrac = (dz <= 1e-5).mean()
+        assert dfrac >= min_frac, dfrac
+        assert dz.max() <= 1e-3, dz.max()
+    return frac, dfrac

@@ -66,6 +66,8 @@ def test_curved_derivatives_and_q(gpu, sess, orc, N, n):
         assert np.isfinite(got).all()
         err = np.abs(got - J[c])
         assert (err <= dJ[c]).all(), (c, float((err / dJ[c]).max()))
+        # the field-level bar for FP32 derivatives: max |du - du_64| <= 1e-5 max |du_64|
+        assert err.max() <= 1e-5 * np.abs(J[c]).max(), (c, err.max() / np.abs(J[c]).max())
     # Q
     Q = torch.full_like(uvw32[0], float("nan"))
     S.sem_qcriterion(sess.ctx, m, *uvw32, Q)

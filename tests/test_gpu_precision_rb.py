@@ -4,13 +4,14 @@ and temperature (2.15 GB of FP32), Q at every arithmetic of sem_qcriterion again
 oracle on sampled elements (per-node bounds from the arithmetic, errors printed per result: FP32, BF16,
 FP16, split BF16, TF32),
 the temperature isosurface T = 0.5 next to the Q isosurface (cases bit-exact on sampled
-elements) and one 3840x2160 frame holding both fields' surfaces."""
+elements) and one 3840x2160 frame holding both fields' surfaces, compared pixel by pixel with
+the oracle's raster of the same triangles."""
 import numpy as np
 import pytest
 import torch
 
 import sem_inputs as si
-from _helpers import box_factors, grad_bounds, grad_bounds_prec, host64, q_bound
+from _helpers import box_factors, compare_images, grad_bounds, grad_bounds_prec, host64, q_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +66,7 @@ def test_q_every_precision_full_size_sampled(gpu, sess, orc, rb):
     derr = np.abs(dgot - J[0])
     assert (derr <= grad_bounds(D, uvw[0], g, 8, J[0])).all()  # per-node FP32 bound
     drel = derr.max() / np.abs(J[0]).max()
+    assert drel <= 1e-5, drel  # the field-level bar for FP32 derivatives
     print("\n64^3 precision workload, sampled elements:", f"du/dx_j FP32 {drel:.3e};",
           "; ".join(f"Q {k} {v:.3e}" for k, v in report.items()), "(max error / max |Q_fp64|)")
     assert report["FP32"] < report["BF16X2"] < report["TF32"] < report["BF16"] and report["FP16"] < report["BF16"]
@@ -109,5 +111,11 @@ def test_temperature_and_q_isosurfaces_and_one_frame(gpu, sess, orc, rb):
     blue = covered & (img[..., 2] > img[..., 0])
     assert red.sum() > 1000 and blue.sum() > 1000
     used, peak = S.sem_memory(sess.ctx)
-    print(f"\n64^3: {nq} Q triangles, {nt} T triangles, {covered.mean():.3f} of 3840x2160 covered; "
+    # the whole 3840x2160 frame against the oracle's raster of the same FP32 triangles
+    ref_img, ref_dep, _ = orc.render(host64(tris).reshape(-1, 3, 3), [nq, nt], colours.astype(np.float64),
+                                     w.camera)
+    frac, dfrac = compare_images(img.astype(np.uint8), depth.view(Hd, Wd).cpu().numpy(), ref_img, ref_dep)
+    print(f"\n64^3: {nq} Q triangles, {nt} T triangles, {covered.mean():.3f} of 3840x2160 covered, "
+          f"{frac * 100:.3f}% of pixels within 1/255 of the oracle, {dfrac * 100:.3f}% of compared depths "
+          f"within 1e-5; "
           f"library memory {used / 2**20:.1f} MiB (peak {peak / 2**20:.1f} MiB)")

@@ -191,3 +191,40 @@ def test_hausdorff_kd_equals_brute_force():
     B = rng.normal(size=(500, 3)) * 1.3 + 0.2
     assert abs(ae.hausdorff_kd(A, B) - ae.hausdorff(A, B)) < 1e-12
     assert ae.hausdorff_kd(A, A) == 0.0
+
+
+def test_encode_decode_equal_the_forward_pass():
+    """encode() and decode() restate the forward pass for the latent and the reconstruction;
+    they must give forward()'s Z and Y exactly (forward() is the path the finite-difference
+    test pins), on a network whose layers are all of different widths so a transposed or
+    swapped weight cannot broadcast."""
+    rng = np.random.default_rng(11)
+    dims = (9, 6, 4, 5, 9)
+    p = {}
+    for l in range(4):
+        p[f"W{l + 1}"] = rng.normal(0, 0.7, size=(dims[l + 1], dims[l]))
+        p[f"b{l + 1}"] = rng.normal(0, 0.3, size=dims[l + 1])
+    X = rng.normal(0, 1, size=(7, dims[0]))
+    _, cache = ae.forward(p, X)
+    np.testing.assert_array_equal(ae.encode(p, X), cache["Z"])
+    np.testing.assert_array_equal(ae.decode(p, cache["Z"]), cache["Y"])
+    # with a rounded latent, decode of the rounded Z is the decoder forward() ran
+    rnd = ae.round_bf16
+    _, cq = ae.forward(p, X, latent_round=rnd)
+    np.testing.assert_array_equal(ae.decode(p, rnd(ae.encode(p, X))), cq["Y"])
+
+
+def test_encode_decode_scalar_network_closed_form():
+    """A 1-1-1-1-1 network evaluated by hand with the tabulated Phi(1) = 0.8413447460685429
+    (Abramowitz & Stegun 26.2): x = 1, H1 = 2x - 1 = 1, A1 = Phi(1), Z = 3 Phi(1) + 0.5;
+    the decoder's b3 is chosen so that H3 = Z - (Z* - 1) = 1 at the tabulated Z*, then
+    Y = -2 Phi(1) + 0.25.  A dropped bias, a GELU on the latent or on the output, or a wrong
+    sign changes the values."""
+    phi1 = 0.8413447460685429
+    z_star = 3.0 * phi1 + 0.5
+    p = {"W1": np.array([[2.0]]), "b1": np.array([-1.0]), "W2": np.array([[3.0]]), "b2": np.array([0.5]),
+         "W3": np.array([[1.0]]), "b3": np.array([1.0 - z_star]), "W4": np.array([[-2.0]]), "b4": np.array([0.25])}
+    z = ae.encode(p, np.array([[1.0]]))
+    assert abs(z[0, 0] - z_star) < 1e-15
+    y = ae.decode(p, z)
+    assert abs(y[0, 0] - (-2.0 * phi1 + 0.25)) < 1e-14

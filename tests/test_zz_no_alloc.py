@@ -4,7 +4,10 @@ Some callers may not allocate device memory while they run (an in situ hook insi
 step whose GPU memory the solver has already committed); for them the library keeps the
 isosurface scratch in a fixed device array.  This file runs last (its name sorts last) so a
 failure here stops a `-x` run only after every other test has run.  It also passes alone in a
-fresh process: the library looks the array's address up on the first call on a device.
+fresh process: sem_create looks the array's address up and loads the entry point's kernels.
+The cases span the three scan forms the fixed scratch must hold: one block (up to 8192
+elements), one launch of up to 32 tiles (up to 131072) and the three-kernel scan beyond, up to
+the limit; results are checked against the regular entry point and against the oracle.
 """
 import math
 
@@ -13,6 +16,7 @@ import pytest
 import torch
 
 import sem_inputs as si
+from _helpers import host64
 
 pytestmark = pytest.mark.gpu
 
@@ -59,3 +63,28 @@ def test_noalloc_rejects_meshes_beyond_its_limit(gpu, sess):
         S.sem_isosurface_noalloc(sess.ctx, m, f, 0.5, None)
     assert ex.value.status == S.SEM_ERR_ARG
     assert str(S.SEM_NOALLOC_MAX_ELEMENTS) in str(ex.value)
+
+
+@pytest.mark.parametrize("N,nel", [(2, 47), (1, 58)])
+def test_noalloc_large_meshes_against_oracle(gpu, sess, orc, N, nel):
+    """103823 elements of order 2 (the one-launch tiled scan) and 195112 elements of order 1
+    (the three-kernel scan with its tile sums in the fixed array), a sphere |x - c|^2 = r^2 at
+    two radii in a row: every cell's case and every element's triangle count equal the oracle's
+    from the same FP32 field, and the triangles equal sem_isosurface's."""
+    S = gpu
+    mesh = si.uniform_box((nel,) * 3, (0.0,) * 3, (1.0,) * 3, N)
+    xyz = mesh.xyz().numpy()
+    m = sess.mesh(N, xyz)
+    E = mesh.E
+    assert E > (131072 if N == 1 else 8192)
+    for r in (0.31, 0.42):
+        f = si.sphere_field(mesh, (0.47, 0.52, 0.5), r)
+        f32 = f.float().cuda().contiguous()
+        (n0, t0, e0, c0), (n1, t1, e1, c1) = _both(S, sess.ctx, m, f32, 0.0, E, N)
+        assert n0 == n1 and n0 > 1000
+        assert torch.equal(c0, c1) and torch.equal(e0, e1)
+        assert (t0.double() - t1.double()).abs().max().item() <= 1e-5
+        ref = orc.isosurface(N, xyz, host64(f32).reshape(E, -1), 0.0, want_tris=False)
+        np.testing.assert_array_equal(c1.numpy().reshape(E, -1), ref["cases"])
+        np.testing.assert_array_equal(np.bincount(e1.numpy(), minlength=E), ref["elem_ntri"])
+        assert n1 == ref["ntri"]
