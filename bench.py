@@ -50,6 +50,7 @@ RB_COLOURS = [[0.9, 0.3, 0.2], [0.2, 0.5, 0.9]]
 KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_sem_q8": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_iso_count_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
+                  "k_iso_count_p": "paper_2312_09888_gb300/csrc/sem_iso.cu",
                   "k_iso_emit_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
                   "k_raster_small": "paper_2312_09888_gb300/csrc/sem_render.cu",
                   "k_resolve": "paper_2312_09888_gb300/csrc/sem_render.cu"}
@@ -66,6 +67,7 @@ def algorithmic_bytes_per_step(name, P):
         "k_sem_q8": 16 * P.npts,
         # per field: read once for all its isovalues + one int32 count per element and isovalue
         "k_iso_count_m": sum(4 * P.npts + 4 * P.E * s["niso"] for s in surf),
+        "k_iso_count_p": sum(4 * P.npts + 4 * P.E * s["niso"] for s in surf),
         # per field: its active elements read + 36 B per triangle written + the offsets read
         "k_iso_emit_m": sum(4 * NP3 * s["active_elems"] + 36 * s["ntri"] + 8 * (s["niso"] * P.E + 1) for s in surf),
         # 36 B per triangle read (the 64-bit depth keys live in L2)

@@ -317,21 +317,27 @@ __device__ __forceinline__ int pair_case(uint32_t r00, uint32_t r01, uint32_t r1
 
 #define COUNT_WARPS 8
 
-// The masks of all isovalues of element fe, built from register-held values: lane w keeps
-// mask word w of each isovalue and stores it; the activity bits come from warp AND/OR
-// reductions of the words.  For orders with at most 32 mask words (N <= 9).
+// The element's values for the register-held masks below: lane l holds nodes 32 w + l.
 template <int NP>
-__device__ __forceinline__ unsigned load_masks_reg(const float *__restrict__ fe, const IsoSet &S,
-                                                   uint32_t *__restrict__ m, int lane)
+__device__ __forceinline__ void load_vals(const float *__restrict__ fe, float (&v)[MaskGeo<NP>::NW], int lane)
 {
     using G = MaskGeo<NP>;
-    static_assert(G::NW <= 32, "one mask word per lane");
-    float v[G::NW];
 #pragma unroll
     for (int w = 0; w < G::NW; ++w) {
         const int n = w * 32 + lane;
         v[w] = ((G::NP3 % 32 == 0) || n < G::NP3) ? __ldg(fe + n) : 0.f;
     }
+}
+
+// The masks of all isovalues of an element from its register-held values: lane w keeps mask
+// word w of each isovalue and stores it; the activity bits come from warp AND/OR reductions
+// of the words.  For orders with at most 32 mask words (N <= 9).
+template <int NP>
+__device__ __forceinline__ unsigned masks_from_vals(const float (&v)[MaskGeo<NP>::NW], const IsoSet &S,
+                                                    uint32_t *__restrict__ m, int lane)
+{
+    using G = MaskGeo<NP>;
+    static_assert(G::NW <= 32, "one mask word per lane");
     // lanes >= NW hold the neutral words of the reductions (AND: all ones, OR: zero)
     const uint32_t vmask = lane >= G::NW ? 0u
                            : (G::NP3 % 32 == 0 || lane < G::NW - 1) ? ~0u
@@ -355,6 +361,15 @@ __device__ __forceinline__ unsigned load_masks_reg(const float *__restrict__ fe,
         if (any_in != 0u && all_in != ~0u) active |= 1u << q;
     }
     return active;
+}
+
+template <int NP>
+__device__ __forceinline__ unsigned load_masks_reg(const float *__restrict__ fe, const IsoSet &S,
+                                                   uint32_t *__restrict__ m, int lane)
+{
+    float v[MaskGeo<NP>::NW];
+    load_vals<NP>(fe, v, lane);
+    return masks_from_vals<NP>(v, S, m, lane);
 }
 
 // Triangle counts of element e for every isovalue from its masks (and every cell's case when
@@ -412,6 +427,63 @@ __global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_m(const float *_
     else active = load_masks<NP>(f + e * G::NP3, nullptr, S, m, lane);
     __syncwarp();
     count_element<NP>(m, active, S, e, E, s_nt, cnt, cases, lane);
+}
+
+// Persistent form for orders with at most 32 mask words (N <= 9): warps stride over the
+// elements, and each issues the loads of its next element before it classifies the current
+// one, so two elements per warp are in flight and no block is launched per 8 elements.  The
+// grid is one resident wave (SMs x blocks per SM).
+template <int NP>
+__global__ void __launch_bounds__(32 * COUNT_WARPS) k_iso_count_p(const float *__restrict__ f,
+                                                                 const __grid_constant__ IsoSet S, int64_t E,
+                                                                 int32_t *__restrict__ cnt, uint8_t *__restrict__ cases)
+{
+    using G = MaskGeo<NP>;
+    __shared__ uint32_t s_m[COUNT_WARPS][SEM_MAX_ISO * G::MW];
+    __shared__ uint8_t s_nt[256];
+    for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = c_ntri[t];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * COUNT_WARPS;
+    int64_t e = (int64_t)blockIdx.x * COUNT_WARPS + w;
+    if (e >= E) return;
+    uint32_t *m = s_m[w];
+    float v[G::NW];
+    load_vals<NP>(f + e * G::NP3, v, lane);
+    for (; e < E; e += stride) {
+        float nv[G::NW];
+        const int64_t en = e + stride;
+        if (en < E) load_vals<NP>(f + en * G::NP3, nv, lane);
+        __syncwarp();  // the previous element's readers of m are done
+        const unsigned active = masks_from_vals<NP>(v, S, m, lane);
+        __syncwarp();
+        count_element<NP>(m, active, S, e, E, s_nt, cnt, cases, lane);
+        if (en < E) {
+#pragma unroll
+            for (int q = 0; q < G::NW; ++q) v[q] = nv[q];
+        }
+    }
+}
+
+// Launch of the counting pass: the persistent kernel for N <= 9, else one warp per element.
+template <int NP>
+static sem_status launch_count(sem_ctx *ctx, const float *f, const IsoSet &S, int64_t E, int32_t *cnt,
+                               uint8_t *cases)
+{
+    if constexpr (MaskGeo<NP>::NW <= 32) {
+        static KernelSetup ks;  // per instantiation and device
+        int per_sm = 1;
+        SEM_TRY(kernel_setup(ctx, ks, k_iso_count_p<NP>, 32 * COUNT_WARPS, 0, &per_sm));
+        int64_t grid = (int64_t)ctx->sm_count * per_sm;
+        const int64_t need = (E + COUNT_WARPS - 1) / COUNT_WARPS;
+        if (grid > need) grid = need;
+        SEM_TRACED(ctx, "k_iso_count_p", k_iso_count_p<NP><<<(unsigned)grid, 32 * COUNT_WARPS, 0, ctx->stream>>>(
+            f, S, E, cnt, cases));
+    } else {
+        SEM_TRACED(ctx, "k_iso_count_m", k_iso_count_m<NP><<<(unsigned)((E + COUNT_WARPS - 1) / COUNT_WARPS),
+                                                            32 * COUNT_WARPS, 0, ctx->stream>>>(f, S, E, cnt, cases));
+    }
+    return sem_cuda(ctx, cudaGetLastError(), "k_iso_count launch");
 }
 
 // per-warp dynamic shared memory of the emit kernel: the element's field, a window of the
@@ -709,9 +781,7 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
     auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
     void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
-    SEM_TRACED(ctx, "k_iso_count_m", k_iso_count_m<NP><<<(unsigned)((E + COUNT_WARPS - 1) / COUNT_WARPS), 32 * COUNT_WARPS, 0, ctx->stream>>>(
-        f, S, E, cnt, cases));
-    SEM_CU(ctx, cudaGetLastError());
+    SEM_TRY(launch_count<NP>(ctx, f, S, E, cnt, cases));
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
     // segment starts offs[q*E], q = 0..niso (the last one is the grand total)
     SEM_CU(ctx, cudaMemcpy2DAsync(ctx->h_pinned, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t),
@@ -751,9 +821,7 @@ static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const floa
     int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
     auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
     void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
-    SEM_TRACED(ctx, "k_iso_count_m", k_iso_count_m<NP><<<(unsigned)((E + COUNT_WARPS - 1) / COUNT_WARPS), 32 * COUNT_WARPS, 0, ctx->stream>>>(
-        f, S, E, cnt, cases));
-    SEM_CU(ctx, cudaGetLastError());
+    SEM_TRY(launch_count<NP>(ctx, f, S, E, cnt, cases));
     SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
     if (append) {
         SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(offs, E, S.niso, counts_dev));

@@ -45,105 +45,104 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, i
     return r;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t *__restrict__ in, int64_t n,
-                                                              int64_t *__restrict__ bsum)
+// Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", NVIDIA technical report, 2016).  Each block takes the next
+// tile from a ticket counter, scans it, publishes the tile's sum, then folds the published
+// values of the tiles before it -- tile sums until it meets a published inclusive prefix -- and
+// publishes its own inclusive prefix.  Tiles are taken in ticket order, so a block waits only
+// on tiles held by blocks that are already running and never wait on it: every wait ends.  Each
+// is bounded all the same (SEM_WAIT_LIMIT polls, then SEM_ERR_TIMEOUT on the device flag).
+// state[0] is the ticket, state[1 + t] tile t's status: 2 flag bits (0 nothing yet, 1 the tile
+// sum, 2 the inclusive prefix) above a 62-bit value; the caller zeroes state before the launch.
+#define LB_SHIFT 62
+#define LB_VALUE ((1ull << LB_SHIFT) - 1ull)
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
 {
-    __shared__ int64_t s_w[33];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-    int64_t v = 0;
-#pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q)
-        if (base + q < n) v += in[base + q];
-    int64_t tot;
-    block_excl_scan(v, s_w, tot);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// single block: exclusive scan of the nb block sums in place; bsum[nb] = grand total
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(int64_t *__restrict__ bsum, int64_t nb)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
-    __shared__ int64_t s_w[33];
-    int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
-        const int64_t b = b0 + threadIdx.x;
-        const int64_t v = b < nb ? bsum[b] : 0;
-        int64_t tot;
-        const int64_t ex = block_excl_scan(v, s_w, tot);
-        if (b < nb) bsum[b] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) bsum[nb] = carry;
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const int32_t *__restrict__ in, int64_t n,
-                                                             const int64_t *__restrict__ bsum, int64_t nb,
-                                                             int64_t *__restrict__ out)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int32_t *__restrict__ in, int64_t n, int64_t nb,
+                                                                int64_t *__restrict__ out,
+                                                                unsigned long long *__restrict__ state, int *err)
 {
     __shared__ int64_t s_w[33];
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    __shared__ int64_t s_tile, s_before;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(state, 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    unsigned long long *st = state + 1;
+    const int64_t base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int64_t x[SCAN_ITEMS];
+    if (base + SCAN_ITEMS <= n) {
+        const int4 c = *reinterpret_cast<const int4 *>(in + base);  // in is 16-byte aligned
+        x[0] = c.x;
+        x[1] = c.y;
+        x[2] = c.z;
+        x[3] = c.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS; ++q) x[q] = base + q < n ? in[base + q] : 0;
+    }
     int64_t v = 0;
 #pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        x[q] = base + q < n ? in[base + q] : 0;
-        v += x[q];
-    }
+    for (int q = 0; q < SCAN_ITEMS; ++q) v += x[q];
     int64_t tot;
-    int64_t run = block_excl_scan(v, s_w, tot) + bsum[blockIdx.x];
+    const int64_t ex = block_excl_scan(v, s_w, tot);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lane == 0) st_release_u64(st + tile, ((tile == 0 ? 2ull : 1ull) << LB_SHIFT) | (unsigned long long)tot);
+        int64_t before = 0;
+        int64_t p = tile - 1;  // the nearest tile not folded in yet
+        long long polls = 0;
+        while (p >= 0) {
+            // lane l reads tile p - l; before tile 0 there is an inclusive prefix of 0
+            const int64_t q = p - lane;
+            const unsigned long long w = q >= 0 ? ld_acquire_u64(st + q) : (2ull << LB_SHIFT);
+            const unsigned flag = (unsigned)(w >> LB_SHIFT);
+            const unsigned nr = __ballot_sync(0xffffffffu, flag == 0u);
+            const unsigned pm = __ballot_sync(0xffffffffu, flag == 2u);
+            const int kp = pm ? __ffs(pm) - 1 : 32;  // nearest lane holding an inclusive prefix
+            const int kn = nr ? __ffs(nr) - 1 : 32;  // nearest lane whose tile has published nothing
+            const int take = min(kp + 1, kn);        // lanes [0, take): tile sums (and the prefix)
+            int64_t part = lane < take ? (int64_t)(w & LB_VALUE) : 0;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+            before += part;
+            if (kp < kn) break;  // reached an inclusive prefix
+            p -= take;
+            if (take == 0 && ++polls >= SEM_WAIT_LIMIT) {
+                if (lane == 0) atomicOr(err, 1 << SEM_ERR_TIMEOUT);
+                break;
+            }
+        }
+        if (lane == 0) {
+            if (tile > 0) st_release_u64(st + tile, (2ull << LB_SHIFT) | (unsigned long long)(before + tot));
+            s_before = before;
+        }
+    }
+    __syncthreads();
+    int64_t run = s_before + ex;
 #pragma unroll
     for (int q = 0; q < SCAN_ITEMS; ++q) {
         if (base + q < n) out[base + q] = run;
         run += x[q];
     }
-    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = bsum[nb];
-}
-
-// One launch for up to SCAN_SELF_MAX_TILES tiles: block b sums the counts of the tiles before
-// its own by itself (16-byte loads of at most (SCAN_SELF_MAX_TILES - 1) * 16 KB, just written by
-// the producer and still in L2), then scans its tile -- no tile-sum pass, no inter-block wait.
-#define SCAN_SELF_MAX_TILES 32
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_self(const int32_t *__restrict__ in, int64_t n, int64_t nb,
-                                                            int64_t *__restrict__ out)
-{
-    __shared__ int64_t s_w[33];
-    // counts before this tile: b * SCAN_TILE of them, a multiple of 4 (in is 16-byte aligned)
-    const int4 *in4 = reinterpret_cast<const int4 *>(in);
-    // (SCAN_TILE / 4) / SCAN_THREADS = 1 vector per thread and tile: eight tiles' loads in flight
-    static_assert(SCAN_TILE / 4 == SCAN_THREADS, "one 16-byte load per thread and tile");
-    int64_t pre = 0;
-    const int nbefore = (int)blockIdx.x;
-    for (int t0 = 0; t0 < nbefore; t0 += 8) {
-        int4 c[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            c[k] = t0 + k < nbefore ? in4[(int64_t)(t0 + k) * SCAN_THREADS + threadIdx.x] : make_int4(0, 0, 0, 0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) pre += (int64_t)c[k].x + c[k].y + c[k].z + c[k].w;
-    }
-    int64_t before;
-    block_excl_scan(pre, s_w, before);
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-    int64_t x[SCAN_ITEMS];
-    int64_t v = 0;
-#pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        x[q] = base + q < n ? in[base + q] : 0;
-        v += x[q];
-    }
-    int64_t tot;
-    int64_t run = block_excl_scan(v, s_w, tot) + before;
-#pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q) {
-        if (base + q < n) out[base + q] = run;
-        run += x[q];
-    }
-    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = before + tot;
+    if (tile == nb - 1 && threadIdx.x == 0) out[n] = s_before + tot;
 }
 
 // One block for small inputs: thread t scans its contiguous chunk of ceil(n / 1024) entries
 // (sum, block-wide scan of the sums, then the chunk's offsets), so the whole scan is a single
-// launch; used up to SCAN_SINGLE_MAX entries (8 per thread: beyond that one SM's serial chunks
-// cost more than the three-kernel scan, measured 194 us against 20 us at 98304 entries).
+// launch with no state to reset; used up to SCAN_SINGLE_MAX entries (8 per thread: beyond that
+// one SM's serial chunks cost more than a multi-block scan, measured 194 us against 20 us at
+// 98304 entries).
 #define SCAN_SINGLE_MAX (SCAN_THREADS * 8)
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t *__restrict__ in, int64_t n,
                                                               int64_t *__restrict__ out)
@@ -172,15 +171,13 @@ sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n
         SEM_TRACED(ctx, "k_scan_single", k_scan_single<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, out));
         return sem_cuda(ctx, cudaGetLastError(), "scan launch");
     }
+    if ((reinterpret_cast<uintptr_t>(in) & 15u) != 0)
+        return sem_fail(ctx, SEM_ERR_ARG, "scan: counts not 16-byte aligned");
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
-    if (nb <= SCAN_SELF_MAX_TILES && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
-        SEM_TRACED(ctx, "k_scan_self", k_scan_self<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, nb, out));
-        return sem_cuda(ctx, cudaGetLastError(), "scan launch");
-    }
-    int64_t *bsum = reinterpret_cast<int64_t *>(tmp);
-    SEM_TRACED(ctx, "k_scan_reduce", k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum));
-    SEM_TRACED(ctx, "k_scan_blocks", k_scan_blocks<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb));
-    SEM_TRACED(ctx, "k_scan_apply", k_scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum, nb, out));
+    auto *state = reinterpret_cast<unsigned long long *>(tmp);
+    SEM_CU(ctx, cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (size_t)(nb + 1), ctx->stream));
+    SEM_TRACED(ctx, "k_scan_lookback", k_scan_lookback<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(
+        in, n, nb, out, state, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "scan launch");
 }
 
@@ -188,10 +185,7 @@ sem_status scan_load_kernels(sem_ctx *ctx)
 {
     cudaFuncAttributes a;
     SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_single));
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_self));
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_reduce));
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_blocks));
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_apply));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_lookback));
     return SEM_OK;
 }
 

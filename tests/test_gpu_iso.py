@@ -194,10 +194,10 @@ def test_channel_full_size_sampled(gpu, sess, orc):
 
 @pytest.mark.parametrize("shape", [(64, 32, 32), (65537, 1, 1)])
 def test_scan_at_the_one_launch_limit(gpu, sess, orc, shape):
-    """2 isovalues x 65536 elements = 131072 counts (32 tiles of 4096: the one-launch scan, each
-    block summing the tiles before its own) and x 65537 = 131074 counts (33 tiles: the
-    three-kernel scan); counts and the triangles' elements against the oracle.  Per-node
-    random values, so nearly every element holds triangles."""
+    """2 isovalues x 65536 elements = 131072 counts (exactly 32 tiles of 4096 of the look-back
+    scan) and x 65537 = 131074 counts (33 tiles, the last holding 2 counts); counts and the
+    triangles' elements against the oracle.  Per-node random values, so nearly every element
+    holds triangles."""
     mesh = si.uniform_box(shape, (0, 0, 0), (1, 1, 1), 1)
     xyz = mesh.xyz().numpy()
     f32 = dev32(si.random_nodal(mesh, 1, seed=shape[0])[0].numpy())  # (E, 8)
@@ -249,9 +249,9 @@ def test_emit_autotuner_choice_does_not_change_the_triangles(gpu, sess):
 
 
 def test_many_elements_multi_isovalue_uses_the_multi_block_scan(gpu, sess, orc):
-    """64^3 elements of order 1 x 2 isovalues = 524288 counts: the three-kernel scan (the
-    single-block scan takes at most 8192, the one-launch tile scan 32 tiles of 4096); counts and
-    offsets against the oracle."""
+    """64^3 elements of order 1 x 2 isovalues = 524288 counts: 128 tiles of the look-back scan
+    (the single-block scan takes at most 8192), so tiles fold up to four 32-tile windows of
+    their predecessors; counts and offsets against the oracle."""
     mesh = si.uniform_box((64, 64, 64), (0, 0, 0), (1, 1, 1), 1)
     xyz = mesh.xyz().numpy()
     f32 = dev32(si.sphere_field(mesh, (0.5, 0.5, 0.5), 0.3).numpy())

@@ -5,9 +5,9 @@ step whose GPU memory the solver has already committed); for them the library ke
 isosurface scratch in a fixed device array.  This file runs last (its name sorts last) so a
 failure here stops a `-x` run only after every other test has run.  It also passes alone in a
 fresh process: sem_create looks the array's address up and loads the entry point's kernels.
-The cases span the three scan forms the fixed scratch must hold: one block (up to 8192
-elements), one launch of up to 32 tiles (up to 131072) and the three-kernel scan beyond, up to
-the limit; results are checked against the regular entry point and against the oracle.
+The cases span both scan forms whose state the fixed scratch holds: one block (up to 8192
+elements) and the single-pass look-back scan over tiles of 4096 beyond, up to the limit;
+results are checked against the regular entry point and against the oracle.
 """
 import math
 
@@ -67,10 +67,10 @@ def test_noalloc_rejects_meshes_beyond_its_limit(gpu, sess):
 
 @pytest.mark.parametrize("N,nel", [(2, 47), (1, 58)])
 def test_noalloc_large_meshes_against_oracle(gpu, sess, orc, N, nel):
-    """103823 elements of order 2 (the one-launch tiled scan) and 195112 elements of order 1
-    (the three-kernel scan with its tile sums in the fixed array), a sphere |x - c|^2 = r^2 at
-    two radii in a row: every cell's case and every element's triangle count equal the oracle's
-    from the same FP32 field, and the triangles equal sem_isosurface's."""
+    """103823 elements of order 2 (26 tiles of the look-back scan) and 195112 elements of
+    order 1 (48 tiles, their status words in the fixed array), a sphere |x - c|^2 = r^2 at two
+    radii in a row: every cell's case and every element's triangle count equal the oracle's from
+    the same FP32 field, and the triangles equal sem_isosurface's."""
     S = gpu
     mesh = si.uniform_box((nel,) * 3, (0.0,) * 3, (1.0,) * 3, N)
     xyz = mesh.xyz().numpy()
