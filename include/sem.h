@@ -228,6 +228,19 @@ SEM_API sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *mesh
                                               const float *isos_host, int niso, float *tris, int32_t *tri_elem,
                                               int64_t cap, int64_t *counts_dev, uint8_t *cases);
 
+/* sem_qcriterion (FP32) followed by sem_isosurface_multi_async of Q at isos_host[0..niso-1], with
+ * the isosurface pass's per-element triangle counting done by the Q kernel itself from the Q it
+ * has just computed, so Q is not read back from memory for counting (on N = 7 box meshes; on other
+ * meshes the two passes run one after the other).  Q, the triangles, counts_dev and every error
+ * are exactly those of the two calls: Q and tris bit for bit.  No host synchronisation; may be
+ * captured in a CUDA graph (scratch rule of sem_isosurface_multi_async).  u, v, w, Q: device,
+ * E*(N+1)^3 floats each, Q not aliasing the inputs; other arguments as
+ * sem_isosurface_multi_async (no per-cell cases). */
+SEM_API sem_status sem_qcriterion_isosurface_async(sem_ctx *ctx, const sem_mesh *mesh, const float *u,
+                                                   const float *v, const float *w, float *Q, const float *isos_host,
+                                                   int niso, float *tris, int32_t *tri_elem, int64_t cap,
+                                                   int64_t *counts_dev);
+
 /* sem_isosurface_multi_async appending behind triangles already in `tris`, so that the
  * isosurfaces of several fields (e.g. Q and temperature) fill one buffer back to back and one
  * sem_render_async draws them as consecutive segments, all without host synchronisation.

@@ -73,6 +73,7 @@ def _declare(L):
     L.sem_isosurface_multi.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_multi_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_multi_append_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
+    L.sem_qcriterion_isosurface_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, i64, vp]
     L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
@@ -104,7 +105,7 @@ def _declare(L):
                                           C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_debug_set_wait_limit", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
-                 "sem_isosurface_multi_append_async", "sem_render_async",
+                 "sem_isosurface_multi_append_async", "sem_qcriterion_isosurface_async", "sem_render_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
@@ -313,6 +314,23 @@ def sem_isosurface_multi_async(ctx, mesh, f, isos, tris, counts_dev, tri_elem=No
                                               _dev(tri_elem, "tri_elem", torch.int32, allow_none=True), int(cap),
                                               _dev(counts_dev, "counts_dev", torch.int64),
                                               _dev(cases, "cases", torch.uint8, allow_none=True))
+    _check(ctx, st)
+
+
+def sem_qcriterion_isosurface_async(ctx, mesh, u, v, w, Q, isos, tris, counts_dev, tri_elem=None,
+                                    cap: Optional[int] = None) -> None:
+    """sem_qcriterion then sem_isosurface_multi_async of Q, the counting pass done by the Q kernel
+    (N = 7 box meshes); no host synchronisation.  Same results as the two calls."""
+    import torch
+    iv = np.ascontiguousarray(np.asarray(isos, dtype=np.float32).reshape(-1))
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    st = get_lib().sem_qcriterion_isosurface_async(ctx, mesh, _dev(u, "u", torch.float32), _dev(v, "v", torch.float32),
+                                                   _dev(w, "w", torch.float32), _dev(Q, "Q", torch.float32),
+                                                   iv.ctypes.data_as(C.c_void_p), len(iv),
+                                                   _dev(tris, "tris", torch.float32, allow_none=True),
+                                                   _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
+                                                   int(cap), _dev(counts_dev, "counts_dev", torch.int64))
     _check(ctx, st)
 
 

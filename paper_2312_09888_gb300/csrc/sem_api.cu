@@ -734,6 +734,34 @@ sem_status sem_isosurface_multi_async(sem_ctx *ctx, const sem_mesh *m, const flo
     return iso_run_multi_async(ctx, m, f, isos, niso, tris, tri_elem, cap, counts_dev, cases);
 }
 
+sem_status sem_qcriterion_isosurface_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v,
+                                           const float *w, float *Q, const float *isos, int niso, float *tris,
+                                           int32_t *tri_elem, int64_t cap, int64_t *counts_dev)
+{
+    SEM_TRY(check_common(ctx, m, "sem_qcriterion_isosurface_async"));
+    if (!isos || niso < 1 || niso > SEM_MAX_ISO)
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_isosurface_async: need 1 <= niso <= %d isovalues",
+                        SEM_MAX_ISO);
+    for (int q = 0; q < niso; ++q)
+        if (isnan(isos[q]))
+            return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_isosurface_async: isovalue %d is NaN", q);
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_isosurface_async: negative cap");
+    SEM_TRY(check_ptr(ctx, counts_dev, "sem_qcriterion_isosurface_async", "counts_dev", false, 8));
+    if (m->E == 0) return sem_cuda(ctx, cudaMemsetAsync(counts_dev, 0, sizeof(int64_t) * (niso + 1), ctx->stream),
+                                   "cudaMemsetAsync");
+    if (m->E * (int64_t)niso > ((int64_t)1 << 31))
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_qcriterion_isosurface_async: E*niso too large");
+    const char *fn = "sem_qcriterion_isosurface_async";
+    SEM_TRY(check_ptr(ctx, u, fn, "u"));
+    SEM_TRY(check_ptr(ctx, v, fn, "v"));
+    SEM_TRY(check_ptr(ctx, w, fn, "w"));
+    SEM_TRY(check_ptr(ctx, Q, fn, "Q"));
+    if (Q == u || Q == v || Q == w) return sem_fail(ctx, SEM_ERR_ARG, "%s: Q aliases an input", fn);
+    SEM_TRY(check_ptr(ctx, tris, fn, "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, fn, "tri_elem", true, 4));
+    return iso_run_q_multi_async(ctx, m, u, v, w, Q, isos, niso, tris, tri_elem, cap, counts_dev);
+}
+
 sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos,
                                              int niso, float *tris, int32_t *tri_elem, int64_t cap,
                                              int64_t *counts_dev, uint8_t *cases)

@@ -28,6 +28,9 @@ struct sem_ctx {
     // device address of sem_isosurface_noalloc's fixed scratch array on this device (resolved
     // by sem_create, so a context made after a device reset looks it up again)
     void *noalloc_scratch = nullptr;
+    // device address of the case table's triangle counts (256 bytes), for kernels outside the
+    // isosurface unit that classify cells
+    const uint8_t *d_ntri = nullptr;
     // pinned host words for small read-backs (counts, totals)
     int64_t *h_pinned = nullptr;   // 16 int64 slots
     double *h_pinned_d = nullptr;  // 4 double slots
@@ -171,6 +174,10 @@ sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *nt
 // launchers (argument checking happens in sem_api.cu)
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                         float *Q);
+// Q (N = 7 box meshes) and, in the same kernel, the per-element triangle counts cnt[q E + e] of
+// Q's isosurfaces at isos[0..niso-1]
+sem_status qcrit_count_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                              float *Q, int niso, const float *isos, int32_t *cnt);
 sem_status qcrit_tc_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q,
                            sem_prec prec, const double *D64);
 sem_status deriv_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, float *dx, float *dy, float *dz);
@@ -183,6 +190,9 @@ sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
                                float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases,
                                bool append = false);
+sem_status iso_run_q_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                                 float *Q, const float *isos, int niso, float *tris, int32_t *tri_elem, int64_t cap,
+                                 int64_t *counts_dev);
 sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,
                            int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases);
 sem_status iso_noalloc_prepare(sem_ctx *ctx);

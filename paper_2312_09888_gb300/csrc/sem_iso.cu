@@ -64,6 +64,9 @@ sem_status iso_upload_tables(sem_ctx *ctx, const float *s_all, const int32_t *nt
     SEM_CU(ctx, cudaMemcpyToSymbol(c_s, s_all, sizeof(float) * (SEM_MAX_ORDER + 1) * MP));
     SEM_CU(ctx, cudaMemcpyToSymbol(c_ntri, n8, sizeof n8));
     SEM_CU(ctx, cudaMemcpyToSymbol(c_edge, e8, sizeof e8));
+    void *nt = nullptr;
+    SEM_CU(ctx, cudaGetSymbolAddress(&nt, c_ntri));
+    ctx->d_ntri = static_cast<const uint8_t *>(nt);
     return SEM_OK;
 }
 
@@ -805,33 +808,79 @@ __global__ void k_seg_ends(const int64_t *__restrict__ offs, int64_t E, int niso
     if (q <= niso) counts_dev[q] = counts_dev[0] + offs[(int64_t)q * E];
 }
 
-// No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
-// raises the context's device flag and writes no triangle.  With `append`, counts_dev[0] is an
-// input (the first triangle's index in tris) and only counts_dev[1..niso] are written.
-template <int NP>
-static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, float *tris,
-                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases, bool append)
+// The library scratch of one asynchronous isosurface pass: counts [q][e], offsets, the emit
+// work counter and the scan state.
+struct IsoScratch {
+    int32_t *cnt;
+    int64_t *offs;
+    unsigned long long *next;
+    void *tmp;
+};
+
+static sem_status iso_scratch_async(sem_ctx *ctx, int64_t n, IsoScratch &X)
 {
-    const int64_t E = m->E, n = E * S.niso;
     const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
     const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
     void *scr;
     SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, cnt_bytes + off_bytes + 256 + scan_tmp_bytes(n), &scr));
-    int32_t *cnt = reinterpret_cast<int32_t *>(scr);
-    int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
-    auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
-    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
-    SEM_TRY(launch_count<NP>(ctx, f, S, E, cnt, cases));
-    SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
+    X.cnt = reinterpret_cast<int32_t *>(scr);
+    X.offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
+    X.next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
+    X.tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
+    return SEM_OK;
+}
+
+// From the counts on: scan, segment starts to counts_dev, emit.  With `append`, counts_dev[0] is
+// an input (the first triangle's index in tris) and only counts_dev[1..niso] are written.
+template <int NP>
+static sem_status iso_tail_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S,
+                                 const IsoScratch &X, float *tris, int32_t *tri_elem, int64_t cap,
+                                 int64_t *counts_dev, bool append)
+{
+    const int64_t E = m->E, n = E * S.niso;
+    SEM_TRY(scan_i32_i64(ctx, X.cnt, X.offs, n, X.tmp));
     if (append) {
-        SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(offs, E, S.niso, counts_dev));
+        SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(X.offs, E, S.niso, counts_dev));
         SEM_CU(ctx, cudaGetLastError());
     } else {
-        SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t),
+        SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), X.offs, sizeof(int64_t) * E, sizeof(int64_t),
                                       S.niso + 1, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (!tris) return SEM_OK;
-    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, append ? counts_dev : nullptr);
+    return emit<NP>(ctx, m, f, S, X.offs, tris, tri_elem, cap, X.next, append ? counts_dev : nullptr);
+}
+
+// No host synchronisation: segment starts go to counts_dev (device), a capacity overflow
+// raises the context's device flag and writes no triangle.
+template <int NP>
+static sem_status iso_multi_async_np(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, float *tris,
+                                     int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases, bool append)
+{
+    IsoScratch X;
+    SEM_TRY(iso_scratch_async(ctx, m->E * S.niso, X));
+    SEM_TRY(launch_count<NP>(ctx, f, S, m->E, X.cnt, cases));
+    return iso_tail_async<NP>(ctx, m, f, S, X, tris, tri_elem, cap, counts_dev, append);
+}
+
+// Q and its isosurfaces with the counting pass fused into the Q kernel (N = 7 box meshes): the
+// Q kernel writes Q and every element's triangle counts, then scan and emit as above.  Other
+// meshes run the Q kernel and the isosurface passes one after the other (same results).
+sem_status iso_run_q_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                                 float *Q, const float *isos, int niso, float *tris, int32_t *tri_elem, int64_t cap,
+                                 int64_t *counts_dev)
+{
+    if (m->N != 7 || m->curved) {
+        SEM_TRY(qcrit_launch(ctx, m, u, v, w, Q));
+        return iso_run_multi_async(ctx, m, Q, isos, niso, tris, tri_elem, cap, counts_dev, nullptr, false);
+    }
+    IsoSet S;
+    memset(&S, 0, sizeof S);
+    S.niso = niso;
+    for (int q = 0; q < niso; ++q) S.iso[q] = isos[q];
+    IsoScratch X;
+    SEM_TRY(iso_scratch_async(ctx, m->E * S.niso, X));
+    SEM_TRY(qcrit_count_launch(ctx, m, u, v, w, Q, niso, isos, X.cnt));
+    return iso_tail_async<8>(ctx, m, Q, S, X, tris, tri_elem, cap, counts_dev, false);
 }
 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,

@@ -248,6 +248,12 @@ struct GBatch {
     const float *f[3][QB_MAX];
     float *o[3][QB_MAX];
     const float4 *g[QB_MAX];
+    // k_sem_q8<true> only (one partition): isovalues of Q whose per-element triangle counts the
+    // kernel also writes, cnt[q E + e], and the case table's triangle counts (256 bytes)
+    int niso;
+    float iso[SEM_MAX_ISO];
+    int32_t *cnt;
+    const uint8_t *ntri;
 };
 
 // the partition holding group grp (largest p with gstart[p] <= grp)
@@ -478,12 +484,56 @@ constexpr int XS = 2 * CS;                                // exchange: s then t 
 constexpr size_t SMEM = sizeof(float) * (2 * STAGE + XS);
 }  // namespace q8
 
+// Triangle counts of one stage's elements from their node-row inside-bits (COUNT = true):
+// rows[q][el][k * 8 + j] holds bit i = [Q(i, j, k) >= iso_q].  Thread (el, k, j) classifies the
+// cut cells of row pair (j, k) (j, k < 7) as the isosurface pass does, each warp sums its half of
+// the element, and part[q][el][half] receives the sums (their total is the element's count: the
+// same as the counting pass of sem_isosurface_multi on the stored Q, bit-exact, as the same FP32
+// values meet the same isovalues).
+__device__ __forceinline__ void q8_count_stage(const GBatch &B, const uint8_t (*rows)[q8::EPB][64],
+                                               int (*part)[q8::EPB][2], const uint8_t *s_nt, int ne, int el,
+                                               int k, int j, int warp, int lane)
+{
+    for (int q = 0; q < B.niso; ++q) {
+        int acc = 0;
+        if (el < ne && j < 7 && k < 7) {
+            const uint8_t *r = rows[q][el];
+            const uint32_t r00 = r[k * 8 + j], r01 = r[k * 8 + j + 1], r10 = r[k * 8 + 8 + j], r11 = r[k * 8 + 9 + j];
+            const uint32_t A = r00 & r01 & r10 & r11, O = r00 | r01 | r10 | r11;
+            for (uint32_t act = (O | (O >> 1)) & ~(A & (A >> 1)) & 0x7Fu; act; act &= act - 1u) {
+                const int i = __ffs(act) - 1;
+                const int cs = (int)(((r00 >> i) & 3u) | (((r01 >> i) & 3u) << 2) | (((r10 >> i) & 3u) << 4) |
+                                     (((r11 >> i) & 3u) << 6));
+                acc += s_nt[cs];
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (lane == 0) part[q][el][warp & 1] = acc;
+    }
+}
+
+// The counts of the stage before (its sums are complete after a barrier): cnt[q E + e0 + el].
+__device__ __forceinline__ void q8_count_write(const GBatch &B, const int (*part)[q8::EPB][2], int64_t e0, int ne,
+                                               int tid)
+{
+    const int q = tid / q8::EPB, el = tid % q8::EPB;
+    if (q < B.niso && el < ne) B.cnt[(int64_t)q * B.E[0] + e0 + el] = part[q][el][0] + part[q][el][1];
+}
+
+template <bool COUNT>
 __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatch B, int *err)
 {
     using namespace q8;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_abort;
+    // COUNT: the stage's node-row inside-bits per isovalue, and the case table's triangle counts
+    __shared__ uint8_t s_rows[COUNT ? SEM_MAX_ISO : 1][EPB][64];
+    __shared__ int s_part[COUNT ? SEM_MAX_ISO : 1][EPB][2];
+    __shared__ uint8_t s_nt[COUNT ? 256 : 1];
+    if constexpr (COUNT)
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) s_nt[t] = B.ntri[t];
     float *X = smem + 2 * STAGE;  // exchange buffer
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     // r-line owner (el, k, j)
@@ -552,6 +602,13 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
         }
         __syncthreads();
         if (s_abort) break;
+        if constexpr (COUNT)
+            if (it > 0) {  // the previous stage's sums are complete
+                int pp;
+                int64_t pe0;
+                const int pne = elems(grp - gridDim.x, pp, pe0);
+                q8_count_write(B, s_part, pe0, pne, tid);
+            }
         const int64_t e = e0 + el;
         const float4 g = B.g[p][el < ne ? e : e0];
         const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
@@ -566,8 +623,11 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
 #pragma unroll
                 for (int m = 0; m < 8; ++m) u[m] = U[oe * ES + (warp * 8 + m) * 8 + oi];
                 deriv8_eo(u, d);
+                // exchange rows (k, j) hold node i at position i ^ (j & 4): rows j = 0..3 and 4..7
+                // keep their halves in swapped places, so the row owners' 16-byte reads below are
+                // conflict-free in node order
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) X[oe * ES + (warp * 8 + jj) * 8 + oi] = d[jj];
+                for (int jj = 0; jj < 8; ++jj) X[oe * ES + (warp * 8 + jj) * 8 + (oi ^ (jj & 4))] = d[jj];
             }
             // t-lines of plane `warp`: d/dt at nodes (i, j, k') for k' = 0..7
             {
@@ -576,7 +636,7 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
                 for (int m = 0; m < 8; ++m) u[m] = U[oe * ES + (m * 8 + warp) * 8 + oi];
                 deriv8_eo(u, d);
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) X[CS + oe * ES + (kk * 8 + warp) * 8 + oi] = d[kk];
+                for (int kk = 0; kk < 8; ++kk) X[CS + oe * ES + (kk * 8 + warp) * 8 + (oi ^ (warp & 4))] = d[kk];
             }
             // r-line of the owner (el, k, j)
             float dr[8];
@@ -590,10 +650,10 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
             __syncthreads();  // the exchange holds this component's s and t derivatives
             float ds[8], dt[8];
             {
+                // the swizzled rows: nodes 0..3 sit in half sw, nodes 4..7 in half sw ^ 1
                 const float4 *sp = reinterpret_cast<const float4 *>(X + el * ES + (k * 8 + j) * 8);
                 const float4 *tp = reinterpret_cast<const float4 *>(X + CS + el * ES + (k * 8 + j) * 8);
-                const float4 sA = sp[sw], sB = sp[sw ^ 1], tA = tp[sw], tB = tp[sw ^ 1];
-                const float4 slo = sw ? sB : sA, shi = sw ? sA : sB, tlo = sw ? tB : tA, thi = sw ? tA : tB;
+                const float4 slo = sp[sw], shi = sp[sw ^ 1], tlo = tp[sw], thi = tp[sw ^ 1];
                 ds[0] = slo.x; ds[1] = slo.y; ds[2] = slo.z; ds[3] = slo.w;
                 ds[4] = shi.x; ds[5] = shi.y; ds[6] = shi.z; ds[7] = shi.w;
                 dt[0] = tlo.x; dt[1] = tlo.y; dt[2] = tlo.z; dt[3] = tlo.w;
@@ -621,18 +681,38 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
                     q[i] = fmaf(c23 * tv[i], ds[i], q[i]);
                     q[i] = fmaf(c33 * dt[i], dt[i], q[i]);
                 }
+                if constexpr (COUNT)  // the row's inside-bits, complete for the stage at the barrier below
+                    for (int qi = 0; qi < B.niso; ++qi) {
+                        uint32_t bits = 0;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) bits |= (q[i] >= B.iso[qi] ? 1u : 0u) << i;
+                        s_rows[qi][el][k * 8 + j] = (uint8_t)bits;
+                    }
             }
             __syncthreads();  // the exchange is free for the next component
         }
+
         if (el < ne) store_line<8>(B.o[0][p] + e * NP3 + (k * 8 + j) * 8, q);
         if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
             issue(grp + 2 * gridDim.x, s);
             pending |= 1u << s;
         }
+        // after the copy two stages ahead is on its way: the stage's triangle counts
+        if constexpr (COUNT) q8_count_stage(B, s_rows, s_part, s_nt, ne, el, k, j, warp, lane);
     }
     if (s_abort && tid == 0) {
         for (int s = 0; s < 2; ++s)
             if ((pending >> s) & 1u) mbar_wait_bounded(&bar[s], (phase >> s) & 1u, nullptr);
+    }
+    if constexpr (COUNT) {
+        // the last stage's counts (s_abort is uniform: every thread has seen the same value)
+        __syncthreads();
+        if (!s_abort && it > 0) {
+            int pp;
+            int64_t pe0;
+            const int pne = elems((int64_t)blockIdx.x + (int64_t)(it - 1) * gridDim.x, pp, pe0);
+            q8_count_write(B, s_part, pe0, pne, tid);
+        }
     }
 }
 
@@ -659,16 +739,18 @@ static void fill_batch(GBatch &B, int n, int epb, const sem_mesh *const *m, cons
     B.gstart[n] = g;
 }
 
+template <bool COUNT>
 static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
 {
-    static KernelSetup ks;
+    static KernelSetup ks;  // per instantiation and device
     int per_sm = 1;
-    SEM_TRY(kernel_setup(ctx, ks, k_sem_q8, 256, q8::SMEM, &per_sm));
+    SEM_TRY(kernel_setup(ctx, ks, k_sem_q8<COUNT>, 256, q8::SMEM, &per_sm));
     const int64_t ngroups = B.gstart[B.n];
     if (ngroups == 0) return SEM_OK;
     int64_t grid = (int64_t)ctx->sm_count * per_sm;
     if (grid > ngroups) grid = ngroups;
-    SEM_TRACED(ctx, "k_sem_q8", k_sem_q8<<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(B, ctx->d_flag));
+    SEM_TRACED(ctx, COUNT ? "k_sem_q8_count" : "k_sem_q8",
+               k_sem_q8<COUNT><<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(B, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_sem_q8 launch");
 }
 
@@ -698,7 +780,7 @@ static sem_status dispatch(sem_ctx *ctx, int N, int n, const sem_mesh *const *m,
     if (NC == 3 && N == 7) {
         fill_batch(B, n, q8::EPB, m, f0, f1, f2, o0, o1, o2);
         B.wait_limit = ctx->wait_limit;
-        return launch_q8(ctx, B);
+        return launch_q8<false>(ctx, B);
     }
     switch (N + 1) {
 #define SEM_CASE(NPV)                                                        \
@@ -796,6 +878,19 @@ static sem_status launch_gen(sem_ctx *ctx, const sem_mesh *m, const float *f0, c
 #undef SEM_CASE
     default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
     }
+}
+
+sem_status qcrit_count_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                              float *Q, int niso, const float *isos, int32_t *cnt)
+{
+    GBatch B;
+    fill_batch(B, 1, q8::EPB, &m, &u, &v, &w, &Q, nullptr, nullptr);
+    B.wait_limit = ctx->wait_limit;
+    B.niso = niso;
+    for (int q = 0; q < niso; ++q) B.iso[q] = isos[q];
+    B.cnt = cnt;
+    B.ntri = ctx->d_ntri;
+    return launch_q8<true>(ctx, B);
 }
 
 sem_status qcrit_launch(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w, float *Q)

@@ -249,11 +249,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_sem_q_tc(const float *__restrict
                 const bool live = slot / 3 < ne;
                 const float *col = stage + s * NS * SLOT_F + slot * SLOT_F + i;
                 uint8_t *rowB = sB + b * L::NA * B_BYTES + slot * 1024 + i * 128;
+                // the column's level shift: (I (x) D) and (D (x) I) have rows summing to zero, so
+                // subtracting the column's first value leaves S and T unchanged in exact arithmetic
+                // and leaves only the column's variation to be rounded to the operand type
+                const float c0 = live ? col[0] : 0.f;
 #pragma unroll
                 for (int kc = 0; kc < 8; ++kc) {
                     float v[8];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) v[t] = live ? col[(kc * 8 + t) * 8] : 0.f;
+                    for (int t = 0; t < 8; ++t) v[t] = live ? col[(kc * 8 + t) * 8] - c0 : 0.f;
                     if constexpr (TF32) {
                         // K = 8 kc + t: block kc / 4, 16-byte chunks 2 (kc % 4) and 2 (kc % 4) + 1
                         uint8_t *rb = rowB + (kc >> 2) * (NCOL * 128);

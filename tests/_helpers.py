@@ -58,17 +58,25 @@ def grad_bounds(D, u, g, NP, ref):
 
 def grad_bounds_prec(D, u, g, NP, ref, eps_st, abs_st=0.0):
     """As grad_bounds, with the s- and t-contractions done in a 16-bit type: rounding the
-    element data and D to it (unit roundoff eps_st each) adds 2 eps_st sum |D||u| per node;
-    values below the type's normal range round with an absolute error abs_st instead (FP16:
-    2^-25), adding abs_st sum |D|."""
+    element data and D to it (unit roundoff eps_st each) adds 2 eps_st sum |D||u - c| per node,
+    where c is the value the kernel subtracts from the node's column (i fixed) before rounding,
+    the column's first value u[0][0][i] (the contraction operators' rows sum to zero, so the
+    shift leaves the result unchanged); |u - c| <= |u| + |c|.  Values below the type's normal
+    range round with an absolute error abs_st instead (FP16: 2^-25), adding abs_st sum |D|."""
     bs = ref_abs_contractions(D, u, NP)
+    A = np.maximum(np.abs(D), np.abs(D[:, ::-1]))
+    U = np.abs(u).reshape(-1, NP, NP, NP)
+    col = np.broadcast_to(U[:, :1, :1, :], U.shape)  # |c| of each node's column
+    cs = [None, (np.einsum("jm->j", A)[None, None, :, None] * col).reshape(u.shape),
+          (np.einsum("km->k", A)[None, :, None, None] * col).reshape(u.shape)]
     dsum = np.abs(D).sum(axis=1).max()
     floor = 1e-12 * np.abs(ref).max(axis=0)
     out = []
     for a in range(3):
         e_in = 0.0 if a == 0 else 2.0 * eps_st
         a_in = 0.0 if a == 0 else 2.0 * abs_st * dsum
-        out.append(((2.0 * (NP + 1) * EPS32 + 2.0 * e_in) * bs[a] + a_in) * np.abs(g[:, a:a + 1])
+        data = bs[a] if a == 0 else bs[a] + cs[a]
+        out.append(((2.0 * (NP + 1) * EPS32) * bs[a] + 2.0 * e_in * data + a_in) * np.abs(g[:, a:a + 1])
                    + 4.0 * EPS32 * np.abs(ref[a]) + floor)
     return np.stack(out)
 

@@ -326,3 +326,63 @@ def test_append_overflow_is_flagged_and_writes_nothing(gpu, sess):
     ref = torch.empty(nt * 9, device="cuda")
     S.sem_isosurface_multi(sess.ctx, m, T, [0.5], ref)
     assert torch.equal(tris[5 * 9:], ref) and (tris[:5 * 9] == -1.0).all()
+
+
+@pytest.mark.parametrize("N,nel,isos", [(7, (6, 6, 6), [0.05, 0.2, 0.4]), (7, (7, 5, 3), [0.1]),
+                                        (7, (1, 1, 1), [0.1, 0.3]), (5, (4, 3, 3), [0.1, 0.2])])
+def test_fused_q_isosurface_equals_separate_calls(gpu, sess, N, nel, isos):
+    """sem_qcriterion_isosurface_async (for N = 7 the counting pass runs inside the Q kernel)
+    against sem_qcriterion + sem_isosurface_multi_async on the same velocity: Q, segment starts
+    and triangles bit for bit, eager and replayed from a CUDA graph; element counts that leave a
+    partial 4-element group, a single element, and an order that runs the passes unfused."""
+    S = gpu
+    import math
+    mesh = si.uniform_box(nel, (0.0,) * 3, (2 * math.pi,) * 3, N)
+    m = sess.mesh(N, mesh.xyz().numpy())
+    f = si.taylor_green(mesh, 1e-3, si.seed_for(1, 9))
+    vel = [f[c].float().cuda().contiguous() for c in range(3)]
+    Q0 = torch.empty_like(vel[0])
+    S.sem_qcriterion(sess.ctx, m, *vel, Q0)
+    counts = S.sem_isosurface_multi(sess.ctx, m, Q0, isos, None)
+    cap = sum(counts) + 64
+    ref_t = torch.full((cap * 9,), -1.0, device="cuda")
+    ref_c = torch.zeros(len(isos) + 1, dtype=torch.int64, device="cuda")
+    S.sem_isosurface_multi_async(sess.ctx, m, Q0, isos, ref_t, ref_c, cap=cap)
+    Q = torch.full_like(vel[0], float("nan"))
+    tris = torch.full((cap * 9,), -1.0, device="cuda")
+    cnt = torch.full((len(isos) + 1,), -5, dtype=torch.int64, device="cuda")
+
+    def fused():
+        S.sem_qcriterion_isosurface_async(sess.ctx, m, *vel, Q, isos, tris, cnt, cap=cap)
+
+    fused()
+    S.sem_synchronize(sess.ctx)
+    assert torch.equal(Q, Q0)
+    assert torch.equal(cnt, ref_c) and int(cnt[-1]) == sum(counts)
+    assert torch.equal(tris, ref_t)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        fused()
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    Q.fill_(float("nan"))
+    tris.fill_(-1.0)
+    cnt.fill_(-5)
+    g.replay()
+    S.sem_synchronize(sess.ctx)
+    assert torch.equal(Q, Q0) and torch.equal(cnt, ref_c) and torch.equal(tris, ref_t)
+
+
+def test_fused_q_isosurface_overflow_is_flagged(gpu, sess):
+    S = gpu
+    w = si.tgv_box(nel=4)
+    m = sess.mesh(7, w.mesh.xyz().numpy())
+    vel = [w.fields[c].float().cuda().contiguous() for c in range(3)]
+    Q = torch.empty_like(vel[0])
+    tris = torch.full((50 * 9,), -1.0, device="cuda")
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda")
+    S.sem_qcriterion_isosurface_async(sess.ctx, m, *vel, Q, [0.1], tris, cnt, cap=50)
+    with pytest.raises(S.SemError) as ex:
+        S.sem_synchronize(sess.ctx)
+    assert ex.value.status == S.SEM_ERR_CAPACITY
+    assert int(cnt[-1]) > 50 and (tris == -1.0).all()

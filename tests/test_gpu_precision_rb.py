@@ -94,6 +94,13 @@ def test_temperature_and_q_isosurfaces_and_one_frame(gpu, sess, orc, rb):
         np.testing.assert_array_equal(cases[-1].reshape(-1), ref["cases"].reshape(-1))
     nq, nt = counts
     assert nq > 0 and nt > 0
+    # the fused form (counting inside the Q kernel) at full size: the same Q and count
+    Qf = torch.empty_like(Q)
+    cf = torch.zeros(2, dtype=torch.int64, device="cuda")
+    S.sem_qcriterion_isosurface_async(sess.ctx, m, f[0], f[1], f[2], Qf, [q_iso], None, cf)
+    S.sem_synchronize(sess.ctx)
+    assert torch.equal(Qf, Q) and cf.cpu().tolist() == [0, nq]
+    del Qf
     tris = torch.empty((nq + nt) * 9, device="cuda")
     S.sem_isosurface(sess.ctx, m, Q, q_iso, tris[:nq * 9])
     S.sem_isosurface(sess.ctx, m, f[3], t_iso, tris[nq * 9:])

@@ -21,7 +21,7 @@ def test_trace_counts_the_frame_kernels(gpu, sess):
     tr = S.sem_trace_collect(sess.ctx)
     qk = "k_sem_q8"  # the Q kernel of order 7
     assert tr[qk][1] == 3 and tr[qk][0] > 0.0
-    assert tr["k_iso_count_m"][1] == 1
+    assert tr["k_iso_count_p"][1] == 1  # the persistent counting pass (N <= 9)
     assert list(tr)[0] == qk  # first-launch order
     assert sum(counts) > 0
     assert S.sem_trace_collect(sess.ctx) == {}  # collecting cleared the record
