@@ -557,112 +557,138 @@ def measure_curved(S, ctx, vel, box_mesh, steps=20, warmup=3):
     return out
 
 
-def measure_batched(S, ctx, steps=20, warmup=3):
-    """Batching workload: 16 partitions of E_p ~ U{4096..40960} elements (seeded) and orders
-    N_p in {5, 7, 9}, each the first E_p elements of a ceil(E_p^(1/3))^3 lattice of [0, 2 pi]^3
-    with a phase-shifted Taylor-Green field; per step Q of every partition, 4 isovalues of Q and
-    of u per partition, one 1024x1024 frame per partition and field.  Three forms of the same
-    step: the plain path (one host-synchronised call after another), one CUDA graph with one Q
-    launch per partition, and one CUDA graph with the batched Q."""
-    import math as _m
+BATCH_FRACS = (0.05, 0.1, 0.2, 0.4)
+
+
+def measure_batched(S, ctx, snapshots=64, steps=3):
+    """The batching workload (one CUDA graph per time step): 64 snapshots of the Taylor-Green
+    field with phase 2 pi s / 64 in x and y and 1e-3 noise, each over 16 partitions of uneven
+    size and mixed order (batched_partitions); per snapshot Q of every partition
+    (sem_qcriterion_batch: one persistent launch per order), the isosurfaces of Q and of u at
+    {0.05, 0.1, 0.2, 0.4} of their maxima, every partition's appended behind the previous one's in
+    one triangle buffer per field, and one 1024x1024 frame per (snapshot, field, isovalue), each
+    drawing that isovalue's segments of all 16 partitions (sem_render_segments_async): 512 frames
+    per graph.  The snapshots' velocities stay resident (as a solver's fields would be); when
+    they do not fit in 60 % of the free memory, the graph cycles over as many distinct ones as
+    fit (each still larger than L2).  Against the same calls issued eagerly with the host waiting
+    for every snapshot (the plain path)."""
     import numpy as np
     import torch
     import sem_inputs as si
-    rng = np.random.default_rng(si.seed_for(4, 0))
-    parts = []
-    for p in range(16):
-        Ep, N = int(rng.integers(4096, 40961)), int(rng.choice([5, 7, 9]))
-        n = int(_m.ceil(Ep ** (1.0 / 3.0) - 1e-9))
-        mesh = si.uniform_box((n, n, n), (0.0,) * 3, (2 * _m.pi,) * 3, N)
-        xyz = mesh.xyz("cuda")[:, :Ep].contiguous()
-        vel = si.taylor_green(mesh, 0.0, 0, "cuda", phase=2 * _m.pi * p / 64)[:, :Ep].float().contiguous()
-        m = S.sem_load_mesh(ctx, N, xyz.cpu().numpy())
-        del xyz
-        cam = si.box_camera_persp((0.0,) * 3, (2 * _m.pi,) * 3, 1024, 1024)
-        q = torch.empty_like(vel[0])
-        parts.append(dict(m=m, E=Ep, N=N, vel=vel, Q=q, cam=cam))
+    t_setup = time.perf_counter()
+    parts = si.batching_partitions()
     E_total = sum(p["E"] for p in parts)
-    qmax = 1.0  # Taylor-Green: max Q = 1; u in [-1, 1]
-    qisos = [f * qmax for f in (0.05, 0.1, 0.2, 0.4)]
-    uisos = [-0.5, 0.0, 0.25, 0.5]
+    nodes = sum(p["E"] * (p["N"] + 1) ** 3 for p in parts)
+    free, _ = torch.cuda.mem_get_info()
+    distinct = int(max(1, min(snapshots, (0.6 * free) // (12 * nodes + 1))))
+    phases = [2 * math.pi * s / 64 for s in range(distinct)]
     for p in parts:
-        S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
-        cq = S.sem_isosurface_multi(ctx, p["m"], p["Q"], qisos, None)
-        cu = S.sem_isosurface_multi(ctx, p["m"], p["vel"][0], uisos, None)
-        p["cap"] = [int(sum(cq) * 1.1) + 1024, int(sum(cu) * 1.1) + 1024]
-        p["tris"] = [torch.empty(c * 9, device="cuda") for c in p["cap"]]
-        p["cnt"] = [torch.zeros(5, dtype=torch.int64, device="cuda") for _ in range(2)]
-        p["img"] = [torch.empty(1024 * 1024 * 4, dtype=torch.uint8, device="cuda") for _ in range(2)]
-        p["counts"] = [cq, cu]
+        p["m"] = S.sem_load_mesh(ctx, p["N"], p["mesh"].xyz_range(0, p["E"]))
+        p["snap"] = [v.contiguous() for v in si.taylor_green_snapshots(p["mesh"], p["E"], phases, 1e-3,
+                                                                        si.seed_for(4, 1 + len(parts)), "cuda")]
+        p["Q"] = torch.empty(p["E"] * (p["N"] + 1) ** 3, device="cuda")
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_setup
+    meshes = [p["m"] for p in parts]
+
+    def comps(d):
+        return [[p["snap"][d][c].view(-1) for p in parts] for c in range(3)]
+
+    # isovalues from snapshot 0's maxima (setup, untimed)
+    u0, v0, w0 = comps(0)
+    S.sem_qcriterion_batch(ctx, meshes, u0, v0, w0, [p["Q"] for p in parts])
+    qmax = max(S.sem_field_max(ctx, p["Q"]) for p in parts)
+    umax = max(S.sem_field_max(ctx, u) for u in u0)
+    isos = [[float(np.float32(f * qmax)) for f in BATCH_FRACS], [float(np.float32(f * umax)) for f in BATCH_FRACS]]
+    # triangle buffers sized by the largest snapshot (counts of every snapshot, host-synchronised)
+    need = [0, 0]
+    for d in range(distinct):
+        ud, vd, wd = comps(d)
+        S.sem_qcriterion_batch(ctx, meshes, ud, vd, wd, [p["Q"] for p in parts])
+        for f in range(2):
+            tot = 0
+            for k, p in enumerate(parts):
+                tot += sum(S.sem_isosurface_multi(ctx, p["m"], p["Q"] if f == 0 else ud[k], isos[f], None))
+            need[f] = max(need[f], tot)
+    cap = [int(n * 1.02) + 4096 for n in need]
+    tris = [torch.empty(c * 9, device="cuda") for c in cap]
+    cnt = [torch.zeros(16 * 4 + 1, dtype=torch.int64, device="cuda") for _ in range(2)]
+    frames = torch.empty((snapshots, 2, 4, 1024 * 1024 * 4), dtype=torch.uint8, device="cuda")
+    cam = si.box_camera_persp((0.0,) * 3, (2 * math.pi,) * 3, 1024, 1024)
+    colours = [[0.9, 0.35, 0.25], [0.25, 0.6, 0.9], [0.35, 0.85, 0.4], [0.95, 0.8, 0.25]] * 16
+    masks = [sum(1 << (4 * k + q) for k in range(16)) for q in range(4)]
+
+    def snapshot(s):
+        ud, vd, wd = comps(s % distinct)
+        S.sem_qcriterion_batch(ctx, meshes, ud, vd, wd, [p["Q"] for p in parts])
+        for f in range(2):
+            for k, p in enumerate(parts):
+                fld = p["Q"] if f == 0 else ud[k]
+                fn = S.sem_isosurface_multi_async if k == 0 else S.sem_isosurface_multi_append_async
+                fn(ctx, p["m"], fld, isos[f], tris[f], cnt[f][4 * k:4 * k + 5], cap=cap[f])
+            for q in range(4):
+                S.sem_render_segments_async(ctx, tris[f], cap[f], cnt[f], 64, colours, masks[q], cam, 1024, 1024,
+                                            frames[s, f, q], None)
+
+    def step():
+        for s in range(snapshots):
+            snapshot(s)
 
     def plain():
-        for p in parts:
-            S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
-            for k, (fld, isos) in enumerate(((p["Q"], qisos), (p["vel"][0], uisos))):
-                c = S.sem_isosurface_multi(ctx, p["m"], fld, isos, p["tris"][k], cap=p["cap"][k])
-                S.sem_render(ctx, p["tris"][k], sum(c), c, None, p["cam"], 1024, 1024, p["img"][k], None)
-
-    def tail():
-        for p in parts:
-            for k, (fld, isos) in enumerate(((p["Q"], qisos), (p["vel"][0], uisos))):
-                S.sem_isosurface_multi_async(ctx, p["m"], fld, isos, p["tris"][k], p["cnt"][k], cap=p["cap"][k])
-                S.sem_render_async(ctx, p["tris"][k], p["cap"][k], p["cnt"][k], 4, None, p["cam"], 1024, 1024,
-                                   p["img"][k], None)
-
-    def per_partition():
-        for p in parts:
-            S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"])
-        tail()
-
-    def batched():
-        S.sem_qcriterion_batch(ctx, [p["m"] for p in parts], [p["vel"][0] for p in parts],
-                               [p["vel"][1] for p in parts], [p["vel"][2] for p in parts], [p["Q"] for p in parts])
-        tail()
+        for s in range(snapshots):
+            snapshot(s)
+            S.sem_synchronize(ctx)
 
     stream = torch.cuda.current_stream()
+    step()  # first call of each shape: scratch sized, launch widths tuned
+    S.sem_synchronize(ctx)
+    t0 = time.perf_counter()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(ctx, torch.cuda.current_stream())
+        step()
+    S.sem_set_stream(ctx, stream)
+    g.replay()  # instantiation
+    torch.cuda.synchronize()
+    capture_s = time.perf_counter() - t0
 
-    def timed(fn):
-        for _ in range(warmup):
-            fn()
+    def timed(fn, n):
+        fn()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(steps):
+        for _ in range(n):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        return a.elapsed_time(b) / steps
+        return a.elapsed_time(b) / n
 
-    def graph_of(fn):
-        fn()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            S.sem_set_stream(ctx, torch.cuda.current_stream())
-            fn()
-        S.sem_set_stream(ctx, stream)
-        return g.replay
-
-    ms_plain = timed(plain)
-    ms_pp = timed(graph_of(per_partition))
-    ms_b = timed(graph_of(batched))
-    S.sem_synchronize(ctx)
-    # the Q stage alone, per partition vs batched (graphs)
-    qpp = graph_of(lambda: [S.sem_qcriterion(ctx, p["m"], *p["vel"], p["Q"]) for p in parts])
-    qb = graph_of(lambda: S.sem_qcriterion_batch(ctx, [p["m"] for p in parts], [p["vel"][0] for p in parts],
-                                                 [p["vel"][1] for p in parts], [p["vel"][2] for p in parts],
-                                                 [p["Q"] for p in parts]))
-    ms_qpp, ms_qb = timed(qpp), timed(qb)
+    ms_graph = timed(g.replay, steps)
+    S.sem_synchronize(ctx)  # capacity or timeout flags raised inside the graph
+    ms_plain = timed(plain, 1)
+    covered = float((frames[:, :, :, 3::4] > 0).float().mean())
+    out = {"workload": f"{snapshots} snapshots x 16 partitions (E_p ~ U{{4096..40960}}, N_p in {{5,7,9}}, "
+                       f"{E_total} elements, {nodes} nodes per snapshot) of the Taylor-Green field with 1e-3 noise; "
+                       "Q and u isosurfaces at {0.05,0.1,0.2,0.4} of their maxima; one 1024x1024 frame per "
+                       "snapshot, field and isovalue (512 per graph); one CUDA graph per time step",
+           "snapshots": snapshots, "distinct_resident_snapshots": distinct,
+           "resident_velocity_bytes": int(12 * nodes * distinct), "elements_per_snapshot": E_total,
+           "orders": [p["N"] for p in parts], "partition_elements": [p["E"] for p in parts],
+           "frames_per_graph": snapshots * 8, "graph_nodes_approx": None,
+           "graph_ms": round(ms_graph, 3), "graph_frames_per_s": round(snapshots * 8 / (ms_graph * 1e-3), 1),
+           "graph_elements_per_s": round(snapshots * E_total / (ms_graph * 1e-3), 1),
+           "plain_ms": round(ms_plain, 3), "plain_frames_per_s": round(snapshots * 8 / (ms_plain * 1e-3), 1),
+           "plain_elements_per_s": round(snapshots * E_total / (ms_plain * 1e-3), 1),
+           "graph_speedup_vs_plain": round(ms_plain / ms_graph, 3),
+           "max_triangles_per_snapshot": need, "frame_coverage": round(covered, 4),
+           "setup_s": {"generate": round(gen_s, 1), "capture_and_instantiate": round(capture_s, 2)},
+           "autotune_widths": S.sem_autotune_width_choices(ctx)}
+    del g, frames, tris
     for p in parts:
         S.sem_mesh_free(p["m"])
-    eps = lambda ms: round(E_total / (ms * 1e-3), 1)  # noqa: E731
-    return {"workload": "16 partitions, E_p ~ U{4096..40960}, N_p in {5,7,9}, Taylor-Green; Q + 4 isovalues "
-                        "of Q and of u + one 1024x1024 frame per partition and field",
-            "elements": E_total, "orders": [p["N"] for p in parts],
-            "plain_ms": round(ms_plain, 4), "plain_elements_per_s": eps(ms_plain),
-            "graph_per_partition_ms": round(ms_pp, 4), "graph_per_partition_elements_per_s": eps(ms_pp),
-            "graph_batched_ms": round(ms_b, 4), "graph_batched_elements_per_s": eps(ms_b),
-            "q_only_per_partition_ms": round(ms_qpp, 4), "q_only_batched_ms": round(ms_qb, 4)}
+    parts.clear()
+    torch.cuda.empty_cache()
+    return out
 
 
 def _peaks():
@@ -895,7 +921,7 @@ def run_ours(args):
 
     ctx2 = S.sem_create(local, torch.cuda.current_stream())
     try:
-        batched = measure_batched(S, ctx2) if args.batched else None
+        batched = None if args.no_batched else measure_batched(S, ctx2, snapshots=args.batched_snapshots)
         learned = None
         if not args.no_learned:
             bpk = peaks.get("bf16_tflops")
@@ -1069,8 +1095,9 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the autoencoder measurement")
     ap.add_argument("--curved", action="store_true",
                     help="also time sem_qcriterion on a general (curved) 32^3 mesh (extra.channel32.curved)")
-    ap.add_argument("--batched", action="store_true",
-                    help="also time the batching workload: plain path vs CUDA graph vs batched Q (batched)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batching workload (64 snapshots x 16 partitions x 2 fields x 4 isovalues per graph)")
+    ap.add_argument("--batched-snapshots", type=int, default=64)
     ap.add_argument("--q-precisions", action="store_true",
                     help="also time sem_qcriterion at FP32, BF16, FP16, split BF16 and TF32 (q_precisions)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

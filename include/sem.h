@@ -311,6 +311,19 @@ SEM_API sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntr
                                     int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H,
                                     uint8_t *rgba, float *depth);
 
+/* sem_render_async with up to 64 segments, of which only those whose bit is set in seg_mask
+ * (bit s for segment s) are drawn, e.g. one isovalue out of the (partition, isovalue) segments
+ * that several sem_isosurface_multi_async / _append_async calls wrote back to back.  Triangles of
+ * segments not drawn neither cover pixels nor take part in the depth test; the frame equals
+ * sem_render of the drawn segments' triangles alone with their indices unchanged (ties between
+ * equal depths still go to the lower index).  nseg in [1, 64]; seg_rgb (HOST, 3 nseg floats, or
+ * NULL = the built-in palette repeated every 16 segments).  Other arguments and rules as
+ * sem_render_async. */
+SEM_API sem_status sem_render_segments_async(sem_ctx *ctx, const float *tris, int64_t ntri_max,
+                                             const int64_t *seg_start_dev, int nseg, const float *seg_rgb,
+                                             uint64_t seg_mask, const sem_camera *cam, int W, int H, uint8_t *rgba,
+                                             float *depth);
+
 /* FP64 reductions of a triangle soup (device, ntri*9 floats): out_host[0] = total area
  * sum |(p1-p0)x(p2-p0)|/2, out_host[1] = enclosed volume sum p0.(p1 x p2)/6 (divergence
  * theorem; positive when normals point out of the enclosed region).  Synchronises. */
@@ -410,6 +423,18 @@ SEM_API sem_status sem_autotune_set(sem_ctx *ctx, int on);
  * milliseconds. */
 SEM_API sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t *E, int *niso, int *units,
                                            float *ms);
+/* The same switch tunes launch widths whose choice does not change any result: the persistent Q
+ * kernels' CTAs per SM (so the elements each CTA walks through; kind 1: the N = 7 Q kernel,
+ * 2: the N = 7 Q kernel with triangle counting, 3: other orders' Q, 4: other orders'
+ * derivatives), chosen per (kind, order N, elements) among 1 .. the resident maximum; and the
+ * grids of the render's large-triangle and resolve passes (kind 5, N = W, size = H), chosen per
+ * frame size among five (large, resolve) pairs of CTAs per SM, width 0..4 = (6, 8), (4, 4),
+ * (8, 16), (2, 8), (6, 2).  The first call of a key with tuning on, outside stream capture and
+ * tracing, runs every candidate (twice, the second timed) and keeps the fastest; the others use
+ * the widest Q launch and pair 0.  sem_autotune_width_entry reads choice k (SEM_ERR_ARG past the
+ * last one). */
+SEM_API sem_status sem_autotune_width_entry(sem_ctx *ctx, int k, int *kind, int *N, int64_t *size, int *width,
+                                            float *ms);
 SEM_API sem_status sem_autotune_entry(sem_ctx *ctx, int k, int64_t *M, int *N, int *K, int *mode, int *bn,
                                       int *stages, int *split, float *ms);
 

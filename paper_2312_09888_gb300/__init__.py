@@ -75,6 +75,8 @@ def _declare(L):
     L.sem_isosurface_multi_append_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_qcriterion_isosurface_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, i64, vp]
     L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
+    L.sem_render_segments_async.argtypes = [vp, vp, i64, vp, i32, vp, C.c_uint64, C.POINTER(sem_camera), i32, i32,
+                                            vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
     L.sem_render.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_surface_measures.argtypes = [vp, vp, i64, vp]
@@ -103,9 +105,12 @@ def _declare(L):
     L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 6 + [C.POINTER(f32)]
     L.sem_autotune_emit_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                           C.POINTER(f32)]
+    L.sem_autotune_width_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
+                                           C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_debug_set_wait_limit", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
                  "sem_isosurface_multi_append_async", "sem_qcriterion_isosurface_async", "sem_render_async",
+                 "sem_render_segments_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
         getattr(L, name).restype = i32
@@ -366,6 +371,21 @@ def sem_render_async(ctx, tris, ntri_max: int, seg_start_dev, nseg: int, seg_rgb
     _check(ctx, st)
 
 
+def sem_render_segments_async(ctx, tris, ntri_max: int, seg_start_dev, nseg: int, seg_rgb, seg_mask: int, cam: dict,
+                              W: int, H: int, rgba, depth=None) -> None:
+    """sem_render_async of up to 64 segments, drawing only those whose bit is set in seg_mask."""
+    import torch
+    rgb = None if seg_rgb is None else np.ascontiguousarray(np.asarray(seg_rgb, dtype=np.float32).reshape(-1))
+    camc = make_camera(cam)
+    st = get_lib().sem_render_segments_async(ctx, _dev(tris, "tris", torch.float32, allow_none=ntri_max == 0),
+                                             int(ntri_max), _dev(seg_start_dev, "seg_start_dev", torch.int64),
+                                             int(nseg), None if rgb is None else rgb.ctypes.data_as(C.c_void_p),
+                                             C.c_uint64(int(seg_mask) & ((1 << 64) - 1)), C.byref(camc), int(W),
+                                             int(H), _dev(rgba, "rgba", torch.uint8),
+                                             _dev(depth, "depth", torch.float32, allow_none=True))
+    _check(ctx, st)
+
+
 def sem_isosurface_noalloc(ctx, mesh, f, iso: float, tris, tri_elem=None, cases=None,
                            cap: Optional[int] = None) -> int:
     """As sem_isosurface, for callers that may not allocate device memory during the call:
@@ -571,6 +591,19 @@ def sem_autotune_emit_choices(ctx) -> list:
         if st != SEM_OK:
             return out
         out.append((N.value, E.value, nq.value, units.value, ms.value))
+        k += 1
+
+
+def sem_autotune_width_choices(ctx) -> list:
+    """Launch widths the autotuner chose: (kind, N, size, width, ms) per entry (see sem.h)."""
+    out = []
+    k = 0
+    while True:
+        kind, N, size, width, ms = C.c_int(), C.c_int(), C.c_int64(), C.c_int(), C.c_float()
+        if get_lib().sem_autotune_width_entry(ctx, k, C.byref(kind), C.byref(N), C.byref(size), C.byref(width),
+                                              C.byref(ms)) != SEM_OK:
+            return out
+        out.append((kind.value, N.value, size.value, width.value, ms.value))
         k += 1
 
 

@@ -1150,6 +1150,7 @@ sem_status sem_autotune_set(sem_ctx *ctx, int on)
     if (!on) {
         ctx->gemm_tune.clear();
         ctx->emit_tune.clear();
+        ctx->width_tune.clear();
     }
     return SEM_OK;
 }
@@ -1165,6 +1166,21 @@ sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t *E, int 
     *E = t.E;
     *niso = t.niso;
     *units = t.units;
+    *ms = t.ms;
+    return SEM_OK;
+}
+
+sem_status sem_autotune_width_entry(sem_ctx *ctx, int k, int *kind, int *N, int64_t *size, int *width, float *ms)
+{
+    if (!ctx || !kind || !N || !size || !width || !ms) return SEM_ERR_ARG;
+    if (k < 0 || k >= (int)ctx->width_tune.size())
+        return sem_fail(ctx, SEM_ERR_ARG, "sem_autotune_width_entry: index %d outside [0, %d)", k,
+                        (int)ctx->width_tune.size());
+    const auto &t = ctx->width_tune[k];
+    *kind = t.kind;
+    *N = t.N;
+    *size = t.size;
+    *width = t.width;
     *ms = t.ms;
     return SEM_OK;
 }

@@ -791,25 +791,43 @@ sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mesh *m, co
     return iso_run_multi_async(ctx, m, f, isos, niso, tris, tri_elem, cap, counts_dev, cases, true);
 }
 
-sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
-                            const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
+static sem_status render_async_checked(sem_ctx *ctx, const char *fn, const float *tris, int64_t ntri_max,
+                                       const int64_t *seg_start_dev, int nseg, int max_seg, const float *seg_rgb,
+                                       unsigned long long seg_mask, const sem_camera *cam, int W, int H,
+                                       uint8_t *rgba, float *depth)
 {
     if (!ctx) return SEM_ERR_ARG;
     SEM_CU(ctx, cudaSetDevice(ctx->device));
-    if (!cam) return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: cam is NULL");
-    if (W < 1 || H < 1 || W > 16384 || H > 16384) return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad size");
-    if (ntri_max < 0 || ntri_max >= ((int64_t)1 << 31) || nseg < 1 || nseg > 16)
-        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad ntri_max or nseg");
-    SEM_TRY(check_ptr(ctx, seg_start_dev, "sem_render_async", "seg_start_dev", false, 8));
-    SEM_TRY(check_ptr(ctx, tris, "sem_render_async", "tris", ntri_max == 0, 4));
-    SEM_TRY(check_ptr(ctx, rgba, "sem_render_async", "rgba"));
-    SEM_TRY(check_ptr(ctx, depth, "sem_render_async", "depth", true));
+    if (!cam) return sem_fail(ctx, SEM_ERR_ARG, "%s: cam is NULL", fn);
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return sem_fail(ctx, SEM_ERR_ARG, "%s: bad size", fn);
+    if (ntri_max < 0 || ntri_max >= ((int64_t)1 << 31) || nseg < 1 || nseg > max_seg)
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: bad ntri_max or nseg", fn);
+    SEM_TRY(check_ptr(ctx, seg_start_dev, fn, "seg_start_dev", false, 8));
+    SEM_TRY(check_ptr(ctx, tris, fn, "tris", ntri_max == 0, 4));
+    SEM_TRY(check_ptr(ctx, rgba, fn, "rgba"));
+    SEM_TRY(check_ptr(ctx, depth, fn, "depth", true));
     if (!(cam->znear > 0.f) || !(cam->zfar > cam->znear))
-        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: need 0 < znear < zfar");
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: need 0 < znear < zfar", fn);
     if (cam->ortho ? !(cam->half_h > 0.f) : !(cam->fovy_deg > 0.f && cam->fovy_deg < 180.f))
-        return sem_fail(ctx, SEM_ERR_ARG, "sem_render_async: bad projection parameters");
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: bad projection parameters", fn);
     std::vector<int64_t> dummy(nseg, 0);
-    return render_run(ctx, tris, ntri_max, dummy.data(), nseg, seg_rgb, cam, W, H, rgba, depth, seg_start_dev);
+    return render_run(ctx, tris, ntri_max, dummy.data(), nseg, seg_rgb, cam, W, H, rgba, depth, seg_start_dev,
+                      seg_mask);
+}
+
+sem_status sem_render_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
+                            const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
+{
+    return render_async_checked(ctx, "sem_render_async", tris, ntri_max, seg_start_dev, nseg, 16, seg_rgb, ~0ull,
+                                cam, W, H, rgba, depth);
+}
+
+sem_status sem_render_segments_async(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
+                                     int nseg, const float *seg_rgb, uint64_t seg_mask, const sem_camera *cam, int W,
+                                     int H, uint8_t *rgba, float *depth)
+{
+    return render_async_checked(ctx, "sem_render_segments_async", tris, ntri_max, seg_start_dev, nseg, 64, seg_rgb,
+                                (unsigned long long)seg_mask, cam, W, H, rgba, depth);
 }
 
 sem_status sem_isosurface_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, float iso, float *tris,

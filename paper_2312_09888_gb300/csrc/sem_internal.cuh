@@ -58,6 +58,15 @@ struct sem_ctx {
         float ms;
     };
     std::vector<EmitTune> emit_tune;
+    // and the launch width of persistent kernels (CTAs per SM, so elements per CTA) and the
+    // render passes' grids, per (kernel, order, size); kind names the kernel (see LaunchTune)
+    struct WidthTune {
+        int kind, N;
+        int64_t size;
+        int width;
+        float ms;
+    };
+    std::vector<WidthTune> width_tune;
     // device bytes the library holds for this context (scratch arenas, tables, meshes,
     // autoencoders) and their high-water mark
     int64_t mem_now = 0, mem_peak = 0;
@@ -162,6 +171,47 @@ inline sem_status kernel_setup(sem_ctx *ctx, KernelSetup &ks, K kern, int thread
     return SEM_OK;
 }
 
+// Launch-width autotuner of persistent kernels whose output does not depend on the width:
+// the first call of a given (kind, N, size) with tuning on and the stream not being captured runs
+// `launch(w)` for every candidate width (each twice, the second timed with CUDA events), keeps the
+// fastest and reuses it; otherwise `dflt`.  The last candidate's output is the call's output.
+enum { TUNE_Q8 = 1, TUNE_Q8_COUNT = 2, TUNE_QGRAD = 3, TUNE_QGRAD_DERIV = 4, TUNE_RENDER = 5 };
+template <class Launch>
+inline sem_status width_tuned(sem_ctx *ctx, int kind, int N, int64_t size, const int *cand, int ncand, int dflt,
+                              Launch launch)
+{
+    for (const auto &t : ctx->width_tune)
+        if (t.kind == kind && t.N == N && t.size == size) return launch(t.width);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (!ctx->autotune || cs != cudaStreamCaptureStatusNone || ctx->trace_on || ncand < 2) return launch(dflt);
+    cudaEvent_t e0, e1;
+    SEM_CU(ctx, cudaEventCreate(&e0));
+    SEM_CU(ctx, cudaEventCreate(&e1));
+    int best = dflt;
+    float best_ms = 1e30f;
+    sem_status st = SEM_OK;
+    for (int c = 0; c < ncand && st == SEM_OK; ++c) {
+        for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
+            if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
+            if (st == SEM_OK) st = launch(cand[c]);
+            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+        }
+        float ms = 0.f;
+        if (st == SEM_OK) st = sem_cuda(ctx, cudaEventSynchronize(e1), "event");
+        if (st == SEM_OK) st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event");
+        if (st == SEM_OK && ms < best_ms) {
+            best_ms = ms;
+            best = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    SEM_TRY(st);
+    ctx->width_tune.push_back({kind, N, size, best, best_ms});
+    return SEM_OK;
+}
+
 static inline bool sem_aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // ------------------------------------------------------------------------------------------
@@ -198,7 +248,7 @@ sem_status iso_run_noalloc(sem_ctx *ctx, const sem_mesh *m, const float *f, floa
 sem_status iso_noalloc_prepare(sem_ctx *ctx);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
-                      const int64_t *seg_start_dev = nullptr);
+                      const int64_t *seg_start_dev = nullptr, unsigned long long seg_mask = ~0ull);
 sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);
 sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host);
 

@@ -739,6 +739,15 @@ static void fill_batch(GBatch &B, int n, int epb, const sem_mesh *const *m, cons
     B.gstart[n] = g;
 }
 
+// Candidate launch widths of a persistent Q kernel: 1 .. max_per_sm resident CTAs per SM (the
+// elements each CTA walks through scale inversely), the widest first
+static int q_width_candidates(int max_per_sm, int *cand)
+{
+    int n = 0;
+    for (int w = max_per_sm; w >= 1 && n < 4; --w) cand[n++] = w;
+    return n;
+}
+
 template <bool COUNT>
 static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
 {
@@ -747,11 +756,17 @@ static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
     SEM_TRY(kernel_setup(ctx, ks, k_sem_q8<COUNT>, 256, q8::SMEM, &per_sm));
     const int64_t ngroups = B.gstart[B.n];
     if (ngroups == 0) return SEM_OK;
-    int64_t grid = (int64_t)ctx->sm_count * per_sm;
-    if (grid > ngroups) grid = ngroups;
-    SEM_TRACED(ctx, COUNT ? "k_sem_q8_count" : "k_sem_q8",
-               k_sem_q8<COUNT><<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(B, ctx->d_flag));
-    return sem_cuda(ctx, cudaGetLastError(), "k_sem_q8 launch");
+    int cand[4];
+    const int nc = q_width_candidates(per_sm, cand);
+    int64_t E = 0;
+    for (int p = 0; p < B.n; ++p) E += B.E[p];
+    return width_tuned(ctx, COUNT ? TUNE_Q8_COUNT : TUNE_Q8, 7, E, cand, nc, per_sm, [&](int w) -> sem_status {
+        int64_t grid = (int64_t)ctx->sm_count * w;
+        if (grid > ngroups) grid = ngroups;
+        SEM_TRACED(ctx, COUNT ? "k_sem_q8_count" : "k_sem_q8",
+                   k_sem_q8<COUNT><<<(unsigned)grid, 256, q8::SMEM, ctx->stream>>>(B, ctx->d_flag));
+        return sem_cuda(ctx, cudaGetLastError(), "k_sem_q8 launch");
+    });
 }
 
 template <int NP, int NC>
@@ -765,10 +780,18 @@ static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
     SEM_TRY(kernel_setup(ctx, ks, kern, C::NT, smem, &per_sm));
     const int64_t ngroups = B.gstart[B.n];
     if (ngroups == 0) return SEM_OK;
-    int64_t grid = (int64_t)ctx->sm_count * per_sm;
-    if (grid > ngroups) grid = ngroups;
-    SEM_TRACED(ctx, "k_sem_grad", kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(B, ctx->d_flag));
-    return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
+    int cand[4];
+    const int nc = q_width_candidates(per_sm, cand);
+    int64_t E = 0;
+    for (int p = 0; p < B.n; ++p) E += B.E[p];
+    return width_tuned(ctx, NC == 3 ? TUNE_QGRAD : TUNE_QGRAD_DERIV, NP - 1, E, cand, nc, per_sm,
+                       [&](int w) -> sem_status {
+                           int64_t grid = (int64_t)ctx->sm_count * w;
+                           if (grid > ngroups) grid = ngroups;
+                           SEM_TRACED(ctx, "k_sem_grad",
+                                      kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(B, ctx->d_flag));
+                           return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
+                       });
 }
 
 template <int NC>

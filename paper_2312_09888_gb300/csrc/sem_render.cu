@@ -35,6 +35,7 @@
 
 #define SMALL_PX 32        // boxes with at most this many pixel centres: the warp's candidate list
 #define LARGE_THREADS 256
+#define RENDER_MAX_SEG 64  // segments of sem_render_segments_async (16 for sem_render, sem_render_async)
 
 struct RenderParams {
     float eye[3], s[3], u[3], f[3];
@@ -46,9 +47,10 @@ struct RenderParams {
     float hw, hh;        // W / 2, H / 2 (viewport: sx = hw (xn + 1), sy = hh (1 - yn))
     float wmax, hmax;    // W - 1, H - 1
     int nseg;
-    int seg_end[16];
-    float rgb[16][3];
+    int seg_end[RENDER_MAX_SEG];
+    float rgb[RENDER_MAX_SEG][3];
     const int64_t *seg_dev;  // device segment starts [nseg + 1] (asynchronous render), or null
+    unsigned long long seg_mask;  // bit s set: segment s is drawn (all ones: every segment)
 };
 
 // Screen position of one vertex; the NDC depth is finished in setup_tri only for triangles that
@@ -269,15 +271,26 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         s_next = sg < P.nseg - 1 ? seg_start(P, sg + 1) : INT64_MAX;
     }
     __syncthreads();
+    if (P.seg_mask != ~0ull) {
+        // a block whose triangles all lie in segments that are not drawn leaves at once
+        __shared__ int s_any;
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int sg = s_sg0; sg < P.nseg && seg_start(P, sg) < t0 + nt_blk; ++sg) any |= (int)((P.seg_mask >> sg) & 1ull);
+            s_any = any;
+        }
+        __syncthreads();
+        if (!s_any) return;
+    }
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
     bool is_large = false;
     int npx = 0;
-    if ((int)threadIdx.x < nt_blk) {
+    const int sg = (int)threadIdx.x < nt_blk ? (t < s_next ? s_sg0 : seg_of(P, t, s_sg0)) : 0;
+    if ((int)threadIdx.x < nt_blk && ((P.seg_mask >> sg) & 1ull)) {
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
             // only triangles that cover a pixel centre can win a pixel: their colour, once
-            const int sg = t < s_next ? s_sg0 : seg_of(P, t, s_sg0);
             colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, sg);
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
@@ -441,8 +454,9 @@ static void unit3(double *a)
 
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
-                      const int64_t *seg_start_dev)
+                      const int64_t *seg_start_dev, unsigned long long seg_mask)
 {
+    if (nseg < 1 || nseg > RENDER_MAX_SEG) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: nseg=%d", nseg);
     RenderParams P;
     memset(&P, 0, sizeof P);
     double f[3], s[3], u[3], up[3];
@@ -490,11 +504,12 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     P.hmax = (float)(H - 1);
     P.nseg = nseg;
     P.seg_dev = seg_start_dev;
+    P.seg_mask = nseg == 64 ? seg_mask : (seg_mask | ~((1ull << nseg) - 1ull));
     int64_t acc = 0;
     for (int k = 0; k < nseg; ++k) {
         acc += seg_ntri[k];
         P.seg_end[k] = (int)acc;
-        for (int c = 0; c < 3; ++c) P.rgb[k][c] = seg_rgb ? seg_rgb[3 * k + c] : kPalette[k][c];
+        for (int c = 0; c < 3; ++c) P.rgb[k][c] = seg_rgb ? seg_rgb[3 * k + c] : kPalette[k % 16][c];
     }
     const int ntri = (int)ntri64;
     const int64_t npx = (int64_t)W * H;
@@ -519,21 +534,30 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     int32_t *nlarge = reinterpret_cast<int32_t *>(lscr);
     int32_t *large = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(lscr) + 256);
     uint32_t *colors = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(lscr) + 256 + list_bytes);
-    // until k_resolve has run, the keys are not all "empty"
-    ctx->render_keys_dirty = true;
-    SEM_CU(ctx, cudaMemsetAsync(nlarge, 0, sizeof(int32_t), ctx->stream));
-    if (ntri > 0) {
-        SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(tris, ntri, P, keys, large, nlarge,
-                                                                                            colors));
+    // one frame; the widths of the persistent large-triangle pass and of the resolve pass (in
+    // CTAs per SM) come from the context's autotuner, chosen per frame size on the first frame:
+    // the frame leaves the key buffer all "empty" again, so every candidate draws the same image
+    static const int kLarge[5] = {6, 4, 8, 2, 6}, kResolve[5] = {8, 4, 16, 8, 2};
+    auto frame = [&](int w) -> sem_status {
+        // until k_resolve has run, the keys are not all "empty"
+        ctx->render_keys_dirty = true;
+        SEM_CU(ctx, cudaMemsetAsync(nlarge, 0, sizeof(int32_t), ctx->stream));
+        if (ntri > 0) {
+            SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(
+                                                  tris, ntri, P, keys, large, nlarge, colors));
+            SEM_CU(ctx, cudaGetLastError());
+            SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<kLarge[w] * ctx->sm_count, LARGE_THREADS, 0,
+                                                               ctx->stream>>>(tris, large, nlarge, P, keys));
+            SEM_CU(ctx, cudaGetLastError());
+        }
+        const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>((npx / 4 + 255) / 256,
+                                                                     (int64_t)kResolve[w] * ctx->sm_count));
+        SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)rgrid, 256, 0, ctx->stream>>>(
+                                         colors, npx, keys, reinterpret_cast<uint32_t *>(rgba), depth));
         SEM_CU(ctx, cudaGetLastError());
-        SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<6 * ctx->sm_count, LARGE_THREADS, 0, ctx->stream>>>(tris, large, nlarge, P, keys));
-        SEM_CU(ctx, cudaGetLastError());
-    }
-    SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((npx / 4 + 255) / 256,
-                                                                                          8 * ctx->sm_count)),
-                                               256, 0, ctx->stream>>>(
-                                     colors, npx, keys, reinterpret_cast<uint32_t *>(rgba), depth));
-    SEM_CU(ctx, cudaGetLastError());
-    ctx->render_keys_dirty = false;
-    return SEM_OK;
+        ctx->render_keys_dirty = false;
+        return SEM_OK;
+    };
+    static const int kCand[5] = {0, 1, 2, 3, 4};
+    return width_tuned(ctx, TUNE_RENDER, W, H, kCand, ntri > 0 ? 5 : 1, 0, frame);
 }

@@ -214,6 +214,33 @@ def taylor_green(mesh: BoxMesh, noise_sigma: float = 0.0, seed: int = 0, device=
     return torch.stack([mesh.gather(c, idx) for c in comps])
 
 
+def taylor_green_snapshots(mesh: BoxMesh, E: int, phases, noise_sigma: float, seed: int,
+                           device="cuda") -> list:
+    """The snapshots of the batching workload: for each phase, (3, E, NP^3) float32 of the first
+    E elements of ``mesh`` holding taylor_green()'s field (u = sin x cos y cos z, v = -cos x sin y
+    cos z, w = 0, shifted by the phase in x and y) plus i.i.d. N(0, sigma^2) noise per global node
+    (shared face nodes share the sample).  The noise comes from torch's generator seeded with
+    ``seed`` on the device rather than numpy's on the host, so 64 snapshots of 16 partitions take
+    seconds; the values therefore differ from taylor_green()'s for the same seed, not their law."""
+    X, Y, Z = mesh.grids(device)
+    shape = mesh.global_shape()
+    idx = mesh.flat_index(device)[:E]
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    out = []
+    for ph in phases:
+        Xp, Yp = X + ph, Y + ph
+        base = [torch.sin(Xp) * torch.cos(Yp) * torch.cos(Z), -torch.cos(Xp) * torch.sin(Yp) * torch.cos(Z), None]
+        comps = []
+        for c in range(3):
+            f = torch.randn(shape, generator=g, device=device, dtype=torch.float64) * noise_sigma
+            if base[c] is not None:
+                f += base[c]
+            comps.append(f.reshape(-1)[idx].float())
+        out.append(torch.stack(comps))
+    return out
+
+
 def _random_modes(rng, nmodes, kmin, kmax, int_x, int_y, even_z):
     ks, amps, dirs, phases = [], [], [], []
     for _ in range(nmodes):
@@ -399,6 +426,20 @@ def rb_box(nel: int = 64, N: int = 7, W: int = 3840, H: int = 2160, device="cpu"
     cam = box_camera_persp((0.0, 0.0, 0.0), (TWO_PI, TWO_PI, 1.0), W, H,
                            direction=(1.0, -1.2, 0.8), up=(0.0, 0.0, 1.0))
     return Workload(f"rb_{nel}^3_N{N}", 3, mesh, [0.1], cam, f, extra=dict(t_iso=0.5))
+
+
+def batching_partitions() -> list:
+    """The batching workload's 16 partitions: E_p ~ U{4096..40960} elements and N_p in {5, 7, 9}
+    (seeded), each the lexicographically first E_p elements of a ceil(E_p^(1/3))^3 lattice of
+    [0, 2 pi]^3.  Returns dicts with E, N and mesh (the whole lattice; its first E elements are
+    the partition)."""
+    rng = np.random.default_rng(seed_for(4, 0))
+    parts = []
+    for _ in range(16):
+        Ep, N = int(rng.integers(4096, 40961)), int(rng.choice([5, 7, 9]))
+        n = int(math.ceil(Ep ** (1.0 / 3.0) - 1e-9))
+        parts.append(dict(E=Ep, N=N, mesh=uniform_box((n, n, n), (0.0,) * 3, (TWO_PI,) * 3, N)))
+    return parts
 
 
 def element_slice(w: Workload, e0: int, e1: int) -> dict:

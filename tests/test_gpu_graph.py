@@ -386,3 +386,55 @@ def test_fused_q_isosurface_overflow_is_flagged(gpu, sess):
         S.sem_synchronize(sess.ctx)
     assert ex.value.status == S.SEM_ERR_CAPACITY
     assert int(cnt[-1]) > 50 and (tris == -1.0).all()
+
+
+def test_batching_partitions_against_the_oracle_sampled(gpu, sess, orc):
+    """The batching workload's partitions at full size (16 partitions of U{4096..40960} elements,
+    orders 5, 7 and 9), snapshot 1: Q of all partitions in one batched call, then the Q and u
+    isosurfaces at the workload's four isovalues.  On 48 seeded sampled elements per partition,
+    Q within its per-node bound and every cell's case equal the oracle's (from the GPU's FP32 Q
+    for the isosurface), and the elements' triangle counts equal the oracle's."""
+    import math
+    from _helpers import box_factors, grad_bounds, q_bound
+    S = gpu
+    parts = si.batching_partitions()
+    for p in parts:
+        p["xyz"] = p["mesh"].xyz_range(0, p["E"])
+        p["m"] = sess.mesh(p["N"], p["xyz"])
+        p["vel"] = si.taylor_green_snapshots(p["mesh"], p["E"], [2 * math.pi / 64], 1e-3, si.seed_for(4, 17))[0]
+        p["Q"] = torch.empty(p["E"] * (p["N"] + 1) ** 3, device="cuda")
+    S.sem_qcriterion_batch(sess.ctx, [p["m"] for p in parts], [p["vel"][0].reshape(-1) for p in parts],
+                           [p["vel"][1].reshape(-1) for p in parts], [p["vel"][2].reshape(-1) for p in parts],
+                           [p["Q"] for p in parts])
+    qmax = max(S.sem_field_max(sess.ctx, p["Q"]) for p in parts)
+    umax = max(S.sem_field_max(sess.ctx, p["vel"][0].reshape(-1)) for p in parts)
+    fr = (0.05, 0.1, 0.2, 0.4)
+    isos = [[float(np.float32(f * qmax)) for f in fr], [float(np.float32(f * umax)) for f in fr]]
+    rng = np.random.default_rng(si.seed_for(4, 3))
+    for p in parts:
+        N, E = p["N"], p["E"]
+        NP3, N3 = (N + 1) ** 3, N ** 3
+        sample = np.sort(rng.choice(E, 48, replace=False))
+        st = torch.as_tensor(sample, device="cuda")
+        vel = p["vel"][:, st].double().cpu().numpy()
+        xs = p["xyz"][:, sample]
+        J = orc.gradient(N, xs, vel)
+        ref = orc.q_from_gradient(J)
+        Qs = p["Q"].view(E, NP3)[st].double().cpu().numpy()
+        dJ = np.stack([grad_bounds(orc.dmat(N), vel[c], box_factors(xs), N + 1, J[c]) for c in range(3)])
+        assert (np.abs(Qs - ref) <= q_bound(J, dJ)).all(), (N, E)
+        for f, fld in enumerate((p["Q"], p["vel"][0].reshape(-1))):
+            cs = torch.empty(4 * E * N3, dtype=torch.uint8, device="cuda")
+            counts = S.sem_isosurface_multi(sess.ctx, p["m"], fld, isos[f], None, cases=cs)
+            tris = torch.empty(max(1, sum(counts)) * 9, device="cuda")
+            te = torch.empty(max(1, sum(counts)), dtype=torch.int32, device="cuda")
+            S.sem_isosurface_multi(sess.ctx, p["m"], fld, isos[f], tris, tri_elem=te)
+            starts = np.concatenate([[0], np.cumsum(counts)])
+            tev = te.cpu().numpy()
+            fs = fld.view(E, NP3)[st].double().cpu().numpy()
+            for q in range(4):
+                r = orc.isosurface(N, xs, fs, isos[f][q], want_tris=False)
+                got = cs.view(4, E, N3)[q][st].cpu().numpy()
+                np.testing.assert_array_equal(got, r["cases"])
+                per_elem = np.bincount(tev[starts[q]:starts[q + 1]], minlength=E)[sample]
+                np.testing.assert_array_equal(per_elem, r["elem_ntri"])

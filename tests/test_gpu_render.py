@@ -175,3 +175,45 @@ def test_channel_benchmark_frame_full_size(gpu, sess, orc):
     assert (img[..., 3] > 0).mean() > 0.2
     print(f"\nchannel 32^3 frame: {n} triangles, {frac * 100:.3f}% of pixels within 1/255, "
           f"{dfrac * 100:.3f}% of compared depths within 1e-5")
+
+
+@pytest.mark.parametrize("nseg,seed", [(3, 1), (40, 2), (64, 3)])
+def test_render_segments_mask_draws_only_the_chosen_segments(gpu, sess, nseg, seed):
+    """sem_render_segments_async with a segment mask equals sem_render of the same buffer in which
+    the triangles of the segments not drawn are made degenerate (zero area: dropped) at the same
+    indices, bit for bit in colour and depth; one colour for all segments, up to 64 segments with
+    uneven boundaries."""
+    S = gpu
+    w = si.tgv_box(nel=6)
+    m = sess.mesh(7, w.mesh.xyz().numpy())
+    vel = [w.fields[c].float().cuda().contiguous() for c in range(3)]
+    Q = torch.empty_like(vel[0])
+    S.sem_qcriterion(sess.ctx, m, *vel, Q)
+    qmax = S.sem_field_max(sess.ctx, Q)
+    isos = [float(np.float32(f * qmax)) for f in (0.05, 0.1, 0.2)]
+    counts = S.sem_isosurface_multi(sess.ctx, m, Q, isos, None)
+    n = sum(counts)
+    tris = torch.empty(n * 9, device="cuda")
+    S.sem_isosurface_multi(sess.ctx, m, Q, isos, tris)
+    rng = np.random.default_rng(seed)
+    if nseg == 3:
+        starts = np.concatenate([[0], np.cumsum(counts)])
+        mask = 0b101
+    else:
+        starts = np.concatenate([[0], np.sort(rng.choice(np.arange(1, n), nseg - 1, replace=False)), [n]])
+        mask = int(rng.integers(1, 1 << 62)) | (1 << (nseg - 1))
+    sd = torch.as_tensor(starts.astype(np.int64), device="cuda")
+    cam, W, H = w.camera, w.camera["W"], w.camera["H"]
+    rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+    depth = torch.zeros(H * W, device="cuda")
+    S.sem_render_segments_async(sess.ctx, tris, n, sd, nseg, [[0.8, 0.4, 0.2]] * nseg, mask, cam, W, H, rgba, depth)
+    ref_t = tris.clone().view(-1, 9)
+    for sgm in range(nseg):
+        if not (mask >> sgm) & 1:
+            ref_t[starts[sgm]:starts[sgm + 1]] = 0.0
+    r_rgba = torch.zeros_like(rgba)
+    r_depth = torch.zeros_like(depth)
+    S.sem_render(sess.ctx, ref_t.view(-1), n, [n], [[0.8, 0.4, 0.2]], cam, W, H, r_rgba, r_depth)
+    S.sem_synchronize(sess.ctx)
+    assert torch.equal(rgba, r_rgba) and torch.equal(depth, r_depth)
+    assert (rgba.view(-1, 4)[:, 3] > 0).any()
