@@ -405,7 +405,7 @@ SEM_API sem_status sem_ae_decode(sem_ae *ae, const uint16_t *latent, int64_t E, 
 /* Autotuner of the tensor-core GEMM (on by default).  The first product of a given (M, N, K,
  * epilogue) on a context runs every candidate tile shape on the call's own data -- tile width
  * BN in {64, 128, 256}, 3 or 4 pipeline stages, and for FP32 weight gradients a K split in
- * {1, 2, 4, 8} with an ordered reduction of the partial sums -- and keeps the fastest (CUDA
+ * {1, 2, 4, 8, 16, 32} (at least 4 K blocks per split) with an ordered reduction of the partial sums -- and keeps the fastest (CUDA
  * events); later products of that shape reuse it.  Under stream capture, or when off, the
  * default (BN 128 where N allows, 4 stages, no split) runs.  sem_autotune_set(ctx, 0) turns
  * tuning off and forgets the choices; sem_autotune_entry reads choice k (SEM_ERR_ARG past the

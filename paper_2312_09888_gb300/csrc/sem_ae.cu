@@ -99,9 +99,17 @@ __device__ __forceinline__ void load8_bf16(const bf16 *p, float (&v)[8])
     for (int c = 0; c < 8; ++c) v[c] = __bfloat162float(t[c]);
 }
 
-// The fused tail of one row's 8 consecutive output columns n .. n+7.
-__device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, float (&v)[8], float &loss_acc,
-                                          float *__restrict__ c32)
+// The transposed copy (out_t) of the warp's 32 rows goes through shared memory: element (column
+// c, row lane) at tstage[c * 32 + lane], written back after the warp's last column as 16-byte
+// chunks of 8 rows, so a store covers 8 columns x 64 bytes instead of one 2-byte value per column.
+__device__ __forceinline__ void put_t(bf16 *__restrict__ tstage, int cl, float x)
+{
+    tstage[cl * 32 + (threadIdx.x & 31)] = __float2bfloat16_rn(x);
+}
+
+// The fused tail of one row's 8 consecutive output columns n .. n+7 (cl: n's column in the tile).
+__device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, int cl, float (&v)[8],
+                                          float &loss_acc, float *__restrict__ c32, bf16 *__restrict__ tstage)
 {
     if (row >= P.m_valid) {
         if (P.mode == EPI_LOSS) {
@@ -109,9 +117,12 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
             // otherwise reach the weight gradients)
             const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             store8_bf16(P.out + row * P.ld_out + n, z);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(0.f);
         }
+        // the transposed copy's padding rows are zero in every mode (the staging tile is written
+        // back whole)
+        if (P.out_t)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, 0.f);
         return;
     }
     switch (P.mode) {
@@ -132,7 +143,7 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
         store8_bf16(P.out + row * P.ld_out + n, v);
         store8_bf16(P.aux + row * P.ld_out + n, a);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(a[c]);
+        for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, a[c]);
         return;
     }
     case EPI_BIAS:
@@ -142,7 +153,7 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
             for (int c = 0; c < 8; ++c) v[c] += P.bias[n + c];
         store8_bf16(P.out + row * P.ld_out + n, v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
     }
     case EPI_LOSS: {
@@ -156,7 +167,7 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
         }
         store8_bf16(P.out + row * P.ld_out + n, v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
     }
     case EPI_DGELU: {
@@ -166,7 +177,7 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
         for (int c = 0; c < 8; ++c) v[c] *= gelu_grad_f(h[c]);
         store8_bf16(P.out + row * P.ld_out + n, v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) P.out_t[(int64_t)(n + c) * P.ld_t + row] = __float2bfloat16_rn(v[c]);
+        for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
     }
     case EPI_DECODE: {
@@ -267,18 +278,42 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (!ok) s_abort = 1;
         tc::fence_after_sync();
         if (ok && !*(volatile int *)&s_abort) {
+            // warps 2..5: one per TMEM lane quarter q = warp % 4 (a warp may only read its own)
             const int q = warp & 3;
+            const int cbeg = 0, cend = BN;
             const int64_t row = (int64_t)blockIdx.x * BM + q * 32 + lane;
             float loss_acc = 0.f;
             float *c32 = P.c32 + (int64_t)blockIdx.z * P.split_stride;  // this K slice's partial array
-            for (int c0 = 0; c0 < BN; c0 += 8) {
-                uint32_t r[8];
-                tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
-                tc::tmem_wait_ld();
-                float v[8];
+            // the pipeline's shared memory is idle once the accumulator is complete: warp q's
+            // transposed staging tile (BN columns x 32 rows of BF16)
+            bf16 *tstage = reinterpret_cast<bf16 *>(smem) + q * (BN * 32);
+            // 32 columns per TMEM round: four loads in flight, one wait
+            for (int c0 = cbeg; c0 < cend; c0 += 32) {
+                uint32_t r[4][8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
-                epilogue8(P, row, blockIdx.y * BN + c0, v, loss_acc, c32);
+                for (int h = 0; h < 4; ++h) tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0 + 8 * h), r[h]);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    float v[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[h][c]);
+                    epilogue8(P, row, blockIdx.y * BN + c0 + 8 * h, c0 + 8 * h, v, loss_acc, c32, tstage);
+                }
+            }
+            const bool has_t = P.out_t && (P.mode == EPI_BIAS_GELU || P.mode == EPI_BIAS || P.mode == EPI_LOSS ||
+                                           P.mode == EPI_DGELU || P.mode == EPI_PLAIN);
+            if (has_t) {
+                // out_t[n][row0 .. row0 + 31] for the tile's columns n: lane l takes column c + l / 4,
+                // rows 8 (l % 4) .. + 7 (row0 and ld_t are multiples of 32, so 16-byte aligned)
+                __syncwarp();
+                const int64_t row0 = (int64_t)blockIdx.x * BM + q * 32;
+                const int cq = lane >> 2, part = lane & 3;
+                for (int c = cbeg; c < cend; c += 8) {
+                    const int cl = c + cq;
+                    const uint4 val = *reinterpret_cast<const uint4 *>(tstage + cl * 32 + part * 8);
+                    *reinterpret_cast<uint4 *>(P.out_t + (int64_t)(blockIdx.y * BN + cl) * P.ld_t + row0 + part * 8) = val;
+                }
             }
             if (P.mode == EPI_LOSS) {
 #pragma unroll
@@ -580,9 +615,12 @@ sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, in
         if (N % bn != 0) continue;
         for (int nst : {3, 4}) {
             cand.push_back(GemmCfg{bn, nst, 1});
+            // K splits for the FP32 weight gradients, whose output tiles are few and K long
+            // (K = the batch): at least 4 K blocks per split, at most 8 CTAs per SM in all
             if (P.mode == EPI_F32 && tiles < 2 * ctx->sm_count)
-                for (int sp : {2, 4, 8})
-                    if (nk / sp >= 4) cand.push_back(GemmCfg{bn, nst, sp});
+                for (int sp : {2, 4, 8, 16, 32})
+                    if (nk / sp >= 4 && (M / BM) * (int64_t)(N / bn) * sp <= 8 * (int64_t)ctx->sm_count)
+                        cand.push_back(GemmCfg{bn, nst, sp});
         }
     }
     cudaEvent_t e0, e1;

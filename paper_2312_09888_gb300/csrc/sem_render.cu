@@ -415,8 +415,10 @@ __global__ void __launch_bounds__(256) k_resolve(const uint32_t *__restrict__ co
     const ulonglong2 empty = make_ulonglong2(~0ull, ~0ull);
     for (int64_t q = tid; q < n4; q += stride) {
         const ulonglong2 a = k2[2 * q], b = k2[2 * q + 1];
-        k2[2 * q] = empty;  // ready for the next frame
-        k2[2 * q + 1] = empty;
+        // ready for the next frame: only keys some triangle wrote need resetting (most pixels of
+        // an isosurface frame stay background and already hold "empty")
+        if ((a.x & a.y) != ~0ull) k2[2 * q] = empty;
+        if ((b.x & b.y) != ~0ull) k2[2 * q + 1] = empty;
         uint4 c;
         float4 d;
         resolve_one(a.x, colors, c.x, d.x);
