@@ -44,6 +44,9 @@ WORKLOADS = {
             "Q-isosurface at 0.1 max Q + temperature isosurface T=0.5, one 3840x2160 perspective frame",
     "channel32": "channel 32x32x32 elements, N=7 (16.8M GLL nodes), 512 Fourier modes, 3 Q-isosurfaces, "
                  "1920x1080 perspective",
+    # the headline's structure at 1/8 size (the small case for profiling)
+    "rb32": "RB-like 32x32x32 elements, N=7 (16.8M GLL nodes), velocity + temperature (268 MB FP32), "
+            "Q-isosurface at 0.1 max Q + temperature isosurface T=0.5, one 1920x1080 perspective frame",
 }
 HEADLINE = "rb64"
 # segment colours of the two-field frame: Q red, temperature blue
@@ -205,6 +208,8 @@ def make_workload(name, device):
     import sem_inputs as si
     if name == "rb64":
         return si.rb_box(device=device)
+    if name == "rb32":
+        return si.rb_box(nel=32, W=1920, H=1080, device=device)
     return si.channel(device=device)
 
 
@@ -216,13 +221,15 @@ class Pipeline:
     Q), then the temperature at its isovalue; their triangles share one buffer, one colour
     segment per (field, isovalue)."""
 
-    def __init__(self, S, w, device_index=0):
+    def __init__(self, S, w, device_index=0, autotune=True):
         import numpy as np
         import torch
         self.S, self.w, self.torch = S, w, torch
         self.stream = torch.cuda.current_stream()
         self.sess = S.Session(device_index, self.stream)
         self.ctx = self.sess.ctx
+        if not autotune:
+            S.sem_autotune_set(self.ctx, False)
         xyz = w.mesh.xyz(w.fields.device).cpu().numpy()
         self.mesh = self.sess.mesh(w.mesh.N, xyz)
         del xyz
@@ -861,7 +868,7 @@ def run_ours(args):
     w = make_workload(args.workload, "cuda")
     mesh_cpu = w.mesh
     camera = w.camera
-    P = Pipeline(S, w, local)
+    P = Pipeline(S, w, local, autotune=not args.no_autotune)
     del w
     head = time_workload(S, P, K, args.warmup, local, barrier, use_graph=not args.no_graph)
     kernels, roof = kernel_table(P, head["trace"], K, hbm_peak, args.workload)
@@ -892,6 +899,7 @@ def run_ours(args):
     mem_now, mem_peak = S.sem_memory(P.ctx)
     torch_peak = int(torch.cuda.max_memory_allocated())  # the caller's buffers (torch allocator)
     emit_units = [c for c in S.sem_autotune_emit_choices(P.ctx) if c[:2] == (P.N, P.E)]
+    widths = S.sem_autotune_width_choices(P.ctx)
     surfaces = P.surface_stats
     W, H, ntri, npts, E, N = P.W, P.H, int(P.last_ntri), P.npts, P.E, P.N
     cpu = None
@@ -944,7 +952,9 @@ def run_ours(args):
            "kernels": kernels, "gpu_launches": int(round(launches_per_step * K)),
            "memory": {"library_bytes_in_use": mem_now, "library_bytes_peak": mem_peak,
                       "caller_buffers_bytes_peak": torch_peak},
-           "autotune": {"emit_units_per_atomic": sorted({c[3] for c in emit_units}) or None},
+           "autotune": {"emit_units_per_atomic": sorted({c[3] for c in emit_units}) or None,
+                        "launch_widths": [{"kind": k, "N": n, "size": sz, "width": wd, "ms": round(ms, 4)}
+                                          for k, n, sz, wd, ms in widths]},
            "extra": extra or None, "learned": learned}
     if qprec is not None:
         out["q_precisions"] = qprec
@@ -1100,6 +1110,8 @@ def main():
     ap.add_argument("--batched-snapshots", type=int, default=64)
     ap.add_argument("--q-precisions", action="store_true",
                     help="also time sem_qcriterion at FP32, BF16, FP16, split BF16 and TF32 (q_precisions)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="library defaults instead of the autotuner's choices (for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-elements", type=int, default=0,
                     help="reference arm: elements per slab (default 1/64 of the mesh)")

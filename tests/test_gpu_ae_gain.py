@@ -21,7 +21,7 @@ from oracle import ae as ora
 pytestmark = pytest.mark.gpu
 
 STEPS, BATCH, LR0 = 20000, 8192, 1e-3
-HELD_OUT = (200, 225, 249)
+HELD_OUT = tuple(range(200, 250))  # every held-out snapshot
 
 
 @pytest.fixture(scope="module")
@@ -78,7 +78,7 @@ def test_autoencoder_beats_legendre_truncation_at_equal_payload(trained):
         f = si.ae_snapshot(s, nel=32, device="cuda")
         fc = si.ae_snapshot(s, nel=32, noise=0.0, device="cuda")
         rec = _roundtrip(S, sess, ae, f)
-        sel = np.random.default_rng(s).choice(f.shape[1], 2048, replace=False)
+        sel = np.random.default_rng(s).choice(f.shape[1], 256, replace=False)
         fin = f[:, sel].cpu().double().numpy()
         fcl = fc[:, sel].cpu().double().numpy()
         r_ae = rec[:, sel].cpu().double().numpy()
@@ -86,13 +86,21 @@ def test_autoencoder_beats_legendre_truncation_at_equal_payload(trained):
         e_ae, e_leg = _rel(r_ae, fin), _rel(r_leg, fin)
         c_ae, c_leg = _rel(r_ae, fcl), _rel(r_leg, fcl)
         report.append((s, e_ae, e_leg, c_ae, c_leg))
-        # vs the transmitted (noisy) field and vs the noise-free field
+        # vs the transmitted (noisy) field and vs the noise-free field.  Against the input, both
+        # errors sit on the same floor: the i.i.d. 1e-3 noise (relative ~3e-3 of the field) that no
+        # 48-value code of a 1536-value element can carry, so the margin there is small; against
+        # the noise-free field -- what the in situ frame is meant to show -- the code must be at
+        # least 15 % better than the 16-mode truncation at the same payload.
         assert e_ae < e_leg, (s, e_ae, e_leg)
-        assert c_ae < c_leg, (s, c_ae, c_leg)
+        assert c_ae <= 0.85 * c_leg, (s, c_ae, c_leg)
     print(f"\nfinal training loss {final:.3e}")
     for s, e_ae, e_leg, c_ae, c_leg in report:
-        print(f"held-out s={s}: rel. L2 error vs input  AE {e_ae:.3e}  Legendre-16/BF16 {e_leg:.3e}; "
-              f"vs noise-free  AE {c_ae:.3e}  Legendre-16/BF16 {c_leg:.3e}")
+        if s in (200, 225, 249):
+            print(f"held-out s={s}: rel. L2 error vs input  AE {e_ae:.3e}  Legendre-16/BF16 {e_leg:.3e}; "
+                  f"vs noise-free  AE {c_ae:.3e}  Legendre-16/BF16 {c_leg:.3e}")
+    r = np.array([x[1:] for x in report])
+    print(f"all {len(report)} held-out snapshots: AE / Legendre error ratio vs input {np.min(r[:, 0] / r[:, 1]):.3f}.."
+          f"{np.max(r[:, 0] / r[:, 1]):.3f}, vs noise-free {np.min(r[:, 2] / r[:, 3]):.3f}..{np.max(r[:, 2] / r[:, 3]):.3f}")
 
 
 def test_decoded_field_through_q_isosurface_and_frame(trained):
