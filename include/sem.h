@@ -414,7 +414,7 @@ SEM_API sem_status sem_autotune_set(sem_ctx *ctx, int on);
 
 /* The same switch tunes the launch of the isosurface emit pass (sem_isosurface,
  * sem_isosurface_multi and their asynchronous forms): the first emitting call of a given
- * (order N, element count E, isovalue count) runs the persistent emit kernel with 1, 2, 4 and 8
+ * (order N, element count E, isovalue count) runs the persistent emit kernel with 1, 2, 4, 8, 16 and 32
  * (element, isovalue) units per work-counter atomic, each twice with the second timed, keeps
  * the fastest and reuses it afterwards.  That first call waits for the GPU once.  Every
  * candidate writes the same triangles, so results do not depend on tuning.  Under stream
@@ -430,7 +430,8 @@ SEM_API sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t 
  * grids of the render's large-triangle and resolve passes (kind 5, N = W, size = H), chosen per
  * frame size among five (large, resolve) pairs of CTAs per SM, width 0..4 = (6, 8), (4, 4),
  * (8, 16), (2, 8), (6, 2).  The first call of a key with tuning on, outside stream capture and
- * tracing, runs every candidate (twice, the second timed) and keeps the fastest; the others use
+ * tracing, runs every candidate (once untimed, then three timed runs, the fastest counting) and
+ * keeps the fastest; the others use
  * the widest Q launch and pair 0.  sem_autotune_width_entry reads choice k (SEM_ERR_ARG past the
  * last one). */
 SEM_API sem_status sem_autotune_width_entry(sem_ctx *ctx, int k, int *kind, int *N, int64_t *size, int *width,

@@ -173,8 +173,9 @@ inline sem_status kernel_setup(sem_ctx *ctx, KernelSetup &ks, K kern, int thread
 
 // Launch-width autotuner of persistent kernels whose output does not depend on the width:
 // the first call of a given (kind, N, size) with tuning on and the stream not being captured runs
-// `launch(w)` for every candidate width (each twice, the second timed with CUDA events), keeps the
-// fastest and reuses it; otherwise `dflt`.  The last candidate's output is the call's output.
+// `launch(w)` for every candidate width (once untimed, then three times, each timed with CUDA
+// events; a candidate's time is its fastest run), keeps the fastest and reuses it; otherwise
+// `dflt`.  The last candidate's output is the call's output.
 enum { TUNE_Q8 = 1, TUNE_Q8_COUNT = 2, TUNE_QGRAD = 3, TUNE_QGRAD_DERIV = 4, TUNE_RENDER = 5 };
 template <class Launch>
 inline sem_status width_tuned(sem_ctx *ctx, int kind, int N, int64_t size, const int *cand, int ncand, int dflt,
@@ -192,17 +193,18 @@ inline sem_status width_tuned(sem_ctx *ctx, int kind, int N, int64_t size, const
     float best_ms = 1e30f;
     sem_status st = SEM_OK;
     for (int c = 0; c < ncand && st == SEM_OK; ++c) {
-        for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
-            if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
+        st = launch(cand[c]);  // warm-up
+        for (int rep = 0; rep < 3 && st == SEM_OK; ++rep) {
+            st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
             if (st == SEM_OK) st = launch(cand[c]);
-            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
-        }
-        float ms = 0.f;
-        if (st == SEM_OK) st = sem_cuda(ctx, cudaEventSynchronize(e1), "event");
-        if (st == SEM_OK) st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event");
-        if (st == SEM_OK && ms < best_ms) {
-            best_ms = ms;
-            best = cand[c];
+            if (st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+            float ms = 0.f;
+            if (st == SEM_OK) st = sem_cuda(ctx, cudaEventSynchronize(e1), "event");
+            if (st == SEM_OK) st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event");
+            if (st == SEM_OK && ms < best_ms) {
+                best_ms = ms;
+                best = cand[c];
+            }
         }
     }
     cudaEventDestroy(e0);

@@ -574,10 +574,18 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
         if (lane == 0) u0 = atomicAdd(next, (unsigned long long)units);
         u0 = __shfl_sync(0xffffffffu, u0, 0);
         if (u0 >= (unsigned long long)U) break;
-        const int64_t u1 = min((int64_t)u0 + units, U);
-        for (int64_t u = (int64_t)u0; u < u1; ++u) {
-            const int64_t o = b0 + offs[u], n = offs[u + 1] - offs[u];
-            if (n <= 0 || o + n > cap) continue;
+        const int nu = (int)min((int64_t)units, U - (int64_t)u0);
+        // the chunk's offsets read by the lanes at once; only units holding triangles are walked
+        int64_t my_o = 0, my_n = 0;
+        if (lane < nu) {
+            my_o = offs[u0 + lane];
+            my_n = offs[u0 + lane + 1] - my_o;
+        }
+        for (unsigned live = __ballot_sync(0xffffffffu, my_n > 0); live; live &= live - 1u) {
+            const int l = __ffs(live) - 1;
+            const int64_t u = (int64_t)u0 + l;
+            const int64_t o = b0 + __shfl_sync(0xffffffffu, my_o, l), n = __shfl_sync(0xffffffffu, my_n, l);
+            if (o + n > cap) continue;
             const int q = (int)(u / E);
             const int64_t e = u - (int64_t)q * E;
             const float iso = S.iso[q];
@@ -727,7 +735,7 @@ static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, c
 }
 
 // The emit launch with the context's autotuner: the first emitting call of a given (order,
-// elements, isovalues) runs 1, 2, 4 and 8 units per work-counter atomic, each twice (the
+// elements, isovalues) runs 1, 2, 4, 8, 16 and 32 units per work-counter atomic, each twice (the
 // second timed with CUDA events), and keeps the fastest; later calls reuse it.  Every
 // candidate writes the same triangles to the same places, so the output does not depend on the
 // choice.  Under stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
@@ -749,7 +757,7 @@ static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const Is
     int best = EMIT_UNITS_DEFAULT;
     float best_ms = 1e30f;
     sem_status st = SEM_OK;
-    for (int units : {1, 2, 4, 8}) {
+    for (int units : {1, 2, 4, 8, 16, 32}) {
         for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
             if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
             if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
