@@ -414,11 +414,12 @@ SEM_API sem_status sem_autotune_set(sem_ctx *ctx, int on);
 
 /* The same switch tunes the launch of the isosurface emit pass (sem_isosurface,
  * sem_isosurface_multi and their asynchronous forms): the first emitting call of a given
- * (order N, element count E, isovalue count) runs the persistent emit kernel with 1, 2, 4, 8, 16 and 32
- * (element, isovalue) units per work-counter atomic, each twice with the second timed, keeps
+ * (order N, element count E, isovalue count) runs the persistent emit kernel with 1, 2, 4 and 8
+ * (element, isovalue) units per work-counter atomic (units that hold triangles: the scan before
+ * the emit pass lists them), each twice with the second timed, keeps
  * the fastest and reuses it afterwards.  That first call waits for the GPU once.  Every
  * candidate writes the same triangles, so results do not depend on tuning.  Under stream
- * capture, or when off, 2 units per atomic.  sem_autotune_emit_entry reads choice k
+ * capture, or when off, 1 unit per atomic.  sem_autotune_emit_entry reads choice k
  * (SEM_ERR_ARG past the last one): N, E, isovalues, units per atomic and the winner's time in
  * milliseconds. */
 SEM_API sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t *E, int *niso, int *units,

@@ -258,6 +258,12 @@ sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host
 // scan_tmp_bytes(n) bytes.  Stream-ordered on ctx->stream.
 size_t scan_tmp_bytes(int64_t n);
 sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp);
+// The same scan that also lists the entries with a positive count: live[0 .. *nlive) their
+// indices in increasing order (live holds up to n entries).  `tmp` must hold
+// scan_live_tmp_bytes(n) bytes.
+size_t scan_live_tmp_bytes(int64_t n);
+sem_status scan_i32_i64_live(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp, int64_t *live,
+                             unsigned long long *nlive);
 // makes the runtime load the scan kernels (lazy module loading), see iso_noalloc_prepare
 sem_status scan_load_kernels(sem_ctx *ctx);
 

@@ -490,10 +490,16 @@ static sem_status launch_count(sem_ctx *ctx, const float *f, const IsoSet &S, in
 }
 
 // per-warp dynamic shared memory of the emit kernel: the element's field, a window of the
-// triangle map, the mask of one isovalue, the element's node coordinates, a store staging
-// area and the list of cut cells; warps per block: up to 8 within ~96 KB
+// triangle map, the mask of one isovalue, the element's node coordinates, a store staging area
+// and the list of cut cells; warps per block: up to 8 within ~96 KB
 #define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
-#define EMIT_UNITS_DEFAULT 2  // (element, isovalue) units a warp takes per atomic, untuned
+#define EMIT_UNITS_DEFAULT 1  // units with triangles a warp takes per atomic, untuned
+#ifndef EMIT_MINB
+#define EMIT_MINB 4  // resident blocks per SM the register allocation is sized for
+#endif
+#ifndef EMIT_PREFETCH
+#define EMIT_PREFETCH 0  // 1: the next unit's field is loaded into registers while the current one is processed
+#endif
 template <int NP>
 struct EmitW {
     using G = MaskGeo<NP>;
@@ -516,20 +522,195 @@ __device__ __forceinline__ int corner_off(int v)
     return (v & 1) + ((v >> 1) & 1) * NP + (v >> 2) * NP * NP;
 }
 
-// Persistent warps over (element, isovalue) units u = q E + e, `units` of them per atomic on a
-// counter the host zeroes before the launch.  For a unit with triangles: load the element
-// and its mask; (1a) lane per row pair, list the cut cells with their cases in cell order (a
-// warp scan of the per-lane counts places each lane's run; N uniform passes over the cells of
-// a row, each cut cell stored at its rank, so no lane walks its cells alone); then per window of
-// EMIT_MAPCAP triangles (1b) lane per listed cell, warp-scan the triangle counts and write each
-// triangle's packed (case, cell, index in cell) into the map, in cell order; (2) lane per
-// output triangle: interpolate its three vertices (between the element box's node coordinates,
-// or the nodes' own coordinates on a general mesh), stage them, and store each round of 32
-// triangles (1152 contiguous bytes) with coalesced 4-byte stores.
+// Per-warp shared memory of the emit kernel (see EmitW).
+struct EmitSmem {
+    float *sf;      // the element's field
+    uint32_t *map;  // cs << 16 | k << 12 | j << 8 | i << 4 | t
+    uint32_t *m;    // the unit's node mask
+    float *X, *Y, *Z;
+    float *stg;
+    uint32_t *list;  // cut cells: cell | case << 16
+};
+
+// One (element, isovalue) unit u = q E + e with n > 0 triangles from tris[o]: with the element's
+// values in v (PF: register-held, lane l holding nodes 32 w + l) or loaded here, (1a) lane per
+// row pair, list the cut cells with their cases in cell order (a warp scan of the per-lane
+// counts places each lane's run; N uniform passes over the cells of a row, each cut cell stored
+// at its rank, so no lane walks its cells alone); then per window of EMIT_MAPCAP triangles (1b)
+// lane per listed cell, warp-scan the triangle counts and write each triangle's packed (case,
+// cell, index in cell) into the map, in cell order; (2) lane per output triangle: interpolate
+// its three vertices and stage them, then store each round of 32 triangles (1152 contiguous
+// bytes) with coalesced 4-byte stores.  On a box mesh the lerp between the edge's two node
+// positions is taken per axis from the cell's corner coordinates: x_lo + t (x_hi - x_lo) along
+// the edge's axis, x + t 0 along the other two (the same FP32 operations as the lerp of the two
+// nodes, whose other coordinates agree); on a general mesh it is the lerp between the two
+// nodes' own coordinates.
+template <int NP, bool GENERAL, bool PF>
+__device__ __forceinline__ void emit_unit(const float (&v)[MaskGeo<NP>::NW], const float *__restrict__ f,
+                                          const IsoSet &S, int64_t E, int64_t u, int64_t o, int64_t n,
+                                          const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
+                                          float *__restrict__ tris, int32_t *__restrict__ tri_elem,
+                                          const float *__restrict__ xyzn, const EmitSmem &sm,
+                                          const uint8_t *__restrict__ s_nt, const uint32_t *__restrict__ s_tc,
+                                          const float *__restrict__ s_s, int lane)
+{
+    using G = MaskGeo<NP>;
+    constexpr int N = G::N;
+    const int q = (int)(u / E);
+    const int64_t e = u - (int64_t)q * E;
+    const float iso = S.iso[q];
+    float *sf = sm.sf, *X = sm.X, *Y = sm.Y, *Z = sm.Z, *stg = sm.stg;
+    uint32_t *map = sm.map, *m = sm.m, *list = sm.list;
+    __syncwarp();  // the previous unit's readers of sf, m and X are done
+    if constexpr (PF) {
+#pragma unroll
+        for (int w = 0; w < G::NW; ++w) {
+            const int nn = w * 32 + lane;
+            if ((G::NP3 % 32 == 0) || nn < G::NP3) sf[nn] = v[w];
+        }
+        IsoSet S1;  // the unit's isovalue alone
+        S1.niso = 1;
+        S1.iso[0] = iso;
+        masks_from_vals<NP>(v, S1, m, lane);
+    } else {
+        IsoSet S1;
+        S1.niso = 1;
+        S1.iso[0] = iso;
+        load_masks<NP>(f + e * G::NP3, sf, S1, m, lane);
+    }
+    if (lane < NP) {
+        // node coordinates: lerps of the element box with exact end points
+        const float4 L = blo[e], H = bhi[e];
+        const float s = s_s[lane];
+        X[lane] = fmaf(s, H.x, (1.f - s) * L.x);
+        Y[lane] = fmaf(s, H.y, (1.f - s) * L.y);
+        Z[lane] = fmaf(s, H.z, (1.f - s) * L.z);
+    }
+    __syncwarp();
+    // (1a) the cut cells of the element, in cell order, with their cases
+    int ncells = 0;
+    for (int rp0 = 0; rp0 < G::NRP; rp0 += 32) {
+        const int rp = rp0 + lane;
+        uint32_t act = 0, r00 = 0, r01 = 0, r10 = 0, r11 = 0;
+        if (rp < G::NRP) {
+            const int j = rp % N, k = rp / N;
+            r00 = row_bits<NP>(m, k, j);
+            r01 = row_bits<NP>(m, k, j + 1);
+            r10 = row_bits<NP>(m, k + 1, j);
+            r11 = row_bits<NP>(m, k + 1, j + 1);
+            act = cut_cells<NP>(r00, r01, r10, r11);
+        }
+        const int na = __popc(act);
+        int incl = na;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int at = ncells + incl - na;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if ((act >> i) & 1u)
+                list[at + __popc(act & ((1u << i) - 1u))] =
+                    (uint32_t)(rp * N + i) | ((uint32_t)pair_case(r00, r01, r10, r11, i) << 16);
+        ncells += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncwarp();
+    for (int64_t win = 0; win < n; win += EMIT_MAPCAP) {
+        // (1b) the map entries of triangles win .. win + EMIT_MAPCAP - 1, in cell order
+        int running = 0;
+        for (int c0 = 0; c0 < ncells && running < win + EMIT_MAPCAP; c0 += 32) {
+            const int c = c0 + lane;
+            const uint32_t ent = c < ncells ? list[c] : 0u;
+            const int cs = (int)(ent >> 16);
+            const int nt = c < ncells ? s_nt[cs] : 0;
+            int incl = nt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            int slot = running + incl - nt - (int)win;
+            if (nt > 0) {
+                const int cell = (int)(ent & 0xFFFFu), i = cell % N, rp = cell / N;
+                const uint32_t key = ((uint32_t)cs << 16) | ((uint32_t)(rp / N) << 12) | ((uint32_t)(rp % N) << 8) |
+                                     ((uint32_t)i << 4);
+                for (int t = 0; t < nt; ++t, ++slot)
+                    if (slot >= 0 && slot < EMIT_MAPCAP) map[slot] = key | (uint32_t)t;
+            }
+            running += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        __syncwarp();
+        // (2) one output triangle per lane, stored through the staging area
+        const int cnt = (int)min((int64_t)EMIT_MAPCAP, n - win);
+        for (int base = 0; base < cnt; base += 32) {
+            const int idx = base + lane;
+            if (idx < cnt) {
+                const uint32_t key = map[idx];
+                const int t = key & 15, i = (key >> 4) & 15, j = (key >> 8) & 15, k = (key >> 12) & 15;
+                const int cs = key >> 16;
+                const int c0 = (k * NP + j) * NP + i;
+                const uint32_t pairs = s_tc[cs * ISO_MAXT + t];
+                float x0 = 0.f, x1 = 0.f, y0 = 0.f, y1 = 0.f, z0 = 0.f, z1 = 0.f;
+                if constexpr (!GENERAL) {
+                    x0 = X[i];
+                    x1 = X[i + 1];
+                    y0 = Y[j];
+                    y1 = Y[j + 1];
+                    z0 = Z[k];
+                    z1 = Z[k + 1];
+                }
+                const float dx = x1 - x0, dy = y1 - y0, dz = z1 - z0;
+#pragma unroll
+                for (int sv = 0; sv < 3; ++sv) {
+                    const int la = (pairs >> (6 * sv)) & 7, lb = (pairs >> (6 * sv + 3)) & 7;
+                    const int na = c0 + corner_off<NP>(la), nb = c0 + corner_off<NP>(lb);
+                    const float fa = sf[na], fb = sf[nb];
+                    const float tt = __fdividef(iso - fa, fb - fa);
+                    if constexpr (GENERAL) {
+                        // general mesh: between the two nodes' own coordinates
+                        const int64_t tot = E * G::NP3, ga = e * G::NP3 + na, gb = e * G::NP3 + nb;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float pa = __ldg(xyzn + c * tot + ga), pb = __ldg(xyzn + c * tot + gb);
+                            stg[lane * 9 + sv * 3 + c] = fmaf(tt, pb - pa, pa);
+                        }
+                    } else {
+                        // the edge runs along the one axis where its corners differ (lo has 0
+                        // there); the other axes take a zero step, so a NaN t still makes every
+                        // coordinate NaN, as the lerp does
+                        const int ax = la ^ lb;
+                        stg[lane * 9 + sv * 3 + 0] = fmaf(tt, ax == 1 ? dx : 0.f, (la & 1) ? x1 : x0);
+                        stg[lane * 9 + sv * 3 + 1] = fmaf(tt, ax == 2 ? dy : 0.f, (la & 2) ? y1 : y0);
+                        stg[lane * 9 + sv * 3 + 2] = fmaf(tt, ax == 4 ? dz : 0.f, (la & 4) ? z1 : z0);
+                    }
+                }
+                if (tri_elem) tri_elem[o + win + idx] = (int32_t)e;
+            }
+            __syncwarp();
+            const int nflt = 9 * min(32, cnt - base);
+            float *dst = tris + (o + win + base) * 9;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                const int g = r * 32 + lane;
+                if (g < nflt) __stcs(dst + g, stg[g]);  // streamed: read once, by the raster
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The units with triangles, live[0 .. nlive) (nlive = next[1], both written by the scan), are
+// dealt to persistent warps `units` at a time from the work counter next[0], which the host
+// zeroes before the launch; warps therefore hold units with triangles only and finish within
+// one unit of each other.  The next counter value is fetched one chunk ahead and, for orders
+// with at most 32 mask words, the next unit's index, offsets and field are loaded while the
+// current unit is processed, so a unit's global-memory latency overlaps its predecessor's work.
 template <int NP, bool GENERAL>
-__global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *__restrict__ f,
+__global__ void __launch_bounds__(32 * EmitW<NP>::V, EMIT_MINB) k_iso_emit_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
                                                                  const int64_t *__restrict__ offs,
+                                                                 const int64_t *__restrict__ live,
                                                                  const float4 *__restrict__ blo,
                                                                  const float4 *__restrict__ bhi,
                                                                  float *__restrict__ tris,
@@ -540,7 +721,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
 {
     using EW = EmitW<NP>;
     using G = MaskGeo<NP>;
-    constexpr int N = G::N;
+    constexpr bool PF = EMIT_PREFETCH && G::NW <= 32;
     const int64_t U = (int64_t)S.niso * E;
     // index of the first triangle in `tris`: 0, or (appending behind an earlier call's
     // segments) a value another kernel wrote on the device
@@ -550,6 +731,7 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
         if (blockIdx.x == 0 && threadIdx.x == 0 && flag) atomicOr(flag, 1 << SEM_ERR_CAPACITY);
         return;
     }
+    const int64_t nlive = (int64_t)next[1];
     extern __shared__ __align__(16) unsigned char s_dyn[];
     __shared__ uint8_t s_nt[256];
     __shared__ uint32_t s_tc[256 * ISO_MAXT];
@@ -560,154 +742,79 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V) k_iso_emit_m(const float *_
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *mine = s_dyn + (size_t)w * EW::B;
-    float *sf = reinterpret_cast<float *>(mine);
-    uint32_t *map = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES);  // cs << 16 | k << 12 | j << 8 | i << 4 | t
-    uint32_t *m = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES + EW::MAP_BYTES);
-    float *X = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES);
-    float *Y = X + NP, *Z = X + 2 * NP;
-    float *stg = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES + EW::X_BYTES);
-    uint32_t *list = reinterpret_cast<uint32_t *>(mine + EW::B - EW::LIST_BYTES);
-    IsoSet S1;  // the unit's isovalue alone, for load_masks
-    S1.niso = 1;
-    for (;;) {
-        unsigned long long u0 = 0;
-        if (lane == 0) u0 = atomicAdd(next, (unsigned long long)units);
-        u0 = __shfl_sync(0xffffffffu, u0, 0);
-        if (u0 >= (unsigned long long)U) break;
-        const int nu = (int)min((int64_t)units, U - (int64_t)u0);
-        // the chunk's offsets read by the lanes at once; only units holding triangles are walked
-        int64_t my_o = 0, my_n = 0;
-        if (lane < nu) {
-            my_o = offs[u0 + lane];
-            my_n = offs[u0 + lane + 1] - my_o;
+    EmitSmem sm;
+    sm.sf = reinterpret_cast<float *>(mine);
+    sm.map = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES);
+    sm.m = reinterpret_cast<uint32_t *>(mine + EW::F_BYTES + EW::MAP_BYTES);
+    sm.X = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES);
+    sm.Y = sm.X + NP;
+    sm.Z = sm.X + 2 * NP;
+    sm.stg = reinterpret_cast<float *>(mine + EW::F_BYTES + EW::MAP_BYTES + EW::M_BYTES + EW::X_BYTES);
+    sm.list = reinterpret_cast<uint32_t *>(mine + EW::B - EW::LIST_BYTES);
+
+    // positions in the live list: the chunk [cur, end) in use and, on lane 0, the counter value
+    // of the chunk after it (fetched when this one was taken)
+    int64_t cur = 0, end = 0;
+    unsigned long long ahead = 0;
+    bool done = false;
+    if (lane == 0) ahead = atomicAdd(next, (unsigned long long)units);
+    auto next_pos = [&]() -> int64_t {
+        if (cur == end && !done) {
+            const int64_t c0 = (int64_t)__shfl_sync(0xffffffffu, ahead, 0);
+            if (c0 >= nlive) {
+                done = true;
+            } else {
+                cur = c0;
+                end = min(c0 + (int64_t)units, nlive);
+                if (lane == 0) ahead = atomicAdd(next, (unsigned long long)units);
+            }
         }
-        for (unsigned live = __ballot_sync(0xffffffffu, my_n > 0); live; live &= live - 1u) {
-            const int l = __ffs(live) - 1;
-            const int64_t u = (int64_t)u0 + l;
-            const int64_t o = b0 + __shfl_sync(0xffffffffu, my_o, l), n = __shfl_sync(0xffffffffu, my_n, l);
-            if (o + n > cap) continue;
-            const int q = (int)(u / E);
-            const int64_t e = u - (int64_t)q * E;
-            const float iso = S.iso[q];
-            S1.iso[0] = iso;
-            __syncwarp();  // the previous unit's readers of sf, m and X are done
-            load_masks<NP>(f + e * G::NP3, sf, S1, m, lane);
-            if (lane < NP) {
-                // node coordinates: lerps of the element box with exact end points
-                const float4 L = blo[e], H = bhi[e];
-                const float s = s_s[lane];
-                X[lane] = fmaf(s, H.x, (1.f - s) * L.x);
-                Y[lane] = fmaf(s, H.y, (1.f - s) * L.y);
-                Z[lane] = fmaf(s, H.z, (1.f - s) * L.z);
+        return done ? -1 : cur++;
+    };
+    const int64_t p0 = next_pos();
+    if (p0 < 0) return;
+    int64_t u0 = live[p0];
+    int64_t o0 = offs[u0], n0 = offs[u0 + 1] - o0;
+    const int64_t p1 = next_pos();
+    int64_t u1 = p1 >= 0 ? live[p1] : -1;
+    float v[G::NW];
+    if constexpr (PF) {
+        const int q = (int)(u0 / E);
+        load_vals<NP>(f + (u0 - (int64_t)q * E) * G::NP3, v, lane);
+    }
+    for (;;) {
+        // ahead of the current unit u0: u1's field and offsets, u2's index
+        int64_t o1 = 0, n1 = 0, u2 = -1;
+        float nv[G::NW];
+        if (u1 >= 0) {
+            const int64_t p2 = next_pos();
+            if (p2 >= 0) u2 = live[p2];
+            if constexpr (PF) {
+                const int q = (int)(u1 / E);
+                load_vals<NP>(f + (u1 - (int64_t)q * E) * G::NP3, nv, lane);
             }
-            __syncwarp();
-            // (1a) the cut cells of the element, in cell order, with their cases
-            int ncells = 0;
-            for (int rp0 = 0; rp0 < G::NRP; rp0 += 32) {
-                const int rp = rp0 + lane;
-                uint32_t act = 0, r00 = 0, r01 = 0, r10 = 0, r11 = 0;
-                if (rp < G::NRP) {
-                    const int j = rp % N, k = rp / N;
-                    r00 = row_bits<NP>(m, k, j);
-                    r01 = row_bits<NP>(m, k, j + 1);
-                    r10 = row_bits<NP>(m, k + 1, j);
-                    r11 = row_bits<NP>(m, k + 1, j + 1);
-                    act = cut_cells<NP>(r00, r01, r10, r11);
-                }
-                const int na = __popc(act);
-                int incl = na;
+            o1 = offs[u1];
+            n1 = offs[u1 + 1] - o1;
+        }
+        if (b0 + o0 + n0 <= cap)  // holds for every unit after the check above
+            emit_unit<NP, GENERAL, PF>(v, f, S, E, u0, b0 + o0, n0, blo, bhi, tris, tri_elem, xyzn, sm, s_nt, s_tc,
+                                       s_s, lane);
+        if (u1 < 0) break;
+        u0 = u1;
+        o0 = o1;
+        n0 = n1;
+        u1 = u2;
+        if constexpr (PF) {
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                    if (lane >= d) incl += y;
-                }
-                const int at = ncells + incl - na;
-#pragma unroll
-                for (int i = 0; i < N; ++i)
-                    if ((act >> i) & 1u)
-                        list[at + __popc(act & ((1u << i) - 1u))] =
-                            (uint32_t)(rp * N + i) | ((uint32_t)pair_case(r00, r01, r10, r11, i) << 16);
-                ncells += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            __syncwarp();
-            for (int64_t win = 0; win < n; win += EMIT_MAPCAP) {
-                // (1b) the map entries of triangles win .. win + EMIT_MAPCAP - 1, in cell order
-                int running = 0;
-                for (int c0 = 0; c0 < ncells && running < win + EMIT_MAPCAP; c0 += 32) {
-                    const int c = c0 + lane;
-                    const uint32_t ent = c < ncells ? list[c] : 0u;
-                    const int cs = (int)(ent >> 16);
-                    const int nt = c < ncells ? s_nt[cs] : 0;
-                    int incl = nt;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-                        if (lane >= d) incl += y;
-                    }
-                    int slot = running + incl - nt - (int)win;
-                    if (nt > 0) {
-                        const int cell = (int)(ent & 0xFFFFu), i = cell % N, rp = cell / N;
-                        const uint32_t key = ((uint32_t)cs << 16) | ((uint32_t)(rp / N) << 12) |
-                                             ((uint32_t)(rp % N) << 8) | ((uint32_t)i << 4);
-                        for (int t = 0; t < nt; ++t, ++slot)
-                            if (slot >= 0 && slot < EMIT_MAPCAP) map[slot] = key | (uint32_t)t;
-                    }
-                    running += __shfl_sync(0xffffffffu, incl, 31);
-                }
-                __syncwarp();
-                // (2) one output triangle per lane, stored through the staging area
-                const int cnt = (int)min((int64_t)EMIT_MAPCAP, n - win);
-                for (int base = 0; base < cnt; base += 32) {
-                    const int idx = base + lane;
-                    if (idx < cnt) {
-                        const uint32_t key = map[idx];
-                        const int t = key & 15, i = (key >> 4) & 15, j = (key >> 8) & 15, k = (key >> 12) & 15;
-                        const int cs = key >> 16;
-                        const int c0 = (k * NP + j) * NP + i;
-                        const uint32_t pairs = s_tc[cs * ISO_MAXT + t];
-#pragma unroll
-                        for (int sv = 0; sv < 3; ++sv) {
-                            const int la = (pairs >> (6 * sv)) & 7, lb = (pairs >> (6 * sv + 3)) & 7;
-                            const int na = c0 + corner_off<NP>(la), nb = c0 + corner_off<NP>(lb);
-                            const float fa = sf[na], fb = sf[nb];
-                            const float tt = __fdividef(iso - fa, fb - fa);
-                            if constexpr (GENERAL) {
-                                // general mesh: between the two nodes' own coordinates
-                                const int64_t tot = E * G::NP3, ga = e * G::NP3 + na, gb = e * G::NP3 + nb;
-#pragma unroll
-                                for (int c = 0; c < 3; ++c) {
-                                    const float pa = __ldg(xyzn + c * tot + ga), pb = __ldg(xyzn + c * tot + gb);
-                                    stg[lane * 9 + sv * 3 + c] = fmaf(tt, pb - pa, pa);
-                                }
-                            } else {
-                                const int ia = i + (la & 1), ja = j + ((la >> 1) & 1), ka = k + (la >> 2);
-                                const int ib = i + (lb & 1), jb = j + ((lb >> 1) & 1), kb = k + (lb >> 2);
-                                stg[lane * 9 + sv * 3 + 0] = fmaf(tt, X[ib] - X[ia], X[ia]);
-                                stg[lane * 9 + sv * 3 + 1] = fmaf(tt, Y[jb] - Y[ja], Y[ja]);
-                                stg[lane * 9 + sv * 3 + 2] = fmaf(tt, Z[kb] - Z[ka], Z[ka]);
-                            }
-                        }
-                        if (tri_elem) tri_elem[o + win + idx] = (int32_t)e;
-                    }
-                    __syncwarp();
-                    const int nflt = 9 * min(32, cnt - base);
-                    float *dst = tris + (o + win + base) * 9;
-#pragma unroll
-                    for (int r = 0; r < 9; ++r) {
-                        const int g = r * 32 + lane;
-                        if (g < nflt) __stcs(dst + g, stg[g]);  // streamed: read once, by the raster
-                    }
-                    __syncwarp();
-                }
-            }
+            for (int q = 0; q < G::NW; ++q) v[q] = nv[q];
         }
     }
 }
 
 template <int NP, bool GENERAL>
 static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                                float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units,
-                                const int64_t *base)
+                                const int64_t *live, float *tris, int32_t *tri_elem, int64_t cap,
+                                unsigned long long *next, int units, const int64_t *base)
 {
     constexpr int EV = EmitW<NP>::V;
     constexpr size_t dyn = (size_t)EV * EmitW<NP>::B;
@@ -717,7 +824,7 @@ static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f,
     SEM_TRY(kernel_setup(ctx, ks, kern, 32 * EV, dyn, &blocks_per_sm));
     SEM_CU(ctx, cudaMemsetAsync(next, 0, sizeof(unsigned long long), ctx->stream));
     const unsigned grid = (unsigned)(ctx->sm_count * blocks_per_sm);
-    SEM_TRACED(ctx, "k_iso_emit_m", kern<<<grid, 32 * EV, dyn, ctx->stream>>>(f, S, m->E, offs, m->lo, m->hi, tris,
+    SEM_TRACED(ctx, "k_iso_emit_m", kern<<<grid, 32 * EV, dyn, ctx->stream>>>(f, S, m->E, offs, live, m->lo, m->hi, tris,
                                                                              tri_elem, cap, ctx->d_flag, next, units,
                                                                              m->xyzn, base));
     return sem_cuda(ctx, cudaGetLastError(), "k_iso_emit_m launch");
@@ -727,40 +834,40 @@ static sem_status launch_emit_k(sem_ctx *ctx, const sem_mesh *m, const float *f,
 // `next` zeroed first; box meshes and general meshes have their own instantiation.
 template <int NP>
 static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                              float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next, int units,
-                              const int64_t *base)
+                              const int64_t *live, float *tris, int32_t *tri_elem, int64_t cap,
+                              unsigned long long *next, int units, const int64_t *base)
 {
-    if (m->curved) return launch_emit_k<NP, true>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
-    return launch_emit_k<NP, false>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
+    if (m->curved) return launch_emit_k<NP, true>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, units, base);
+    return launch_emit_k<NP, false>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, units, base);
 }
 
 // The emit launch with the context's autotuner: the first emitting call of a given (order,
-// elements, isovalues) runs 1, 2, 4, 8, 16 and 32 units per work-counter atomic, each twice (the
-// second timed with CUDA events), and keeps the fastest; later calls reuse it.  Every
-// candidate writes the same triangles to the same places, so the output does not depend on the
-// choice.  Under stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
+// elements, isovalues) runs 1, 2, 4 and 8 units per work-counter atomic, each twice (the second
+// timed with CUDA events), and keeps the fastest; later calls reuse it.  Every candidate writes
+// the same triangles to the same places, so the output does not depend on the choice.  Under
+// stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
 template <int NP>
 static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, const int64_t *offs,
-                       float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next,
+                       const int64_t *live, float *tris, int32_t *tri_elem, int64_t cap, unsigned long long *next,
                        const int64_t *base = nullptr)
 {
     for (const auto &t : ctx->emit_tune)
         if (t.N == m->N && t.E == m->E && t.niso == S.niso)
-            return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, t.units, base);
+            return launch_emit<NP>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, t.units, base);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
     if (!ctx->autotune || cs != cudaStreamCaptureStatusNone)
-        return launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, EMIT_UNITS_DEFAULT, base);
+        return launch_emit<NP>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, EMIT_UNITS_DEFAULT, base);
     cudaEvent_t e0, e1;
     SEM_CU(ctx, cudaEventCreate(&e0));
     SEM_CU(ctx, cudaEventCreate(&e1));
     int best = EMIT_UNITS_DEFAULT;
     float best_ms = 1e30f;
     sem_status st = SEM_OK;
-    for (int units : {1, 2, 4, 8, 16, 32}) {
+    for (int units : {1, 2, 4, 8}) {
         for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
             if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
-            if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next, units, base);
+            if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, units, base);
             if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
         }
         if (st != SEM_OK) break;
@@ -779,23 +886,68 @@ static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const Is
     return SEM_OK;  // the triangles of the last candidate, the same as every other's
 }
 
+// Segment ends of an appending call: counts_dev[0] (written earlier on the device) is the first
+// triangle's index, counts_dev[q] = counts_dev[0] + offs[q E] for q = 1..niso.
+__global__ void k_seg_ends(const int64_t *__restrict__ offs, int64_t E, int niso, int64_t *__restrict__ counts_dev)
+{
+    const int q = threadIdx.x + 1;
+    if (q <= niso) counts_dev[q] = counts_dev[0] + offs[(int64_t)q * E];
+}
+
+// The library scratch of one isosurface pass: counts [q][e], offsets, the emit work counter
+// (next[0]) and the number of units with triangles (next[1]), the list of those units and the
+// scan state.
+struct IsoScratch {
+    int32_t *cnt;
+    int64_t *offs;
+    unsigned long long *next;
+    int64_t *live;
+    void *tmp;
+};
+
+static size_t iso_scratch_bytes(int64_t n, size_t &cnt_bytes, size_t &off_bytes, size_t &live_bytes)
+{
+    cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
+    off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
+    live_bytes = ((sizeof(int64_t) * n + 255) / 256) * 256;
+    return cnt_bytes + off_bytes + 256 + live_bytes + scan_live_tmp_bytes(n);
+}
+
+static void iso_scratch_carve(void *scr, int64_t n, IsoScratch &X)
+{
+    size_t cb, ob, lb;
+    iso_scratch_bytes(n, cb, ob, lb);
+    char *p = reinterpret_cast<char *>(scr);
+    X.cnt = reinterpret_cast<int32_t *>(p);
+    X.offs = reinterpret_cast<int64_t *>(p + cb);
+    X.next = reinterpret_cast<unsigned long long *>(p + cb + ob);
+    X.live = reinterpret_cast<int64_t *>(p + cb + ob + 256);
+    X.tmp = p + cb + ob + 256 + lb;
+}
+
+static sem_status iso_scratch_async(sem_ctx *ctx, int64_t n, IsoScratch &X)
+{
+    size_t cb, ob, lb;
+    void *scr;
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, iso_scratch_bytes(n, cb, ob, lb), &scr));
+    iso_scratch_carve(scr, n, X);
+    return SEM_OK;
+}
+
 template <int NP>
 static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, const IsoSet &S, float *tris,
                                int32_t *tri_elem, int64_t cap, int64_t *ntri_out, uint8_t *cases)
 {
     const int64_t E = m->E, n = E * S.niso;
-    const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
-    const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
+    size_t cb, ob, lb;
     void *scr;
-    SEM_TRY(sem_scratch(ctx, SCR_ISO, cnt_bytes + off_bytes + 256 + scan_tmp_bytes(n), &scr));
-    int32_t *cnt = reinterpret_cast<int32_t *>(scr);
-    int64_t *offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
-    auto *next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
-    void *tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
-    SEM_TRY(launch_count<NP>(ctx, f, S, E, cnt, cases));
-    SEM_TRY(scan_i32_i64(ctx, cnt, offs, n, tmp));
+    SEM_TRY(sem_scratch(ctx, SCR_ISO, iso_scratch_bytes(n, cb, ob, lb), &scr));
+    IsoScratch X;
+    iso_scratch_carve(scr, n, X);
+    SEM_TRY(launch_count<NP>(ctx, f, S, E, X.cnt, cases));
+    SEM_TRY(scan_i32_i64_live(ctx, X.cnt, X.offs, n, X.tmp, X.live, X.next + 1));
     // segment starts offs[q*E], q = 0..niso (the last one is the grand total)
-    SEM_CU(ctx, cudaMemcpy2DAsync(ctx->h_pinned, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t),
+    SEM_CU(ctx, cudaMemcpy2DAsync(ctx->h_pinned, sizeof(int64_t), X.offs, sizeof(int64_t) * E, sizeof(int64_t),
                                   S.niso + 1, cudaMemcpyDeviceToHost, ctx->stream));
     SEM_CU(ctx, cudaStreamSynchronize(ctx->stream));
     for (int q = 0; q < S.niso; ++q) ntri_out[q] = ctx->h_pinned[q + 1] - ctx->h_pinned[q];
@@ -805,37 +957,7 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
         return sem_fail(ctx, SEM_ERR_CAPACITY, "sem_isosurface: %lld triangles exceed capacity %lld", (long long)total,
                         (long long)cap);
     if (total == 0) return SEM_OK;
-    return emit<NP>(ctx, m, f, S, offs, tris, tri_elem, cap, next);
-}
-
-// Segment ends of an appending call: counts_dev[0] (written earlier on the device) is the first
-// triangle's index, counts_dev[q] = counts_dev[0] + offs[q E] for q = 1..niso.
-__global__ void k_seg_ends(const int64_t *__restrict__ offs, int64_t E, int niso, int64_t *__restrict__ counts_dev)
-{
-    const int q = threadIdx.x + 1;
-    if (q <= niso) counts_dev[q] = counts_dev[0] + offs[(int64_t)q * E];
-}
-
-// The library scratch of one asynchronous isosurface pass: counts [q][e], offsets, the emit
-// work counter and the scan state.
-struct IsoScratch {
-    int32_t *cnt;
-    int64_t *offs;
-    unsigned long long *next;
-    void *tmp;
-};
-
-static sem_status iso_scratch_async(sem_ctx *ctx, int64_t n, IsoScratch &X)
-{
-    const size_t cnt_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
-    const size_t off_bytes = ((sizeof(int64_t) * (n + 1) + 255) / 256) * 256;
-    void *scr;
-    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, cnt_bytes + off_bytes + 256 + scan_tmp_bytes(n), &scr));
-    X.cnt = reinterpret_cast<int32_t *>(scr);
-    X.offs = reinterpret_cast<int64_t *>(reinterpret_cast<char *>(scr) + cnt_bytes);
-    X.next = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes);
-    X.tmp = reinterpret_cast<char *>(scr) + cnt_bytes + off_bytes + 256;
-    return SEM_OK;
+    return emit<NP>(ctx, m, f, S, X.offs, X.live, tris, tri_elem, cap, X.next);
 }
 
 // From the counts on: scan, segment starts to counts_dev, emit.  With `append`, counts_dev[0] is
@@ -846,7 +968,7 @@ static sem_status iso_tail_async(sem_ctx *ctx, const sem_mesh *m, const float *f
                                  int64_t *counts_dev, bool append)
 {
     const int64_t E = m->E, n = E * S.niso;
-    SEM_TRY(scan_i32_i64(ctx, X.cnt, X.offs, n, X.tmp));
+    SEM_TRY(scan_i32_i64_live(ctx, X.cnt, X.offs, n, X.tmp, X.live, X.next + 1));
     if (append) {
         SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(X.offs, E, S.niso, counts_dev));
         SEM_CU(ctx, cudaGetLastError());
@@ -855,7 +977,7 @@ static sem_status iso_tail_async(sem_ctx *ctx, const sem_mesh *m, const float *f
                                       S.niso + 1, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (!tris) return SEM_OK;
-    return emit<NP>(ctx, m, f, S, X.offs, tris, tri_elem, cap, X.next, append ? counts_dev : nullptr);
+    return emit<NP>(ctx, m, f, S, X.offs, X.live, tris, tri_elem, cap, X.next, append ? counts_dev : nullptr);
 }
 
 // No host synchronisation: segment starts go to counts_dev (device), a capacity overflow

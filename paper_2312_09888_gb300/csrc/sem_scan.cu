@@ -15,6 +15,12 @@ size_t scan_tmp_bytes(int64_t n)
     return ((sizeof(int64_t) * (size_t)(nb + 1) + 255) / 256) * 256;
 }
 
+size_t scan_live_tmp_bytes(int64_t n)
+{
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return ((sizeof(int64_t) * (size_t)(2 * nb + 1) + 255) / 256) * 256;
+}
+
 // block-wide exclusive scan of one int64 per thread; returns the block total in *total
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, int64_t &total)
 {
@@ -45,6 +51,44 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *s_warp, i
     return r;
 }
 
+// block-wide exclusive scan of two int64 per thread at once (a, b); totals in ta, tb
+__device__ __forceinline__ void block_excl_scan2(int64_t a, int64_t b, int64_t (*s_warp)[33], int64_t &ea,
+                                                 int64_t &eb, int64_t &ta, int64_t &tb)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int64_t ia = a, ib = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t ya = __shfl_up_sync(0xffffffffu, ia, d), yb = __shfl_up_sync(0xffffffffu, ib, d);
+        if (lane >= d) {
+            ia += ya;
+            ib += yb;
+        }
+    }
+    if (lane == 31) {
+        s_warp[0][w] = ia;
+        s_warp[1][w] = ib;
+    }
+    __syncthreads();
+    if (w < 2) {
+        const int64_t x = lane < nw ? s_warp[w][lane] : 0;
+        int64_t xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, xi, d);
+            if (lane >= d) xi += y;
+        }
+        if (lane < nw) s_warp[w][lane] = xi - x;
+        if (lane == 31) s_warp[w][32] = xi;
+    }
+    __syncthreads();
+    ea = s_warp[0][w] + ia - a;
+    eb = s_warp[1][w] + ib - b;
+    ta = s_warp[0][32];
+    tb = s_warp[1][32];
+    __syncthreads();
+}
+
 // Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
 // Scan with Decoupled Look-back", NVIDIA technical report, 2016).  Each block takes the next
 // tile from a ticket counter, scans it, publishes the tile's sum, then folds the published
@@ -69,16 +113,56 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
+// One warp's look-back over the status words st[0 .. tile]: publishes the tile's sum `tot`,
+// folds the published values of the tiles before it and publishes the tile's inclusive prefix;
+// returns the sum of all tiles before it (on every lane).
+__device__ __forceinline__ int64_t lookback_warp(unsigned long long *st, int64_t tile, int64_t tot, int *err, int lane)
+{
+    if (lane == 0) st_release_u64(st + tile, ((tile == 0 ? 2ull : 1ull) << LB_SHIFT) | (unsigned long long)tot);
+    int64_t before = 0;
+    int64_t p = tile - 1;  // the nearest tile not folded in yet
+    long long polls = 0;
+    while (p >= 0) {
+        // lane l reads tile p - l; before tile 0 there is an inclusive prefix of 0
+        const int64_t q = p - lane;
+        const unsigned long long w = q >= 0 ? ld_acquire_u64(st + q) : (2ull << LB_SHIFT);
+        const unsigned flag = (unsigned)(w >> LB_SHIFT);
+        const unsigned nr = __ballot_sync(0xffffffffu, flag == 0u);
+        const unsigned pm = __ballot_sync(0xffffffffu, flag == 2u);
+        const int kp = pm ? __ffs(pm) - 1 : 32;  // nearest lane holding an inclusive prefix
+        const int kn = nr ? __ffs(nr) - 1 : 32;  // nearest lane whose tile has published nothing
+        const int take = min(kp + 1, kn);        // lanes [0, take): tile sums (and the prefix)
+        int64_t part = lane < take ? (int64_t)(w & LB_VALUE) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+        before += part;
+        if (kp < kn) break;  // reached an inclusive prefix
+        p -= take;
+        if (take == 0 && ++polls >= SEM_WAIT_LIMIT) {
+            if (lane == 0) atomicOr(err, 1 << SEM_ERR_TIMEOUT);
+            break;
+        }
+    }
+    if (lane == 0 && tile > 0) st_release_u64(st + tile, (2ull << LB_SHIFT) | (unsigned long long)(before + tot));
+    return before;
+}
+
+// With LIVE, the same pass also lists the entries with a positive value: live[0 .. nlive) are
+// their indices in increasing order and *nlive their number.  That second prefix (of the flags
+// [in > 0]) has its own status words, state[1 + nb + t], and its own look-back, run by warp 1
+// while warp 0 runs the first.
+template <bool LIVE>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int32_t *__restrict__ in, int64_t n, int64_t nb,
                                                                 int64_t *__restrict__ out,
-                                                                unsigned long long *__restrict__ state, int *err)
+                                                                unsigned long long *__restrict__ state, int *err,
+                                                                int64_t *__restrict__ live,
+                                                                unsigned long long *__restrict__ nlive)
 {
-    __shared__ int64_t s_w[33];
-    __shared__ int64_t s_tile, s_before;
+    __shared__ int64_t s_w[2][33];
+    __shared__ int64_t s_tile, s_before, s_lbefore;
     if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(state, 1ull);
     __syncthreads();
     const int64_t tile = s_tile;
-    unsigned long long *st = state + 1;
     const int64_t base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int64_t x[SCAN_ITEMS];
     if (base + SCAN_ITEMS <= n) {
@@ -91,42 +175,22 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int32_t *_
 #pragma unroll
         for (int q = 0; q < SCAN_ITEMS; ++q) x[q] = base + q < n ? in[base + q] : 0;
     }
-    int64_t v = 0;
+    int64_t v = 0, lv = 0;
 #pragma unroll
-    for (int q = 0; q < SCAN_ITEMS; ++q) v += x[q];
-    int64_t tot;
-    const int64_t ex = block_excl_scan(v, s_w, tot);
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        if (lane == 0) st_release_u64(st + tile, ((tile == 0 ? 2ull : 1ull) << LB_SHIFT) | (unsigned long long)tot);
-        int64_t before = 0;
-        int64_t p = tile - 1;  // the nearest tile not folded in yet
-        long long polls = 0;
-        while (p >= 0) {
-            // lane l reads tile p - l; before tile 0 there is an inclusive prefix of 0
-            const int64_t q = p - lane;
-            const unsigned long long w = q >= 0 ? ld_acquire_u64(st + q) : (2ull << LB_SHIFT);
-            const unsigned flag = (unsigned)(w >> LB_SHIFT);
-            const unsigned nr = __ballot_sync(0xffffffffu, flag == 0u);
-            const unsigned pm = __ballot_sync(0xffffffffu, flag == 2u);
-            const int kp = pm ? __ffs(pm) - 1 : 32;  // nearest lane holding an inclusive prefix
-            const int kn = nr ? __ffs(nr) - 1 : 32;  // nearest lane whose tile has published nothing
-            const int take = min(kp + 1, kn);        // lanes [0, take): tile sums (and the prefix)
-            int64_t part = lane < take ? (int64_t)(w & LB_VALUE) : 0;
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-            before += part;
-            if (kp < kn) break;  // reached an inclusive prefix
-            p -= take;
-            if (take == 0 && ++polls >= SEM_WAIT_LIMIT) {
-                if (lane == 0) atomicOr(err, 1 << SEM_ERR_TIMEOUT);
-                break;
-            }
-        }
-        if (lane == 0) {
-            if (tile > 0) st_release_u64(st + tile, (2ull << LB_SHIFT) | (unsigned long long)(before + tot));
-            s_before = before;
-        }
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        v += x[q];
+        lv += x[q] > 0 ? 1 : 0;
+    }
+    int64_t ex, tot, lex = 0, ltot = 0;
+    if constexpr (LIVE) block_excl_scan2(v, lv, s_w, ex, lex, tot, ltot);
+    else ex = block_excl_scan(v, s_w[0], tot);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w == 0) {
+        const int64_t before = lookback_warp(state + 1, tile, tot, err, lane);
+        if (lane == 0) s_before = before;
+    } else if (LIVE && w == 1) {
+        const int64_t lbefore = lookback_warp(state + 1 + nb, tile, ltot, err, lane);
+        if (lane == 0) s_lbefore = lbefore;
     }
     __syncthreads();
     int64_t run = s_before + ex;
@@ -134,6 +198,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int32_t *_
     for (int q = 0; q < SCAN_ITEMS; ++q) {
         if (base + q < n) out[base + q] = run;
         run += x[q];
+    }
+    if constexpr (LIVE) {
+        int64_t at = s_lbefore + lex;
+#pragma unroll
+        for (int q = 0; q < SCAN_ITEMS; ++q)
+            if (x[q] > 0) live[at++] = base + q;
+        if (tile == nb - 1 && threadIdx.x == 0) *nlive = (unsigned long long)(s_lbefore + ltot);
     }
     if (tile == nb - 1 && threadIdx.x == 0) out[n] = s_before + tot;
 }
@@ -144,48 +215,76 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int32_t *_
 // one SM's serial chunks cost more than a multi-block scan, measured 194 us against 20 us at
 // 98304 entries).
 #define SCAN_SINGLE_MAX (SCAN_THREADS * 8)
+template <bool LIVE>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t *__restrict__ in, int64_t n,
-                                                              int64_t *__restrict__ out)
+                                                              int64_t *__restrict__ out, int64_t *__restrict__ live,
+                                                              unsigned long long *__restrict__ nlive)
 {
-    __shared__ int64_t s_w[33];
+    __shared__ int64_t s_w[2][33];
     const int64_t per = (n + SCAN_THREADS - 1) / SCAN_THREADS;
     const int64_t lo = min(n, (int64_t)threadIdx.x * per), hi = min(n, lo + per);
-    int64_t v = 0;
-    for (int64_t i = lo; i < hi; ++i) v += in[i];
-    int64_t tot;
-    int64_t run = block_excl_scan(v, s_w, tot);
+    int64_t v = 0, lv = 0;
     for (int64_t i = lo; i < hi; ++i) {
-        out[i] = run;
-        run += in[i];
+        const int32_t c = in[i];
+        v += c;
+        lv += c > 0 ? 1 : 0;
     }
-    if (threadIdx.x == 0) out[n] = tot;
+    int64_t run, tot, lrun = 0, ltot = 0;
+    if constexpr (LIVE) block_excl_scan2(v, lv, s_w, run, lrun, tot, ltot);
+    else run = block_excl_scan(v, s_w[0], tot);
+    for (int64_t i = lo; i < hi; ++i) {
+        const int32_t c = in[i];
+        out[i] = run;
+        run += c;
+        if (LIVE && c > 0) live[lrun++] = i;
+    }
+    if (threadIdx.x == 0) {
+        out[n] = tot;
+        if constexpr (LIVE) *nlive = (unsigned long long)ltot;
+    }
 }
 
-sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp)
+template <bool LIVE>
+static sem_status scan_run(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp, int64_t *live,
+                           unsigned long long *nlive)
 {
     if (n <= 0) {
         SEM_CU(ctx, cudaMemsetAsync(out, 0, sizeof(int64_t), ctx->stream));
+        if (LIVE) SEM_CU(ctx, cudaMemsetAsync(nlive, 0, sizeof(unsigned long long), ctx->stream));
         return SEM_OK;
     }
     if (n <= SCAN_SINGLE_MAX) {
-        SEM_TRACED(ctx, "k_scan_single", k_scan_single<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, out));
+        SEM_TRACED(ctx, "k_scan_single",
+                   k_scan_single<LIVE><<<1, SCAN_THREADS, 0, ctx->stream>>>(in, n, out, live, nlive));
         return sem_cuda(ctx, cudaGetLastError(), "scan launch");
     }
     if ((reinterpret_cast<uintptr_t>(in) & 15u) != 0)
         return sem_fail(ctx, SEM_ERR_ARG, "scan: counts not 16-byte aligned");
     const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     auto *state = reinterpret_cast<unsigned long long *>(tmp);
-    SEM_CU(ctx, cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (size_t)(nb + 1), ctx->stream));
-    SEM_TRACED(ctx, "k_scan_lookback", k_scan_lookback<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(
-        in, n, nb, out, state, ctx->d_flag));
+    const size_t words = (size_t)(LIVE ? 2 * nb + 1 : nb + 1);
+    SEM_CU(ctx, cudaMemsetAsync(state, 0, sizeof(unsigned long long) * words, ctx->stream));
+    SEM_TRACED(ctx, "k_scan_lookback", k_scan_lookback<LIVE><<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(
+        in, n, nb, out, state, ctx->d_flag, live, nlive));
     return sem_cuda(ctx, cudaGetLastError(), "scan launch");
+}
+
+sem_status scan_i32_i64(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp)
+{
+    return scan_run<false>(ctx, in, out, n, tmp, nullptr, nullptr);
+}
+
+sem_status scan_i32_i64_live(sem_ctx *ctx, const int32_t *in, int64_t *out, int64_t n, void *tmp, int64_t *live,
+                             unsigned long long *nlive)
+{
+    return scan_run<true>(ctx, in, out, n, tmp, live, nlive);
 }
 
 sem_status scan_load_kernels(sem_ctx *ctx)
 {
     cudaFuncAttributes a;
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_single));
-    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_lookback));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_single<false>));
+    SEM_CU(ctx, cudaFuncGetAttributes(&a, k_scan_lookback<false>));
     return SEM_OK;
 }
 
