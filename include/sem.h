@@ -75,6 +75,8 @@ typedef enum {
 #define SEM_MC_MAXT 12
 /* Most isovalues one sem_isosurface_multi call extracts. */
 #define SEM_MAX_ISO 8
+/* Most further fields one sem_qcriterion_isosurface_fields_async call extracts. */
+#define SEM_MAX_FIELDS 4
 
 /* Camera of sem_render.  View basis f = unit(center-eye), s = unit(f x up), u = s x f;
  * view coordinates xv = s.(p-eye), yv = u.(p-eye), zv = f.(p-eye).
@@ -256,6 +258,32 @@ SEM_API sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mes
                                                      const float *isos_host, int niso, float *tris,
                                                      int32_t *tri_elem, int64_t cap, int64_t *counts_dev,
                                                      uint8_t *cases);
+
+/* Q of (u, v, w) with its isosurfaces, and the isosurfaces of nfields further fields of the same
+ * mesh, into one triangle buffer in one call: the result of sem_qcriterion_isosurface_async(Q at
+ * q_isos[0..q_niso-1]) followed, for k = 0..nfields-1, by sem_isosurface_multi_append_async of
+ * fields[k] at its f_niso[k] isovalues (f_isos holds them back to back, field 0's first), each
+ * appending behind the one before.  Q, tris, tri_elem and counts_dev are bit for bit those of that
+ * call sequence.  counts_dev: device int64[1 + q_niso + sum f_niso] receives every segment start,
+ * Q's isovalues first then the fields' in order, and the grand total last.
+ * Concurrency: after the Q kernel, the further fields' passes (counting, scan, emit) run on an
+ * auxiliary stream of the context, forked from and joined back to the context's stream within
+ * the call, so they overlap Q's scan and emit; stream order as seen by the caller is unchanged,
+ * and the whole call may be captured in a CUDA graph (scratch rule of sem_isosurface_multi_async).
+ * While the context's emit autotuner (sem_autotune_set) still has to time a launch of this call,
+ * the passes run one after the other on the context's stream so that its timings are not
+ * disturbed.  Each field keeps scratch of its own.  Arguments: fields: HOST array of nfields
+ * device pointers (E*(N+1)^3 floats each); f_isos, f_niso: HOST; 0 <= nfields <= SEM_MAX_FIELDS,
+ * 1 <= q_niso, f_niso[k] <= SEM_MAX_ISO; cap: capacity of the whole buffer; a total above it
+ * writes no triangle of the segment that overflows (or of any later one) and raises
+ * SEM_ERR_CAPACITY on the device flag.  Other arguments and errors as
+ * sem_qcriterion_isosurface_async. */
+SEM_API sem_status sem_qcriterion_isosurface_fields_async(sem_ctx *ctx, const sem_mesh *mesh, const float *u,
+                                                          const float *v, const float *w, float *Q,
+                                                          const float *q_isos, int q_niso, int nfields,
+                                                          const float *const *fields, const float *f_isos,
+                                                          const int *f_niso, float *tris, int32_t *tri_elem,
+                                                          int64_t cap, int64_t *counts_dev);
 
 /* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
 #define SEM_NOALLOC_MAX_ELEMENTS 262144

@@ -29,6 +29,7 @@ SEM_MAX_ORDER = 15
 SEM_NOALLOC_MAX_ELEMENTS = 262144
 SEM_MC_MAXT = 12
 SEM_MAX_ISO = 8
+SEM_MAX_FIELDS = 4
 
 _lock = threading.Lock()
 _lib = None
@@ -74,6 +75,8 @@ def _declare(L):
     L.sem_isosurface_multi_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_isosurface_multi_append_async.argtypes = [vp, vp, vp, vp, i32, vp, vp, i64, vp, vp]
     L.sem_qcriterion_isosurface_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, vp, vp, i64, vp]
+    L.sem_qcriterion_isosurface_fields_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp,
+                                                         i64, vp]
     L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_render_segments_async.argtypes = [vp, vp, i64, vp, i32, vp, C.c_uint64, C.POINTER(sem_camera), i32, i32,
                                             vp, vp]
@@ -109,7 +112,8 @@ def _declare(L):
                                            C.POINTER(f32)]
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_debug_set_wait_limit", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
-                 "sem_isosurface_multi_append_async", "sem_qcriterion_isosurface_async", "sem_render_async",
+                 "sem_isosurface_multi_append_async", "sem_qcriterion_isosurface_async",
+                 "sem_qcriterion_isosurface_fields_async", "sem_render_async",
                  "sem_render_segments_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
@@ -336,6 +340,33 @@ def sem_qcriterion_isosurface_async(ctx, mesh, u, v, w, Q, isos, tris, counts_de
                                                    _dev(tris, "tris", torch.float32, allow_none=True),
                                                    _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
                                                    int(cap), _dev(counts_dev, "counts_dev", torch.int64))
+    _check(ctx, st)
+
+
+def sem_qcriterion_isosurface_fields_async(ctx, mesh, u, v, w, Q, q_isos, fields, f_isos, tris, counts_dev,
+                                           tri_elem=None, cap: Optional[int] = None) -> None:
+    """Q and its isosurfaces, then the isosurfaces of further fields appended behind them, in one
+    call whose further-field passes run on the context's auxiliary stream, overlapping Q's scan
+    and emit.  ``fields``: list of CUDA float32 tensors; ``f_isos``: one list of isovalues per
+    field; counts_dev: int64 CUDA tensor of 1 + len(q_isos) + sum(len(f)) entries (all segment
+    starts, then the total).  Same results as sem_qcriterion_isosurface_async followed by one
+    sem_isosurface_multi_append_async per field."""
+    import torch
+    qv = np.ascontiguousarray(np.asarray(q_isos, dtype=np.float32).reshape(-1))
+    if len(fields) != len(f_isos):
+        raise ValueError("one list of isovalues per field")
+    fv = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32).reshape(-1) for x in f_isos])
+                              if f_isos else np.zeros(0, np.float32))
+    fn = np.ascontiguousarray(np.asarray([len(x) for x in f_isos], dtype=np.int32))
+    fp = (C.c_void_p * max(1, len(fields)))(*[_dev(f, "fields[k]", torch.float32) for f in fields])
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    st = get_lib().sem_qcriterion_isosurface_fields_async(
+        ctx, mesh, _dev(u, "u", torch.float32), _dev(v, "v", torch.float32), _dev(w, "w", torch.float32),
+        _dev(Q, "Q", torch.float32), qv.ctypes.data_as(C.c_void_p), len(qv), len(fields),
+        C.cast(fp, C.c_void_p), fv.ctypes.data_as(C.c_void_p), fn.ctypes.data_as(C.c_void_p),
+        _dev(tris, "tris", torch.float32, allow_none=True), _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
+        int(cap), _dev(counts_dev, "counts_dev", torch.int64))
     _check(ctx, st)
 
 

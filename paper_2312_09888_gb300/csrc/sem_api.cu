@@ -320,7 +320,13 @@ void sem_destroy(sem_ctx *ctx)
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t ev : ctx->trace_pool) cudaEventDestroy(ev);
-    for (int s = 0; s < 4; ++s)
+    if (ctx->aux) {
+        cudaStreamSynchronize(ctx->aux);
+        cudaStreamDestroy(ctx->aux);
+    }
+    for (cudaEvent_t ev : {ctx->ev_fork, ctx->ev_qseg, ctx->ev_join})
+        if (ev) cudaEventDestroy(ev);
+    for (int s = 0; s < SCR_COUNT; ++s)
         if (ctx->scratch[s]) cudaFree(ctx->scratch[s]);
     if (ctx->d_flag) cudaFree(ctx->d_flag);
     for (int s = 0; s < 3; ++s)
@@ -760,6 +766,53 @@ sem_status sem_qcriterion_isosurface_async(sem_ctx *ctx, const sem_mesh *m, cons
     SEM_TRY(check_ptr(ctx, tris, fn, "tris", true, 4));
     SEM_TRY(check_ptr(ctx, tri_elem, fn, "tri_elem", true, 4));
     return iso_run_q_multi_async(ctx, m, u, v, w, Q, isos, niso, tris, tri_elem, cap, counts_dev);
+}
+
+sem_status sem_qcriterion_isosurface_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v,
+                                                  const float *w, float *Q, const float *q_isos, int q_niso,
+                                                  int nfields, const float *const *fields, const float *f_isos,
+                                                  const int *f_niso, float *tris, int32_t *tri_elem, int64_t cap,
+                                                  int64_t *counts_dev)
+{
+    const char *fn = "sem_qcriterion_isosurface_fields_async";
+    SEM_TRY(check_common(ctx, m, fn));
+    if (!q_isos || q_niso < 1 || q_niso > SEM_MAX_ISO)
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: need 1 <= q_niso <= %d isovalues", fn, SEM_MAX_ISO);
+    if (nfields < 0 || nfields > SEM_MAX_FIELDS)
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: need 0 <= nfields <= %d", fn, SEM_MAX_FIELDS);
+    if (nfields > 0 && (!fields || !f_isos || !f_niso))
+        return sem_fail(ctx, SEM_ERR_ARG, "%s: fields, f_isos and f_niso are required when nfields > 0", fn);
+    for (int q = 0; q < q_niso; ++q)
+        if (isnan(q_isos[q])) return sem_fail(ctx, SEM_ERR_ARG, "%s: Q isovalue %d is NaN", fn, q);
+    int total_niso = q_niso;
+    for (int k = 0, at = 0; k < nfields; ++k) {
+        if (f_niso[k] < 1 || f_niso[k] > SEM_MAX_ISO)
+            return sem_fail(ctx, SEM_ERR_ARG, "%s: field %d: need 1 <= f_niso <= %d isovalues", fn, k, SEM_MAX_ISO);
+        for (int q = 0; q < f_niso[k]; ++q, ++at)
+            if (isnan(f_isos[at])) return sem_fail(ctx, SEM_ERR_ARG, "%s: field %d: isovalue %d is NaN", fn, k, q);
+        total_niso += f_niso[k];
+    }
+    if (cap < 0) return sem_fail(ctx, SEM_ERR_ARG, "%s: negative cap", fn);
+    SEM_TRY(check_ptr(ctx, counts_dev, fn, "counts_dev", false, 8));
+    if (m->E == 0)
+        return sem_cuda(ctx, cudaMemsetAsync(counts_dev, 0, sizeof(int64_t) * (total_niso + 1), ctx->stream),
+                        "cudaMemsetAsync");
+    for (int k = -1; k < nfields; ++k)
+        if (m->E * (int64_t)(k < 0 ? q_niso : f_niso[k]) > ((int64_t)1 << 31))
+            return sem_fail(ctx, SEM_ERR_ARG, "%s: E*niso too large", fn);
+    SEM_TRY(check_ptr(ctx, u, fn, "u"));
+    SEM_TRY(check_ptr(ctx, v, fn, "v"));
+    SEM_TRY(check_ptr(ctx, w, fn, "w"));
+    SEM_TRY(check_ptr(ctx, Q, fn, "Q"));
+    if (Q == u || Q == v || Q == w) return sem_fail(ctx, SEM_ERR_ARG, "%s: Q aliases an input", fn);
+    for (int k = 0; k < nfields; ++k) {
+        SEM_TRY(check_ptr(ctx, fields[k], fn, "fields[k]"));
+        if (fields[k] == Q) return sem_fail(ctx, SEM_ERR_ARG, "%s: field %d aliases Q", fn, k);
+    }
+    SEM_TRY(check_ptr(ctx, tris, fn, "tris", true, 4));
+    SEM_TRY(check_ptr(ctx, tri_elem, fn, "tri_elem", true, 4));
+    return iso_run_q_fields_async(ctx, m, u, v, w, Q, q_isos, q_niso, nfields, fields, f_isos, f_niso, tris, tri_elem,
+                                  cap, counts_dev);
 }
 
 sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos,

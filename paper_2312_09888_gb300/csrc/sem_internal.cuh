@@ -15,6 +15,11 @@
 // ------------------------------------------------------------------------------------------
 // Host-side objects
 
+// scratch arenas (each call uses its own so calls never overlap in scratch); SCR_ISO_F0 + k
+// holds the isosurface pass of further field k of sem_qcriterion_isosurface_fields_async, which
+// runs on the auxiliary stream while Q's pass (SCR_ISO) runs on the context's stream
+enum { SCR_ISO = 0, SCR_RENDER = 1, SCR_MISC = 2, SCR_TRI = 3, SCR_ISO_F0 = 4, SCR_COUNT = 4 + SEM_MAX_FIELDS };
+
 struct sem_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -35,8 +40,12 @@ struct sem_ctx {
     int64_t *h_pinned = nullptr;   // 16 int64 slots
     double *h_pinned_d = nullptr;  // 4 double slots
     // grow-only device scratch arenas
-    void *scratch[4] = {nullptr, nullptr, nullptr, nullptr};
-    size_t scratch_bytes[4] = {0, 0, 0, 0};
+    void *scratch[SCR_COUNT] = {};
+    size_t scratch_bytes[SCR_COUNT] = {};
+    // auxiliary stream and the events that fork it from `stream` and join it back (created on
+    // first use by sem_qcriterion_isosurface_fields_async)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_qseg = nullptr, ev_join = nullptr;
     // the render key buffer must read "empty" (all ones) at the start of a frame
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
@@ -122,8 +131,6 @@ struct sem_mesh {
     float *xyzn = nullptr;
 };
 
-// scratch arenas (each call uses its own so calls never overlap in scratch)
-enum { SCR_ISO = 0, SCR_RENDER = 1, SCR_MISC = 2, SCR_TRI = 3 };
 
 // set ctx->err and return st
 sem_status sem_fail(sem_ctx *ctx, sem_status st, const char *fmt, ...);
@@ -242,6 +249,12 @@ sem_status iso_run_multi(sem_ctx *ctx, const sem_mesh *m, const float *f, const 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
                                float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases,
                                bool append = false);
+// Q, its isosurfaces and those of nf further fields, appended behind Q's; the further fields'
+// passes run on ctx->aux (see sem_qcriterion_isosurface_fields_async)
+sem_status iso_run_q_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                                  float *Q, const float *q_isos, int q_niso, int nf, const float *const *fields,
+                                  const float *f_isos, const int *f_niso, float *tris, int32_t *tri_elem,
+                                  int64_t cap, int64_t *counts_dev);
 sem_status iso_run_q_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                                  float *Q, const float *isos, int niso, float *tris, int32_t *tri_elem, int64_t cap,
                                  int64_t *counts_dev);

@@ -925,11 +925,11 @@ static void iso_scratch_carve(void *scr, int64_t n, IsoScratch &X)
     X.tmp = p + cb + ob + 256 + lb;
 }
 
-static sem_status iso_scratch_async(sem_ctx *ctx, int64_t n, IsoScratch &X)
+static sem_status iso_scratch_async(sem_ctx *ctx, int64_t n, IsoScratch &X, int arena = SCR_ISO)
 {
     size_t cb, ob, lb;
     void *scr;
-    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_ISO, iso_scratch_bytes(n, cb, ob, lb), &scr));
+    SEM_TRY(sem_scratch_nogrow_in_capture(ctx, arena, iso_scratch_bytes(n, cb, ob, lb), &scr));
     iso_scratch_carve(scr, n, X);
     return SEM_OK;
 }
@@ -960,6 +960,26 @@ static sem_status iso_multi_np(sem_ctx *ctx, const sem_mesh *m, const float *f, 
     return emit<NP>(ctx, m, f, S, X.offs, X.live, tris, tri_elem, cap, X.next);
 }
 
+// Segment starts of a pass whose offsets are in offs: counts_dev[q] = offs[q E] for q = 0..niso,
+// or, appending, counts_dev[q] = counts_dev[0] + offs[q E] for q = 1..niso (counts_dev[0], the
+// index in tris of the pass's first triangle, an input written earlier on the device).
+static sem_status iso_segments_async(sem_ctx *ctx, int64_t E, int niso, const int64_t *offs, int64_t *counts_dev,
+                                     bool append)
+{
+    if (append) {
+        SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(offs, E, niso, counts_dev));
+        return sem_cuda(ctx, cudaGetLastError(), "k_seg_ends launch");
+    }
+    SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), offs, sizeof(int64_t) * E, sizeof(int64_t), niso + 1,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    return SEM_OK;
+}
+
+static sem_status iso_scan_async(sem_ctx *ctx, int64_t n, const IsoScratch &X)
+{
+    return scan_i32_i64_live(ctx, X.cnt, X.offs, n, X.tmp, X.live, X.next + 1);
+}
+
 // From the counts on: scan, segment starts to counts_dev, emit.  With `append`, counts_dev[0] is
 // an input (the first triangle's index in tris) and only counts_dev[1..niso] are written.
 template <int NP>
@@ -967,15 +987,8 @@ static sem_status iso_tail_async(sem_ctx *ctx, const sem_mesh *m, const float *f
                                  const IsoScratch &X, float *tris, int32_t *tri_elem, int64_t cap,
                                  int64_t *counts_dev, bool append)
 {
-    const int64_t E = m->E, n = E * S.niso;
-    SEM_TRY(scan_i32_i64_live(ctx, X.cnt, X.offs, n, X.tmp, X.live, X.next + 1));
-    if (append) {
-        SEM_TRACED(ctx, "k_seg_ends", k_seg_ends<<<1, 32, 0, ctx->stream>>>(X.offs, E, S.niso, counts_dev));
-        SEM_CU(ctx, cudaGetLastError());
-    } else {
-        SEM_CU(ctx, cudaMemcpy2DAsync(counts_dev, sizeof(int64_t), X.offs, sizeof(int64_t) * E, sizeof(int64_t),
-                                      S.niso + 1, cudaMemcpyDeviceToDevice, ctx->stream));
-    }
+    SEM_TRY(iso_scan_async(ctx, m->E * S.niso, X));
+    SEM_TRY(iso_segments_async(ctx, m->E, S.niso, X.offs, counts_dev, append));
     if (!tris) return SEM_OK;
     return emit<NP>(ctx, m, f, S, X.offs, X.live, tris, tri_elem, cap, X.next, append ? counts_dev : nullptr);
 }
@@ -1011,6 +1024,144 @@ sem_status iso_run_q_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *u
     SEM_TRY(iso_scratch_async(ctx, m->E * S.niso, X));
     SEM_TRY(qcrit_count_launch(ctx, m, u, v, w, Q, niso, isos, X.cnt));
     return iso_tail_async<8>(ctx, m, Q, S, X, tris, tri_elem, cap, counts_dev, false);
+}
+
+// ------------------------------------------------------------------------------------------
+// Q, its isosurfaces and the isosurfaces of further fields in one call, the further fields'
+// passes on the context's auxiliary stream (sem_qcriterion_isosurface_fields_async).
+//
+//   stream:  Q kernel (+ Q's counts) -> fork -> Q scan, Q segments -> ev_qseg -> Q emit -> join
+//   aux:                                fork -> per field k: count, scan, [wait ev_qseg],
+//                                               segments (appending), emit -> ev_join
+//
+// Field k's segments start where field k-1's (or Q's) end, a value written on the device, so
+// only the first field's append waits for Q; its counting and scan start with Q's scan.  The
+// results are those of the same passes run one after the other.  (A fork before the Q kernel,
+// with the first field counted by a slim kernel in the registers and shared memory the Q kernel
+// leaves on each SM, was slower: four warps per SM count too slowly, and they slow the Q kernel.)
+
+// true when the emit autotuner has a choice for (order, elements, isovalues), or will not time one
+static bool emit_settled(sem_ctx *ctx, const sem_mesh *m, int niso)
+{
+    if (!ctx->autotune) return true;
+    for (const auto &t : ctx->emit_tune)
+        if (t.N == m->N && t.E == m->E && t.niso == niso) return true;
+    return false;
+}
+
+static sem_status aux_ready(sem_ctx *ctx)
+{
+    if (ctx->aux) return SEM_OK;
+    int lo = 0, hi = 0, prio = 0;
+    SEM_CU(ctx, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    if (ctx->stream && cudaStreamGetPriority(ctx->stream, &prio) != cudaSuccess) prio = 0;
+    cudaStream_t s = nullptr;
+    SEM_CU(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio));
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    for (int k = 0; k < 3; ++k) {
+        const cudaError_t e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < k; ++j) cudaEventDestroy(ev[j]);
+            cudaStreamDestroy(s);
+            return sem_cuda(ctx, e, "cudaEventCreateWithFlags");
+        }
+    }
+    ctx->aux = s;
+    ctx->ev_fork = ev[0];
+    ctx->ev_qseg = ev[1];
+    ctx->ev_join = ev[2];
+    return SEM_OK;
+}
+
+// the further fields' passes, on ctx->stream (whichever stream that is at the time); with
+// `wait_q`, the first append waits for ev_qseg (Q's segment starts)
+template <int NP>
+static sem_status fields_passes(sem_ctx *ctx, const sem_mesh *m, int nf, const float *const *fields,
+                                const IsoSet *SF, const IsoScratch *XF, float *tris, int32_t *tri_elem, int64_t cap,
+                                int64_t *cd, bool wait_q)
+{
+    for (int k = 0; k < nf; ++k) {
+        SEM_TRY(launch_count<NP>(ctx, fields[k], SF[k], m->E, XF[k].cnt, nullptr));
+        SEM_TRY(iso_scan_async(ctx, m->E * SF[k].niso, XF[k]));
+        if (k == 0 && wait_q) SEM_CU(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qseg, 0));
+        SEM_TRY(iso_segments_async(ctx, m->E, SF[k].niso, XF[k].offs, cd, true));
+        if (tris) SEM_TRY(emit<NP>(ctx, m, fields[k], SF[k], XF[k].offs, XF[k].live, tris, tri_elem, cap, XF[k].next, cd));
+        cd += SF[k].niso;
+    }
+    return SEM_OK;
+}
+
+template <int NP>
+static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                              float *Q, const IsoSet &SQ, int nf, const float *const *fields, const IsoSet *SF,
+                              float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev)
+{
+    const int64_t E = m->E;
+    IsoScratch XQ, XF[SEM_MAX_FIELDS];
+    SEM_TRY(iso_scratch_async(ctx, E * SQ.niso, XQ, SCR_ISO));
+    for (int k = 0; k < nf; ++k) SEM_TRY(iso_scratch_async(ctx, E * SF[k].niso, XF[k], SCR_ISO_F0 + k));
+    // the Q kernel, counting Q's triangles itself where it can
+    if (NP == 8 && !m->curved) {
+        SEM_TRY(qcrit_count_launch(ctx, m, u, v, w, Q, SQ.niso, SQ.iso, XQ.cnt));
+    } else {
+        SEM_TRY(qcrit_launch(ctx, m, u, v, w, Q));
+        SEM_TRY(launch_count<NP>(ctx, Q, SQ, E, XQ.cnt, nullptr));
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    bool fork = nf > 0;
+    if (fork && cs == cudaStreamCaptureStatusNone && tris) {
+        // an emit launch still to be timed: one stream, so the tuner's timings are its own
+        fork = emit_settled(ctx, m, SQ.niso);
+        for (int k = 0; k < nf && fork; ++k) fork = emit_settled(ctx, m, SF[k].niso);
+    }
+    if (!fork) {
+        SEM_TRY(iso_tail_async<NP>(ctx, m, Q, SQ, XQ, tris, tri_elem, cap, counts_dev, false));
+        return fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, false);
+    }
+    SEM_TRY(aux_ready(ctx));
+    cudaStream_t main = ctx->stream;
+    SEM_CU(ctx, cudaEventRecord(ctx->ev_fork, main));
+    SEM_CU(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    // Q's scan and segment starts, then the fields' passes on aux, then Q's emit; the join is
+    // recorded whatever happens, so a capture in progress never holds an unjoined stream
+    sem_status st = iso_scan_async(ctx, E * SQ.niso, XQ);
+    if (st == SEM_OK) st = iso_segments_async(ctx, E, SQ.niso, XQ.offs, counts_dev, false);
+    if (st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(ctx->ev_qseg, main), "cudaEventRecord");
+    ctx->stream = ctx->aux;
+    if (st == SEM_OK)
+        st = fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, true);
+    ctx->stream = main;
+    const cudaError_t ej = cudaEventRecord(ctx->ev_join, ctx->aux);
+    if (st == SEM_OK && tris)
+        st = emit<NP>(ctx, m, Q, SQ, XQ.offs, XQ.live, tris, tri_elem, cap, XQ.next);
+    const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(main, ctx->ev_join, 0) : ej;
+    SEM_TRY(st);
+    return sem_cuda(ctx, ew, "join of the auxiliary stream");
+}
+
+sem_status iso_run_q_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
+                                  float *Q, const float *q_isos, int q_niso, int nf, const float *const *fields,
+                                  const float *f_isos, const int *f_niso, float *tris, int32_t *tri_elem,
+                                  int64_t cap, int64_t *counts_dev)
+{
+    IsoSet SQ, SF[SEM_MAX_FIELDS];
+    memset(&SQ, 0, sizeof SQ);
+    memset(SF, 0, sizeof SF);
+    SQ.niso = q_niso;
+    for (int q = 0; q < q_niso; ++q) SQ.iso[q] = q_isos[q];
+    for (int k = 0, at = 0; k < nf; ++k) {
+        SF[k].niso = f_niso[k];
+        for (int q = 0; q < f_niso[k]; ++q) SF[k].iso[q] = f_isos[at++];
+    }
+    switch (m->N + 1) {
+#define SEM_CASE(NPV) \
+    case NPV: return q_fields_np<NPV>(ctx, m, u, v, w, Q, SQ, nf, fields, SF, tris, tri_elem, cap, counts_dev);
+        SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
+        SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
+#undef SEM_CASE
+    default: return sem_fail(ctx, SEM_ERR_ARG, "order N=%d not supported", m->N);
+    }
 }
 
 sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, const float *isos, int niso,
