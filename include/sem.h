@@ -271,8 +271,8 @@ SEM_API sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mes
  * the call, so they overlap Q's scan and emit; stream order as seen by the caller is unchanged,
  * and the whole call may be captured in a CUDA graph (scratch rule of sem_isosurface_multi_async).
  * While the context's emit autotuner (sem_autotune_set) still has to time a launch of this call,
- * the passes run one after the other on the context's stream so that its timings are not
- * disturbed.  Each field keeps scratch of its own.  Arguments: fields: HOST array of nfields
+ * or the kernel trace (sem_trace_enable) is on, the passes run one after the other on the
+ * context's stream, so that each timing is the kernel's own.  Each field keeps scratch of its own.  Arguments: fields: HOST array of nfields
  * device pointers (E*(N+1)^3 floats each); f_isos, f_niso: HOST; 0 <= nfields <= SEM_MAX_FIELDS,
  * 1 <= q_niso, f_niso[k] <= SEM_MAX_ISO; cap: capacity of the whole buffer; a total above it
  * writes no triangle of the segment that overflows (or of any later one) and raises

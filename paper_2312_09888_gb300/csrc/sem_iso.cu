@@ -494,12 +494,7 @@ static sem_status launch_count(sem_ctx *ctx, const float *f, const IsoSet &S, in
 // and the list of cut cells; warps per block: up to 8 within ~96 KB
 #define EMIT_MAPCAP 256  // map window: triangles of one (element, isovalue) handled per pass
 #define EMIT_UNITS_DEFAULT 1  // units with triangles a warp takes per atomic, untuned
-#ifndef EMIT_MINB
-#define EMIT_MINB 4  // resident blocks per SM the register allocation is sized for
-#endif
-#ifndef EMIT_PREFETCH
-#define EMIT_PREFETCH 0  // 1: the next unit's field is loaded into registers while the current one is processed
-#endif
+#define EMIT_MINB 4  // resident blocks per SM the register allocation is sized for (64 registers a thread)
 template <int NP>
 struct EmitW {
     using G = MaskGeo<NP>;
@@ -532,9 +527,8 @@ struct EmitSmem {
     uint32_t *list;  // cut cells: cell | case << 16
 };
 
-// One (element, isovalue) unit u = q E + e with n > 0 triangles from tris[o]: with the element's
-// values in v (PF: register-held, lane l holding nodes 32 w + l) or loaded here, (1a) lane per
-// row pair, list the cut cells with their cases in cell order (a warp scan of the per-lane
+// One (element, isovalue) unit u = q E + e with n > 0 triangles from tris[o]: load the element
+// and its mask for the unit's isovalue, then (1a) lane per row pair, list the cut cells with their cases in cell order (a warp scan of the per-lane
 // counts places each lane's run; N uniform passes over the cells of a row, each cut cell stored
 // at its rank, so no lane walks its cells alone); then per window of EMIT_MAPCAP triangles (1b)
 // lane per listed cell, warp-scan the triangle counts and write each triangle's packed (case,
@@ -545,9 +539,8 @@ struct EmitSmem {
 // the edge's axis, x + t 0 along the other two (the same FP32 operations as the lerp of the two
 // nodes, whose other coordinates agree); on a general mesh it is the lerp between the two
 // nodes' own coordinates.
-template <int NP, bool GENERAL, bool PF>
-__device__ __forceinline__ void emit_unit(const float (&v)[MaskGeo<NP>::NW], const float *__restrict__ f,
-                                          const IsoSet &S, int64_t E, int64_t u, int64_t o, int64_t n,
+template <int NP, bool GENERAL>
+__device__ __forceinline__ void emit_unit(const float *__restrict__ f, const IsoSet &S, int64_t E, int64_t u, int64_t o, int64_t n,
                                           const float4 *__restrict__ blo, const float4 *__restrict__ bhi,
                                           float *__restrict__ tris, int32_t *__restrict__ tri_elem,
                                           const float *__restrict__ xyzn, const EmitSmem &sm,
@@ -562,18 +555,8 @@ __device__ __forceinline__ void emit_unit(const float (&v)[MaskGeo<NP>::NW], con
     float *sf = sm.sf, *X = sm.X, *Y = sm.Y, *Z = sm.Z, *stg = sm.stg;
     uint32_t *map = sm.map, *m = sm.m, *list = sm.list;
     __syncwarp();  // the previous unit's readers of sf, m and X are done
-    if constexpr (PF) {
-#pragma unroll
-        for (int w = 0; w < G::NW; ++w) {
-            const int nn = w * 32 + lane;
-            if ((G::NP3 % 32 == 0) || nn < G::NP3) sf[nn] = v[w];
-        }
+    {
         IsoSet S1;  // the unit's isovalue alone
-        S1.niso = 1;
-        S1.iso[0] = iso;
-        masks_from_vals<NP>(v, S1, m, lane);
-    } else {
-        IsoSet S1;
         S1.niso = 1;
         S1.iso[0] = iso;
         load_masks<NP>(f + e * G::NP3, sf, S1, m, lane);
@@ -703,9 +686,8 @@ __device__ __forceinline__ void emit_unit(const float (&v)[MaskGeo<NP>::NW], con
 // The units with triangles, live[0 .. nlive) (nlive = next[1], both written by the scan), are
 // dealt to persistent warps `units` at a time from the work counter next[0], which the host
 // zeroes before the launch; warps therefore hold units with triangles only and finish within
-// one unit of each other.  The next counter value is fetched one chunk ahead and, for orders
-// with at most 32 mask words, the next unit's index, offsets and field are loaded while the
-// current unit is processed, so a unit's global-memory latency overlaps its predecessor's work.
+// one unit of each other.  The next counter value is fetched one chunk ahead, and the next
+// unit's index and offsets are loaded while the current unit is processed.
 template <int NP, bool GENERAL>
 __global__ void __launch_bounds__(32 * EmitW<NP>::V, EMIT_MINB) k_iso_emit_m(const float *__restrict__ f,
                                                                  const __grid_constant__ IsoSet S, int64_t E,
@@ -720,8 +702,6 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V, EMIT_MINB) k_iso_emit_m(con
                                                                  const int64_t *__restrict__ base)
 {
     using EW = EmitW<NP>;
-    using G = MaskGeo<NP>;
-    constexpr bool PF = EMIT_PREFETCH && G::NW <= 32;
     const int64_t U = (int64_t)S.niso * E;
     // index of the first triangle in `tris`: 0, or (appending behind an earlier call's
     // segments) a value another kernel wrote on the device
@@ -777,37 +757,22 @@ __global__ void __launch_bounds__(32 * EmitW<NP>::V, EMIT_MINB) k_iso_emit_m(con
     int64_t o0 = offs[u0], n0 = offs[u0 + 1] - o0;
     const int64_t p1 = next_pos();
     int64_t u1 = p1 >= 0 ? live[p1] : -1;
-    float v[G::NW];
-    if constexpr (PF) {
-        const int q = (int)(u0 / E);
-        load_vals<NP>(f + (u0 - (int64_t)q * E) * G::NP3, v, lane);
-    }
     for (;;) {
-        // ahead of the current unit u0: u1's field and offsets, u2's index
+        // ahead of the current unit u0: u1's offsets, u2's index
         int64_t o1 = 0, n1 = 0, u2 = -1;
-        float nv[G::NW];
         if (u1 >= 0) {
             const int64_t p2 = next_pos();
             if (p2 >= 0) u2 = live[p2];
-            if constexpr (PF) {
-                const int q = (int)(u1 / E);
-                load_vals<NP>(f + (u1 - (int64_t)q * E) * G::NP3, nv, lane);
-            }
             o1 = offs[u1];
             n1 = offs[u1 + 1] - o1;
         }
         if (b0 + o0 + n0 <= cap)  // holds for every unit after the check above
-            emit_unit<NP, GENERAL, PF>(v, f, S, E, u0, b0 + o0, n0, blo, bhi, tris, tri_elem, xyzn, sm, s_nt, s_tc,
-                                       s_s, lane);
+            emit_unit<NP, GENERAL>(f, S, E, u0, b0 + o0, n0, blo, bhi, tris, tri_elem, xyzn, sm, s_nt, s_tc, s_s, lane);
         if (u1 < 0) break;
         u0 = u1;
         o0 = o1;
         n0 = n1;
         u1 = u2;
-        if constexpr (PF) {
-#pragma unroll
-            for (int q = 0; q < G::NW; ++q) v[q] = nv[q];
-        }
     }
 }
 
@@ -1109,9 +1074,10 @@ static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, c
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
-    bool fork = nf > 0;
+    // one stream while the kernel trace is on (each traced kernel's time is then its own) or an
+    // emit launch is still to be timed (so are the tuner's timings)
+    bool fork = nf > 0 && !ctx->trace_on;
     if (fork && cs == cudaStreamCaptureStatusNone && tris) {
-        // an emit launch still to be timed: one stream, so the tuner's timings are its own
         fork = emit_settled(ctx, m, SQ.niso);
         for (int k = 0; k < nf && fork; ++k) fork = emit_settled(ctx, m, SF[k].niso);
     }

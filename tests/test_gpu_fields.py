@@ -91,8 +91,8 @@ def test_fields_call_equals_the_call_sequence(gpu, sess, N, nel):
         cnt.fill_(-9)
         call()
         check(label)
-    # the forked call's kernels: on N = 7 box meshes Q's triangles are counted by the Q kernel,
-    # the further fields' by the counting pass
+    # the call's kernels (one stream while tracing): on N = 7 box meshes Q's triangles are
+    # counted by the Q kernel, the further fields' by the counting pass
     S.sem_trace_enable(sess.ctx, True)
     S.sem_trace_collect(sess.ctx)
     call()
