@@ -272,7 +272,8 @@ SEM_API sem_status sem_isosurface_multi_append_async(sem_ctx *ctx, const sem_mes
  * and the whole call may be captured in a CUDA graph (scratch rule of sem_isosurface_multi_async).
  * While the context's emit autotuner (sem_autotune_set) still has to time a launch of this call,
  * or the kernel trace (sem_trace_enable) is on, the passes run one after the other on the
- * context's stream, so that each timing is the kernel's own.  Each field keeps scratch of its own.  Arguments: fields: HOST array of nfields
+ * context's stream, so that each timing is the kernel's own; so they do when the call is
+ * captured before any uncaptured call of it has created the auxiliary stream.  Each field keeps scratch of its own.  Arguments: fields: HOST array of nfields
  * device pointers (E*(N+1)^3 floats each); f_isos, f_niso: HOST; 0 <= nfields <= SEM_MAX_FIELDS,
  * 1 <= q_niso, f_niso[k] <= SEM_MAX_ISO; cap: capacity of the whole buffer; a total above it
  * writes no triangle of the segment that overflows (or of any later one) and raises
@@ -284,6 +285,24 @@ SEM_API sem_status sem_qcriterion_isosurface_fields_async(sem_ctx *ctx, const se
                                                           const float *const *fields, const float *f_isos,
                                                           const int *f_niso, float *tris, int32_t *tri_elem,
                                                           int64_t cap, int64_t *counts_dev);
+
+/* One in situ frame in one call: sem_qcriterion_isosurface_fields_async (Q, its isosurfaces and
+ * the further fields' isosurfaces into tris, segment starts into counts_dev) followed by
+ * sem_render_async of all nseg = q_niso + sum f_niso segments (colours seg_rgb[3*nseg], HOST, or
+ * NULL for the palette) into rgba/depth.  The frame is drawn in parts: each stream rasterises the
+ * segments it has just emitted -- Q's on the context's stream, the further fields' on the
+ * auxiliary stream -- into the same depth keys, and the large-triangle pass and the resolve run
+ * once, after the join.  rgba, depth, Q, tris, tri_elem and counts_dev are bit for bit those of
+ * the two calls.  The first call for a frame size, while the context's autotuner still has to
+ * choose the render's launch widths, runs the two calls as such (so they are timed on a whole
+ * frame).  No host synchronisation; may be captured in a CUDA graph (scratch rule of
+ * sem_isosurface_multi_async; render scratch likewise sized by an uncaptured call).  Arguments
+ * and errors as the two calls (cap < 2^31, nseg <= 64); one frame in progress per context. */
+SEM_API sem_status sem_frame_async(sem_ctx *ctx, const sem_mesh *mesh, const float *u, const float *v, const float *w,
+                                   float *Q, const float *q_isos, int q_niso, int nfields, const float *const *fields,
+                                   const float *f_isos, const int *f_niso, float *tris, int32_t *tri_elem,
+                                   int64_t cap, int64_t *counts_dev, const float *seg_rgb, const sem_camera *cam,
+                                   int W, int H, uint8_t *rgba, float *depth);
 
 /* Largest mesh (in elements) that sem_isosurface_noalloc accepts. */
 #define SEM_NOALLOC_MAX_ELEMENTS 262144
@@ -444,7 +463,7 @@ SEM_API sem_status sem_autotune_set(sem_ctx *ctx, int on);
  * sem_isosurface_multi and their asynchronous forms): the first emitting call of a given
  * (order N, element count E, isovalue count) runs the persistent emit kernel with 1, 2, 4 and 8
  * (element, isovalue) units per work-counter atomic (units that hold triangles: the scan before
- * the emit pass lists them), each twice with the second timed, keeps
+ * the emit pass lists them), each once untimed and three times timed (its fastest run counts), keeps
  * the fastest and reuses it afterwards.  That first call waits for the GPU once.  Every
  * candidate writes the same triangles, so results do not depend on tuning.  Under stream
  * capture, or when off, 1 unit per atomic.  sem_autotune_emit_entry reads choice k

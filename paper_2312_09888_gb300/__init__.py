@@ -78,6 +78,8 @@ def _declare(L):
     L.sem_qcriterion_isosurface_fields_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp,
                                                          i64, vp]
     L.sem_render_async.argtypes = [vp, vp, i64, vp, i32, vp, C.POINTER(sem_camera), i32, i32, vp, vp]
+    L.sem_frame_async.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, i64, vp, vp,
+                                  C.POINTER(sem_camera), i32, i32, vp, vp]
     L.sem_render_segments_async.argtypes = [vp, vp, i64, vp, i32, vp, C.c_uint64, C.POINTER(sem_camera), i32, i32,
                                             vp, vp]
     L.sem_isosurface_noalloc.argtypes = [vp, vp, vp, f32, vp, vp, i64, C.POINTER(i64), vp]
@@ -113,7 +115,7 @@ def _declare(L):
     for name in ("sem_create", "sem_set_stream", "sem_synchronize", "sem_debug_set_wait_limit", "sem_load_mesh", "sem_mesh_info",
                  "sem_derivatives", "sem_qcriterion", "sem_isosurface", "sem_isosurface_multi", "sem_isosurface_multi_async",
                  "sem_isosurface_multi_append_async", "sem_qcriterion_isosurface_async",
-                 "sem_qcriterion_isosurface_fields_async", "sem_render_async",
+                 "sem_qcriterion_isosurface_fields_async", "sem_frame_async", "sem_render_async",
                  "sem_render_segments_async",
                  "sem_isosurface_noalloc", "sem_render", "sem_surface_measures",
                  "sem_field_max", "sem_gll"):
@@ -352,13 +354,7 @@ def sem_qcriterion_isosurface_fields_async(ctx, mesh, u, v, w, Q, q_isos, fields
     starts, then the total).  Same results as sem_qcriterion_isosurface_async followed by one
     sem_isosurface_multi_append_async per field."""
     import torch
-    qv = np.ascontiguousarray(np.asarray(q_isos, dtype=np.float32).reshape(-1))
-    if len(fields) != len(f_isos):
-        raise ValueError("one list of isovalues per field")
-    fv = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32).reshape(-1) for x in f_isos])
-                              if f_isos else np.zeros(0, np.float32))
-    fn = np.ascontiguousarray(np.asarray([len(x) for x in f_isos], dtype=np.int32))
-    fp = (C.c_void_p * max(1, len(fields)))(*[_dev(f, "fields[k]", torch.float32) for f in fields])
+    qv, fv, fn, fp = _fields_args(q_isos, fields, f_isos)
     if cap is None:
         cap = 0 if tris is None else tris.numel() // 9
     st = get_lib().sem_qcriterion_isosurface_fields_async(
@@ -367,6 +363,40 @@ def sem_qcriterion_isosurface_fields_async(ctx, mesh, u, v, w, Q, q_isos, fields
         C.cast(fp, C.c_void_p), fv.ctypes.data_as(C.c_void_p), fn.ctypes.data_as(C.c_void_p),
         _dev(tris, "tris", torch.float32, allow_none=True), _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
         int(cap), _dev(counts_dev, "counts_dev", torch.int64))
+    _check(ctx, st)
+
+
+def _fields_args(q_isos, fields, f_isos):
+    import torch
+    qv = np.ascontiguousarray(np.asarray(q_isos, dtype=np.float32).reshape(-1))
+    if len(fields) != len(f_isos):
+        raise ValueError("one list of isovalues per field")
+    fv = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32).reshape(-1) for x in f_isos])
+                              if f_isos else np.zeros(0, np.float32))
+    fn = np.ascontiguousarray(np.asarray([len(x) for x in f_isos], dtype=np.int32))
+    fp = (C.c_void_p * max(1, len(fields)))(*[_dev(f, "fields[k]", torch.float32) for f in fields])
+    return qv, fv, fn, fp
+
+
+def sem_frame_async(ctx, mesh, u, v, w, Q, q_isos, fields, f_isos, tris, counts_dev, seg_rgb, cam: dict, W: int,
+                    H: int, rgba, depth=None, tri_elem=None, cap: Optional[int] = None) -> None:
+    """One frame in one call: sem_qcriterion_isosurface_fields_async then sem_render_async of all
+    its segments (colours ``seg_rgb``: one RGB row per segment, or None), each stream drawing the
+    segments it has just emitted and one resolve after the join.  Same results as the two calls."""
+    import torch
+    qv, fv, fn, fp = _fields_args(q_isos, fields, f_isos)
+    if cap is None:
+        cap = 0 if tris is None else tris.numel() // 9
+    rgb = None if seg_rgb is None else np.ascontiguousarray(np.asarray(seg_rgb, dtype=np.float32).reshape(-1))
+    camc = make_camera(cam)
+    st = get_lib().sem_frame_async(
+        ctx, mesh, _dev(u, "u", torch.float32), _dev(v, "v", torch.float32), _dev(w, "w", torch.float32),
+        _dev(Q, "Q", torch.float32), qv.ctypes.data_as(C.c_void_p), len(qv), len(fields), C.cast(fp, C.c_void_p),
+        fv.ctypes.data_as(C.c_void_p), fn.ctypes.data_as(C.c_void_p),
+        _dev(tris, "tris", torch.float32, allow_none=True), _dev(tri_elem, "tri_elem", torch.int32, allow_none=True),
+        int(cap), _dev(counts_dev, "counts_dev", torch.int64), None if rgb is None else rgb.ctypes.data_as(C.c_void_p),
+        C.byref(camc), int(W), int(H), _dev(rgba, "rgba", torch.uint8), _dev(depth, "depth", torch.float32,
+                                                                                allow_none=True))
     _check(ctx, st)
 
 

@@ -15,6 +15,8 @@
 // ------------------------------------------------------------------------------------------
 // Host-side objects
 
+struct RenderFrame;  // a frame drawn in parts (sem_render.cu)
+
 // scratch arenas (each call uses its own so calls never overlap in scratch); SCR_ISO_F0 + k
 // holds the isosurface pass of further field k of sem_qcriterion_isosurface_fields_async, which
 // runs on the auxiliary stream while Q's pass (SCR_ISO) runs on the context's stream
@@ -46,6 +48,8 @@ struct sem_ctx {
     // first use by sem_qcriterion_isosurface_fields_async)
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_qseg = nullptr, ev_join = nullptr;
+    // the frame sem_frame_async draws in parts (created on first use)
+    RenderFrame *frame = nullptr;
     // the render key buffer must read "empty" (all ones) at the start of a frame
     bool render_keys_dirty = true;
     // tensor-core operand A (the stacked derivative matrices) per 16-bit type: 0 BF16, 1 FP16
@@ -250,11 +254,13 @@ sem_status iso_run_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *f, 
                                float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, uint8_t *cases,
                                bool append = false);
 // Q, its isosurfaces and those of nf further fields, appended behind Q's; the further fields'
-// passes run on ctx->aux (see sem_qcriterion_isosurface_fields_async)
+// passes run on ctx->aux (see sem_qcriterion_isosurface_fields_async).  With `draw`, each
+// group's segments are drawn into the frame begun by render_frame_begin right after its emit,
+// on the stream that emitted them.
 sem_status iso_run_q_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                                   float *Q, const float *q_isos, int q_niso, int nf, const float *const *fields,
                                   const float *f_isos, const int *f_niso, float *tris, int32_t *tri_elem,
-                                  int64_t cap, int64_t *counts_dev);
+                                  int64_t cap, int64_t *counts_dev, bool draw = false);
 sem_status iso_run_q_multi_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                                  float *Q, const float *isos, int niso, float *tris, int32_t *tri_elem, int64_t cap,
                                  int64_t *counts_dev);
@@ -264,6 +270,17 @@ sem_status iso_noalloc_prepare(sem_ctx *ctx);
 sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64_t *seg_ntri, int nseg,
                       const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
                       const int64_t *seg_start_dev = nullptr, unsigned long long seg_mask = ~0ull);
+// A frame drawn in parts (sem_frame_async): begun on ctx->stream (segment starts on the device,
+// ntri_max the buffer's capacity), segments [seg_lo, seg_hi) drawn as part `part` (0..7, each
+// part once per frame) on ctx->stream (whichever stream that is at the time), ended -- large triangles, resolve into rgba/depth -- on ctx->stream.
+sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
+                              int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
+                              float *depth);
+sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int seg_hi, int part);
+sem_status render_frame_end(sem_ctx *ctx, const float *tris);
+void render_frame_free(sem_ctx *ctx);
+// true when the render's launch widths for W x H are chosen, or will not be timed
+bool render_width_settled(sem_ctx *ctx, int W, int H);
 sem_status measures_run(sem_ctx *ctx, const float *tris, int64_t ntri, double *out_host);
 sem_status fieldmax_run(sem_ctx *ctx, const float *f, int64_t n, float *out_host);
 

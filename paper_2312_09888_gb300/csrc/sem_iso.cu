@@ -807,8 +807,9 @@ static sem_status launch_emit(sem_ctx *ctx, const sem_mesh *m, const float *f, c
 }
 
 // The emit launch with the context's autotuner: the first emitting call of a given (order,
-// elements, isovalues) runs 1, 2, 4 and 8 units per work-counter atomic, each twice (the second
-// timed with CUDA events), and keeps the fastest; later calls reuse it.  Every candidate writes
+// elements, isovalues) runs 1, 2, 4 and 8 units per work-counter atomic, each once untimed and
+// three times timed with CUDA events (a candidate's time is its fastest run), and keeps the
+// fastest; later calls reuse it.  Every candidate writes
 // the same triangles to the same places, so the output does not depend on the choice.  Under
 // stream capture, or with tuning off, EMIT_UNITS_DEFAULT.
 template <int NP>
@@ -830,17 +831,20 @@ static sem_status emit(sem_ctx *ctx, const sem_mesh *m, const float *f, const Is
     float best_ms = 1e30f;
     sem_status st = SEM_OK;
     for (int units : {1, 2, 4, 8}) {
-        for (int rep = 0; rep < 2 && st == SEM_OK; ++rep) {
-            if (rep == 1) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
+        // once untimed, then three timed runs; the candidate's time is its fastest
+        float cand_ms = 1e30f;
+        for (int rep = 0; rep < 4 && st == SEM_OK; ++rep) {
+            if (rep > 0) st = sem_cuda(ctx, cudaEventRecord(e0, ctx->stream), "event");
             if (st == SEM_OK) st = launch_emit<NP>(ctx, m, f, S, offs, live, tris, tri_elem, cap, next, units, base);
-            if (rep == 1 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+            if (rep > 0 && st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(e1, ctx->stream), "event");
+            if (rep > 0 && st == SEM_OK) st = sem_cuda(ctx, cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            if (rep > 0 && st == SEM_OK) st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event");
+            if (rep > 0 && st == SEM_OK && ms < cand_ms) cand_ms = ms;
         }
         if (st != SEM_OK) break;
-        float ms = 0.f;
-        if ((st = sem_cuda(ctx, cudaEventSynchronize(e1), "event")) != SEM_OK) break;
-        if ((st = sem_cuda(ctx, cudaEventElapsedTime(&ms, e0, e1), "event")) != SEM_OK) break;
-        if (ms < best_ms) {
-            best_ms = ms;
+        if (cand_ms < best_ms) {
+            best_ms = cand_ms;
             best = units;
         }
     }
@@ -1017,9 +1021,11 @@ static bool emit_settled(sem_ctx *ctx, const sem_mesh *m, int niso)
 static sem_status aux_ready(sem_ctx *ctx)
 {
     if (ctx->aux) return SEM_OK;
-    int lo = 0, hi = 0, prio = 0;
-    SEM_CU(ctx, cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    if (ctx->stream && cudaStreamGetPriority(ctx->stream, &prio) != cudaSuccess) prio = 0;
+    int prio = 0;  // the context stream's priority (the legacy default stream's: 0)
+    if (ctx->stream && cudaStreamGetPriority(ctx->stream, &prio) != cudaSuccess) {
+        cudaGetLastError();  // not an error of the call: clear it so later launch checks stay clean
+        prio = 0;
+    }
     cudaStream_t s = nullptr;
     SEM_CU(ctx, cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio));
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -1043,7 +1049,7 @@ static sem_status aux_ready(sem_ctx *ctx)
 template <int NP>
 static sem_status fields_passes(sem_ctx *ctx, const sem_mesh *m, int nf, const float *const *fields,
                                 const IsoSet *SF, const IsoScratch *XF, float *tris, int32_t *tri_elem, int64_t cap,
-                                int64_t *cd, bool wait_q)
+                                int64_t *cd, bool wait_q, bool draw, int seg0)
 {
     for (int k = 0; k < nf; ++k) {
         SEM_TRY(launch_count<NP>(ctx, fields[k], SF[k], m->E, XF[k].cnt, nullptr));
@@ -1051,7 +1057,9 @@ static sem_status fields_passes(sem_ctx *ctx, const sem_mesh *m, int nf, const f
         if (k == 0 && wait_q) SEM_CU(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_qseg, 0));
         SEM_TRY(iso_segments_async(ctx, m->E, SF[k].niso, XF[k].offs, cd, true));
         if (tris) SEM_TRY(emit<NP>(ctx, m, fields[k], SF[k], XF[k].offs, XF[k].live, tris, tri_elem, cap, XF[k].next, cd));
+        if (draw && tris) SEM_TRY(render_frame_draw(ctx, tris, seg0, seg0 + SF[k].niso, 1 + k));
         cd += SF[k].niso;
+        seg0 += SF[k].niso;
     }
     return SEM_OK;
 }
@@ -1059,7 +1067,7 @@ static sem_status fields_passes(sem_ctx *ctx, const sem_mesh *m, int nf, const f
 template <int NP>
 static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                               float *Q, const IsoSet &SQ, int nf, const float *const *fields, const IsoSet *SF,
-                              float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev)
+                              float *tris, int32_t *tri_elem, int64_t cap, int64_t *counts_dev, bool draw)
 {
     const int64_t E = m->E;
     IsoScratch XQ, XF[SEM_MAX_FIELDS];
@@ -1075,15 +1083,19 @@ static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, c
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
     // one stream while the kernel trace is on (each traced kernel's time is then its own) or an
-    // emit launch is still to be timed (so are the tuner's timings)
-    bool fork = nf > 0 && !ctx->trace_on;
+    // emit launch is still to be timed (so are the tuner's timings), and under a capture that
+    // began before the auxiliary stream existed (creating a stream is not done during capture)
+    if (nf > 0 && cs == cudaStreamCaptureStatusNone) SEM_TRY(aux_ready(ctx));  // whether it forks or not
+    bool fork = nf > 0 && !ctx->trace_on && ctx->aux;
     if (fork && cs == cudaStreamCaptureStatusNone && tris) {
         fork = emit_settled(ctx, m, SQ.niso);
         for (int k = 0; k < nf && fork; ++k) fork = emit_settled(ctx, m, SF[k].niso);
     }
     if (!fork) {
         SEM_TRY(iso_tail_async<NP>(ctx, m, Q, SQ, XQ, tris, tri_elem, cap, counts_dev, false));
-        return fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, false);
+        if (draw && tris) SEM_TRY(render_frame_draw(ctx, tris, 0, SQ.niso, 0));
+        return fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, false, draw,
+                                 SQ.niso);
     }
     SEM_TRY(aux_ready(ctx));
     cudaStream_t main = ctx->stream;
@@ -1096,11 +1108,12 @@ static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, c
     if (st == SEM_OK) st = sem_cuda(ctx, cudaEventRecord(ctx->ev_qseg, main), "cudaEventRecord");
     ctx->stream = ctx->aux;
     if (st == SEM_OK)
-        st = fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, true);
+        st = fields_passes<NP>(ctx, m, nf, fields, SF, XF, tris, tri_elem, cap, counts_dev + SQ.niso, true, draw,
+                               SQ.niso);
     ctx->stream = main;
     const cudaError_t ej = cudaEventRecord(ctx->ev_join, ctx->aux);
-    if (st == SEM_OK && tris)
-        st = emit<NP>(ctx, m, Q, SQ, XQ.offs, XQ.live, tris, tri_elem, cap, XQ.next);
+    if (st == SEM_OK && tris) st = emit<NP>(ctx, m, Q, SQ, XQ.offs, XQ.live, tris, tri_elem, cap, XQ.next);
+    if (st == SEM_OK && draw && tris) st = render_frame_draw(ctx, tris, 0, SQ.niso, 0);
     const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(main, ctx->ev_join, 0) : ej;
     SEM_TRY(st);
     return sem_cuda(ctx, ew, "join of the auxiliary stream");
@@ -1109,7 +1122,7 @@ static sem_status q_fields_np(sem_ctx *ctx, const sem_mesh *m, const float *u, c
 sem_status iso_run_q_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *u, const float *v, const float *w,
                                   float *Q, const float *q_isos, int q_niso, int nf, const float *const *fields,
                                   const float *f_isos, const int *f_niso, float *tris, int32_t *tri_elem,
-                                  int64_t cap, int64_t *counts_dev)
+                                  int64_t cap, int64_t *counts_dev, bool draw)
 {
     IsoSet SQ, SF[SEM_MAX_FIELDS];
     memset(&SQ, 0, sizeof SQ);
@@ -1122,7 +1135,7 @@ sem_status iso_run_q_fields_async(sem_ctx *ctx, const sem_mesh *m, const float *
     }
     switch (m->N + 1) {
 #define SEM_CASE(NPV) \
-    case NPV: return q_fields_np<NPV>(ctx, m, u, v, w, Q, SQ, nf, fields, SF, tris, tri_elem, cap, counts_dev);
+    case NPV: return q_fields_np<NPV>(ctx, m, u, v, w, Q, SQ, nf, fields, SF, tris, tri_elem, cap, counts_dev, draw);
         SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
         SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
 #undef SEM_CASE

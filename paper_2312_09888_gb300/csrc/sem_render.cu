@@ -30,6 +30,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "sem_internal.cuh"
 
@@ -234,30 +235,31 @@ __device__ __forceinline__ int seg_of(const RenderParams &P, int64_t t, int sg)
     return sg;
 }
 
-// One thread per triangle for the setup (its 36 bytes staged through shared memory with
-// coalesced loads); then each warp spreads the pixel-centre tests of its 32 triangles evenly
-// over its lanes, so a lane never idles while a neighbour walks a bigger box; a pixel test
-// finds its triangle from one warp OR of the list starts in its round and a rank -> lane table.
-__global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
-                                                      const __grid_constant__ RenderParams P,
-                                                      unsigned long long *__restrict__ keys,
-                                                      int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
-                                                      uint32_t *__restrict__ colors)
+// Shared memory of one block's tile of up to 256 triangles.
+struct RasterSmem {
+    __align__(16) float tri[256 * 9];
+    SmallRecs rec;
+    uint8_t lane_of[8][32];
+    int sg0;       // segment of the tile's first triangle
+    int any;       // some triangle of the tile lies in a drawn segment
+    int64_t next;  // start of the segment after sg0
+};
+
+// One tile: triangles t0 .. t0 + nt - 1 (segment search from sg_from).  One thread per triangle
+// for the setup (its 36 bytes staged through shared memory with coalesced loads); then each warp
+// spreads the pixel-centre tests of its 32 triangles evenly over its lanes, so a lane never
+// idles while a neighbour walks a bigger box; a pixel test finds its triangle from one warp OR
+// of the list starts in its round and a rank -> lane table.  Block-uniform exits only; the
+// caller synchronises the block before it reuses `sm`.
+__device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int t0, int nt_blk, int sg_from,
+                                            const RenderParams &P, unsigned long long *__restrict__ keys,
+                                            int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
+                                            uint32_t *__restrict__ colors, RasterSmem &sm)
 {
-    __shared__ __align__(16) float s_tri[256 * 9];
-    __shared__ SmallRecs s_rec;
-    __shared__ uint8_t s_lane_of[8][32];
-    __shared__ int s_sg0;        // segment of the block's first triangle
-    __shared__ int64_t s_next;   // start of the segment after it
-    if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
-    const int t0 = blockIdx.x * 256;
-    // blocks past the (device-clamped) triangle count have no work; the whole block leaves
-    // before its first barrier
-    if (t0 >= ntri) return;
-    const int nt_blk = min(256, ntri - t0);
+    float *s_tri = sm.tri;
     const float *src = tris + (int64_t)t0 * 9;
     if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-        // 16-byte loads when the block's 36-byte triangles start on a 16-byte boundary
+        // 16-byte loads when the tile's 36-byte triangles start on a 16-byte boundary
         const int n4 = nt_blk * 9 / 4;
         for (int q = threadIdx.x; q < n4; q += 256)
             reinterpret_cast<float4 *>(s_tri)[q] = __ldcs(reinterpret_cast<const float4 *>(src) + q);
@@ -266,27 +268,27 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = __ldcs(src + q);
     }
     if (threadIdx.x == 0) {
-        const int sg = seg_of(P, t0, 0);
-        s_sg0 = sg;
-        s_next = sg < P.nseg - 1 ? seg_start(P, sg + 1) : INT64_MAX;
+        const int sg = seg_of(P, t0, sg_from);
+        sm.sg0 = sg;
+        sm.next = sg < P.nseg - 1 ? seg_start(P, sg + 1) : INT64_MAX;
     }
     __syncthreads();
     if (P.seg_mask != ~0ull) {
-        // a block whose triangles all lie in segments that are not drawn leaves at once
-        __shared__ int s_any;
+        // a tile whose triangles all lie in segments that are not drawn is done at once
         if (threadIdx.x == 0) {
             int any = 0;
-            for (int sg = s_sg0; sg < P.nseg && seg_start(P, sg) < t0 + nt_blk; ++sg) any |= (int)((P.seg_mask >> sg) & 1ull);
-            s_any = any;
+            for (int sg = sm.sg0; sg < P.nseg && seg_start(P, sg) < t0 + nt_blk; ++sg)
+                any |= (int)((P.seg_mask >> sg) & 1ull);
+            sm.any = any;
         }
         __syncthreads();
-        if (!s_any) return;
+        if (!sm.any) return;
     }
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
     bool is_large = false;
     int npx = 0;
-    const int sg = (int)threadIdx.x < nt_blk ? (t < s_next ? s_sg0 : seg_of(P, t, s_sg0)) : 0;
+    const int sg = (int)threadIdx.x < nt_blk ? (t < sm.next ? sm.sg0 : seg_of(P, t, sm.sg0)) : 0;
     if ((int)threadIdx.x < nt_blk && ((P.seg_mask >> sg) & 1ull)) {
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
             colors[t] = shade_rgba(P, s_tri + threadIdx.x * 9, sg);
             const int nx = S.px1 - S.px0 + 1, ny = S.py1 - S.py0 + 1;
             if (nx * ny <= SMALL_PX) {
-                if (store_rec(s_rec, threadIdx.x, S, P.W)) npx = nx * ny;
+                if (store_rec(sm.rec, threadIdx.x, S, P.W)) npx = nx * ny;
             } else {
                 is_large = true;
             }
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     // owners: the lanes with candidates, in lane order; their lists start at excl, increasing.
     // Owner rank -> lane in a 32-byte table.
     const unsigned owners = __ballot_sync(0xffffffffu, npx > 0);
-    uint8_t *lane_of = s_lane_of[threadIdx.x >> 5];
+    uint8_t *lane_of = sm.lane_of[threadIdx.x >> 5];
     if (npx > 0) lane_of[__popc(owners & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
     // each round: lane `lane` takes candidate r + lane of the warp's list.  The owners whose
@@ -340,8 +342,8 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
         const int L = lane_of[rank & 31];
         const int first = __shfl_sync(0xffffffffu, excl, L);
         const int i = wbase + L;
-        const float4 a = s_rec.a[i], b = s_rec.b[i], c = s_rec.c[i];
-        const int4 d = s_rec.d[i];
+        const float4 a = sm.rec.a[i], b = sm.rec.b[i], c = sm.rec.c[i];
+        const int4 d = sm.rec.d[i];
         const int k = idx - first;
         const int ky = (k * d.y) >> 10, kx = k - ky * d.z;
         float z;
@@ -349,6 +351,53 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
             const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | (unsigned)(t0 + i);
             atomicMin(keys + (unsigned)(d.x + ky * W + kx), key);
         }
+    }
+}
+
+// One tile of 256 triangles per block, triangles [0, ntri) (ntri clamped to the device total
+// of the segments when they come from the device).
+__global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
+                                                      const __grid_constant__ RenderParams P,
+                                                      unsigned long long *__restrict__ keys,
+                                                      int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
+                                                      uint32_t *__restrict__ colors)
+{
+    __shared__ RasterSmem sm;
+    if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
+    const int t0 = blockIdx.x * 256;
+    // blocks past the (device-clamped) triangle count have no work; the whole block leaves
+    // before its first barrier
+    if (t0 >= ntri) return;
+    raster_tile(tris, t0, min(256, ntri - t0), 0, P, keys, large, nlarge, colors, sm);
+}
+
+// The triangles of segments [seg_lo, seg_hi), their range read from the device segment starts
+// and clamped to the buffer's ntri: a persistent grid whose blocks take the 256-triangle tiles
+// of the whole buffer that meet the range from a counter (zeroed when the frame begins), so they
+// finish within a tile of each other; the tiles stay on the buffer's 256-triangle grid (only the
+// range's first tile can start unaligned) and are clipped to the range.  Used where a frame is
+// drawn in parts, one part per stream, before one resolve.
+__global__ void __launch_bounds__(256, 6) k_raster_range(const float *__restrict__ tris, int ntri, int seg_lo,
+                                                         int seg_hi, const __grid_constant__ RenderParams P,
+                                                         unsigned long long *__restrict__ keys,
+                                                         int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
+                                                         uint32_t *__restrict__ colors, int *__restrict__ next_tile)
+{
+    __shared__ RasterSmem sm;
+    __shared__ int s_k[2];  // the current tile's counter value and the next one's
+    // clamped to the buffer's capacity, as k_raster_small clamps the device total
+    const int64_t hi = min(seg_start(P, seg_hi), (int64_t)ntri), lo = min(seg_start(P, seg_lo), hi);
+    if (threadIdx.x == 0) s_k[0] = atomicAdd(next_tile, 1);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const int64_t tile = lo / 256 + s_k[cur];
+        if (tile * 256 >= hi) break;  // block-uniform
+        // the next tile's counter value, fetched while this one is drawn (read after the barrier
+        // at the end of this iteration)
+        if (threadIdx.x == 0) s_k[cur ^ 1] = atomicAdd(next_tile, 1);
+        const int64_t a = max(tile * 256, lo), b = min(tile * 256 + 256, hi);
+        raster_tile(tris, (int)a, (int)(b - a), seg_lo, P, keys, large, nlarge, colors, sm);
+        __syncthreads();  // the tile's shared memory is free for the next
     }
 }
 
@@ -454,12 +503,29 @@ static void unit3(double *a)
     a[2] /= n;
 }
 
-sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int64_t *seg_ntri, int nseg,
-                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
-                      const int64_t *seg_start_dev, unsigned long long seg_mask)
+// A frame's parameters and buffers: the key buffer (kept all "empty" between frames), the
+// large-triangle counter and list, the per-triangle colours.
+#define RENDER_MAX_PARTS 8  // parts of a frame drawn in parts, each with its tile counter
+struct RenderFrame {
+    RenderParams P;
+    unsigned long long *keys = nullptr;
+    int32_t *nlarge = nullptr, *large = nullptr;
+    int *next_tile = nullptr;  // [RENDER_MAX_PARTS] tile counters of the parts
+    uint32_t *colors = nullptr;
+    int ntri = 0;
+    int64_t npx = 0;
+    uint8_t *rgba = nullptr;
+    float *depth = nullptr;
+};
+
+// Projection, segment table and buffers of one frame (no launch but the one-time reset of a new
+// key buffer, on ctx->stream).
+static sem_status render_setup(sem_ctx *ctx, RenderFrame &F, int64_t ntri64, const int64_t *seg_ntri, int nseg,
+                               const float *seg_rgb, const sem_camera *cam, int W, int H,
+                               const int64_t *seg_start_dev, unsigned long long seg_mask)
 {
     if (nseg < 1 || nseg > RENDER_MAX_SEG) return sem_fail(ctx, SEM_ERR_ARG, "sem_render: nseg=%d", nseg);
-    RenderParams P;
+    RenderParams &P = F.P;
     memset(&P, 0, sizeof P);
     double f[3], s[3], u[3], up[3];
     for (int k = 0; k < 3; ++k) {
@@ -515,7 +581,6 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     }
     const int ntri = (int)ntri64;
     const int64_t npx = (int64_t)W * H;
-
     // scratch: key buffer (kept all-ones between frames) in its own arena; the large-triangle
     // counter and list in another
     const size_t b_keys = sizeof(unsigned long long) * (size_t)npx;
@@ -532,34 +597,123 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     const size_t nt1 = (size_t)(ntri > 0 ? ntri : 1);
     const size_t list_bytes = ((sizeof(int32_t) * nt1 + 255) / 256) * 256;
     SEM_TRY(sem_scratch_nogrow_in_capture(ctx, SCR_TRI, 256 + list_bytes + sizeof(uint32_t) * nt1, &lscr));
-    unsigned long long *keys = reinterpret_cast<unsigned long long *>(kscr);
-    int32_t *nlarge = reinterpret_cast<int32_t *>(lscr);
-    int32_t *large = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(lscr) + 256);
-    uint32_t *colors = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(lscr) + 256 + list_bytes);
-    // one frame; the widths of the persistent large-triangle pass and of the resolve pass (in
-    // CTAs per SM) come from the context's autotuner, chosen per frame size on the first frame:
-    // the frame leaves the key buffer all "empty" again, so every candidate draws the same image
-    static const int kLarge[5] = {6, 4, 8, 2, 6}, kResolve[5] = {8, 4, 16, 8, 2};
+    F.keys = reinterpret_cast<unsigned long long *>(kscr);
+    F.nlarge = reinterpret_cast<int32_t *>(lscr);
+    F.next_tile = reinterpret_cast<int *>(lscr) + 1;
+    F.large = reinterpret_cast<int32_t *>(reinterpret_cast<char *>(lscr) + 256);
+    F.colors = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(lscr) + 256 + list_bytes);
+    F.ntri = ntri;
+    F.npx = npx;
+    return SEM_OK;
+}
+
+// the widths of the persistent large-triangle pass and of the resolve pass (in CTAs per SM), one
+// pair per candidate of the context's autotuner, chosen per frame size on the first frame
+static const int kLarge[5] = {6, 4, 8, 2, 6}, kResolve[5] = {8, 4, 16, 8, 2};
+
+static sem_status frame_begin(sem_ctx *ctx, const RenderFrame &F)
+{
+    // until k_resolve has run, the keys are not all "empty"
+    ctx->render_keys_dirty = true;
+    // the large-triangle count and the parts' tile counters
+    SEM_CU(ctx, cudaMemsetAsync(F.nlarge, 0, sizeof(int32_t) * (1 + RENDER_MAX_PARTS), ctx->stream));
+    return SEM_OK;
+}
+
+static sem_status frame_end(sem_ctx *ctx, const RenderFrame &F, const float *tris, int w, uint8_t *rgba, float *depth)
+{
+    if (F.ntri > 0) {
+        SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<kLarge[w] * ctx->sm_count, LARGE_THREADS, 0,
+                                                           ctx->stream>>>(tris, F.large, F.nlarge, F.P, F.keys));
+        SEM_CU(ctx, cudaGetLastError());
+    }
+    const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>((F.npx / 4 + 255) / 256,
+                                                                 (int64_t)kResolve[w] * ctx->sm_count));
+    SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)rgrid, 256, 0, ctx->stream>>>(
+                                     F.colors, F.npx, F.keys, reinterpret_cast<uint32_t *>(rgba), depth));
+    SEM_CU(ctx, cudaGetLastError());
+    ctx->render_keys_dirty = false;
+    return SEM_OK;
+}
+
+sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int64_t *seg_ntri, int nseg,
+                      const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth,
+                      const int64_t *seg_start_dev, unsigned long long seg_mask)
+{
+    RenderFrame F;
+    SEM_TRY(render_setup(ctx, F, ntri64, seg_ntri, nseg, seg_rgb, cam, W, H, seg_start_dev, seg_mask));
+    // one frame; the frame leaves the key buffer all "empty" again, so every candidate width of
+    // the autotuner draws the same image
     auto frame = [&](int w) -> sem_status {
-        // until k_resolve has run, the keys are not all "empty"
-        ctx->render_keys_dirty = true;
-        SEM_CU(ctx, cudaMemsetAsync(nlarge, 0, sizeof(int32_t), ctx->stream));
-        if (ntri > 0) {
-            SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(
-                                                  tris, ntri, P, keys, large, nlarge, colors));
-            SEM_CU(ctx, cudaGetLastError());
-            SEM_TRACED(ctx, "k_raster_large", k_raster_large<<<kLarge[w] * ctx->sm_count, LARGE_THREADS, 0,
-                                                               ctx->stream>>>(tris, large, nlarge, P, keys));
+        SEM_TRY(frame_begin(ctx, F));
+        if (F.ntri > 0) {
+            SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(F.ntri + 255) / 256, 256, 0, ctx->stream>>>(
+                                                  tris, F.ntri, F.P, F.keys, F.large, F.nlarge, F.colors));
             SEM_CU(ctx, cudaGetLastError());
         }
-        const int64_t rgrid = std::max<int64_t>(1, std::min<int64_t>((npx / 4 + 255) / 256,
-                                                                     (int64_t)kResolve[w] * ctx->sm_count));
-        SEM_TRACED(ctx, "k_resolve", k_resolve<<<(unsigned)rgrid, 256, 0, ctx->stream>>>(
-                                         colors, npx, keys, reinterpret_cast<uint32_t *>(rgba), depth));
-        SEM_CU(ctx, cudaGetLastError());
-        ctx->render_keys_dirty = false;
-        return SEM_OK;
+        return frame_end(ctx, F, tris, w, rgba, depth);
     };
     static const int kCand[5] = {0, 1, 2, 3, 4};
-    return width_tuned(ctx, TUNE_RENDER, W, H, kCand, ntri > 0 ? 5 : 1, 0, frame);
+    return width_tuned(ctx, TUNE_RENDER, W, H, kCand, F.ntri > 0 ? 5 : 1, 0, frame);
+}
+
+// ------------------------------------------------------------------------------------------
+// A frame drawn in parts (sem_frame_async): begun on the context's stream, its segment ranges
+// drawn on whichever stream produced their triangles, ended (large triangles, resolve) on the
+// context's stream once every part is ordered before it.  One frame in progress per context.
+sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
+                              int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
+                              float *depth)
+{
+    if (!ctx->frame) ctx->frame = new RenderFrame();
+    RenderFrame &F = *ctx->frame;
+    std::vector<int64_t> zeros(nseg > 0 ? nseg : 1, 0);
+    SEM_TRY(render_setup(ctx, F, ntri_max, zeros.data(), nseg, seg_rgb, cam, W, H, seg_start_dev, ~0ull));
+    F.rgba = rgba;
+    F.depth = depth;
+    (void)tris;
+    return frame_begin(ctx, F);
+}
+
+// Segments [seg_lo, seg_hi) of the frame begun last, as its part `part` (each part of a frame
+// has its own tile counter), on ctx->stream.
+sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int seg_hi, int part)
+{
+    RenderFrame &F = *ctx->frame;
+    if (part < 0 || part >= RENDER_MAX_PARTS) return sem_fail(ctx, SEM_ERR_ARG, "frame part %d", part);
+    if (F.ntri <= 0 || seg_lo >= seg_hi) return SEM_OK;
+    static KernelSetup ks;
+    int per_sm = 1;
+    SEM_TRY(kernel_setup(ctx, ks, k_raster_range, 256, 0, &per_sm));
+    const int64_t tiles = ((int64_t)F.ntri + 255) / 256 + 1;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)per_sm * ctx->sm_count);
+    SEM_TRACED(ctx, "k_raster_range", k_raster_range<<<(unsigned)grid, 256, 0, ctx->stream>>>(
+                                          tris, F.ntri, seg_lo, seg_hi, F.P, F.keys, F.large, F.nlarge, F.colors,
+                                          F.next_tile + part));
+    return sem_cuda(ctx, cudaGetLastError(), "k_raster_range launch");
+}
+
+// Large triangles and resolve of the frame begun last, on ctx->stream, with the launch widths the
+// autotuner chose for this frame size (the defaults when it has not chosen yet).
+sem_status render_frame_end(sem_ctx *ctx, const float *tris)
+{
+    RenderFrame &F = *ctx->frame;
+    int w = 0;
+    for (const auto &t : ctx->width_tune)
+        if (t.kind == TUNE_RENDER && t.N == F.P.W && t.size == F.P.H) w = t.width;
+    return frame_end(ctx, F, tris, w, F.rgba, F.depth);
+}
+
+bool render_width_settled(sem_ctx *ctx, int W, int H)
+{
+    if (!ctx->autotune || ctx->trace_on) return true;
+    for (const auto &t : ctx->width_tune)
+        if (t.kind == TUNE_RENDER && t.N == W && t.size == H) return true;
+    return false;
+}
+
+void render_frame_free(sem_ctx *ctx)
+{
+    delete ctx->frame;
+    ctx->frame = nullptr;
 }

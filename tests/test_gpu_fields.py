@@ -205,3 +205,96 @@ def test_fields_call_argument_errors(gpu, sess):
         with pytest.raises(S.SemError) as ex:
             S.sem_qcriterion_isosurface_fields_async(sess.ctx, m, *vel, Q, [0.1], kw["fields"], kw["fisos"], tris, cnt)
         assert ex.value.status == S.SEM_ERR_ARG, kw
+
+
+@pytest.mark.parametrize("N,nel", [(7, 5), (5, 4)])
+def test_frame_call_equals_fields_call_and_render(gpu, sess, N, nel):
+    """sem_frame_async against sem_qcriterion_isosurface_fields_async + sem_render_async: frame
+    (RGBA and depth), triangles and segment starts bit for bit -- on its first call (the render's
+    launch widths still to be chosen: the two calls as such), later calls (each stream draws its
+    own segments, one resolve), traced (one stream), with tuning off, and replayed from a graph."""
+    S = gpu
+    mesh, f = _case(N, nel)
+    m = sess.mesh(N, mesh.xyz().numpy())
+    vel = [f[c].float().cuda().contiguous() for c in range(3)]
+    T = f[3].float().cuda().contiguous()
+    U = vel[0].clone()
+    Qr = torch.empty_like(vel[0])
+    S.sem_qcriterion(sess.ctx, m, *vel, Qr)
+    qisos = [float(np.float32(0.1 * S.sem_field_max(sess.ctx, Qr)))]
+    fields, fisos = [T, U], [[0.5], [0.0, 0.05]]
+    nseg = 1 + 1 + 2
+    cols = [[0.9, 0.3, 0.2], [0.2, 0.5, 0.9], [0.3, 0.8, 0.3], [0.8, 0.8, 0.2]]
+    cam = si.box_camera_persp((0.0, 0.0, 0.0), (2 * math.pi, 2 * math.pi, 1.0), 320, 180,
+                              direction=(1.0, -1.2, 0.8), up=(0.0, 0.0, 1.0))
+    W, H = cam["W"], cam["H"]
+    total = sum(sum(S.sem_isosurface_multi(sess.ctx, m, x, iv, None)) for x, iv in ((Qr, qisos), (T, [0.5]),
+                                                                                (U, [0.0, 0.05])))
+    cap = total + 64
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    S.sem_autotune_set(sess.ctx, False)  # the reference at the default launch widths
+    Q = torch.empty_like(vel[0])
+    rt = torch.full((cap * 9,), -2.0, device="cuda")
+    rc = torch.empty(nseg + 1, dtype=torch.int64, device="cuda")
+    r_rgba = torch.empty(H * W * 4, dtype=torch.uint8, device="cuda")
+    r_depth = torch.empty(H * W, device="cuda")
+    S.sem_qcriterion_isosurface_fields_async(sess.ctx, m, *vel, Q, qisos, fields, fisos, rt, rc, cap=cap)
+    S.sem_render_async(sess.ctx, rt, cap, rc, nseg, cols, cam, W, H, r_rgba, r_depth)
+    S.sem_synchronize(sess.ctx)
+    assert int(rc[-1]) == total and (r_rgba.view(H, W, 4)[..., 3] == 255).float().mean() > 0.05
+    S.sem_autotune_set(sess.ctx, True)
+    tris = torch.empty_like(rt)
+    cnt = torch.empty_like(rc)
+    rgba = torch.empty_like(r_rgba)
+    depth = torch.empty_like(r_depth)
+
+    def call():
+        S.sem_frame_async(sess.ctx, m, *vel, Q, qisos, fields, fisos, tris, cnt, cols, cam, W, H, rgba, depth,
+                          cap=cap)
+
+    def check(label):
+        snap = (rgba.clone(), depth.clone(), tris.clone(), cnt.clone())
+        S.sem_synchronize(sess.ctx)
+        assert torch.equal(snap[3], rc), label
+        assert torch.equal(snap[2], rt), label
+        assert torch.equal(snap[0], r_rgba), label
+        assert torch.equal(snap[1], r_depth), label
+
+    def reset():
+        tris.fill_(-2.0)
+        cnt.fill_(-9)
+        rgba.fill_(7)
+        depth.fill_(-1.0)
+
+    for label in ("first call (tuning)", "second call (in parts)"):
+        reset()
+        call()
+        check(label)
+    S.sem_trace_enable(sess.ctx, True)
+    S.sem_trace_collect(sess.ctx)
+    reset()
+    call()
+    S.sem_synchronize(sess.ctx)
+    names = S.sem_trace_collect(sess.ctx)
+    S.sem_trace_enable(sess.ctx, False)
+    assert names["k_raster_range"][1] == 3 and "k_raster_small" not in names, names  # Q, T, U groups
+    assert names["k_resolve"][1] == 1, names
+    check("traced")
+    S.sem_autotune_set(sess.ctx, False)
+    try:
+        reset()
+        call()
+        check("tuning off")
+    finally:
+        S.sem_autotune_set(sess.ctx, True)
+    call()  # settles the tuners outside the capture
+    S.sem_synchronize(sess.ctx)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+        call()
+    S.sem_set_stream(sess.ctx, torch.cuda.current_stream())
+    for rep in range(2):
+        reset()
+        g.replay()
+        check(f"graph replay {rep}")
