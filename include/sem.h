@@ -293,9 +293,9 @@ SEM_API sem_status sem_qcriterion_isosurface_fields_async(sem_ctx *ctx, const se
  * segments it has just emitted -- Q's on the context's stream, the further fields' on the
  * auxiliary stream -- into the same depth keys, and the large-triangle pass and the resolve run
  * once, after the join.  rgba, depth, Q, tris, tri_elem and counts_dev are bit for bit those of
- * the two calls.  The first call for a frame size, while the context's autotuner still has to
- * choose the render's launch widths, runs the two calls as such (so they are timed on a whole
- * frame).  No host synchronisation; may be captured in a CUDA graph (scratch rule of
+ * the two calls.  With nfields = 0, and on the first call for a frame size while the context's
+ * autotuner still has to choose the render's launch widths (so they are timed on a whole frame),
+ * the call runs the two calls as such.  No host synchronisation; may be captured in a CUDA graph (scratch rule of
  * sem_isosurface_multi_async; render scratch likewise sized by an uncaptured call).  Arguments
  * and errors as the two calls (cap < 2^31, nseg <= 64); one frame in progress per context. */
 SEM_API sem_status sem_frame_async(sem_ctx *ctx, const sem_mesh *mesh, const float *u, const float *v, const float *w,

@@ -864,8 +864,9 @@ sem_status sem_frame_async(sem_ctx *ctx, const sem_mesh *m, const float *u, cons
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
-    if (cs == cudaStreamCaptureStatusNone && !render_width_settled(ctx, W, H)) {
-        // the first frame of this size with the autotuner on: the two calls in sequence, so the
+    if (nfields == 0 || (cs == cudaStreamCaptureStatusNone && !render_width_settled(ctx, W, H))) {
+        // the two calls in sequence: with no further fields there is nothing for a second
+        // stream to overlap, and on the first frame of this size with the autotuner on, the
         // render's launch widths are timed on a whole frame
         SEM_TRY(iso_run_q_fields_async(ctx, m, u, v, w, Q, q_isos, q_niso, nfields, fields, f_isos, f_niso, tris,
                                        tri_elem, cap, counts_dev));

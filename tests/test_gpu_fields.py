@@ -298,3 +298,39 @@ def test_frame_call_equals_fields_call_and_render(gpu, sess, N, nel):
         reset()
         g.replay()
         check(f"graph replay {rep}")
+
+
+def test_frame_call_without_further_fields(gpu, sess):
+    """No further fields: the fused call and one render, as such (k_raster_small, no parts)."""
+    S = gpu
+    mesh, f = _case(7, 4)
+    m = sess.mesh(7, mesh.xyz().numpy())
+    vel = [f[c].float().cuda().contiguous() for c in range(3)]
+    Q0 = torch.empty_like(vel[0])
+    S.sem_qcriterion(sess.ctx, m, *vel, Q0)
+    isos = [float(np.float32(x * S.sem_field_max(sess.ctx, Q0))) for x in (0.1, 0.3)]
+    n = sum(S.sem_isosurface_multi(sess.ctx, m, Q0, isos, None))
+    cam = si.box_camera_persp((0.0, 0.0, 0.0), (2 * math.pi, 2 * math.pi, 1.0), 200, 120,
+                              direction=(1.0, -1.2, 0.8), up=(0.0, 0.0, 1.0))
+    W, H = cam["W"], cam["H"]
+    out = []
+    for frame_call in (False, True):
+        Q = torch.empty_like(vel[0])
+        tris = torch.full(((n + 5) * 9,), -1.0, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+        rgba = torch.zeros(H * W * 4, dtype=torch.uint8, device="cuda")
+        depth = torch.zeros(H * W, device="cuda")
+        S.sem_trace_enable(sess.ctx, True)
+        S.sem_trace_collect(sess.ctx)
+        if frame_call:
+            S.sem_frame_async(sess.ctx, m, *vel, Q, isos, [], [], tris, cnt, None, cam, W, H, rgba, depth)
+        else:
+            S.sem_qcriterion_isosurface_async(sess.ctx, m, *vel, Q, isos, tris, cnt)
+            S.sem_render_async(sess.ctx, tris, n + 5, cnt, 2, None, cam, W, H, rgba, depth)
+        S.sem_synchronize(sess.ctx)
+        names = S.sem_trace_collect(sess.ctx)
+        S.sem_trace_enable(sess.ctx, False)
+        assert "k_raster_range" not in names and names["k_raster_small"][1] == 1, names
+        out.append((Q, tris, cnt, rgba, depth))
+    assert all(torch.equal(a, b) for a, b in zip(*out))
+    assert (out[1][3].view(H, W, 4)[..., 3] == 255).any()
