@@ -873,7 +873,7 @@ sem_status sem_frame_async(sem_ctx *ctx, const sem_mesh *m, const float *u, cons
         std::vector<int64_t> zeros(nseg, 0);
         return render_run(ctx, tris, cap, zeros.data(), nseg, seg_rgb, cam, W, H, rgba, depth, counts_dev);
     }
-    SEM_TRY(render_frame_begin(ctx, tris, cap, counts_dev, nseg, seg_rgb, cam, W, H, rgba, depth));
+    SEM_TRY(render_frame_begin(ctx, cap, counts_dev, nseg, seg_rgb, cam, W, H, rgba, depth));
     SEM_TRY(iso_run_q_fields_async(ctx, m, u, v, w, Q, q_isos, q_niso, nfields, fields, f_isos, f_niso, tris,
                                    tri_elem, cap, counts_dev, true));
     return render_frame_end(ctx, tris);

@@ -273,9 +273,8 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri, const int64
 // A frame drawn in parts (sem_frame_async): begun on ctx->stream (segment starts on the device,
 // ntri_max the buffer's capacity), segments [seg_lo, seg_hi) drawn as part `part` (0..7, each
 // part once per frame) on ctx->stream (whichever stream that is at the time), ended -- large triangles, resolve into rgba/depth -- on ctx->stream.
-sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
-                              int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
-                              float *depth);
+sem_status render_frame_begin(sem_ctx *ctx, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
+                              const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth);
 sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int seg_hi, int part);
 sem_status render_frame_end(sem_ctx *ctx, const float *tris);
 void render_frame_free(sem_ctx *ctx);

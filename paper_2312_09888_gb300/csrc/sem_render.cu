@@ -661,9 +661,8 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
 // A frame drawn in parts (sem_frame_async): begun on the context's stream, its segment ranges
 // drawn on whichever stream produced their triangles, ended (large triangles, resolve) on the
 // context's stream once every part is ordered before it.  One frame in progress per context.
-sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max, const int64_t *seg_start_dev,
-                              int nseg, const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba,
-                              float *depth)
+sem_status render_frame_begin(sem_ctx *ctx, int64_t ntri_max, const int64_t *seg_start_dev, int nseg,
+                              const float *seg_rgb, const sem_camera *cam, int W, int H, uint8_t *rgba, float *depth)
 {
     if (!ctx->frame) ctx->frame = new RenderFrame();
     RenderFrame &F = *ctx->frame;
@@ -671,7 +670,6 @@ sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max,
     SEM_TRY(render_setup(ctx, F, ntri_max, zeros.data(), nseg, seg_rgb, cam, W, H, seg_start_dev, ~0ull));
     F.rgba = rgba;
     F.depth = depth;
-    (void)tris;
     return frame_begin(ctx, F);
 }
 
@@ -679,6 +677,7 @@ sem_status render_frame_begin(sem_ctx *ctx, const float *tris, int64_t ntri_max,
 // has its own tile counter), on ctx->stream.
 sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int seg_hi, int part)
 {
+    if (!ctx->frame) return sem_fail(ctx, SEM_ERR_ARG, "frame draw without a frame begun");
     RenderFrame &F = *ctx->frame;
     if (part < 0 || part >= RENDER_MAX_PARTS) return sem_fail(ctx, SEM_ERR_ARG, "frame part %d", part);
     if (F.ntri <= 0 || seg_lo >= seg_hi) return SEM_OK;
@@ -697,6 +696,7 @@ sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int se
 // autotuner chose for this frame size (the defaults when it has not chosen yet).
 sem_status render_frame_end(sem_ctx *ctx, const float *tris)
 {
+    if (!ctx->frame) return sem_fail(ctx, SEM_ERR_ARG, "frame end without a frame begun");
     RenderFrame &F = *ctx->frame;
     int w = 0;
     for (const auto &t : ctx->width_tune)
