@@ -79,8 +79,9 @@ def algorithmic_bytes_per_step(name, P):
         # per field: its active elements read + 36 B per triangle written + the offsets read
         "k_iso_emit_m": sum(4 * NP3 * s["active_elems"] + 36 * s["ntri"] + 8 * (s["niso"] * P.E + 1) for s in surf),
         # 36 B per triangle read (the 64-bit depth keys live in L2)
-        "k_raster_small": 36 * P.last_ntri,
-        "k_raster_range": 36 * P.last_ntri,
+        # (a frame drawn in parts: Q's part one tile per block, the other fields' parts as ranges)
+        "k_raster_small": 36 * (P.last_ntri if P.nseg == len(P.surfaces[0][1]) else P.surface_stats[0]["ntri"]),
+        "k_raster_range": 36 * sum(st["ntri"] for st in P.surface_stats[1:]),
         # key read 8 B + RGBA 4 B + depth 4 B per pixel, and the winner's colour per covered pixel
         "k_resolve": 16 * P.W * P.H + 4 * P.covered,
     }

@@ -354,16 +354,16 @@ __device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int 
     }
 }
 
-// One tile of 256 triangles per block, triangles [0, ntri) (ntri clamped to the device total
-// of the segments when they come from the device).
-__global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri,
+// One tile of 256 triangles per block, triangles [0, ntri) (ntri clamped to the device start of
+// segment seg_end -- the total for a whole frame -- when the segments come from the device).
+__global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ tris, int ntri, int seg_end,
                                                       const __grid_constant__ RenderParams P,
                                                       unsigned long long *__restrict__ keys,
                                                       int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
                                                       uint32_t *__restrict__ colors)
 {
     __shared__ RasterSmem sm;
-    if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[P.nseg]);
+    if (P.seg_dev) ntri = (int)min((int64_t)ntri, P.seg_dev[seg_end]);
     const int t0 = blockIdx.x * 256;
     // blocks past the (device-clamped) triangle count have no work; the whole block leaves
     // before its first barrier
@@ -648,7 +648,7 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
         SEM_TRY(frame_begin(ctx, F));
         if (F.ntri > 0) {
             SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(F.ntri + 255) / 256, 256, 0, ctx->stream>>>(
-                                                  tris, F.ntri, F.P, F.keys, F.large, F.nlarge, F.colors));
+                                                  tris, F.ntri, F.P.nseg, F.P, F.keys, F.large, F.nlarge, F.colors));
             SEM_CU(ctx, cudaGetLastError());
         }
         return frame_end(ctx, F, tris, w, rgba, depth);
@@ -681,6 +681,13 @@ sem_status render_frame_draw(sem_ctx *ctx, const float *tris, int seg_lo, int se
     RenderFrame &F = *ctx->frame;
     if (part < 0 || part >= RENDER_MAX_PARTS) return sem_fail(ctx, SEM_ERR_ARG, "frame part %d", part);
     if (F.ntri <= 0 || seg_lo >= seg_hi) return SEM_OK;
+    if (seg_lo == 0) {
+        // a part from the buffer's start: one tile per block up to the part's end (blocks past it
+        // leave at once), the faster form
+        SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(F.ntri + 255) / 256, 256, 0, ctx->stream>>>(
+                                              tris, F.ntri, seg_hi, F.P, F.keys, F.large, F.nlarge, F.colors));
+        return sem_cuda(ctx, cudaGetLastError(), "k_raster_small launch");
+    }
     static KernelSetup ks;
     int per_sm = 1;
     SEM_TRY(kernel_setup(ctx, ks, k_raster_range, 256, 0, &per_sm));

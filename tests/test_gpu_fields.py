@@ -277,7 +277,8 @@ def test_frame_call_equals_fields_call_and_render(gpu, sess, N, nel):
     S.sem_synchronize(sess.ctx)
     names = S.sem_trace_collect(sess.ctx)
     S.sem_trace_enable(sess.ctx, False)
-    assert names["k_raster_range"][1] == 3 and "k_raster_small" not in names, names  # Q, T, U groups
+    # Q's part from the buffer's start as one tile per block, the T and U parts as ranges
+    assert names["k_raster_small"][1] == 1 and names["k_raster_range"][1] == 2, names
     assert names["k_resolve"][1] == 1, names
     check("traced")
     S.sem_autotune_set(sess.ctx, False)
