@@ -228,34 +228,58 @@ __device__ __forceinline__ int64_t seg_start(const RenderParams &P, int k)
     return k == 0 ? 0 : (int64_t)P.seg_end[k - 1];
 }
 
-// segment of triangle t, searched upwards from segment sg
-__device__ __forceinline__ int seg_of(const RenderParams &P, int64_t t, int sg)
-{
-    while (sg < P.nseg - 1 && t >= seg_start(P, sg + 1)) ++sg;
-    return sg;
-}
 
 // Shared memory of one block's tile of up to 256 triangles.
 struct RasterSmem {
     __align__(16) float tri[256 * 9];
     SmallRecs rec;
     uint8_t lane_of[8][32];
-    int sg0;       // segment of the tile's first triangle
-    int any;       // some triangle of the tile lies in a drawn segment
-    int64_t next;  // start of the segment after sg0
+    int64_t seg[RENDER_MAX_SEG + 1];  // starts of the drawn segments seg_lo .. seg_hi (the last: an end)
+    int any;                          // some triangle of the tile lies in a drawn segment
 };
 
-// One tile: triangles t0 .. t0 + nt - 1 (segment search from sg_from).  One thread per triangle
-// for the setup (its 36 bytes staged through shared memory with coalesced loads); then each warp
-// spreads the pixel-centre tests of its 32 triangles evenly over its lanes, so a lane never
-// idles while a neighbour walks a bigger box; a pixel test finds its triangle from one warp OR
-// of the list starts in its round and a rank -> lane table.  Block-uniform exits only; the
-// caller synchronises the block before it reuses `sm`.
-__device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int t0, int nt_blk, int sg_from,
-                                            const RenderParams &P, unsigned long long *__restrict__ keys,
+// segment of triangle t (relative to seg_lo) from the starts in shared memory: the last k < ns
+// with seg[k] <= t
+__device__ __forceinline__ int seg_index(const int64_t *seg, int ns, int64_t t)
+{
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One tile: triangles t0 .. t0 + nt - 1, all in segments seg_lo .. seg_hi - 1.  The block first
+// reads the starts of those segments and the end of the last into shared memory (one load per
+// segment, in parallel; only these, as a frame drawn in parts has other parts' starts written by
+// other streams); with a draw mask, a tile whose triangles all lie in segments that are not
+// drawn is done before its triangles are read.
+// Then one thread per triangle for the setup (its 36 bytes staged through shared memory with
+// coalesced loads, its segment by binary search); then each warp spreads the pixel-centre
+// tests of its 32 triangles evenly over its lanes, so a lane never idles while a neighbour walks
+// a bigger box; a pixel test finds its triangle from one warp OR of the list starts in its round
+// and a rank -> lane table.  Block-uniform exits only; the caller synchronises the block before
+// it reuses `sm`.
+__device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int t0, int nt_blk, int seg_lo,
+                                            int seg_hi, const RenderParams &P, unsigned long long *__restrict__ keys,
                                             int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
                                             uint32_t *__restrict__ colors, RasterSmem &sm)
 {
+    const int ns = seg_hi - seg_lo;
+    if ((int)threadIdx.x <= ns) sm.seg[threadIdx.x] = seg_start(P, seg_lo + threadIdx.x);
+    if (P.seg_mask != ~0ull) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int a = seg_lo + seg_index(sm.seg, ns, t0), b = seg_lo + seg_index(sm.seg, ns, t0 + nt_blk - 1);
+            // segments a .. b (b - a < 64)
+            const unsigned long long span = (b - a == 63) ? ~0ull : (((2ull << (b - a)) - 1ull) << a);
+            sm.any = (P.seg_mask & span) != 0ull;
+        }
+        __syncthreads();
+        if (!sm.any) return;
+    }
     float *s_tri = sm.tri;
     const float *src = tris + (int64_t)t0 * 9;
     if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
@@ -267,28 +291,12 @@ __device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int 
     } else {
         for (int q = threadIdx.x; q < nt_blk * 9; q += 256) s_tri[q] = __ldcs(src + q);
     }
-    if (threadIdx.x == 0) {
-        const int sg = seg_of(P, t0, sg_from);
-        sm.sg0 = sg;
-        sm.next = sg < P.nseg - 1 ? seg_start(P, sg + 1) : INT64_MAX;
-    }
     __syncthreads();
-    if (P.seg_mask != ~0ull) {
-        // a tile whose triangles all lie in segments that are not drawn is done at once
-        if (threadIdx.x == 0) {
-            int any = 0;
-            for (int sg = sm.sg0; sg < P.nseg && seg_start(P, sg) < t0 + nt_blk; ++sg)
-                any |= (int)((P.seg_mask >> sg) & 1ull);
-            sm.any = any;
-        }
-        __syncthreads();
-        if (!sm.any) return;
-    }
     const int lane = threadIdx.x & 31;
     const int t = t0 + threadIdx.x;
     bool is_large = false;
     int npx = 0;
-    const int sg = (int)threadIdx.x < nt_blk ? (t < sm.next ? sm.sg0 : seg_of(P, t, sm.sg0)) : 0;
+    const int sg = (int)threadIdx.x < nt_blk ? seg_lo + seg_index(sm.seg, ns, t) : 0;
     if ((int)threadIdx.x < nt_blk && ((P.seg_mask >> sg) & 1ull)) {
         Setup S;
         if (setup_tri(P, s_tri + threadIdx.x * 9, S)) {
@@ -368,7 +376,7 @@ __global__ void __launch_bounds__(256) k_raster_small(const float *__restrict__ 
     // blocks past the (device-clamped) triangle count have no work; the whole block leaves
     // before its first barrier
     if (t0 >= ntri) return;
-    raster_tile(tris, t0, min(256, ntri - t0), 0, P, keys, large, nlarge, colors, sm);
+    raster_tile(tris, t0, min(256, ntri - t0), 0, seg_end, P, keys, large, nlarge, colors, sm);
 }
 
 // The triangles of segments [seg_lo, seg_hi), their range read from the device segment starts
@@ -396,7 +404,7 @@ __global__ void __launch_bounds__(256, 6) k_raster_range(const float *__restrict
         // at the end of this iteration)
         if (threadIdx.x == 0) s_k[cur ^ 1] = atomicAdd(next_tile, 1);
         const int64_t a = max(tile * 256, lo), b = min(tile * 256 + 256, hi);
-        raster_tile(tris, (int)a, (int)(b - a), seg_lo, P, keys, large, nlarge, colors, sm);
+        raster_tile(tris, (int)a, (int)(b - a), seg_lo, seg_hi, P, keys, large, nlarge, colors, sm);
         __syncthreads();  // the tile's shared memory is free for the next
     }
 }
