@@ -265,11 +265,11 @@ __device__ __forceinline__ int seg_index(const int64_t *seg, int ns, int64_t t)
 __device__ __forceinline__ void raster_tile(const float *__restrict__ tris, int t0, int nt_blk, int seg_lo,
                                             int seg_hi, const RenderParams &P, unsigned long long *__restrict__ keys,
                                             int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
-                                            uint32_t *__restrict__ colors, RasterSmem &sm)
+                                            uint32_t *__restrict__ colors, RasterSmem &sm, bool check_mask = true)
 {
     const int ns = seg_hi - seg_lo;
     if ((int)threadIdx.x <= ns) sm.seg[threadIdx.x] = seg_start(P, seg_lo + threadIdx.x);
-    if (P.seg_mask != ~0ull) {
+    if (check_mask && P.seg_mask != ~0ull) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int a = seg_lo + seg_index(sm.seg, ns, t0), b = seg_lo + seg_index(sm.seg, ns, t0 + nt_blk - 1);
@@ -405,6 +405,87 @@ __global__ void __launch_bounds__(256, 6) k_raster_range(const float *__restrict
         if (threadIdx.x == 0) s_k[cur ^ 1] = atomicAdd(next_tile, 1);
         const int64_t a = max(tile * 256, lo), b = min(tile * 256 + 256, hi);
         raster_tile(tris, (int)a, (int)(b - a), seg_lo, seg_hi, P, keys, large, nlarge, colors, sm);
+        __syncthreads();  // the tile's shared memory is free for the next
+    }
+}
+
+// The drawn segments of a frame with a draw mask: a persistent grid whose blocks take the tiles
+// of the drawn segments only, from a counter (zeroed when the frame begins).  Each block lists
+// the drawn segments' 256-triangle tiles (the buffer's tile grid, clipped to the segment) with a
+// prefix sum over at most 64 segments in shared memory, and maps each tile it takes to its
+// segment by binary search; a tile shared by two drawn segments is two work items.  No block
+// reads the triangles of a segment that is not drawn.
+struct MaskedSmem {
+    int64_t start[RENDER_MAX_SEG + 1];  // the frame's segment starts (clamped to the buffer)
+    int64_t first[RENDER_MAX_SEG + 1];  // work items before the k-th drawn segment
+    int seg[RENDER_MAX_SEG];            // the drawn segments, in order
+    int ndrawn;
+    int k[2];                           // the current work item's counter value and the next one's
+};
+
+__global__ void __launch_bounds__(256, 6) k_raster_masked(const float *__restrict__ tris, int ntri,
+                                                          const __grid_constant__ RenderParams P,
+                                                          unsigned long long *__restrict__ keys,
+                                                          int32_t *__restrict__ large, int32_t *__restrict__ nlarge,
+                                                          uint32_t *__restrict__ colors, int *__restrict__ next_item)
+{
+    __shared__ RasterSmem sm;
+    __shared__ MaskedSmem ms;
+    if ((int)threadIdx.x <= P.nseg) ms.start[threadIdx.x] = min(seg_start(P, threadIdx.x), (int64_t)ntri);
+    if (threadIdx.x == 0) ms.k[0] = atomicAdd(next_item, 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // warp 0: the drawn segments with their tile counts, a prefix sum over them
+        const int lane = threadIdx.x;
+        int64_t before = 0;
+        int nd = 0;
+        for (int s0 = 0; s0 < P.nseg; s0 += 32) {
+            const int sg = s0 + lane;
+            int64_t tiles = 0;
+            const bool drawn = sg < P.nseg && ((P.seg_mask >> sg) & 1ull);
+            if (drawn) {
+                const int64_t a = ms.start[sg], b = ms.start[sg + 1];
+                tiles = b > a ? (b + 255) / 256 - a / 256 : 0;
+            }
+            const bool live = drawn && tiles > 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, live);
+            int64_t incl = tiles;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (live) {
+                const int r = nd + __popc(bal & ((1u << lane) - 1u));
+                ms.seg[r] = sg;
+                ms.first[r] = before + incl - tiles;
+            }
+            nd += __popc(bal);
+            before += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) {
+            ms.ndrawn = nd;
+            ms.first[nd] = before;
+        }
+    }
+    __syncthreads();
+    const int nd = ms.ndrawn;
+    for (int cur = 0;; cur ^= 1) {
+        const int64_t item = ms.k[cur];
+        if (item >= ms.first[nd]) break;  // block-uniform
+        if (threadIdx.x == 0) ms.k[cur ^ 1] = atomicAdd(next_item, 1);
+        // the drawn segment holding work item `item`: the last r with first[r] <= item
+        int lo = 0, hi = nd - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ms.first[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int sg = ms.seg[lo];
+        const int64_t a0 = ms.start[sg], b0 = ms.start[sg + 1];
+        const int64_t tile = a0 / 256 + (item - ms.first[lo]);
+        const int64_t a = max(tile * 256, a0), b = min(tile * 256 + 256, b0);
+        raster_tile(tris, (int)a, (int)(b - a), sg, sg + 1, P, keys, large, nlarge, colors, sm, false);
         __syncthreads();  // the tile's shared memory is free for the next
     }
 }
@@ -652,11 +733,25 @@ sem_status render_run(sem_ctx *ctx, const float *tris, int64_t ntri64, const int
     SEM_TRY(render_setup(ctx, F, ntri64, seg_ntri, nseg, seg_rgb, cam, W, H, seg_start_dev, seg_mask));
     // one frame; the frame leaves the key buffer all "empty" again, so every candidate width of
     // the autotuner draws the same image
+    const bool masked = F.P.seg_mask != ~0ull;
+    int masked_per_sm = 1;
+    if (masked) {
+        static KernelSetup ks;
+        SEM_TRY(kernel_setup(ctx, ks, k_raster_masked, 256, 0, &masked_per_sm));
+    }
     auto frame = [&](int w) -> sem_status {
         SEM_TRY(frame_begin(ctx, F));
-        if (F.ntri > 0) {
+        if (F.ntri > 0 && !masked) {
             SEM_TRACED(ctx, "k_raster_small", k_raster_small<<<(F.ntri + 255) / 256, 256, 0, ctx->stream>>>(
                                                   tris, F.ntri, F.P.nseg, F.P, F.keys, F.large, F.nlarge, F.colors));
+            SEM_CU(ctx, cudaGetLastError());
+        } else if (F.ntri > 0) {
+            // a draw mask: only the drawn segments' tiles, from the frame's first tile counter
+            const int64_t grid = std::min<int64_t>(((int64_t)F.ntri + 255) / 256 + F.P.nseg,
+                                                   (int64_t)masked_per_sm * ctx->sm_count);
+            SEM_TRACED(ctx, "k_raster_masked", k_raster_masked<<<(unsigned)grid, 256, 0, ctx->stream>>>(
+                                                   tris, F.ntri, F.P, F.keys, F.large, F.nlarge, F.colors,
+                                                   F.next_tile));
             SEM_CU(ctx, cudaGetLastError());
         }
         return frame_end(ctx, F, tris, w, rgba, depth);
