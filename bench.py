@@ -669,6 +669,13 @@ def measure_batched(S, ctx, snapshots=64, steps=3):
     ms_graph = timed(g.replay, steps)
     S.sem_synchronize(ctx)  # capacity or timeout flags raised inside the graph
     ms_plain = timed(plain, 1)
+    # per-kernel device time of one snapshot, from the library's trace of its eager calls
+    S.sem_trace_enable(ctx, True)
+    S.sem_trace_collect(ctx)
+    snapshot(0)
+    S.sem_synchronize(ctx)
+    per_snapshot = {k: {"ms": round(v[0], 4), "launches": v[1]} for k, v in S.sem_trace_collect(ctx).items()}
+    S.sem_trace_enable(ctx, False)
     covered = float((frames[:, :, :, 3::4] > 0).float().mean())
     out = {"workload": f"{snapshots} snapshots x 16 partitions (E_p ~ U{{4096..40960}}, N_p in {{5,7,9}}, "
                        f"{E_total} elements, {nodes} nodes per snapshot) of the Taylor-Green field with 1e-3 noise; "
@@ -685,6 +692,7 @@ def measure_batched(S, ctx, snapshots=64, steps=3):
            "graph_speedup_vs_plain": round(ms_plain / ms_graph, 3),
            "max_triangles_per_snapshot": need, "frame_coverage": round(covered, 4),
            "setup_s": {"generate": round(gen_s, 1), "capture_and_instantiate": round(capture_s, 2)},
+           "kernels_per_snapshot": per_snapshot,
            "autotune_widths": S.sem_autotune_width_choices(ctx)}
     del g, frames, tris
     for p in parts:
