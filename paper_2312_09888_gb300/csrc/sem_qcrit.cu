@@ -233,7 +233,10 @@ struct QCfg {
 #ifndef SEM_Q_MINB
 #define SEM_Q_MINB 2
 #endif
-    static constexpr int MINB = (NP == 8) ? SEM_Q_MINB : 1;
+    // resident blocks the register allocation is sized for: N = 5 (4 blocks of 252 threads at 64
+    // registers, no spills) and N = 9 (3 blocks of 224 threads) run more warps than at the
+    // compiler's own choice (2 blocks each)
+    static constexpr int MINB = (NP == 8) ? SEM_Q_MINB : (NP == 6 ? 4 : (NP == 10 ? 3 : 1));
 };
 
 // The partitions one launch covers (one partition for sem_qcriterion / sem_derivatives, up to
