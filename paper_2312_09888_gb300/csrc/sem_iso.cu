@@ -5,16 +5,18 @@
 // case = sum_v [f_v >= iso] 2^v; triangles come from the library's generated case table;
 // a cut edge (lo, hi) gets t = (iso - f_lo)/(f_hi - f_lo), p = p_lo + t (p_hi - p_lo).
 //
-// Three passes, one warp per element in each:
-//   k_iso_count  reads the element once (16-byte loads), culls it with warp votes (active
-//                iff some node is >= iso and some is < iso), classifies its cells and writes
-//                the element's triangle count (and optionally every cell's case);
-//   scan         exclusive scan of the counts -> each element's first triangle;
-//   k_iso_emit   re-reads only active elements (the field is usually still in L2),
-//                classifies again, scans the per-cell counts across the warp and writes the
-//                triangles in (element, cell, table) order.
-// Node positions are lerps of the element box with exact end points, so nodes shared by two
-// elements get bit-identical coordinates.
+// Three passes over (element, isovalue) units, all isovalues of a field in one read of it:
+//   counting     k_iso_count_p (persistent, N <= 9) / k_iso_count_m: one warp per element,
+//                node masks by warp ballots, cell classification from node rows, one triangle
+//                count per unit (and optionally every cell's case); for Q on N = 7 box meshes
+//                the Q kernel itself counts (k_sem_q8<true>, sem_qcrit.cu);
+//   scan         k_scan_lookback (sem_scan.cu): exclusive scan of the counts -> each unit's
+//                first triangle, and the list of units that hold triangles;
+//   emit         k_iso_emit_m: persistent warps take listed units, re-read the element, list its
+//                cut cells and write its triangles in (isovalue, element, cell, table) order.
+// sem_isosurface_noalloc keeps the one-isovalue kernels k_iso_count / k_iso_emit (one warp per
+// element, fixed scratch).  Node positions are lerps of the element box with exact end points,
+// so nodes shared by two elements get bit-identical coordinates.
 #include <cuda_runtime.h>
 
 #include <algorithm>

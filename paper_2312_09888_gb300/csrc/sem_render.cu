@@ -10,16 +10,21 @@
 // buffer (8 B/pixel: 16.6 MB at 1920x1080) stays resident in the 129 MB L2.
 //
 // Passes (no host synchronisation):
-//   k_raster_small  one thread per triangle (staged through shared memory): project,
-//                   normalise winding, take the exact range of pixel centres its bounding box
-//                   contains (sub-pixel triangles that contain none are done); for boxes of at
-//                   most SMALL_PX centres, the warp spreads all its triangles' centre tests
-//                   evenly over its lanes and atomicMins the keys.  Larger triangles are
-//                   appended to a list.
-//   k_raster_large  one warp per listed triangle, its lanes stepping 32 candidates at a time
-//                   on the triangle's planes.
-//   k_resolve       grid-stride over groups of four pixels: read the key, reset it for the next
-//                   frame, look up the winner's colour (computed by the raster pass).
+//   k_raster_small   one thread per triangle (staged through shared memory): project,
+//                    normalise winding, take the exact range of pixel centres its bounding box
+//                    contains (sub-pixel triangles that contain none are done); for boxes of at
+//                    most SMALL_PX centres, the warp spreads all its triangles' centre tests
+//                    evenly over its lanes and atomicMins the keys.  Larger triangles are
+//                    appended to a list.  One 256-triangle tile per block.
+//   k_raster_masked  the same per tile, for a frame with a draw mask: a persistent grid over the
+//                    drawn segments' tiles only.
+//   k_raster_range   the same per tile, for a frame drawn in parts (sem_frame_async): a
+//                    persistent grid over the tiles of one part's device range of segments,
+//                    launched on the stream that produced that part's triangles.
+//   k_raster_large   one warp per listed triangle, its lanes stepping 32 candidates at a time
+//                    on the triangle's planes.
+//   k_resolve        grid-stride over groups of four pixels: read the key, reset it for the next
+//                    frame, look up the winner's colour (computed by the raster pass).
 //
 // Why not per-tile shared-memory z-buffers: the isosurface frames consist of millions of
 // triangles a few pixels or less in size, and binning them into tile lists costs two extra
