@@ -107,16 +107,28 @@ __device__ __forceinline__ void put_t(bf16 *__restrict__ tstage, int cl, float x
     tstage[cl * 32 + (threadIdx.x & 31)] = __float2bfloat16_rn(x);
 }
 
+// Modes whose row-major BF16 output (and input) goes through the warp's staged row segments:
+// the lanes hold one row each, so direct 16-byte accesses would touch 32 rows per instruction;
+// staged, each 64-byte row segment of a 32-column round is read or written by 4 lanes at once.
+__device__ __forceinline__ bool staged_rows(int mode)
+{
+    return mode == EPI_BIAS_GELU || mode == EPI_BIAS || mode == EPI_PLAIN || mode == EPI_LOSS || mode == EPI_DGELU;
+}
+
 // The fused tail of one row's 8 consecutive output columns n .. n+7 (cl: n's column in the tile).
+// For the staged modes, sr / sr2 are the lane's 8 columns in the round's staged rows: the input
+// (EPI_LOSS's target, EPI_DGELU's H) is read from sr and the output (EPI_BIAS_GELU: H to sr,
+// gelu H to sr2) written there, for the warp to store.
 __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, int cl, float (&v)[8],
-                                          float &loss_acc, float *__restrict__ c32, bf16 *__restrict__ tstage)
+                                          float &loss_acc, float *__restrict__ c32, bf16 *__restrict__ tstage,
+                                          bf16 *__restrict__ sr, bf16 *__restrict__ sr2)
 {
     if (row >= P.m_valid) {
         if (P.mode == EPI_LOSS) {
             // padding rows of a partial batch carry no gradient (their stale values would
             // otherwise reach the weight gradients)
             const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            store8_bf16(P.out + row * P.ld_out + n, z);
+            store8_bf16(sr, z);
         }
         // the transposed copy's padding rows are zero in every mode (the staging tile is written
         // back whole)
@@ -140,8 +152,8 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
             // gelu of the BF16-rounded pre-activation, the value the backward pass sees
             a[c] = gelu_f(__bfloat162float(__float2bfloat16_rn(v[c])));
         }
-        store8_bf16(P.out + row * P.ld_out + n, v);
-        store8_bf16(P.aux + row * P.ld_out + n, a);
+        store8_bf16(sr, v);
+        store8_bf16(sr2, a);
 #pragma unroll
         for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, a[c]);
         return;
@@ -151,31 +163,31 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
         if (P.mode == EPI_BIAS)
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] += P.bias[n + c];
-        store8_bf16(P.out + row * P.ld_out + n, v);
+        store8_bf16(sr, v);
 #pragma unroll
         for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
     }
     case EPI_LOSS: {
         float x[8];
-        load8_bf16(P.in + row * P.ld_in + n, x);
+        load8_bf16(sr, x);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const float r = v[c] + P.bias[n + c] - x[c];
             loss_acc = fmaf(r, r, loss_acc);
             v[c] = P.scale * r;
         }
-        store8_bf16(P.out + row * P.ld_out + n, v);
+        store8_bf16(sr, v);
 #pragma unroll
         for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
     }
     case EPI_DGELU: {
         float h[8];
-        load8_bf16(P.in + row * P.ld_in + n, h);
+        load8_bf16(sr, h);
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] *= gelu_grad_f(h[c]);
-        store8_bf16(P.out + row * P.ld_out + n, v);
+        store8_bf16(sr, v);
 #pragma unroll
         for (int c = 0; c < 8; ++c) put_t(tstage, cl + c, v[c]);
         return;
@@ -285,20 +297,59 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             float loss_acc = 0.f;
             float *c32 = P.c32 + (int64_t)blockIdx.z * P.split_stride;  // this K slice's partial array
             // the pipeline's shared memory is idle once the accumulator is complete: warp q's
-            // transposed staging tile (BN columns x 32 rows of BF16)
+            // transposed staging tile (BN columns x 32 rows of BF16), then its staged row segments
+            // of one round (32 rows x 32 columns, rows RS apart; a second set for EPI_BIAS_GELU's
+            // gelu H)
+            constexpr int RS = 40;
             bf16 *tstage = reinterpret_cast<bf16 *>(smem) + q * (BN * 32);
+            bf16 *rs = reinterpret_cast<bf16 *>(smem) + 4 * (BN * 32) + q * (2 * 32 * RS), *rs2 = rs + 32 * RS;
+            const bool staged = staged_rows(P.mode), stage_in = P.mode == EPI_LOSS || P.mode == EPI_DGELU;
+            const int64_t row0 = (int64_t)blockIdx.x * BM + q * 32;
+            const int lr = lane >> 2, part = lane & 3;  // the warp's accesses: rows lr + 8 i, 16-byte part
             // 32 columns per TMEM round: four loads in flight, one wait
             for (int c0 = cbeg; c0 < cend; c0 += 32) {
                 uint32_t r[4][8];
 #pragma unroll
                 for (int h = 0; h < 4; ++h) tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0 + 8 * h), r[h]);
+                const int n0 = blockIdx.y * BN + c0;
+                if (stage_in) {
+                    // the round's input rows, 4 lanes per 64-byte row segment (padding rows: zero)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = lr + 8 * i;
+                        const int64_t g = row0 + rr;
+                        const uint4 x = g < P.m_valid ? *reinterpret_cast<const uint4 *>(P.in + g * P.ld_in + n0 + part * 8)
+                                                      : make_uint4(0u, 0u, 0u, 0u);
+                        *reinterpret_cast<uint4 *>(rs + rr * RS + part * 8) = x;
+                    }
+                    __syncwarp();
+                }
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
                     float v[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[h][c]);
-                    epilogue8(P, row, blockIdx.y * BN + c0 + 8 * h, c0 + 8 * h, v, loss_acc, c32, tstage);
+                    epilogue8(P, row, n0 + 8 * h, c0 + 8 * h, v, loss_acc, c32, tstage, rs + lane * RS + 8 * h,
+                              rs2 + lane * RS + 8 * h);
+                }
+                if (staged) {
+                    // the round's output rows, 4 lanes per 64-byte row segment; padding rows are
+                    // not stored, except EPI_LOSS's zero gradient
+                    __syncwarp();
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int rr = lr + 8 * i;
+                        const int64_t g = row0 + rr;
+                        if (g < P.m_valid || P.mode == EPI_LOSS) {
+                            *reinterpret_cast<uint4 *>(P.out + g * P.ld_out + n0 + part * 8) =
+                                *reinterpret_cast<const uint4 *>(rs + rr * RS + part * 8);
+                            if (P.mode == EPI_BIAS_GELU)
+                                *reinterpret_cast<uint4 *>(P.aux + g * P.ld_out + n0 + part * 8) =
+                                    *reinterpret_cast<const uint4 *>(rs2 + rr * RS + part * 8);
+                        }
+                    }
+                    __syncwarp();  // the staged rows are free for the next round
                 }
             }
             const bool has_t = P.out_t && (P.mode == EPI_BIAS_GELU || P.mode == EPI_BIAS || P.mode == EPI_LOSS ||
@@ -307,8 +358,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 // out_t[n][row0 .. row0 + 31] for the tile's columns n: lane l takes column c + l / 4,
                 // rows 8 (l % 4) .. + 7 (row0 and ld_t are multiples of 32, so 16-byte aligned)
                 __syncwarp();
-                const int64_t row0 = (int64_t)blockIdx.x * BM + q * 32;
-                const int cq = lane >> 2, part = lane & 3;
+                const int cq = lane >> 2;
                 for (int c = cbeg; c < cend; c += 8) {
                     const int cl = c + cq;
                     const uint4 val = *reinterpret_cast<const uint4 *>(tstage + cl * 32 + part * 8);
