@@ -520,6 +520,10 @@ def measure_learned(S, ctx, bf16_peak, peak_src, steps=100, warmup=20):
                              "achieved": gemm[best]["tflops"], "peak": bf16_peak, "peak_source": peak_src,
                              "unit": "TFLOP/s", "frac": round(gemm[best]["tflops"] / bf16_peak, 4)},
                 "gemms": gemm,
+                # the autotuner's choice per (M, N, K, epilogue): tile width, stages, K split, persistent
+                "gemm_choices": [{"shape": [c[0], c[1], c[2]], "epilogue": c[3], "bn": c[4], "stages": c[5],
+                                  "split": c[6], "persistent": c[7], "ms": round(c[8], 5)}
+                                 for c in S.sem_autotune_choices(ctx)],
                 "encode_elements_per_s": round(E / (enc_ms * 1e-3), 1),
                 "decode_elements_per_s": round(E / (dec_ms * 1e-3), 1),
                 "latent_bytes_per_element": 96, "in_transit": in_transit}

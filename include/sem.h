@@ -450,13 +450,16 @@ SEM_API sem_status sem_ae_encode(sem_ae *ae, const float *u, const float *v, con
 SEM_API sem_status sem_ae_decode(sem_ae *ae, const uint16_t *latent, int64_t E, float *u, float *v, float *w);
 
 /* Autotuner of the tensor-core GEMM (on by default).  The first product of a given (M, N, K,
- * epilogue) on a context runs every candidate tile shape on the call's own data -- tile width
- * BN in {64, 128, 256}, 3 or 4 pipeline stages, and for FP32 weight gradients a K split in
- * {1, 2, 4, 8, 16, 32} (at least 4 K blocks per split) with an ordered reduction of the partial sums -- and keeps the fastest (CUDA
- * events); later products of that shape reuse it.  Under stream capture, or when off, the
- * default (BN 128 where N allows, 4 stages, no split) runs.  sem_autotune_set(ctx, 0) turns
- * tuning off and forgets the choices; sem_autotune_entry reads choice k (SEM_ERR_ARG past the
- * last one), with the winner's time in milliseconds. */
+ * epilogue) on a context runs every candidate on the call's own data -- tile width BN in
+ * {64, 128, 256}, 3 or 4 pipeline stages; for BN <= 128 also a persistent form (one CTA per SM
+ * walking the output tiles, two TMEM accumulators so that a tile's epilogue overlaps the next
+ * tile's MMAs; the same products in the same order); and for FP32 weight gradients a K split in
+ * {1, 2, 4, 8, 16, 32} (at least 4 K blocks per split) with an ordered reduction of the partial
+ * sums -- and keeps the fastest (CUDA events); later products of that shape reuse it.  Under
+ * stream capture, or when off, the default (BN 128 where N allows, 4 stages, no split, one tile
+ * per CTA) runs.  sem_autotune_set(ctx, 0) turns tuning off and forgets the choices;
+ * sem_autotune_entry reads choice k (SEM_ERR_ARG past the last one), with the winner's time in
+ * milliseconds; `persistent` (may be NULL) receives 1 for the persistent form. */
 SEM_API sem_status sem_autotune_set(sem_ctx *ctx, int on);
 
 /* The same switch tunes the launch of the isosurface emit pass (sem_isosurface,
@@ -485,7 +488,7 @@ SEM_API sem_status sem_autotune_emit_entry(sem_ctx *ctx, int k, int *N, int64_t 
 SEM_API sem_status sem_autotune_width_entry(sem_ctx *ctx, int k, int *kind, int *N, int64_t *size, int *width,
                                             float *ms);
 SEM_API sem_status sem_autotune_entry(sem_ctx *ctx, int k, int64_t *M, int *N, int *K, int *mode, int *bn,
-                                      int *stages, int *split, float *ms);
+                                      int *stages, int *split, int *persistent, float *ms);
 
 /* The library's tensor-core GEMM: C[M][N] = A[M][K] B[N][K]^T, A and B row-major BF16 bit
  * patterns (device, 16-byte aligned), C FP32 (device).  M % 128 == 0, N % 64 == 0,

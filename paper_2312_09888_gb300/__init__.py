@@ -107,7 +107,7 @@ def _declare(L):
     L.sem_ae_decode.argtypes = [vp, vp, i64, vp, vp, vp]
     L.sem_gemm_bf16.argtypes = [vp, vp, vp, i64, i32, i32, vp]
     L.sem_autotune_set.argtypes = [vp, i32]
-    L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 6 + [C.POINTER(f32)]
+    L.sem_autotune_entry.argtypes = [vp, i32, C.POINTER(i64)] + [C.POINTER(i32)] * 7 + [C.POINTER(f32)]
     L.sem_autotune_emit_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                           C.POINTER(f32)]
     L.sem_autotune_width_entry.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32),
@@ -669,12 +669,12 @@ def sem_autotune_width_choices(ctx) -> list:
 
 
 def sem_autotune_choices(ctx) -> list:
-    """[(M, N, K, epilogue, BN, stages, split, ms)] of the tuned GEMM shapes."""
+    """[(M, N, K, epilogue, BN, stages, split, persistent, ms)] of the tuned GEMM shapes."""
     out, k = [], 0
     L = get_lib()
     while True:
         M = C.c_int64(0)
-        v = [C.c_int32(0) for _ in range(6)]
+        v = [C.c_int32(0) for _ in range(7)]
         ms = C.c_float(0)
         st = L.sem_autotune_entry(ctx, k, C.byref(M), *[C.byref(x) for x in v], C.byref(ms))
         if st != SEM_OK:

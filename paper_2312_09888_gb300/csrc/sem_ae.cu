@@ -213,6 +213,91 @@ __device__ __forceinline__ void epilogue8(const EpiArgs &P, int64_t row, int n, 
     }
 }
 
+// The epilogue of one accumulator tile by epilogue warp q (TMEM lane quarter q: a warp may only
+// read its own): TMEM 32 columns per round (four loads in flight, one wait), the fused tail of
+// every 8 columns, the row-major BF16 traffic through the warp's staged row segments `rs` (two
+// sets of 32 rows x EPI_RS, the second for EPI_BIAS_GELU's gelu H) and the transposed copy through
+// its staging tile `tstage` (BN columns x 32 rows).  mt, nt: the tile's M and N indices; kz: its
+// K slice (EPI_F32 with a split K range).
+#define EPI_RS 40
+template <int BN>
+__device__ __forceinline__ void epilogue_tile(const EpiArgs &P, uint32_t tacc, int64_t mt, int nt, int kz, int q,
+                                              int lane, bf16 *__restrict__ tstage, bf16 *__restrict__ rs)
+{
+    const int cbeg = 0, cend = BN;
+    const int64_t row = mt * BM + q * 32 + lane;
+    float loss_acc = 0.f;
+    float *c32 = P.c32 + (int64_t)kz * P.split_stride;  // this K slice's partial array
+    bf16 *rs2 = rs + 32 * EPI_RS;
+    const bool staged = staged_rows(P.mode), stage_in = P.mode == EPI_LOSS || P.mode == EPI_DGELU;
+    const int64_t row0 = mt * BM + q * 32;
+    const int lr = lane >> 2, part = lane & 3;  // the warp's accesses: rows lr + 8 i, 16-byte part
+    // 32 columns per TMEM round: four loads in flight, one wait
+    for (int c0 = cbeg; c0 < cend; c0 += 32) {
+        uint32_t r[4][8];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) tc::tmem_ld8(tacc + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0 + 8 * h), r[h]);
+        const int n0 = nt * BN + c0;
+        if (stage_in) {
+            // the round's input rows, 4 lanes per 64-byte row segment (padding rows: zero)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = lr + 8 * i;
+                const int64_t g = row0 + rr;
+                const uint4 x = g < P.m_valid ? *reinterpret_cast<const uint4 *>(P.in + g * P.ld_in + n0 + part * 8)
+                                              : make_uint4(0u, 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(rs + rr * EPI_RS + part * 8) = x;
+            }
+            __syncwarp();
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[h][c]);
+            epilogue8(P, row, n0 + 8 * h, c0 + 8 * h, v, loss_acc, c32, tstage, rs + lane * EPI_RS + 8 * h,
+                      rs2 + lane * EPI_RS + 8 * h);
+        }
+        if (staged) {
+            // the round's output rows, 4 lanes per 64-byte row segment; padding rows are
+            // not stored, except EPI_LOSS's zero gradient
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = lr + 8 * i;
+                const int64_t g = row0 + rr;
+                if (g < P.m_valid || P.mode == EPI_LOSS) {
+                    *reinterpret_cast<uint4 *>(P.out + g * P.ld_out + n0 + part * 8) =
+                        *reinterpret_cast<const uint4 *>(rs + rr * EPI_RS + part * 8);
+                    if (P.mode == EPI_BIAS_GELU)
+                        *reinterpret_cast<uint4 *>(P.aux + g * P.ld_out + n0 + part * 8) =
+                            *reinterpret_cast<const uint4 *>(rs2 + rr * EPI_RS + part * 8);
+                }
+            }
+            __syncwarp();  // the staged rows are free for the next round
+        }
+    }
+    const bool has_t = P.out_t && (P.mode == EPI_BIAS_GELU || P.mode == EPI_BIAS || P.mode == EPI_LOSS ||
+                                   P.mode == EPI_DGELU || P.mode == EPI_PLAIN);
+    if (has_t) {
+        // out_t[n][row0 .. row0 + 31] for the tile's columns n: lane l takes column c + l / 4,
+        // rows 8 (l % 4) .. + 7 (row0 and ld_t are multiples of 32, so 16-byte aligned)
+        __syncwarp();
+        const int cq = lane >> 2;
+        for (int c = cbeg; c < cend; c += 8) {
+            const int cl = c + cq;
+            const uint4 val = *reinterpret_cast<const uint4 *>(tstage + cl * 32 + part * 8);
+            *reinterpret_cast<uint4 *>(P.out_t + (int64_t)(nt * BN + cl) * P.ld_t + row0 + part * 8) = val;
+        }
+    }
+    if (P.mode == EPI_LOSS) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, d);
+        if (lane == 0) atomicAdd(P.loss, loss_acc);
+    }
+}
+
 // D[M][N] = A[M][K] B[N][K]^T for one BM x BN output tile per CTA.  Warp 0: TMA producer;
 // warp 1: TMEM owner and MMA issuer; warps 2..5: epilogue (warp w reads TMEM lanes
 // 32 (w % 4) .. + 31).  NST-deep ring of (A, B) K-slices of BK = 64 BF16 (one 128-byte
@@ -290,86 +375,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (!ok) s_abort = 1;
         tc::fence_after_sync();
         if (ok && !*(volatile int *)&s_abort) {
-            // warps 2..5: one per TMEM lane quarter q = warp % 4 (a warp may only read its own)
+            // warps 2..5: one per TMEM lane quarter q = warp % 4.  The pipeline's shared memory is
+            // idle once the accumulator is complete: warp q's staging tile and row segments live
+            // there.
             const int q = warp & 3;
-            const int cbeg = 0, cend = BN;
-            const int64_t row = (int64_t)blockIdx.x * BM + q * 32 + lane;
-            float loss_acc = 0.f;
-            float *c32 = P.c32 + (int64_t)blockIdx.z * P.split_stride;  // this K slice's partial array
-            // the pipeline's shared memory is idle once the accumulator is complete: warp q's
-            // transposed staging tile (BN columns x 32 rows of BF16), then its staged row segments
-            // of one round (32 rows x 32 columns, rows RS apart; a second set for EPI_BIAS_GELU's
-            // gelu H)
-            constexpr int RS = 40;
             bf16 *tstage = reinterpret_cast<bf16 *>(smem) + q * (BN * 32);
-            bf16 *rs = reinterpret_cast<bf16 *>(smem) + 4 * (BN * 32) + q * (2 * 32 * RS), *rs2 = rs + 32 * RS;
-            const bool staged = staged_rows(P.mode), stage_in = P.mode == EPI_LOSS || P.mode == EPI_DGELU;
-            const int64_t row0 = (int64_t)blockIdx.x * BM + q * 32;
-            const int lr = lane >> 2, part = lane & 3;  // the warp's accesses: rows lr + 8 i, 16-byte part
-            // 32 columns per TMEM round: four loads in flight, one wait
-            for (int c0 = cbeg; c0 < cend; c0 += 32) {
-                uint32_t r[4][8];
-#pragma unroll
-                for (int h = 0; h < 4; ++h) tc::tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0 + 8 * h), r[h]);
-                const int n0 = blockIdx.y * BN + c0;
-                if (stage_in) {
-                    // the round's input rows, 4 lanes per 64-byte row segment (padding rows: zero)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int rr = lr + 8 * i;
-                        const int64_t g = row0 + rr;
-                        const uint4 x = g < P.m_valid ? *reinterpret_cast<const uint4 *>(P.in + g * P.ld_in + n0 + part * 8)
-                                                      : make_uint4(0u, 0u, 0u, 0u);
-                        *reinterpret_cast<uint4 *>(rs + rr * RS + part * 8) = x;
-                    }
-                    __syncwarp();
-                }
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    float v[8];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[h][c]);
-                    epilogue8(P, row, n0 + 8 * h, c0 + 8 * h, v, loss_acc, c32, tstage, rs + lane * RS + 8 * h,
-                              rs2 + lane * RS + 8 * h);
-                }
-                if (staged) {
-                    // the round's output rows, 4 lanes per 64-byte row segment; padding rows are
-                    // not stored, except EPI_LOSS's zero gradient
-                    __syncwarp();
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int rr = lr + 8 * i;
-                        const int64_t g = row0 + rr;
-                        if (g < P.m_valid || P.mode == EPI_LOSS) {
-                            *reinterpret_cast<uint4 *>(P.out + g * P.ld_out + n0 + part * 8) =
-                                *reinterpret_cast<const uint4 *>(rs + rr * RS + part * 8);
-                            if (P.mode == EPI_BIAS_GELU)
-                                *reinterpret_cast<uint4 *>(P.aux + g * P.ld_out + n0 + part * 8) =
-                                    *reinterpret_cast<const uint4 *>(rs2 + rr * RS + part * 8);
-                        }
-                    }
-                    __syncwarp();  // the staged rows are free for the next round
-                }
-            }
-            const bool has_t = P.out_t && (P.mode == EPI_BIAS_GELU || P.mode == EPI_BIAS || P.mode == EPI_LOSS ||
-                                           P.mode == EPI_DGELU || P.mode == EPI_PLAIN);
-            if (has_t) {
-                // out_t[n][row0 .. row0 + 31] for the tile's columns n: lane l takes column c + l / 4,
-                // rows 8 (l % 4) .. + 7 (row0 and ld_t are multiples of 32, so 16-byte aligned)
-                __syncwarp();
-                const int cq = lane >> 2;
-                for (int c = cbeg; c < cend; c += 8) {
-                    const int cl = c + cq;
-                    const uint4 val = *reinterpret_cast<const uint4 *>(tstage + cl * 32 + part * 8);
-                    *reinterpret_cast<uint4 *>(P.out_t + (int64_t)(blockIdx.y * BN + cl) * P.ld_t + row0 + part * 8) = val;
-                }
-            }
-            if (P.mode == EPI_LOSS) {
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, d);
-                if (lane == 0) atomicAdd(P.loss, loss_acc);
-            }
+            bf16 *rs = reinterpret_cast<bf16 *>(smem) + 4 * (BN * 32) + q * (2 * 32 * EPI_RS);
+            epilogue_tile<BN>(P, tmem, blockIdx.x, blockIdx.y, blockIdx.z, q, lane, tstage, rs);
         }
     }
     // on an abort: wait (bounded) for this CTA's copies still in flight
@@ -588,8 +600,160 @@ __global__ void k_split_reduce(const float *__restrict__ part, int splits, int64
     }
 }
 
+// Plain arrival on an mbarrier (its expected count is the number of arriving warps).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Shared memory of the persistent GEMM: the TMA ring, then the epilogue warps' staging (the ring
+// is busy with the next tile while a tile's epilogue runs, so the staging has its own room).
+template <int BN, int NST>
+struct PersistSmem {
+    static constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr size_t RING = (size_t)NST * STAGE_BYTES;
+    static constexpr size_t EPI = (size_t)4 * BN * 32 * 2 + (size_t)4 * 2 * 32 * EPI_RS * 2;
+    static constexpr size_t BYTES = RING + EPI + 1024;
+};
+
+// The same product with one CTA per SM walking output tiles t = blockIdx.x, + gridDim.x, ...
+// (tile t: M index t % mtiles, N index t / mtiles) and two TMEM accumulators of BN columns:
+// while the epilogue warps drain accumulator i & 1 of tile i, the MMA warp fills the other one
+// with tile i + 1, and the TMA ring runs on across tiles.  Barriers: full/empty for the ring,
+// tfull[b] (MMA -> epilogue: accumulator b holds a finished tile) and tempty[b] (the four
+// epilogue warps -> MMA: accumulator b has been read).  Every wait is bounded; on a time-out
+// the kernel records SEM_ERR_TIMEOUT, every role stops, and before TMEM is freed the kernel waits
+// (bounded) for its copies in flight and for every MMA it issued.  Results are those of
+// k_gemm_bf16: each tile's products are accumulated in the same order.
+template <int BN, int NST>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_bf16_p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int K,
+                  int64_t mtiles, int64_t ntile, const __grid_constant__ EpiArgs P, int *err)
+{
+    using L = PersistSmem<BN, NST>;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], tfull[2], tempty[2], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    __shared__ int s_consumed[NST];
+    // SW128 tiles need 1024-byte alignment
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K / BK;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            s_consumed[s] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(&done, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(&tmem_base, 2 * BN);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    int issued[NST] = {};
+    if (warp == 0 && lane == 0) {
+        // TMA producer: the ring's K slices of every tile this CTA walks
+        int64_t g = 0;  // K slices issued so far
+        for (int64_t t = blockIdx.x; t < ntile && !*(volatile int *)&s_abort; t += gridDim.x) {
+            const int64_t mt = t % mtiles, nt = t / mtiles;
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int s = (int)(g % NST);
+                const int64_t round = g / NST;
+                if (round > 0 && !mbar_wait_bounded(&empty[s], (uint32_t)((round - 1) & 1), err)) {
+                    s_abort = 1;
+                    break;
+                }
+                if (*(volatile int *)&s_abort) break;
+                uint8_t *a = smem + s * L::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[s], L::STAGE_BYTES);
+                tma_load_2d(a, &tmA, kb * BK, (int)(mt * BM), &full[s]);
+                tma_load_2d(a + L::A_BYTES, &tmB, kb * BK, (int)(nt * BN), &full[s]);
+                ++issued[s];
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: tile i into accumulator i & 1, once the epilogue has read that accumulator's
+        // previous tile
+        constexpr uint32_t IDESC = tc::idesc_f16(BM, BN, true);
+        int64_t g = 0;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+            const int b = i & 1, use = i >> 1;
+            if (*(volatile int *)&s_abort ||
+                (use > 0 && !mbar_wait_bounded(&tempty[b], (uint32_t)((use - 1) & 1), err))) {
+                s_abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const uint32_t tacc = tmem + (uint32_t)(b * BN);
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int s = (int)(g % NST);
+                const int64_t round = g / NST;
+                if (*(volatile int *)&s_abort || !mbar_wait_bounded(&full[s], (uint32_t)(round & 1), err)) {
+                    s_abort = 1;
+                    ok = false;
+                    break;
+                }
+                s_consumed[s] = (int)(round + 1);
+                tc::fence_after_sync();
+                const uint32_t a = smem_u32(smem + s * L::STAGE_BYTES), bb = a + L::A_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc::mma_f16(tacc, tc::desc_k_sw128(a + kk * 32), tc::desc_k_sw128(bb + kk * 32), IDESC,
+                                (kb | kk) != 0 ? 1u : 0u);
+                tc::commit(&empty[s]);
+            }
+            if (!ok) break;
+            tc::commit(&tfull[b]);
+        }
+        tc::commit(&done);  // arrives once every MMA this thread issued has completed
+    } else if (warp >= 2) {
+        // epilogue warps: warp q reads TMEM lane quarter q of each finished accumulator
+        const int q = warp & 3;
+        bf16 *tstage = reinterpret_cast<bf16 *>(smem + L::RING) + q * (BN * 32);
+        bf16 *rs = reinterpret_cast<bf16 *>(smem + L::RING) + 4 * (BN * 32) + q * (2 * 32 * EPI_RS);
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+            const int b = i & 1, use = i >> 1;
+            // warp-uniform: the TMEM loads are collective over the warp
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&tfull[b], (uint32_t)(use & 1), err));
+            if (!ok) s_abort = 1;
+            if (!ok || __any_sync(0xffffffffu, *(volatile int *)&s_abort != 0)) break;
+            tc::fence_after_sync();
+            epilogue_tile<BN>(P, tmem + (uint32_t)(b * BN), t % mtiles, (int)(t / mtiles), 0, q, lane, tstage, rs);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+    }
+    // on an abort: wait (bounded) for this CTA's copies still in flight
+    if (warp == 0 && lane == 0 && *(volatile int *)&s_abort) {
+        for (int s = 0; s < NST; ++s)
+            if (issued[s] > s_consumed[s]) mbar_wait_bounded(&full[s], s_consumed[s] & 1, nullptr);
+    }
+    // every MMA complete before TMEM is freed
+    if (warp == 1 && lane == 0) mbar_wait_bounded(&done, 0, nullptr);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 2 * BN);
+    }
+}
+
 struct GemmCfg {
     int bn, nst, split;
+    int persist;  // 1: the persistent kernel (one CTA per SM walking the tiles), split 1 only
 };
 
 template <int BN, int NST>
@@ -602,6 +766,20 @@ sem_status launch_gemm(sem_ctx *ctx, const CUtensorMap &ta, const CUtensorMap &t
     const dim3 grid((unsigned)(M / BM), (unsigned)(N / BN), (unsigned)split);
     SEM_TRACED(ctx, name, k_gemm_bf16<BN, NST><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, P, ctx->d_flag));
     return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16 launch");
+}
+
+template <int BN, int NST>
+sem_status launch_gemm_p(sem_ctx *ctx, const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int N, int K,
+                         const EpiArgs &P, const char *name)
+{
+    constexpr size_t sm = PersistSmem<BN, NST>::BYTES;
+    static KernelSetup ks;  // per instantiation and device
+    SEM_TRY(kernel_setup(ctx, ks, k_gemm_bf16_p<BN, NST>, 0, sm));
+    const int64_t mtiles = M / BM, ntile = mtiles * (N / BN);
+    const unsigned grid = (unsigned)std::min<int64_t>(ntile, ctx->sm_count);
+    SEM_TRACED(ctx, name, k_gemm_bf16_p<BN, NST><<<grid, GEMM_THREADS, sm, ctx->stream>>>(ta, tb, K, mtiles, ntile, P,
+                                                                                         ctx->d_flag));
+    return sem_cuda(ctx, cudaGetLastError(), "k_gemm_bf16_p launch");
 }
 
 // One product in configuration c: tensor maps for its tile shape, the K-split partials (weight
@@ -624,11 +802,15 @@ sem_status run_gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N
     }
     sem_status st;
 #define SEM_GEMM_CASE(BNV, NSTV) \
-    if (c.bn == BNV && c.nst == NSTV) st = launch_gemm<BNV, NSTV>(ctx, ta, tb, M, N, K, Q, c.split, name); else
+    if (!c.persist && c.bn == BNV && c.nst == NSTV) st = launch_gemm<BNV, NSTV>(ctx, ta, tb, M, N, K, Q, c.split, name); else
+#define SEM_GEMM_CASE_P(BNV, NSTV) \
+    if (c.persist && c.split == 1 && c.bn == BNV && c.nst == NSTV) st = launch_gemm_p<BNV, NSTV>(ctx, ta, tb, M, N, K, Q, name); else
     SEM_GEMM_CASE(64, 3) SEM_GEMM_CASE(64, 4) SEM_GEMM_CASE(128, 3) SEM_GEMM_CASE(128, 4)
     SEM_GEMM_CASE(256, 3) SEM_GEMM_CASE(256, 4)
-    return sem_fail(ctx, SEM_ERR_ARG, "no GEMM kernel for BN=%d, %d stages", c.bn, c.nst);
+    SEM_GEMM_CASE_P(64, 3) SEM_GEMM_CASE_P(64, 4) SEM_GEMM_CASE_P(128, 3) SEM_GEMM_CASE_P(128, 4)
+    return sem_fail(ctx, SEM_ERR_ARG, "no GEMM kernel for BN=%d, %d stages, persistent %d", c.bn, c.nst, c.persist);
 #undef SEM_GEMM_CASE
+#undef SEM_GEMM_CASE_P
     SEM_TRY(st);
     if (c.split > 1) {
         const int64_t n = P.m_valid * (int64_t)P.ld_out;
@@ -653,8 +835,8 @@ sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, in
         return sem_fail(ctx, SEM_ERR_ARG, "GEMM shape %lld x %d x %d not tileable", (long long)M, N, K);
     for (const auto &t : ctx->gemm_tune)
         if (t.M == M && t.N == N && t.K == K && t.mode == P.mode)
-            return run_gemm(ctx, A, B, M, N, K, P, GemmCfg{t.bn, t.nst, t.split}, name);
-    const GemmCfg dflt{N % 128 == 0 ? 128 : 64, 4, 1};
+            return run_gemm(ctx, A, B, M, N, K, P, GemmCfg{t.bn, t.nst, t.split, t.persist}, name);
+    const GemmCfg dflt{N % 128 == 0 ? 128 : 64, 4, 1, 0};
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SEM_CU(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
     if (!ctx->autotune || cs != cudaStreamCaptureStatusNone) return run_gemm(ctx, A, B, M, N, K, P, dflt, name);
@@ -664,13 +846,16 @@ sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, in
     for (int bn : {64, 128, 256}) {
         if (N % bn != 0) continue;
         for (int nst : {3, 4}) {
-            cand.push_back(GemmCfg{bn, nst, 1});
+            cand.push_back(GemmCfg{bn, nst, 1, 0});
+            // the persistent form, whose epilogue overlaps the next tile's MMAs (its staging
+            // beside the ring fits up to BN 128)
+            if (bn <= 128) cand.push_back(GemmCfg{bn, nst, 1, 1});
             // K splits for the FP32 weight gradients, whose output tiles are few and K long
             // (K = the batch): at least 4 K blocks per split, at most 8 CTAs per SM in all
             if (P.mode == EPI_F32 && tiles < 2 * ctx->sm_count)
                 for (int sp : {2, 4, 8, 16, 32})
                     if (nk / sp >= 4 && (M / BM) * (int64_t)(N / bn) * sp <= 8 * (int64_t)ctx->sm_count)
-                        cand.push_back(GemmCfg{bn, nst, sp});
+                        cand.push_back(GemmCfg{bn, nst, sp, 0});
         }
     }
     cudaEvent_t e0, e1;
@@ -698,7 +883,7 @@ sem_status gemm(sem_ctx *ctx, const void *A, const void *B, int64_t M, int N, in
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     SEM_TRY(st);
-    ctx->gemm_tune.push_back({M, N, K, P.mode, best.bn, best.nst, best.split, best_ms});
+    ctx->gemm_tune.push_back({M, N, K, P.mode, best.bn, best.nst, best.split, best.persist, best_ms});
     // the outputs (and the loss) of the chosen configuration
     if (P.mode == EPI_LOSS) SEM_CU(ctx, cudaMemsetAsync(P.loss, 0, sizeof(float), ctx->stream));
     return run_gemm(ctx, A, B, M, N, K, P, best, name);
@@ -1274,7 +1459,7 @@ sem_status sem_autotune_width_entry(sem_ctx *ctx, int k, int *kind, int *N, int6
 }
 
 sem_status sem_autotune_entry(sem_ctx *ctx, int k, int64_t *M, int *N, int *K, int *mode, int *bn, int *stages,
-                              int *split, float *ms)
+                              int *split, int *persistent, float *ms)
 {
     if (!ctx || !M || !N || !K || !mode || !bn || !stages || !split || !ms) return SEM_ERR_ARG;
     if (k < 0 || k >= (int)ctx->gemm_tune.size())
@@ -1287,6 +1472,7 @@ sem_status sem_autotune_entry(sem_ctx *ctx, int k, int64_t *M, int *N, int *K, i
     *bn = t.bn;
     *stages = t.nst;
     *split = t.split;
+    if (persistent) *persistent = t.persist;
     *ms = t.ms;
     return SEM_OK;
 }

@@ -58,7 +58,7 @@ struct sem_ctx {
     bool autotune = true;
     struct GemmTune {
         int64_t M;
-        int N, K, mode, bn, nst, split;
+        int N, K, mode, bn, nst, split, persist;
         float ms;
     };
     std::vector<GemmTune> gemm_tune;

@@ -58,8 +58,9 @@ def test_gemm_autotuner_choices_and_determinism(gpu, sess):
     torch.cuda.synchronize()
     ch = [c for c in S.sem_autotune_choices(sess.ctx) if c[:3] == (M, N, K)]
     assert len(ch) == 1
-    _, _, _, mode, bn, stages, split, ms = ch[0]
-    assert bn in (64, 128, 256) and stages in (3, 4) and split in (1, 2, 4, 8) and ms > 0
+    _, _, _, mode, bn, stages, split, persistent, ms = ch[0]
+    assert bn in (64, 128, 256) and stages in (3, 4) and split in (1, 2, 4, 8, 16, 32) and ms > 0
+    assert persistent in (0, 1) and (not persistent or (split == 1 and bn <= 128))
     assert torch.equal(C1, C2)
     S.sem_autotune_set(sess.ctx, False)
     S.sem_gemm_bf16(sess.ctx, A, B, C3)
@@ -70,7 +71,7 @@ def test_gemm_autotuner_choices_and_determinism(gpu, sess):
     ref = a @ b.T
     for Cx in (C1, C3):
         assert (np.abs(Cx.cpu().double().numpy() - ref) <= bound).all()
-    print(f"\n{M}x{N}x{K}: BN {bn}, {stages} stages, K split {split}, {ms * 1e3:.1f} us")
+    print(f"\n{M}x{N}x{K}: BN {bn}, {stages} stages, K split {split}, persistent {persistent}, {ms * 1e3:.1f} us")
 
 
 def test_gemm_rejects_untileable_shapes(gpu, sess):
