@@ -38,3 +38,24 @@ def test_source_hash_ignores_comments_only(tmp_path):
     c.write_text("// header\n__global__ void k(int *x) { x[0] = 2; }\n")
     assert bench._file_sha(str(a)) == bench._file_sha(str(b))
     assert bench._file_sha(str(a)) != bench._file_sha(str(c))
+
+
+def test_byte_model_of_the_frame_in_parts():
+    """The algorithmic bytes the bench divides by: a two-field frame drawn in parts reads every
+    triangle once over its two raster kernels (Q's part one tile per block, the temperature's
+    as a range), and a one-field frame reads them all in the one-tile-per-block kernel."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from types import SimpleNamespace
+    surf = [{"field": "Q", "niso": 1, "ntri": 4647976, "active_elems": 47017},
+            {"field": "T", "niso": 1, "ntri": 1377188, "active_elems": 13965}]
+    two = SimpleNamespace(N=7, E=262144, npts=262144 * 512, surface_stats=surf, last_ntri=6025164, nseg=2,
+                          surfaces=[("Q", [0.1]), (3, [0.5])], W=3840, H=2160, covered=1000)
+    small, rng = bench.algorithmic_bytes_per_step("k_raster_small", two), bench.algorithmic_bytes_per_step(
+        "k_raster_range", two)
+    assert small == 36 * 4647976 and rng == 36 * 1377188 and small + rng == 36 * two.last_ntri
+    # the fused Q kernel: u, v, w read and Q written (16 B per node) + one count per element
+    assert bench.algorithmic_bytes_per_step("k_sem_q8_count", two) == 16 * two.npts + 4 * two.E
+    one = SimpleNamespace(N=7, E=32768, npts=32768 * 512, surface_stats=surf[:1], last_ntri=4647976, nseg=3,
+                          surfaces=[("Q", [0.1, 0.2, 0.3])], W=1920, H=1080, covered=10)
+    assert bench.algorithmic_bytes_per_step("k_raster_small", one) == 36 * one.last_ntri
