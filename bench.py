@@ -52,6 +52,7 @@ HEADLINE = "rb64"
 # segment colours of the two-field frame: Q red, temperature blue
 RB_COLOURS = [[0.9, 0.3, 0.2], [0.2, 0.5, 0.9]]
 KERNEL_SOURCES = {"k_sem_grad": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
+                  "k_sem_qd": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_sem_q8": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_sem_q8_count": "paper_2312_09888_gb300/csrc/sem_qcrit.cu",
                   "k_iso_count_m": "paper_2312_09888_gb300/csrc/sem_iso.cu",
@@ -67,8 +68,10 @@ def algorithmic_bytes_per_step(name, P):
     NP3 = (P.N + 1) ** 3
     surf = P.surface_stats
     table = {
-        # u, v, w read (12 B/node) + Q written (4 B/node)
+        # one component read (4 B/node) + its three derivatives written (12 B/node)
         "k_sem_grad": 16 * P.npts,
+        # u, v, w read (12 B/node) + Q written (4 B/node)
+        "k_sem_qd": 16 * P.npts,
         "k_sem_q8": 16 * P.npts,
         # the same, the Q field's triangle counts written from the kernel (4 B per element and isovalue)
         "k_sem_q8_count": 16 * P.npts + 4 * P.E * P.surface_stats[0]["niso"],

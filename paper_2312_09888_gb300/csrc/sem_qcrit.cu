@@ -10,11 +10,13 @@
 // Design (GB300): the kernel is HBM-bound (16 B of traffic per node for Q, 144 FLOP per node:
 // about 9 FLOP/B, at the FP32 FFMA ridge), so it streams elements through shared memory with
 // the TMA engine (cp.async.bulk, double-buffered, mbarrier completion) in a persistent grid,
-// keeps D in constant memory (FFMA operands straight from the constant bank), and gives each
-// thread one r-line (k, j) of (N+1) nodes of one element: it reads its own row for u_r, its
-// slab k for u_s and its column j for u_t, forms all 9 gradient entries of its (N+1) nodes in
-// registers and writes Q (or the 3 derivatives) with 16-byte stores.  For N = 7 the reads
-// are staggered so that no shared-memory access is bank-conflicted.  Tensor cores are not
+// keeps D in constant memory (FFMA operands straight from the constant bank).  The derivative
+// kernel (k_sem_grad) gives each thread one r-line (k, j) of (N+1) nodes of one element: it
+// reads its own row for u_r, its slab k for u_s and its column j for u_t and writes the three
+// derivatives of its nodes.  The Q kernels (k_sem_q8 for N = 7, k_sem_qd for the other orders)
+// give each thread one r-, one s- and one t-line, so that every shared-memory value is read
+// once per direction; the s- and t-derivatives reach the r-line's owner through an exchange
+// buffer, which folds the six products of Q in registers and writes them.  Tensor cores are not
 // used here: the contractions have K = N+1 = 8, and the element data would have to be
 // transposed between the three directions, costing more shared-memory traffic than the
 // FFMA work they would replace.
@@ -27,9 +29,6 @@
 #include "sem_internal.cuh"
 
 #define MP (SEM_MAX_ORDER + 1)
-#ifndef SEM_Q_FOLD
-#define SEM_Q_FOLD 1
-#endif
 
 __constant__ float c_D[(SEM_MAX_ORDER + 1) * MP * MP];  // [N][i][m], FP32
 
@@ -38,6 +37,9 @@ __constant__ float c_D[(SEM_MAX_ORDER + 1) * MP * MP];  // [N][i][m], FP32
 // and o_m = u_m - u_{7-m}:  (Du)_i = E_i + O_i and (Du)_{7-i} = O_i - E_i, where
 // E_i = sum_m Ae[i][m] e_m and O_i = sum_m Ao[i][m] o_m (m < 4): 48 operations instead of 64.
 __constant__ float2 c_Deo7[4 * 4];
+// D transposed, [N][m][i]: the coefficients (D[i][m], D[i+1][m]) of two nodes' sums side by side
+// (8-byte aligned for even i), one FFMA2 operand
+__constant__ __align__(16) float c_DT[(SEM_MAX_ORDER + 1) * MP * MP];
 
 sem_status qcrit_upload_tables(sem_ctx *ctx, const float *D_all, const float *s_all)
 {
@@ -51,6 +53,11 @@ sem_status qcrit_upload_tables(sem_ctx *ctx, const float *D_all, const float *s_
             eo[i * 4 + m] = make_float2((float)(0.5 * (a + b)), (float)(0.5 * (a - b)));
         }
     SEM_CU(ctx, cudaMemcpyToSymbol(c_Deo7, eo, sizeof eo));
+    std::vector<float> dt((size_t)(SEM_MAX_ORDER + 1) * MP * MP);
+    for (int n = 0; n <= SEM_MAX_ORDER; ++n)
+        for (int i = 0; i < MP; ++i)
+            for (int m = 0; m < MP; ++m) dt[((size_t)n * MP + m) * MP + i] = D_all[((size_t)n * MP + i) * MP + m];
+    SEM_CU(ctx, cudaMemcpyToSymbol(c_DT, dt.data(), sizeof(float) * dt.size()));
     return SEM_OK;
 }
 
@@ -79,25 +86,6 @@ __device__ __forceinline__ void contract_row(float (&row)[NP], float (&dr)[NP])
         for (int m = 1; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
         dr[i] = a;
     }
-}
-
-// One direction at a time (the Q kernel folds each into Q before computing the next).
-template <int NP>
-__device__ __forceinline__ void deriv_r(const float *__restrict__ U, int k, int j, float (&dr)[NP])
-{
-    float row[NP];
-    if constexpr (NP == 8) {
-        const int sw = (j >> 2) & 1;
-        const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
-        float4 A = rp[sw], B = rp[sw ^ 1];
-        float4 lo = sw ? B : A, hi = sw ? A : B;
-        row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
-        row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
-    } else {
-#pragma unroll
-        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
-    }
-    contract_row<NP>(row, dr);
 }
 
 // d/ds at the nodes (i, j, k), i = 0..NP-1, of slab k: the s-line of node i is U[k][.][i], its
@@ -271,11 +259,12 @@ __device__ __forceinline__ int qb_find(const GBatch &B, int64_t grp)
     return lo;
 }
 
-// NC = 3: Q of (f0, f1, f2) -> out0.   NC = 1: gradient of f0 -> (out0, out1, out2).
-template <int NP, int NC>
+// The gradient of f0 -> (out0, out1, out2), one r-line per thread.
+template <int NP>
 __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const __grid_constant__ GBatch B, int *err)
 {
     using C = QCfg<NP>;
+    constexpr int NC = 1;
     constexpr int NP3 = C::NP3, L = C::L, EPB = C::EPB;
     constexpr int STAGE = NC * EPB * NP3;
     constexpr uint32_t BYTES = EPB * NP3 * 4;
@@ -360,75 +349,16 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
             float dr[NP], ds[NP], dt[NP];
             const int64_t off = e * NP3 + (k * NP + j) * NP;
             float *out0 = B.o[0][p], *out1 = B.o[1][p], *out2 = B.o[2][p];
-            if constexpr (NC == 1) {
-                line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+            line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
 #pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    dr[i] *= g.x;
-                    ds[i] *= g.y;
-                    dt[i] *= g.z;
-                }
-                store_line<NP>(out0 + off, dr);
-                store_line<NP>(out1 + off, ds);
-                store_line<NP>(out2 + off, dt);
-            } else {
-#if SEM_Q_FOLD
-                // Q = -1/2 sum_ij J_ij J_ji with J_ij = g_j d_j(u_i): six product terms, each
-                // folded in as soon as its second factor is known; c = -1/2 g_i g_j (x2 off-diagonal)
-                const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
-                const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
-                const float *U0 = st + el * NP3, *U1 = U0 + EPB * NP3, *U2 = U1 + EPB * NP3;
-                float q[NP], su[NP], tu[NP], tv[NP], d[NP];
-                deriv_r<NP>(U0, k, j, d);  // u_r
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = c11 * d[i] * d[i];
-                deriv_s<NP>(U0, k, j, Dj, su);  // u_s
-                deriv_t<NP>(U0, j, Dk, tu);     // u_t
-                deriv_r<NP>(U1, k, j, d);       // v_r
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = fmaf(c12 * su[i], d[i], q[i]);
-                deriv_s<NP>(U1, k, j, Dj, d);   // v_s
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = fmaf(c22 * d[i], d[i], q[i]);
-                deriv_t<NP>(U1, j, Dk, tv);     // v_t
-                deriv_r<NP>(U2, k, j, d);       // w_r
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = fmaf(c13 * tu[i], d[i], q[i]);
-                deriv_s<NP>(U2, k, j, Dj, d);   // w_s
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = fmaf(c23 * tv[i], d[i], q[i]);
-                deriv_t<NP>(U2, j, Dk, d);      // w_t
-#pragma unroll
-                for (int i = 0; i < NP; ++i) q[i] = fmaf(c33 * d[i], d[i], q[i]);
-#else
-                float q[NP], J13[NP], J23[NP];
-                // u: J11 = gx u_r, J12 = gy u_s, J13 = gz u_t
-                line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
-                float J11[NP], J12[NP];
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    J11[i] = g.x * dr[i];
-                    J12[i] = g.y * ds[i];
-                    J13[i] = g.z * dt[i];
-                }
-                // v: J21, J22, J23
-                line_derivs<NP>(st + EPB * NP3 + el * NP3, k, j, Dj, Dk, dr, ds, dt);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float J21 = g.x * dr[i], J22 = g.y * ds[i];
-                    J23[i] = g.z * dt[i];
-                    q[i] = fmaf(J11[i], J11[i], fmaf(J22, J22, 2.f * J12[i] * J21));
-                }
-                // w: J31, J32, J33
-                line_derivs<NP>(st + 2 * EPB * NP3 + el * NP3, k, j, Dj, Dk, dr, ds, dt);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float J31 = g.x * dr[i], J32 = g.y * ds[i], J33 = g.z * dt[i];
-                    q[i] = -0.5f * fmaf(J33, J33, fmaf(2.f * J13[i], J31, fmaf(2.f * J23[i], J32, q[i])));
-                }
-#endif
-                store_line<NP>(out0 + off, q);
+            for (int i = 0; i < NP; ++i) {
+                dr[i] *= g.x;
+                ds[i] *= g.y;
+                dt[i] *= g.z;
             }
+            store_line<NP>(out0 + off, dr);
+            store_line<NP>(out1 + off, ds);
+            store_line<NP>(out2 + off, dt);
         }
         __syncthreads();
         if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
@@ -444,14 +374,233 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
 }
 
 // ------------------------------------------------------------------------------------------
-// Q for N = 7 with direction-owned lines.  In the kernel above every thread contracts along
-// all three directions for its own r-line, so it reads its whole slab and column (128 values
-// per component, mostly broadcast).  Here each direction is contracted by the threads that
+// Q for the other orders with direction-owned lines (the scheme of k_sem_q8 below, for any
+// NP).  A thread that contracts all three directions for its own r-line reads its whole slab
+// and column, (2 NP + 1) NP values per component, and repeats the level shift of every s- and
+// t-line it touches.  Here thread (el, l) of a stage, with (a, b) = (l / NP, l % NP), owns
+// three lines of element el: the r-line (k, j) = (a, b), the s-line (k, i) = (a, b) and the
+// t-line (j, i) = (a, b).  It reads NP values per line; the s- and t-line owners write their NP
+// derivatives to an exchange buffer laid out like the element, [k][j][i], from which the
+// r-line owner reads its node row of each and folds the six products of Q.  Every line is
+// contracted by contract_row's steps (level shift, then the products in m order), the folds
+// come in the same order, so the result is the one-thread-per-r-line result bit for bit.
+// Two nodes' sums share one FFMA2 (two round-to-nearest FMAs per instruction).
+// ------------------------------------------------------------------------------------------
+template <int NP>
+__device__ __forceinline__ float2 DT2(int m, int i)
+{
+    return *reinterpret_cast<const float2 *>(&c_DT[((NP - 1) * MP + m) * MP + i]);
+}
+
+// (D u)_i for i = 0..NP-1 of one line u held in registers (u is shifted in place)
+template <int NP>
+__device__ __forceinline__ void contract_line2(float (&u)[NP], float (&d)[NP])
+{
+#pragma unroll
+    for (int m = 1; m < NP; ++m) u[m] -= u[0];
+#pragma unroll
+    for (int i = 0; i + 1 < NP; i += 2) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 1; m < NP; ++m) acc = __ffma2_rn(DT2<NP>(m, i), make_float2(u[m], u[m]), acc);
+        d[i] = acc.x;
+        d[i + 1] = acc.y;
+    }
+    if constexpr (NP & 1) {
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 1; m < NP; ++m) acc = fmaf(Dc<NP>(NP - 1, m), u[m], acc);
+        d[NP - 1] = acc;
+    }
+}
+
+// NP consecutive floats of shared memory (16- or 8-byte loads where NP allows)
+template <int NP>
+__device__ __forceinline__ void load_row(const float *__restrict__ src, float (&v)[NP])
+{
+    if constexpr (NP % 4 == 0) {
+        const float4 *p = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int q = 0; q < NP / 4; ++q) {
+            const float4 x = p[q];
+            v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+        }
+    } else if constexpr (NP % 2 == 0) {
+        const float2 *p = reinterpret_cast<const float2 *>(src);
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) {
+            const float2 x = p[q];
+            v[2 * q] = x.x; v[2 * q + 1] = x.y;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) v[m] = src[m];
+    }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const __grid_constant__ GBatch B, int *err)
+{
+    using C = QCfg<NP>;
+    constexpr int NP3 = C::NP3, L = C::L, EPB = C::EPB;
+    constexpr int CS = EPB * NP3;  // one component of a stage
+    constexpr int STAGE = 3 * CS;
+    constexpr uint32_t BYTES = CS * 4;
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_abort;
+    float *X = smem + C::NSTAGE * STAGE;  // exchange: three slots of one component's stage size
+
+    const int tid = threadIdx.x;
+    const bool active = tid < EPB * L;
+    const int el = active ? tid / L : 0, l = tid % L, a = l / NP, b = l % NP;
+    const int64_t ngroups = B.gstart[B.n];
+    // group -> (partition, its elements): a full group (EPB elements) can come by bulk copy
+    auto elems = [&](int64_t grp, int &p, int64_t &e0) {
+        p = qb_find(B, grp);
+        e0 = (grp - B.gstart[p]) * EPB;
+        const int64_t left = B.E[p] - e0;
+        return (int)(left < EPB ? left : EPB);
+    };
+    if (tid == 0) {
+        s_abort = 0;
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto full = [&](int64_t grp) {
+        int p;
+        int64_t e0;
+        return C::BULK && grp < ngroups && elems(grp, p, e0) == EPB;
+    };
+    auto issue = [&](int64_t grp, int s) {
+        int p;
+        int64_t e0;
+        elems(grp, p, e0);
+        float *dst = smem + s * STAGE;
+        mbar_arrive_expect_tx(&bar[s], 3 * BYTES);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) bulk_g2s(dst + c * CS, B.f[c][p] + e0 * NP3, BYTES, &bar[s]);
+    };
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {full(blockIdx.x), full((int64_t)blockIdx.x + gridDim.x)};
+    if (tid == 0) {
+        if (pending[0]) issue(blockIdx.x, 0);
+        if (pending[1]) issue((int64_t)blockIdx.x + gridDim.x, 1);
+    }
+
+    int it = 0;
+    for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
+        const int s = C::BULK ? (it & 1) : 0;
+        float *st = smem + s * STAGE;
+        int p;
+        int64_t e0;
+        const int ne = elems(grp, p, e0);
+        if (C::BULK && ne == EPB) {
+            // a wait that ran out leaves the stage pending, so the abort path drains its copy
+            if (mbar_wait_bounded(&bar[s], phase[s], err, B.wait_limit)) {
+                phase[s] ^= 1u;
+                pending[s] = false;
+            } else {
+                s_abort = 1;
+            }
+        } else {
+            for (int c = 0; c < 3; ++c)
+                for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x)
+                    st[c * CS + idx] = B.f[c][p][e0 * NP3 + idx];
+        }
+        __syncthreads();
+        if (s_abort) break;
+        const int64_t e = e0 + el;
+        // Q = -1/2 sum_ij J_ij J_ji, J_ij = g_j d_j(u_i): c = -1/2 g_i g_j (x2 off the diagonal)
+        const float4 g = B.g[p][el < ne ? e : e0];
+        const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
+        const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
+        // this thread's s- and t-lines of component c -> exchange slots xs and xt
+        auto st_lines = [&](int c, int xs, int xt) {
+            if (!active) return;
+            const float *U = st + c * CS + el * NP3;
+            float u[NP], d[NP];
+#pragma unroll
+            for (int m = 0; m < NP; ++m) u[m] = U[(a * NP + m) * NP + b];
+            contract_line2<NP>(u, d);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) X[xs * CS + el * NP3 + (a * NP + m) * NP + b] = d[m];
+#pragma unroll
+            for (int m = 0; m < NP; ++m) u[m] = U[(m * NP + a) * NP + b];
+            contract_line2<NP>(u, d);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) X[xt * CS + el * NP3 + (m * NP + a) * NP + b] = d[m];
+        };
+        auto r_line = [&](int c, float (&dr)[NP]) {
+            float u[NP];
+            load_row<NP>(st + c * CS + el * NP3 + l * NP, u);
+            contract_line2<NP>(u, dr);
+        };
+        auto x_row = [&](int x, float (&v)[NP]) { load_row<NP>(X + x * CS + el * NP3 + l * NP, v); };
+        // the six products, each folded in as soon as its second factor is known; u_t waits in
+        // registers, u_s and v_t in the exchange: slots A = 0, B = 1, C = 2
+        float q[NP], tu[NP], dr[NP], x0[NP], x1[NP];
+        st_lines(0, 0, 1);  // u_s -> A, u_t -> B
+        if (active) {
+            r_line(0, dr);
+#pragma unroll
+            for (int i = 0; i < NP; ++i) q[i] = c11 * dr[i] * dr[i];
+        }
+        __syncthreads();
+        if (active) x_row(1, tu);
+        __syncthreads();    // B is free
+        st_lines(1, 2, 1);  // v_s -> C, v_t -> B
+        if (active) r_line(1, dr);
+        __syncthreads();
+        if (active) {
+            x_row(0, x0);  // u_s
+            x_row(2, x1);  // v_s
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                q[i] = fmaf(c12 * x0[i], dr[i], q[i]);
+                q[i] = fmaf(c22 * x1[i], x1[i], q[i]);
+            }
+        }
+        __syncthreads();    // A and C are free
+        st_lines(2, 0, 2);  // w_s -> A, w_t -> C
+        if (active) r_line(2, dr);
+        __syncthreads();    // the stage is read; the exchange is free again after the next stage's first barrier
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) q[i] = fmaf(c13 * tu[i], dr[i], q[i]);
+            x_row(1, x0);  // v_t
+            x_row(0, x1);  // w_s
+#pragma unroll
+            for (int i = 0; i < NP; ++i) q[i] = fmaf(c23 * x0[i], x1[i], q[i]);
+            x_row(2, x0);  // w_t
+#pragma unroll
+            for (int i = 0; i < NP; ++i) q[i] = fmaf(c33 * x0[i], x0[i], q[i]);
+            if (el < ne) store_line<NP>(B.o[0][p] + e * NP3 + l * NP, q);
+        }
+        if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
+            issue(grp + 2 * (int64_t)gridDim.x, s);
+            pending[s] = true;
+        }
+    }
+    // on an abort, wait (bounded) for copies still in flight into this CTA's shared memory
+    if (C::BULK && s_abort && tid == 0) {
+        for (int s = 0; s < 2; ++s)
+            if (pending[s]) mbar_wait_bounded(&bar[s], phase[s], nullptr);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Q for N = 7 with direction-owned lines.  In k_sem_grad every thread contracts along all
+// three directions for its own r-line, so it reads its whole slab and column (128 values per
+// component, mostly broadcast).  Here each direction is contracted by the threads that
 // own its lines: warp w is the s-line owner of slab k = w (lanes: element el = lane/8, node
 // i = lane%8) and the t-line owner of plane j = w; each reads 8 values with conflict-free
 // 4-byte loads (elements sit 520 floats apart in shared memory, shifting their banks by 8) and
 // passes its 8 derivatives through an exchange buffer to the r-line owner (el, k, j), which
-// contracts its own row and folds the six products of Q exactly as k_sem_grad does.
+// contracts its own row and folds the six products of Q in k_sem_qd's order.
 // 4 elements per stage, 2 stages fed by per-element bulk copies; 3 CTAs per SM.
 // ------------------------------------------------------------------------------------------
 // All eight outputs of the contraction (D u)_i, N = 7, by the even/odd split above; the
@@ -662,7 +811,7 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
                 dt[0] = tlo.x; dt[1] = tlo.y; dt[2] = tlo.z; dt[3] = tlo.w;
                 dt[4] = thi.x; dt[5] = thi.y; dt[6] = thi.z; dt[7] = thi.w;
             }
-            // Q = -1/2 sum_ij J_ij J_ji, J_ij = g_j d_j(u_i): the six products in k_sem_grad's order
+            // Q = -1/2 sum_ij J_ij J_ji, J_ij = g_j d_j(u_i): the six products in k_sem_qd's order
             if (c == 0) {
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
@@ -772,12 +921,12 @@ static sem_status launch_q8(sem_ctx *ctx, const GBatch &B)
     });
 }
 
-template <int NP, int NC>
+template <int NP>
 static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
 {
     using C = QCfg<NP>;
-    const size_t smem = sizeof(float) * (size_t)C::NSTAGE * NC * C::EPB * C::NP3;
-    auto kern = k_sem_grad<NP, NC>;
+    const size_t smem = sizeof(float) * (size_t)C::NSTAGE * C::EPB * C::NP3;
+    auto kern = k_sem_grad<NP>;
     static KernelSetup ks;  // per instantiation and device
     int per_sm = 1;
     SEM_TRY(kernel_setup(ctx, ks, kern, C::NT, smem, &per_sm));
@@ -787,7 +936,7 @@ static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
     const int nc = q_width_candidates(per_sm, cand);
     int64_t E = 0;
     for (int p = 0; p < B.n; ++p) E += B.E[p];
-    return width_tuned(ctx, NC == 3 ? TUNE_QGRAD : TUNE_QGRAD_DERIV, NP - 1, E, cand, nc, per_sm,
+    return width_tuned(ctx, TUNE_QGRAD_DERIV, NP - 1, E, cand, nc, per_sm,
                        [&](int w) -> sem_status {
                            int64_t grid = (int64_t)ctx->sm_count * w;
                            if (grid > ngroups) grid = ngroups;
@@ -795,6 +944,30 @@ static sem_status launch_grad(sem_ctx *ctx, const GBatch &B)
                                       kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(B, ctx->d_flag));
                            return sem_cuda(ctx, cudaGetLastError(), "k_sem_grad launch");
                        });
+}
+
+// Q of the other orders: two stages of the three components and the exchange's three slots
+template <int NP>
+static sem_status launch_qd(sem_ctx *ctx, const GBatch &B)
+{
+    using C = QCfg<NP>;
+    const size_t smem = sizeof(float) * (size_t)(C::NSTAGE * 3 + 3) * C::EPB * C::NP3;
+    auto kern = k_sem_qd<NP>;
+    static KernelSetup ks;  // per instantiation and device
+    int per_sm = 1;
+    SEM_TRY(kernel_setup(ctx, ks, kern, C::NT, smem, &per_sm));
+    const int64_t ngroups = B.gstart[B.n];
+    if (ngroups == 0) return SEM_OK;
+    int cand[4];
+    const int nc = q_width_candidates(per_sm, cand);
+    int64_t E = 0;
+    for (int p = 0; p < B.n; ++p) E += B.E[p];
+    return width_tuned(ctx, TUNE_QGRAD, NP - 1, E, cand, nc, per_sm, [&](int w) -> sem_status {
+        int64_t grid = (int64_t)ctx->sm_count * w;
+        if (grid > ngroups) grid = ngroups;
+        SEM_TRACED(ctx, "k_sem_qd", kern<<<(unsigned)grid, C::NT, smem, ctx->stream>>>(B, ctx->d_flag));
+        return sem_cuda(ctx, cudaGetLastError(), "k_sem_qd launch");
+    });
 }
 
 template <int NC>
@@ -813,7 +986,7 @@ static sem_status dispatch(sem_ctx *ctx, int N, int n, const sem_mesh *const *m,
     case NPV:                                                                \
         fill_batch(B, n, QCfg<NPV>::EPB, m, f0, f1, f2, o0, o1, o2);         \
         B.wait_limit = ctx->wait_limit;                                      \
-        return launch_grad<NPV, NC>(ctx, B);
+        return NC == 3 ? launch_qd<NPV>(ctx, B) : launch_grad<NPV>(ctx, B);
         SEM_CASE(2) SEM_CASE(3) SEM_CASE(4) SEM_CASE(5) SEM_CASE(6) SEM_CASE(7) SEM_CASE(8) SEM_CASE(9)
         SEM_CASE(10) SEM_CASE(11) SEM_CASE(12) SEM_CASE(13) SEM_CASE(14) SEM_CASE(15) SEM_CASE(16)
 #undef SEM_CASE

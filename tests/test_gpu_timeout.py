@@ -27,7 +27,7 @@ def _q_parity(S, ctx, orc, m, xyz, uvw32, N):
     assert (err <= q_bound(J, dJ)).all()
 
 
-# N = 7: k_sem_q8 (4-element stages); N = 5: k_sem_grad<6, 3> (7-element stages; the last,
+# N = 7: k_sem_q8 (4-element stages); N = 5: k_sem_qd<6> (7-element stages; the last,
 # partial group is loaded without a copy); both fill their stages with bulk copies
 @pytest.mark.parametrize("N,nel", [(7, (5, 4, 3)), (5, (5, 4, 3))])
 def test_bounded_wait_runs_out_and_context_recovers(gpu, sess, orc, N, nel):
