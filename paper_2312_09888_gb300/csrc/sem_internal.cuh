@@ -358,6 +358,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// Orders this thread's earlier generic-proxy accesses of shared memory before later async-proxy
+// ones (a bulk copy that overwrites what threads wrote there; the copy's issue must follow a
+// barrier after the fence)
+__device__ __forceinline__ void fence_proxy_async_cta() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // global -> shared bulk copy completing on `bar` (bytes: multiple of 16, both addresses 16B aligned)
 __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
 {

@@ -203,6 +203,10 @@ __device__ __forceinline__ void store_line(float *__restrict__ dst, const float 
         float4 *p = reinterpret_cast<float4 *>(dst);
 #pragma unroll
         for (int q = 0; q < NP / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if constexpr (NP % 2 == 0) {
+        float2 *p = reinterpret_cast<float2 *>(dst);
+#pragma unroll
+        for (int q = 0; q < NP / 2; ++q) p[q] = make_float2(v[2 * q], v[2 * q + 1]);
     } else {
 #pragma unroll
         for (int i = 0; i < NP; ++i) dst[i] = v[i];
@@ -340,6 +344,7 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
             for (int c = 0; c < NC; ++c)
                 for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x)
                     st[c * EPB * NP3 + idx] = B.f[c][p][e0 * NP3 + idx];
+            if (C::BULK) fence_proxy_async_cta();  // a later bulk copy may overwrite these stores
         }
         __syncthreads();
         if (s_abort) break;
@@ -380,8 +385,9 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
 // t-line it touches.  Here thread (el, l) of a stage, with (a, b) = (l / NP, l % NP), owns
 // three lines of element el: the r-line (k, j) = (a, b), the s-line (k, i) = (a, b) and the
 // t-line (j, i) = (a, b).  It reads NP values per line; the s- and t-line owners write their NP
-// derivatives to an exchange buffer laid out like the element, [k][j][i], from which the
-// r-line owner reads its node row of each and folds the six products of Q.  Every line is
+// derivatives to exchange slots laid out like the element, [k][j][i] (three slots of their own
+// and the stage's component-0 part once that is read), from which the r-line owner reads its
+// node row of each and folds the six products of Q: five barriers per stage.  Every line is
 // contracted by contract_row's steps (level shift, then the products in m order), the folds
 // come in the same order, so the result is the one-thread-per-r-line result bit for bit.
 // Two nodes' sums share one FFMA2 (two round-to-nearest FMAs per instruction).
@@ -484,12 +490,21 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const _
 #pragma unroll
         for (int c = 0; c < 3; ++c) bulk_g2s(dst + c * CS, B.f[c][p] + e0 * NP3, BYTES, &bar[s]);
     };
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {full(blockIdx.x), full((int64_t)blockIdx.x + gridDim.x)};
+    // the geometry factors of this thread's element in group grp (loaded one group ahead)
+    auto geo = [&](int64_t grp) {
+        int p;
+        int64_t e0;
+        const int ne = elems(grp, p, e0);
+        return B.g[p][e0 + (el < ne ? el : 0)];
+    };
+    // per stage s: bit s of `phase` is its mbarrier parity, bit s of `pending` a copy in flight
+    uint32_t phase = 0u;
+    uint32_t pending = (full(blockIdx.x) ? 1u : 0u) | (full((int64_t)blockIdx.x + gridDim.x) ? 2u : 0u);
     if (tid == 0) {
-        if (pending[0]) issue(blockIdx.x, 0);
-        if (pending[1]) issue((int64_t)blockIdx.x + gridDim.x, 1);
+        if (pending & 1u) issue(blockIdx.x, 0);
+        if (pending & 2u) issue((int64_t)blockIdx.x + gridDim.x, 1);
     }
+    float4 g_next = blockIdx.x < ngroups ? geo(blockIdx.x) : make_float4(0.f, 0.f, 0.f, 0.f);
 
     int it = 0;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
@@ -498,11 +513,13 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const _
         int p;
         int64_t e0;
         const int ne = elems(grp, p, e0);
+        const float4 g = g_next;
+        if (grp + gridDim.x < ngroups) g_next = geo(grp + gridDim.x);
         if (C::BULK && ne == EPB) {
             // a wait that ran out leaves the stage pending, so the abort path drains its copy
-            if (mbar_wait_bounded(&bar[s], phase[s], err, B.wait_limit)) {
-                phase[s] ^= 1u;
-                pending[s] = false;
+            if (mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err, B.wait_limit)) {
+                phase ^= 1u << s;
+                pending &= ~(1u << s);
             } else {
                 s_abort = 1;
             }
@@ -513,13 +530,17 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const _
         }
         __syncthreads();
         if (s_abort) break;
+        // the other stage was read (fold included) before the barrier above: its next group
+        if (C::BULK && tid == 0 && it > 0 && full(grp + gridDim.x)) {
+            issue(grp + gridDim.x, s ^ 1);
+            pending |= 2u >> s;
+        }
         const int64_t e = e0 + el;
         // Q = -1/2 sum_ij J_ij J_ji, J_ij = g_j d_j(u_i): c = -1/2 g_i g_j (x2 off the diagonal)
-        const float4 g = B.g[p][el < ne ? e : e0];
         const float c11 = -0.5f * g.x * g.x, c22 = -0.5f * g.y * g.y, c33 = -0.5f * g.z * g.z;
         const float c12 = -g.x * g.y, c13 = -g.x * g.z, c23 = -g.y * g.z;
         // this thread's s- and t-lines of component c -> exchange slots xs and xt
-        auto st_lines = [&](int c, int xs, int xt) {
+        auto st_lines = [&](int c, float *xs, float *xt) {
             if (!active) return;
             const float *U = st + c * CS + el * NP3;
             float u[NP], d[NP];
@@ -527,68 +548,71 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const _
             for (int m = 0; m < NP; ++m) u[m] = U[(a * NP + m) * NP + b];
             contract_line2<NP>(u, d);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) X[xs * CS + el * NP3 + (a * NP + m) * NP + b] = d[m];
+            for (int m = 0; m < NP; ++m) xs[el * NP3 + (a * NP + m) * NP + b] = d[m];
 #pragma unroll
             for (int m = 0; m < NP; ++m) u[m] = U[(m * NP + a) * NP + b];
             contract_line2<NP>(u, d);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) X[xt * CS + el * NP3 + (m * NP + a) * NP + b] = d[m];
+            for (int m = 0; m < NP; ++m) xt[el * NP3 + (m * NP + a) * NP + b] = d[m];
         };
         auto r_line = [&](int c, float (&dr)[NP]) {
             float u[NP];
             load_row<NP>(st + c * CS + el * NP3 + l * NP, u);
             contract_line2<NP>(u, dr);
         };
-        auto x_row = [&](int x, float (&v)[NP]) { load_row<NP>(X + x * CS + el * NP3 + l * NP, v); };
-        // the six products, each folded in as soon as its second factor is known; u_t waits in
-        // registers, u_s and v_t in the exchange: slots A = 0, B = 1, C = 2
-        float q[NP], tu[NP], dr[NP], x0[NP], x1[NP];
-        st_lines(0, 0, 1);  // u_s -> A, u_t -> B
+        auto x_row = [&](const float *x, float (&v)[NP]) { load_row<NP>(x + el * NP3 + l * NP, v); };
+        // exchange slots A, B, C, and D: component 0's part of the stage, free once it is read
+        float *XA = X, *XB = X + CS, *XC = X + 2 * CS, *XD = st;
+        // the six products, each folded in as soon as its second factor is known
+        float q[NP], dr[NP], x0[NP], x1[NP];
+        st_lines(0, XA, XB);  // u_s -> A, u_t -> B
         if (active) {
             r_line(0, dr);
 #pragma unroll
             for (int i = 0; i < NP; ++i) q[i] = c11 * dr[i] * dr[i];
         }
-        __syncthreads();
-        if (active) x_row(1, tu);
-        __syncthreads();    // B is free
-        st_lines(1, 2, 1);  // v_s -> C, v_t -> B
+        __syncthreads();      // component 0 is read: D is free
+        st_lines(1, XC, XD);  // v_s -> C, v_t -> D
         if (active) r_line(1, dr);
         __syncthreads();
         if (active) {
-            x_row(0, x0);  // u_s
-            x_row(2, x1);  // v_s
+            x_row(XA, x0);  // u_s
+            x_row(XC, x1);  // v_s
 #pragma unroll
             for (int i = 0; i < NP; ++i) {
                 q[i] = fmaf(c12 * x0[i], dr[i], q[i]);
                 q[i] = fmaf(c22 * x1[i], x1[i], q[i]);
             }
         }
-        __syncthreads();    // A and C are free
-        st_lines(2, 0, 2);  // w_s -> A, w_t -> C
+        __syncthreads();      // A and C are free
+        st_lines(2, XA, XC);  // w_s -> A, w_t -> C
         if (active) r_line(2, dr);
-        __syncthreads();    // the stage is read; the exchange is free again after the next stage's first barrier
+        __syncthreads();
         if (active) {
+            x_row(XB, x0);  // u_t
 #pragma unroll
-            for (int i = 0; i < NP; ++i) q[i] = fmaf(c13 * tu[i], dr[i], q[i]);
-            x_row(1, x0);  // v_t
-            x_row(0, x1);  // w_s
+            for (int i = 0; i < NP; ++i) q[i] = fmaf(c13 * x0[i], dr[i], q[i]);
+            x_row(XD, x0);  // v_t
+            x_row(XA, x1);  // w_s
 #pragma unroll
             for (int i = 0; i < NP; ++i) q[i] = fmaf(c23 * x0[i], x1[i], q[i]);
-            x_row(2, x0);  // w_t
+            x_row(XC, x0);  // w_t
 #pragma unroll
             for (int i = 0; i < NP; ++i) q[i] = fmaf(c33 * x0[i], x0[i], q[i]);
             if (el < ne) store_line<NP>(B.o[0][p] + e * NP3 + l * NP, q);
         }
-        if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
-            issue(grp + 2 * (int64_t)gridDim.x, s);
-            pending[s] = true;
+        if constexpr (C::BULK) {
+            // D (and a group loaded without a copy) was written through the generic proxy; a bulk
+            // copy overwrites the stage after the next barrier
+            fence_proxy_async_cta();
+        } else {
+            __syncthreads();  // one stage: the next group's loads overwrite D, still read by the fold above
         }
     }
     // on an abort, wait (bounded) for copies still in flight into this CTA's shared memory
     if (C::BULK && s_abort && tid == 0) {
         for (int s = 0; s < 2; ++s)
-            if (pending[s]) mbar_wait_bounded(&bar[s], phase[s], nullptr);
+            if ((pending >> s) & 1u) mbar_wait_bounded(&bar[s], (phase >> s) & 1u, nullptr);
     }
 }
 
@@ -751,6 +775,7 @@ __global__ void __launch_bounds__(256, 3) k_sem_q8(const __grid_constant__ GBatc
             for (int c = 0; c < 3; ++c)
                 for (int idx = tid; idx < ne * NP3; idx += 256)
                     st[c * CS + (idx / NP3) * ES + idx % NP3] = B.f[c][p][e0 * NP3 + idx];
+            fence_proxy_async_cta();  // a later bulk copy may overwrite these stores
         }
         __syncthreads();
         if (s_abort) break;
