@@ -10,13 +10,12 @@
 // Design (GB300): the kernel is HBM-bound (16 B of traffic per node for Q, 144 FLOP per node:
 // about 9 FLOP/B, at the FP32 FFMA ridge), so it streams elements through shared memory with
 // the TMA engine (cp.async.bulk, double-buffered, mbarrier completion) in a persistent grid,
-// keeps D in constant memory (FFMA operands straight from the constant bank).  The derivative
-// kernel (k_sem_grad) gives each thread one r-line (k, j) of (N+1) nodes of one element: it
-// reads its own row for u_r, its slab k for u_s and its column j for u_t and writes the three
-// derivatives of its nodes.  The Q kernels (k_sem_q8 for N = 7, k_sem_qd for the other orders)
-// give each thread one r-, one s- and one t-line, so that every shared-memory value is read
-// once per direction; the s- and t-derivatives reach the r-line's owner through an exchange
-// buffer, which folds the six products of Q in registers and writes them.  Tensor cores are not
+// keeps D in constant memory (FFMA operands straight from the constant bank).  Every kernel
+// gives each thread one r-, one s- and one t-line of (N+1) nodes of one element, so that every
+// shared-memory value is read once per direction.  The derivative kernel (k_sem_grad) writes
+// each line's derivatives straight to its output field; in the Q kernels (k_sem_q8 for N = 7,
+// k_sem_qd for the other orders) the s- and t-derivatives reach the r-line's owner through an
+// exchange buffer, which folds the six products of Q in registers and writes them.  Tensor cores are not
 // used here: the contractions have K = N+1 = 8, and the element data would have to be
 // transposed between the three directions, costing more shared-memory traffic than the
 // FFMA work they would replace.
@@ -73,126 +72,56 @@ __device__ __forceinline__ float Dc(int i, int m)
 // instead of its magnitude -- a field with a large mean over thin elements would otherwise
 // lose most of its significant digits to cancellation.
 
-// (D row)_i for one r-line held in registers
 template <int NP>
-__device__ __forceinline__ void contract_row(float (&row)[NP], float (&dr)[NP])
+__device__ __forceinline__ float2 DT2(int m, int i)
+{
+    return *reinterpret_cast<const float2 *>(&c_DT[((NP - 1) * MP + m) * MP + i]);
+}
+
+// (D u)_i for i = 0..NP-1 of one line u held in registers (u is shifted in place); two nodes'
+// sums share one FFMA2 (two round-to-nearest FMAs per instruction)
+template <int NP>
+__device__ __forceinline__ void contract_line2(float (&u)[NP], float (&d)[NP])
 {
 #pragma unroll
-    for (int m = 1; m < NP; ++m) row[m] -= row[0];
+    for (int m = 1; m < NP; ++m) u[m] -= u[0];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        float a = 0.f;
+    for (int i = 0; i + 1 < NP; i += 2) {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m = 1; m < NP; ++m) a = fmaf(Dc<NP>(i, m), row[m], a);
-        dr[i] = a;
+        for (int m = 1; m < NP; ++m) acc = __ffma2_rn(DT2<NP>(m, i), make_float2(u[m], u[m]), acc);
+        d[i] = acc.x;
+        d[i + 1] = acc.y;
+    }
+    if constexpr (NP & 1) {
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 1; m < NP; ++m) acc = fmaf(Dc<NP>(NP - 1, m), u[m], acc);
+        d[NP - 1] = acc;
     }
 }
 
-// d/ds at the nodes (i, j, k), i = 0..NP-1, of slab k: the s-line of node i is U[k][.][i], its
-// level U[k][0][i]
+// NP consecutive floats of shared memory (16- or 8-byte loads where NP allows)
 template <int NP>
-__device__ __forceinline__ void deriv_s(const float *__restrict__ U, int k, int j, const float (&Dj)[NP], float (&ds)[NP])
+__device__ __forceinline__ void load_row(const float *__restrict__ src, float (&v)[NP])
 {
-    if constexpr (NP == 8) {
-        // rows in the order rotated by k (Dj pre-rotated to match); row 0 itself adds zero
-        const float4 *b0 = reinterpret_cast<const float4 *>(U + (k * 8) * 8);
-        const float4 LA = b0[0], LB = b0[1];
+    if constexpr (NP % 4 == 0) {
+        const float4 *p = reinterpret_cast<const float4 *>(src);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ds[i] = 0.f;
+        for (int q = 0; q < NP / 4; ++q) {
+            const float4 x = p[q];
+            v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+        }
+    } else if constexpr (NP % 2 == 0) {
+        const float2 *p = reinterpret_cast<const float2 *>(src);
 #pragma unroll
-        for (int mm = 0; mm < 8; ++mm) {
-            const int m = (mm + k) & 7;
-            const float4 *sp = reinterpret_cast<const float4 *>(U + (k * 8 + m) * 8);
-            const float4 A = sp[0], B = sp[1];
-            const float d = Dj[mm];
-            ds[0] = fmaf(d, A.x - LA.x, ds[0]); ds[1] = fmaf(d, A.y - LA.y, ds[1]);
-            ds[2] = fmaf(d, A.z - LA.z, ds[2]); ds[3] = fmaf(d, A.w - LA.w, ds[3]);
-            ds[4] = fmaf(d, B.x - LB.x, ds[4]); ds[5] = fmaf(d, B.y - LB.y, ds[5]);
-            ds[6] = fmaf(d, B.z - LB.z, ds[6]); ds[7] = fmaf(d, B.w - LB.w, ds[7]);
+        for (int q = 0; q < NP / 2; ++q) {
+            const float2 x = p[q];
+            v[2 * q] = x.x; v[2 * q + 1] = x.y;
         }
     } else {
-        float lv[NP];
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            ds[i] = 0.f;
-            lv[i] = U[(k * NP) * NP + i];
-        }
-#pragma unroll
-        for (int m = 1; m < NP; ++m)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) ds[i] = fmaf(Dj[m], U[(k * NP + m) * NP + i] - lv[i], ds[i]);
-    }
-}
-
-// d/dt at the nodes (i, j, k), i = 0..NP-1, of column j: the t-line of node i is U[.][j][i],
-// its level U[0][j][i]
-template <int NP>
-__device__ __forceinline__ void deriv_t(const float *__restrict__ U, int j, const float (&Dk)[NP], float (&dt)[NP])
-{
-    if constexpr (NP == 8) {
-        // chunk order staggered by j; swap the two accumulator halves at the end
-        const int sw = (j >> 2) & 1;
-        const float4 *b0 = reinterpret_cast<const float4 *>(U + j * 8);
-        const float4 LA = b0[sw], LB = b0[sw ^ 1];
-        float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int m = 1; m < 8; ++m) {
-            const float4 *tp = reinterpret_cast<const float4 *>(U + (m * 8 + j) * 8);
-            const float4 A = tp[sw], B = tp[sw ^ 1];
-            const float d = Dk[m];
-            a0[0] = fmaf(d, A.x - LA.x, a0[0]); a0[1] = fmaf(d, A.y - LA.y, a0[1]);
-            a0[2] = fmaf(d, A.z - LA.z, a0[2]); a0[3] = fmaf(d, A.w - LA.w, a0[3]);
-            a1[0] = fmaf(d, B.x - LB.x, a1[0]); a1[1] = fmaf(d, B.y - LB.y, a1[1]);
-            a1[2] = fmaf(d, B.z - LB.z, a1[2]); a1[3] = fmaf(d, B.w - LB.w, a1[3]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            dt[i] = sw ? a1[i] : a0[i];
-            dt[i + 4] = sw ? a0[i] : a1[i];
-        }
-    } else {
-        float lv[NP];
-#pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            dt[i] = 0.f;
-            lv[i] = U[j * NP + i];
-        }
-#pragma unroll
-        for (int m = 1; m < NP; ++m)
-#pragma unroll
-            for (int i = 0; i < NP; ++i) dt[i] = fmaf(Dk[m], U[(m * NP + j) * NP + i] - lv[i], dt[i]);
-    }
-}
-
-// Derivatives of one component along the three directions for the r-line (k, j) of one
-// element held in shared memory U[k][j][i].  Dj[m] = D[j][(m + k) % NP] when NP == 8 (the
-// slab reads are rotated by k), else D[j][m]; Dk[m] = D[k][m].
-template <int NP>
-__device__ __forceinline__ void line_derivs(const float *__restrict__ U, int k, int j, const float (&Dj)[NP],
-                                            const float (&Dk)[NP], float (&dr)[NP], float (&ds)[NP],
-                                            float (&dt)[NP])
-{
-    if constexpr (NP == 8) {
-        const int sw = (j >> 2) & 1;  // chunk stagger: j = 0..3 and 4..7 hit different banks
-        // --- r: own row, chunk order staggered
-        float row[8];
-        {
-            const float4 *rp = reinterpret_cast<const float4 *>(U + (k * 8 + j) * 8);
-            float4 A = rp[sw], B = rp[sw ^ 1];
-            float4 lo = sw ? B : A, hi = sw ? A : B;
-            row[0] = lo.x; row[1] = lo.y; row[2] = lo.z; row[3] = lo.w;
-            row[4] = hi.x; row[5] = hi.y; row[6] = hi.z; row[7] = hi.w;
-        }
-        contract_row<8>(row, dr);
-        deriv_s<8>(U, k, j, Dj, ds);
-        deriv_t<8>(U, j, Dk, dt);
-    } else {
-        float row[NP];
-#pragma unroll
-        for (int m = 0; m < NP; ++m) row[m] = U[(k * NP + j) * NP + m];
-        contract_row<NP>(row, dr);
-        deriv_s<NP>(U, k, j, Dj, ds);
-        deriv_t<NP>(U, j, Dk, dt);
+        for (int m = 0; m < NP; ++m) v[m] = src[m];
     }
 }
 
@@ -263,14 +192,18 @@ __device__ __forceinline__ int qb_find(const GBatch &B, int64_t grp)
     return lo;
 }
 
-// The gradient of f0 -> (out0, out1, out2), one r-line per thread.
+// The gradient of f0 -> (out0, out1, out2) with direction-owned lines: thread (el, l) of a
+// stage, with (a, b) = (l / NP, l % NP), contracts the r-line (k, j) = (a, b), the s-line
+// (k, i) = (a, b) and the t-line (j, i) = (a, b) of element el, reading NP values per line, and
+// writes each line's derivatives, scaled by the element's factor, straight to its own output
+// field: rows for d/dr, runs of NP nodes for d/ds, and for d/dt stores that are contiguous
+// across the threads of a warp.  No exchange and one barrier per stage after the stage's own.
 template <int NP>
 __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const __grid_constant__ GBatch B, int *err)
 {
     using C = QCfg<NP>;
-    constexpr int NC = 1;
     constexpr int NP3 = C::NP3, L = C::L, EPB = C::EPB;
-    constexpr int STAGE = NC * EPB * NP3;
+    constexpr int STAGE = EPB * NP3;
     constexpr uint32_t BYTES = EPB * NP3 * 4;
     extern __shared__ __align__(128) float smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -278,7 +211,7 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
 
     const int tid = threadIdx.x;
     const bool active = tid < EPB * L;
-    const int el = tid / L, line = tid % L, j = line % NP, k = line / NP;
+    const int el = active ? tid / L : 0, l = tid % L, a = l / NP, b = l % NP;
     const int64_t ngroups = B.gstart[B.n];
     // group -> (partition, its elements): a full group (EPB elements) can come by bulk copy
     auto elems = [&](int64_t grp, int &p, int64_t &e0) {
@@ -287,15 +220,6 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
         const int64_t left = B.E[p] - e0;
         return (int)(left < EPB ? left : EPB);
     };
-
-    float Dj[NP], Dk[NP];
-#pragma unroll
-    for (int m = 0; m < NP; ++m) {
-        const int mj = (NP == 8) ? ((m + k) & 7) : m;
-        Dj[m] = c_D[((NP - 1) * MP + (active ? j : 0)) * MP + mj];
-        Dk[m] = c_D[((NP - 1) * MP + (active ? k : 0)) * MP + m];
-    }
-
     if (tid == 0) {
         s_abort = 0;
         mbar_init(&bar[0], 1);
@@ -313,17 +237,24 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
         int p;
         int64_t e0;
         elems(grp, p, e0);
-        float *dst = smem + s * STAGE;
-        mbar_arrive_expect_tx(&bar[s], NC * BYTES);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) bulk_g2s(dst + c * EPB * NP3, B.f[c][p] + e0 * NP3, BYTES, &bar[s]);
+        mbar_arrive_expect_tx(&bar[s], BYTES);
+        bulk_g2s(smem + s * STAGE, B.f[0][p] + e0 * NP3, BYTES, &bar[s]);
     };
-    uint32_t phase[2] = {0u, 0u};
-    bool pending[2] = {full(blockIdx.x), full((int64_t)blockIdx.x + gridDim.x)};
+    // the geometry factors of this thread's element in group grp (loaded one group ahead)
+    auto geo = [&](int64_t grp) {
+        int p;
+        int64_t e0;
+        const int ne = elems(grp, p, e0);
+        return B.g[p][e0 + (el < ne ? el : 0)];
+    };
+    // per stage s: bit s of `phase` is its mbarrier parity, bit s of `pending` a copy in flight
+    uint32_t phase = 0u;
+    uint32_t pending = (full(blockIdx.x) ? 1u : 0u) | (full((int64_t)blockIdx.x + gridDim.x) ? 2u : 0u);
     if (tid == 0) {
-        if (pending[0]) issue(blockIdx.x, 0);
-        if (pending[1]) issue((int64_t)blockIdx.x + gridDim.x, 1);
+        if (pending & 1u) issue(blockIdx.x, 0);
+        if (pending & 2u) issue((int64_t)blockIdx.x + gridDim.x, 1);
     }
+    float4 g_next = blockIdx.x < ngroups ? geo(blockIdx.x) : make_float4(0.f, 0.f, 0.f, 0.f);
 
     int it = 0;
     for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++it) {
@@ -332,49 +263,57 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
         int p;
         int64_t e0;
         const int ne = elems(grp, p, e0);
+        const float4 g = g_next;
+        if (grp + gridDim.x < ngroups) g_next = geo(grp + gridDim.x);
         if (C::BULK && ne == EPB) {
             // a wait that ran out leaves the stage pending, so the abort path drains its copy
-            if (mbar_wait_bounded(&bar[s], phase[s], err, B.wait_limit)) {
-                phase[s] ^= 1u;
-                pending[s] = false;
+            if (mbar_wait_bounded(&bar[s], (phase >> s) & 1u, err, B.wait_limit)) {
+                phase ^= 1u << s;
+                pending &= ~(1u << s);
             } else {
                 s_abort = 1;
             }
         } else {
-            for (int c = 0; c < NC; ++c)
-                for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x)
-                    st[c * EPB * NP3 + idx] = B.f[c][p][e0 * NP3 + idx];
+            for (int64_t idx = tid; idx < (int64_t)ne * NP3; idx += blockDim.x) st[idx] = B.f[0][p][e0 * NP3 + idx];
             if (C::BULK) fence_proxy_async_cta();  // a later bulk copy may overwrite these stores
         }
         __syncthreads();
         if (s_abort) break;
-        const int64_t e = e0 + el;
         if (active && el < ne) {
-            const float4 g = B.g[p][e];
-            float dr[NP], ds[NP], dt[NP];
-            const int64_t off = e * NP3 + (k * NP + j) * NP;
-            float *out0 = B.o[0][p], *out1 = B.o[1][p], *out2 = B.o[2][p];
-            line_derivs<NP>(st + el * NP3, k, j, Dj, Dk, dr, ds, dt);
+            const float *U = st + el * NP3;
+            const int64_t eb = (e0 + el) * NP3;
+            float u[NP], d[NP];
+            // r-line (k, j) = (a, b): d/dr at the nodes (i, b, a)
+            load_row<NP>(U + l * NP, u);
+            contract_line2<NP>(u, d);
 #pragma unroll
-            for (int i = 0; i < NP; ++i) {
-                dr[i] *= g.x;
-                ds[i] *= g.y;
-                dt[i] *= g.z;
-            }
-            store_line<NP>(out0 + off, dr);
-            store_line<NP>(out1 + off, ds);
-            store_line<NP>(out2 + off, dt);
+            for (int i = 0; i < NP; ++i) d[i] *= g.x;
+            store_line<NP>(B.o[0][p] + eb + l * NP, d);
+            // s-line (k, i) = (a, b): d/ds at the nodes (b, j', a)
+#pragma unroll
+            for (int m = 0; m < NP; ++m) u[m] = U[(a * NP + m) * NP + b];
+            contract_line2<NP>(u, d);
+            float *o1 = B.o[1][p] + eb + a * NP * NP + b;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) o1[m * NP] = d[m] * g.y;
+            // t-line (j, i) = (a, b): d/dt at the nodes (b, a, k')
+#pragma unroll
+            for (int m = 0; m < NP; ++m) u[m] = U[(m * NP + a) * NP + b];
+            contract_line2<NP>(u, d);
+            float *o2 = B.o[2][p] + eb + l;
+#pragma unroll
+            for (int m = 0; m < NP; ++m) o2[m * NP * NP] = d[m] * g.z;
         }
-        __syncthreads();
+        __syncthreads();  // the stage is read
         if (tid == 0 && full(grp + 2 * (int64_t)gridDim.x)) {
             issue(grp + 2 * (int64_t)gridDim.x, s);
-            pending[s] = true;
+            pending |= 1u << s;
         }
     }
     // on an abort, wait (bounded) for copies still in flight into this CTA's shared memory
     if (C::BULK && s_abort && tid == 0) {
         for (int s = 0; s < 2; ++s)
-            if (pending[s]) mbar_wait_bounded(&bar[s], phase[s], nullptr);
+            if ((pending >> s) & 1u) mbar_wait_bounded(&bar[s], (phase >> s) & 1u, nullptr);
     }
 }
 
@@ -388,62 +327,9 @@ __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_grad(const
 // derivatives to exchange slots laid out like the element, [k][j][i] (three slots of their own
 // and the stage's component-0 part once that is read), from which the r-line owner reads its
 // node row of each and folds the six products of Q: five barriers per stage.  Every line is
-// contracted by contract_row's steps (level shift, then the products in m order), the folds
-// come in the same order, so the result is the one-thread-per-r-line result bit for bit.
-// Two nodes' sums share one FFMA2 (two round-to-nearest FMAs per instruction).
+// contracted by contract_line2 (level shift, then the products in m order), the folds come in
+// the same order, so the result is the one-thread-per-r-line result bit for bit.
 // ------------------------------------------------------------------------------------------
-template <int NP>
-__device__ __forceinline__ float2 DT2(int m, int i)
-{
-    return *reinterpret_cast<const float2 *>(&c_DT[((NP - 1) * MP + m) * MP + i]);
-}
-
-// (D u)_i for i = 0..NP-1 of one line u held in registers (u is shifted in place)
-template <int NP>
-__device__ __forceinline__ void contract_line2(float (&u)[NP], float (&d)[NP])
-{
-#pragma unroll
-    for (int m = 1; m < NP; ++m) u[m] -= u[0];
-#pragma unroll
-    for (int i = 0; i + 1 < NP; i += 2) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int m = 1; m < NP; ++m) acc = __ffma2_rn(DT2<NP>(m, i), make_float2(u[m], u[m]), acc);
-        d[i] = acc.x;
-        d[i + 1] = acc.y;
-    }
-    if constexpr (NP & 1) {
-        float acc = 0.f;
-#pragma unroll
-        for (int m = 1; m < NP; ++m) acc = fmaf(Dc<NP>(NP - 1, m), u[m], acc);
-        d[NP - 1] = acc;
-    }
-}
-
-// NP consecutive floats of shared memory (16- or 8-byte loads where NP allows)
-template <int NP>
-__device__ __forceinline__ void load_row(const float *__restrict__ src, float (&v)[NP])
-{
-    if constexpr (NP % 4 == 0) {
-        const float4 *p = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-        for (int q = 0; q < NP / 4; ++q) {
-            const float4 x = p[q];
-            v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-        }
-    } else if constexpr (NP % 2 == 0) {
-        const float2 *p = reinterpret_cast<const float2 *>(src);
-#pragma unroll
-        for (int q = 0; q < NP / 2; ++q) {
-            const float2 x = p[q];
-            v[2 * q] = x.x; v[2 * q + 1] = x.y;
-        }
-    } else {
-#pragma unroll
-        for (int m = 0; m < NP; ++m) v[m] = src[m];
-    }
-}
-
 template <int NP>
 __global__ void __launch_bounds__(QCfg<NP>::NT, QCfg<NP>::MINB) k_sem_qd(const __grid_constant__ GBatch B, int *err)
 {
@@ -1056,7 +942,7 @@ __global__ void __launch_bounds__(GEN_THREADS) k_sem_grad_gen(const float *__res
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 const float *U = s_u + c * NP3;
-                // each line shifted by its first value (D 1 = 0; see contract_row)
+                // each line shifted by its first value (D 1 = 0; see contract_line2)
                 const float lr = U[(k * NP + j) * NP], ls = U[(k * NP) * NP + i], lt = U[j * NP + i];
                 float dr = 0.f, ds = 0.f, dt = 0.f;
 #pragma unroll
