@@ -56,6 +56,11 @@ def test_byte_model_of_the_frame_in_parts():
     assert small == 36 * 4647976 and rng == 36 * 1377188 and small + rng == 36 * two.last_ntri
     # the fused Q kernel: u, v, w read and Q written (16 B per node) + one count per element
     assert bench.algorithmic_bytes_per_step("k_sem_q8_count", two) == 16 * two.npts + 4 * two.E
+    # Q of the other orders (u, v, w in, Q out) and the derivative kernel (u in, three derivatives
+    # out) move 16 B per node each
+    assert bench.algorithmic_bytes_per_step("k_sem_qd", two) == 16 * two.npts
+    assert bench.algorithmic_bytes_per_step("k_sem_grad", two) == 16 * two.npts
+    assert bench.KERNEL_SOURCES["k_sem_qd"] == bench.KERNEL_SOURCES["k_sem_q8"]
     one = SimpleNamespace(N=7, E=32768, npts=32768 * 512, surface_stats=surf[:1], last_ntri=4647976, nseg=3,
                           surfaces=[("Q", [0.1, 0.2, 0.3])], W=1920, H=1080, covered=10)
     assert bench.algorithmic_bytes_per_step("k_raster_small", one) == 36 * one.last_ntri
